@@ -1,0 +1,284 @@
+"""ctypes wrapper of the C oracle.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by
+the benchmark's CPU-baseline leg. The product path never imports it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class Grid(C.Structure):
+    _fields_ = [("res", C.c_int32 * 3), ("bins", C.c_int32), ("origin", C.c_float * 3),
+                ("scale", C.c_float), ("attr_min", C.c_float), ("attr_max", C.c_float)]
+
+
+class View(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("at", C.c_float * 3), ("up", C.c_float * 3),
+                ("fovy_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("light_dir", C.c_float * 3)]
+
+
+class RDesc(C.Structure):
+    _fields_ = [("radius", C.c_float), ("tf", C.c_float * 1024), ("opaque", C.c_int32),
+                ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao", C.c_int32),
+                ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
+                ("kd", C.c_float), ("bg", C.c_float * 3)]
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        L.orc_last_error.restype = C.c_char_p
+        L.orc_record_bits.argtypes = [C.c_int]
+        L.orc_record_bytes.argtypes = [C.c_int]
+        L.orc_fixed_point.argtypes = [vp, i64, vp, vp]
+        L.orc_attr16.argtypes = [vp, i64, C.c_float, C.c_float, vp]
+        L.orc_fit_grid.argtypes = [vp, i64, i32, i32, vp]
+        L.orc_voxelize.argtypes = [vp, vp, vp, i64, i64, vp, C.POINTER(vp)]
+        L.orc_voxset_free.argtypes = [vp]
+        L.orc_voxset_nseg.argtypes = [vp]
+        L.orc_voxset_nseg.restype = i64
+        L.orc_voxset_nvox.argtypes = [vp]
+        L.orc_voxset_nvox.restype = i64
+        L.orc_voxset_export.argtypes = [vp, vp, vp, vp, vp]
+        L.orc_build_lod.argtypes = [vp, C.c_int, vp, C.POINTER(vp)]
+        L.orc_lod_free.argtypes = [vp]
+        L.orc_lod_dims.argtypes = [vp, C.c_int, vp]
+        L.orc_lod_export.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.orc_render.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int, vp, vp, vp, C.c_int]
+        L.orc_primary_ray.argtypes = [vp, i32, i32, vp, vp]
+        L.orc_capsule_entry.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
+        L.orc_march.argtypes = [vp, vp, vp, C.c_double]
+        L.orc_march.restype = C.c_double
+        L.orc_sample.argtypes = [vp, C.c_int, vp]
+        L.orc_sample.restype = C.c_double
+        L.orc_ao_dirs.argtypes = [vp, vp, C.c_int, vp]
+        _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"oracle error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != 0:
+        raise OracleError(rc, lib().orc_last_error().decode())
+
+
+def make_grid(res, bins, origin=(0.0, 0.0, 0.0), scale=1.0, attr_min=0.0, attr_max=0.0) -> Grid:
+    g = Grid()
+    r = (res, res, res) if np.isscalar(res) else tuple(res)
+    g.res[:] = [int(x) for x in r]
+    g.bins = int(bins)
+    g.origin[:] = [float(x) for x in origin]
+    g.scale = float(scale)
+    g.attr_min = float(attr_min)
+    g.attr_max = float(attr_max)
+    return g
+
+
+def record_bytes(bins: int) -> int:
+    return lib().orc_record_bytes(bins)
+
+
+def record_bits(bins: int) -> int:
+    return lib().orc_record_bits(bins)
+
+
+def fixed_point(xyz, grid: Grid):
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    out = np.empty(xyz.shape, np.int32)
+    _check(lib().orc_fixed_point(_p(xyz), len(xyz), C.byref(grid), _p(out)))
+    return out
+
+
+def attr16(attr, amin, amax):
+    attr = np.ascontiguousarray(attr, np.float32)
+    out = np.empty(attr.shape, np.uint16)
+    _check(lib().orc_attr16(_p(attr), len(attr), amin, amax, _p(out)))
+    return out
+
+
+def fit_grid(xyz, rmax, bins) -> Grid:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    g = Grid()
+    _check(lib().orc_fit_grid(_p(xyz), len(xyz), rmax, bins, C.byref(g)))
+    return g
+
+
+class VoxSet:
+    """Oracle voxel model; fields decoded (face_in,u_in,v_in,face_out,u_out,v_out,attr,cont)."""
+
+    def __init__(self, xyz, attr, offsets, grid: Grid):
+        self.grid = grid
+        xyz = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+        attr = None if attr is None else np.ascontiguousarray(attr, np.float32)
+        offsets = np.ascontiguousarray(offsets, np.int64)
+        h = C.c_void_p()
+        _check(lib().orc_voxelize(_p(xyz), _p(attr), _p(offsets), len(offsets) - 1, len(xyz),
+                                  C.byref(grid), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_voxset_free(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nseg(self) -> int:
+        return lib().orc_voxset_nseg(self._h)
+
+    @property
+    def nvox(self) -> int:
+        return lib().orc_voxset_nvox(self._h)
+
+    def export(self):
+        n, v = self.nseg, self.nvox
+        off = np.empty(v + 1, np.uint32)
+        fields = np.empty((n, 8), np.uint8)
+        curve = np.empty(n, np.uint32)
+        ordn = np.empty(n, np.uint32)
+        lib().orc_voxset_export(self._h, _p(off), _p(fields), _p(curve), _p(ordn))
+        return dict(offset=off, fields=fields, curve=curve, ordinal=ordn)
+
+
+class Lod:
+    def __init__(self, vs: VoxSet, levels: int, sigma):
+        self.vs = vs
+        sigma = np.ascontiguousarray(sigma, np.float32)
+        assert sigma.shape == (256,)
+        h = C.c_void_p()
+        _check(lib().orc_build_lod(vs.handle, levels, _p(sigma), C.byref(h)))
+        self._h = h
+        self.levels = levels
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_lod_free(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def dims(self, level):
+        d = np.empty(3, np.int32)
+        lib().orc_lod_dims(self._h, level, _p(d))
+        return tuple(int(x) for x in d)
+
+    def export(self, level):
+        d = self.dims(level)
+        n = d[0] * d[1] * d[2]
+        cnt = np.empty(n, np.uint32)
+        ln = np.empty(n, np.float64)
+        dn = np.empty(n, np.float64)
+        lib().orc_lod_export(self._h, level, _p(cnt), _p(ln), _p(dn))
+        return dict(cnt=cnt, len=ln, dens=dn, dims=d)
+
+    def sample(self, level, x):
+        x = np.ascontiguousarray(x, np.float64)
+        return lib().orc_sample(self._h, level, _p(x))
+
+    def march(self, p, d, max_dist=-1.0):
+        p = np.ascontiguousarray(p, np.float64)
+        d = np.ascontiguousarray(d, np.float64)
+        return lib().orc_march(self._h, _p(p), _p(d), max_dist)
+
+
+def make_view(eye, at, up, fovy_deg, width, height, light_dir) -> View:
+    v = View()
+    v.eye[:] = [float(x) for x in eye]
+    v.at[:] = [float(x) for x in at]
+    v.up[:] = [float(x) for x in up]
+    v.fovy_deg = float(fovy_deg)
+    v.width = int(width)
+    v.height = int(height)
+    v.light_dir[:] = [float(x) for x in light_dir]
+    return v
+
+
+def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False,
+               ao_rays=16, ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0)) -> RDesc:
+    d = RDesc()
+    d.radius = float(radius)
+    tf = np.ascontiguousarray(tf, np.float32).reshape(-1)
+    assert tf.size == 1024
+    d.tf[:] = tf.tolist()
+    d.opaque = int(bool(opaque))
+    d.ert_alpha = float(ert_alpha)
+    d.shadows = int(bool(shadows))
+    d.ao = int(bool(ao))
+    d.ao_rays = int(ao_rays)
+    d.ao_radius = float(ao_radius)
+    d.ka = float(ka)
+    d.kd = float(kd)
+    d.bg[:] = [float(x) for x in bg]
+    return d
+
+
+def pixel_grid(x0, y0, w, h):
+    jj, ii = np.meshgrid(np.arange(y0, y0 + h), np.arange(x0, x0 + w), indexing="ij")
+    return np.stack([ii.reshape(-1), jj.reshape(-1)], 1).astype(np.int32)
+
+
+def render(vs: VoxSet, lod: Lod | None, view: View, rd: RDesc, pix, mode="dda", nthreads=0):
+    """Render the listed pixels (int32 (n, 2) of (i, j)); returns rgba (n,4) f64,
+    tie flags (n,) u8 and counters [voxels, records, lod samples, hits]."""
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
+    n = len(pix)
+    rgba = np.empty((n, 4), np.float64)
+    tie = np.empty(n, np.uint8)
+    cnt = np.zeros(4, np.uint64)
+    m = 1 if mode == "brute" else 0
+    _check(lib().orc_render(vs.handle, lod.handle if lod is not None else None, C.byref(view),
+                            C.byref(rd), _p(pix), n, m, _p(rgba), _p(tie), _p(cnt), int(nthreads)))
+    return rgba, tie, cnt
+
+
+def primary_ray(view: View, i, j):
+    o = np.empty(3, np.float32)
+    d = np.empty(3, np.float32)
+    lib().orc_primary_ray(C.byref(view), i, j, _p(o), _p(d))
+    return o, d
+
+
+def capsule_entry(o, d, a, b, r):
+    arrs = [np.ascontiguousarray(x, np.float64) for x in (o, d, a, b)]
+    t = np.zeros(1)
+    dist = np.zeros(1)
+    hit = lib().orc_capsule_entry(*[_p(x) for x in arrs], float(r), _p(t), _p(dist))
+    return bool(hit), float(t[0]), float(dist[0])
+
+
+def ao_dirs(n, u, k=16):
+    n = np.ascontiguousarray(n, np.float64)
+    u = np.ascontiguousarray(u, np.float64)
+    out = np.empty((k, 3))
+    lib().orc_ao_dirs(_p(n), _p(u), k, _p(out))
+    return out
+
+
+def num_threads() -> int:
+    return len(os.sched_getaffinity(0))

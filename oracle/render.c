@@ -1,0 +1,600 @@
+/*
+ * Oracle ray-caster (TEST INFRASTRUCTURE ONLY; see oracle.h). FP64 throughout,
+ * except where a float decides a discrete outcome that the kernel decides in
+ * float32 (the early-termination test), which is then taken in float32 too.
+ *
+ *   primary rays ........ reading R0 (single-precision ray contract)
+ *   traversal ........... Sec. 4: 3D-DDA from voxel face to voxel face; empty
+ *                         voxels skipped; ties stepped in axis order x, y, z
+ *   intersection ........ Sec. 4 / 4.1: tubes of a user radius around each
+ *                         segment, closed by spheres at the joints (capsules);
+ *                         a voxel only tests its own segments (interactive
+ *                         mode, Sec. 4.1) and owns the hits whose entry point
+ *                         lies in it (reading R1)
+ *   per-voxel sort ...... Sec. 4: hits sorted in visibility order
+ *   shading ............. Sec. 5: normal at the entering intersection and a
+ *                         local illumination model (reading S1)
+ *   compositing ......... Sec. 5.1: front-to-back alpha blending, opacity from
+ *                         the transfer function, alpha termination
+ *   shadows ............. Sec. 5.2, second approach: one ray toward the light
+ *                         sampling the density LoD, coarser with distance
+ *                         (cone opening of one finest voxel; reading S2)
+ *   ambient occlusion ... Sec. 5.3, first approach: hemisphere rays around the
+ *                         normal accumulate density until it reaches 1, the
+ *                         ray passes the radius of influence or leaves the
+ *                         domain; averaged over rays (reading S3)
+ *
+ * Tie flags: where a decision margin of the FP64 computation is so small that
+ * a float32 evaluation of the same decision may go the other way, the pixel
+ * is flagged (bit mask) and parity tests exclude and count it.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define TIE_GRAZE 1
+#define TIE_OWNER 2
+#define TIE_SORT  4
+#define TIE_FRAME 16
+#define TIE_SLAB  32
+
+static const double EPS_G = 5e-6;     /* |distance - radius| at a silhouette */
+static const double EPS_T = 5e-6;     /* entry parameter vs voxel faces / other hits */
+static const double ERR_Q = 2e-7;     /* float32 error scale of a quadratic's root term */
+static const double EPS_F = 1e-5;     /* AO frame switch */
+static const double FRAME_MIN = 1e-3; /* tangent shorter than this: axis fallback */
+
+/* ------------------------------------------------------------------ vectors */
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double *a, const double *b, double *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void norm3(double *a) {
+    double l = sqrt(dot3(a, a));
+    a[0] /= l; a[1] /= l; a[2] /= l;
+}
+
+/* ------------------------------------------------------------------ camera (R0) */
+typedef struct { float F[3], R[3], U[3], th, tw, eye[3]; int W, H; } cam32;
+
+static void cam_setup(const orc_view *v, cam32 *c) {
+    double f[3], up[3], r[3], u[3];
+    for (int a = 0; a < 3; a++) {
+        f[a] = (double)v->at[a] - (double)v->eye[a];
+        up[a] = v->up[a];
+    }
+    norm3(f);
+    cross3(f, up, r);
+    norm3(r);
+    cross3(r, f, u);
+    double th = tan((double)v->fovy_deg * M_PI / 360.0);
+    double tw = th * (double)v->width / (double)v->height;
+    for (int a = 0; a < 3; a++) {
+        c->F[a] = (float)f[a];
+        c->R[a] = (float)r[a];
+        c->U[a] = (float)u[a];
+        c->eye[a] = v->eye[a];
+    }
+    c->th = (float)th;
+    c->tw = (float)tw;
+    c->W = v->width;
+    c->H = v->height;
+}
+
+/* Single-precision ray of pixel (i, j): every operation rounds to float32 in
+ * the order written (the library builds the identical float32 ray). */
+static void cam_ray(const cam32 *c, int32_t i, int32_t j, float org[3], float dir[3]) {
+    float px = (float)(2 * i + 1) / (float)c->W;
+    float sx = (px - 1.0f) * c->tw;
+    float py = (float)(2 * j + 1) / (float)c->H;
+    float sy = (py - 1.0f) * c->th;
+    float d[3];
+    for (int a = 0; a < 3; a++) {
+        float t = sx * c->R[a];
+        float s = c->F[a] + t;
+        float w = sy * c->U[a];
+        d[a] = s - w;
+    }
+    float n2 = d[0] * d[0];
+    float y2 = d[1] * d[1];
+    n2 = n2 + y2;
+    float z2 = d[2] * d[2];
+    n2 = n2 + z2;
+    float inv = 1.0f / sqrtf(n2);
+    for (int a = 0; a < 3; a++) {
+        dir[a] = d[a] * inv;
+        org[a] = c->eye[a];
+    }
+}
+
+void orc_primary_ray(const orc_view *view, int32_t i, int32_t j, float org[3], float dir[3]) {
+    cam32 c;
+    cam_setup(view, &c);
+    cam_ray(&c, i, j, org, dir);
+}
+
+/* ------------------------------------------------------------------ segments */
+static void face_point(int face, int u, int v, int N, double q[3]) {
+    int a = face / 2;
+    int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;
+    q[a] = (face & 1) ? 1.0 : 0.0;
+    q[b0] = (u + 0.5) / N;             /* sub-square centre (Sec. 3.2) */
+    q[b1] = (v + 0.5) / N;
+}
+
+static void seg_world(const orc_voxset *vs, const orc_seg *s, double a[3], double b[3]) {
+    const int32_t *R = vs->grid.res;
+    int64_t vid = s->voxel;
+    double base[3] = {(double)(vid % R[0]), (double)((vid / R[0]) % R[1]), (double)(vid / ((int64_t)R[0] * R[1]))};
+    face_point(s->face_in, s->u_in, s->v_in, vs->grid.bins, a);
+    face_point(s->face_out, s->u_out, s->v_out, vs->grid.bins, b);
+    for (int k = 0; k < 3; k++) { a[k] += base[k]; b[k] += base[k]; }
+}
+
+static int same_geometry(const orc_seg *x, const orc_seg *y) {
+    return x->voxel == y->voxel && x->face_in == y->face_in && x->u_in == y->u_in &&
+           x->v_in == y->v_in && x->face_out == y->face_out && x->u_out == y->u_out &&
+           x->v_out == y->v_out;
+}
+
+/* Distance from the line o + t d (|d| = 1) to the segment [a, b]; *tc = line
+ * parameter of the closest approach. */
+static double line_segment_distance(const double *o, const double *d, const double *a,
+                                    const double *b, double *tc) {
+    double ba[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double ao[3] = {a[0] - o[0], a[1] - o[1], a[2] - o[2]};
+    double L2 = dot3(ba, ba), k = dot3(d, ba);
+    double h = 0.0;
+    if (L2 > 0.0) {
+        double det = L2 - k * k;                 /* |d|^2 L2 - (d.ba)^2 */
+        if (det > 1e-14 * L2) {
+            /* minimise |o + t d - a - h ba|^2 over t, h */
+            double e = dot3(d, ao), f = dot3(ba, ao);
+            h = (k * e - f) / det;
+        }
+        if (h < 0.0) h = 0.0;
+        if (h > 1.0) h = 1.0;
+    }
+    double c[3] = {a[0] + h * ba[0], a[1] + h * ba[1], a[2] + h * ba[2]};
+    double co[3] = {c[0] - o[0], c[1] - o[1], c[2] - o[2]};
+    double t = dot3(co, d);
+    double p[3] = {o[0] + t * d[0] - c[0], o[1] + t * d[1] - c[1], o[2] + t * d[2] - c[2]};
+    *tc = t;
+    return sqrt(dot3(p, p));
+}
+
+/* Smaller root of |o + t d - c|^2 = r^2 (|d| = 1); returns 0 if none. */
+static int sphere_entry(const double *o, const double *d, const double *c, double r,
+                        double *t, double *g) {
+    double oc[3] = {o[0] - c[0], o[1] - c[1], o[2] - c[2]};
+    double b = dot3(oc, d), cc = dot3(oc, oc) - r * r;
+    double h = b * b - cc;                        /* r^2 - (distance centre-to-line)^2 */
+    if (h < 0.0) return 0;
+    *t = -b - sqrt(h);
+    *g = sqrt(h);
+    return 1;
+}
+
+/* Capsule entry: the capsule is the union of the finite cylinder and the two
+ * end spheres, so its first entry is the smallest of: the lateral entry into
+ * the infinite cylinder when that point lies between the end planes, and the
+ * entries into the two spheres. *sens = 1 / (|d_perp| g), g the half chord,
+ * scales the float32 error of the root. */
+static int capsule_entry_s(const double *o, const double *d, const double *a, const double *b,
+                           double r, double *t_out, double *sens) {
+    double tc;
+    if (line_segment_distance(o, d, a, b, &tc) > r) return 0;
+    /* ray origin inside the capsule: no entering intersection ahead */
+    {
+        double ba[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, oa[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+        double L2 = dot3(ba, ba), h = L2 > 0.0 ? dot3(oa, ba) / L2 : 0.0;
+        if (h < 0.0) h = 0.0;
+        if (h > 1.0) h = 1.0;
+        double q[3] = {oa[0] - h * ba[0], oa[1] - h * ba[1], oa[2] - h * ba[2]};
+        if (dot3(q, q) <= r * r) return 0;
+    }
+    int found = 0;
+    double best = 0.0, bsens = 0.0;
+    double ba[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double L2 = dot3(ba, ba);
+    if (L2 > 0.0) {
+        double L = sqrt(L2);
+        double w[3] = {ba[0] / L, ba[1] / L, ba[2] / L};
+        double oa[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+        double dw = dot3(d, w), mw = dot3(oa, w);
+        double dp[3] = {d[0] - dw * w[0], d[1] - dw * w[1], d[2] - dw * w[2]};
+        double mp[3] = {oa[0] - mw * w[0], oa[1] - mw * w[1], oa[2] - mw * w[2]};
+        double A = dot3(dp, dp), B = dot3(dp, mp), C = dot3(mp, mp) - r * r;
+        if (A > 0.0) {
+            double disc = B * B - A * C;
+            if (disc >= 0.0) {
+                double t = (-B - sqrt(disc)) / A;
+                double y = mw + t * dw;             /* axial coordinate of the entry point */
+                if (y >= 0.0 && y <= L) {
+                    found = 1;
+                    best = t;
+                    double s = sqrt(A), g = sqrt(disc) / s;
+                    bsens = 1.0 / fmax(s * g, 1e-12);
+                }
+            }
+        }
+    }
+    double ts, g;
+    if (sphere_entry(o, d, a, r, &ts, &g) && (!found || ts < best)) {
+        found = 1; best = ts; bsens = 1.0 / fmax(g, 1e-12);
+    }
+    if (sphere_entry(o, d, b, r, &ts, &g) && (!found || ts < best)) {
+        found = 1; best = ts; bsens = 1.0 / fmax(g, 1e-12);
+    }
+    if (!found || !(best > 0.0)) return 0;
+    *t_out = best;
+    *sens = bsens;
+    return 1;
+}
+
+int orc_capsule_entry(const double o[3], const double d[3], const double a[3],
+                      const double b[3], double r, double *t, double *dist) {
+    double tc, sens;
+    *dist = line_segment_distance(o, d, a, b, &tc);
+    return capsule_entry_s(o, d, a, b, r, t, &sens);
+}
+
+/* ------------------------------------------------------------------ LoD marches */
+double orc_sample(const orc_lod *L, int l, const double x[3]) {
+    double s = ldexp(1.0, l);
+    double q[3], f[3];
+    int64_t i0[3];
+    for (int a = 0; a < 3; a++) {
+        q[a] = x[a] / s - 0.5;                   /* cell-centred samples */
+        double fl = floor(q[a]);
+        i0[a] = (int64_t)fl;
+        f[a] = q[a] - fl;
+    }
+    const int32_t *dm = L->dims[l];
+    double acc = 0.0;
+    for (int c = 0; c < 8; c++) {
+        int64_t idx[3];
+        double w = 1.0;
+        int inside = 1;
+        for (int a = 0; a < 3; a++) {
+            int bit = (c >> a) & 1;
+            idx[a] = i0[a] + bit;
+            w *= bit ? f[a] : 1.0 - f[a];
+            if (idx[a] < 0 || idx[a] >= dm[a]) inside = 0;   /* zero outside the grid */
+        }
+        if (inside) acc += w * L->dens[l][idx[0] + (int64_t)dm[0] * (idx[1] + (int64_t)dm[1] * idx[2])];
+    }
+    return acc / ldexp(1.0, 3 * l);              /* sum of 8^l voxels -> average */
+}
+
+static int level_of(int64_t s, int levels) {
+    int l = 0;
+    while (((int64_t)2 << l) <= s) l++;          /* floor(log2 s) */
+    return l < levels - 1 ? l : levels - 1;
+}
+
+/* Reading S2: start one voxel from the point, sample level l = floor(log2 s)
+ * (capped at the coarsest level), add density * step, step 2^l; stop at
+ * O >= 1, past max_dist, or once the sample point has left the domain of the
+ * density field: the grid enlarged by half a coarsest-level cell, beyond
+ * which every level's trilinear sample is exactly zero (a ray that has left
+ * this convex box never re-enters it, so stopping there changes nothing). */
+static double march(const orc_lod *L, const double *p, const double *dir,
+                    double max_dist, uint64_t *nsamples) {
+    const int top = L->levels - 1;
+    const double cell = ldexp(1.0, top);
+    double lo = -0.5 * cell, hi[3];
+    for (int a = 0; a < 3; a++) hi[a] = ((double)L->dims[top][a] + 0.5) * cell;
+    double O = 0.0;
+    int64_t s = 1;
+    for (;;) {
+        if (max_dist >= 0.0 && (double)s > max_dist) break;
+        double x[3];
+        int outside = 0;
+        for (int a = 0; a < 3; a++) {
+            x[a] = p[a] + (double)s * dir[a];
+            if (x[a] < lo || x[a] > hi[a]) outside = 1;
+        }
+        if (outside) break;
+        int l = level_of(s, L->levels);
+        O += orc_sample(L, l, x) * ldexp(1.0, l);
+        (*nsamples)++;
+        if (O >= 1.0) break;
+        s += (int64_t)1 << l;
+    }
+    return O;
+}
+
+double orc_march(const orc_lod *L, const double p[3], const double dir[3], double max_dist) {
+    uint64_t n = 0;
+    return march(L, p, dir, max_dist, &n);
+}
+
+/* Reading S3: spherical-Fibonacci directions on the hemisphere around n, in
+ * the frame whose tangent is the tube axis projected onto the tangent plane
+ * (fallback: the world axis least aligned with n). */
+static void ao_dirs_t(const double *n, const double *u, int k, double *dirs, int *tie) {
+    double un = dot3(u, n);
+    double T[3] = {u[0] - un * n[0], u[1] - un * n[1], u[2] - un * n[2]};
+    double m = sqrt(dot3(T, T));
+    if (fabs(m - FRAME_MIN) < EPS_F) *tie |= TIE_FRAME;
+    if (m >= FRAME_MIN) {
+        T[0] /= m; T[1] /= m; T[2] /= m;
+    } else {
+        double an[3] = {fabs(n[0]), fabs(n[1]), fabs(n[2])};
+        int e = 0;
+        for (int a = 1; a < 3; a++) if (an[a] < an[e]) e = a;
+        for (int a = 0; a < 3; a++)
+            if (a != e && fabs(an[a] - an[e]) < EPS_F) *tie |= TIE_FRAME;
+        double E[3] = {0, 0, 0};
+        E[e] = 1.0;
+        double en = dot3(E, n);
+        for (int a = 0; a < 3; a++) T[a] = E[a] - en * n[a];
+        norm3(T);
+    }
+    double B[3];
+    cross3(n, T, B);
+    const double golden = M_PI * (3.0 - sqrt(5.0));
+    for (int i = 0; i < k; i++) {
+        double z = 1.0 - (i + 0.5) / k;
+        double rr = sqrt(1.0 - z * z);
+        double ph = i * golden;
+        double x = rr * cos(ph), y = rr * sin(ph);
+        for (int a = 0; a < 3; a++) dirs[3 * i + a] = T[a] * x + B[a] * y + n[a] * z;
+    }
+}
+
+void orc_ao_dirs(const double n[3], const double u[3], int k, double *dirs) {
+    int tie = 0;
+    ao_dirs_t(n, u, k, dirs, &tie);
+}
+
+/* ------------------------------------------------------------------ per-pixel state */
+typedef struct {
+    double C[3], A;
+    float A32;          /* the termination decision, in float32 */
+    int done;
+    int tie;
+    uint64_t nvox, nrec, nsamp, nhit;
+} pixstate;
+
+typedef struct { double t, eps; int64_t k; } hit;
+
+static int hit_cmp(const void *x, const void *y) {
+    const hit *a = (const hit *)x, *b = (const hit *)y;
+    if (a->t < b->t) return -1;
+    if (a->t > b->t) return 1;
+    return (a->k > b->k) - (a->k < b->k);
+}
+
+/* Shade one hit (reading S1) and composite it front to back (Sec. 5.1). */
+static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *rd,
+                            const double *O, const double *D, const double *Lt,
+                            const hit *h, pixstate *ps) {
+    const orc_seg *s = &vs->seg[h->k];
+    double a[3], b[3];
+    seg_world(vs, s, a, b);
+    double P[3] = {O[0] + h->t * D[0], O[1] + h->t * D[1], O[2] + h->t * D[2]};
+    double ba[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double L2 = dot3(ba, ba), hh = 0.0;
+    if (L2 > 0.0) {
+        double pa[3] = {P[0] - a[0], P[1] - a[1], P[2] - a[2]};
+        hh = dot3(pa, ba) / L2;
+        if (hh < 0.0) hh = 0.0;
+        if (hh > 1.0) hh = 1.0;
+    }
+    double n[3] = {P[0] - (a[0] + hh * ba[0]), P[1] - (a[1] + hh * ba[1]), P[2] - (a[2] + hh * ba[2])};
+    norm3(n);
+    const float *tf = rd->tf + 4 * s->attr;
+    double alpha = rd->opaque ? 1.0 : (double)tf[3];
+
+    double V = 1.0, AO = 1.0;
+    if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
+    if (rd->ao && L && rd->ao_rays > 0) {
+        double u[3] = {ba[0], ba[1], ba[2]};
+        if (L2 > 0.0) { double l = sqrt(L2); u[0] /= l; u[1] /= l; u[2] /= l; }
+        double *dirs = (double *)malloc(sizeof(double) * 3 * (size_t)rd->ao_rays);
+        ao_dirs_t(n, u, rd->ao_rays, dirs, &ps->tie);
+        double occ = 0.0;
+        for (int i = 0; i < rd->ao_rays; i++)
+            occ += fmin(1.0, march(L, P, dirs + 3 * i, rd->ao_radius, &ps->nsamp));
+        free(dirs);
+        AO = 1.0 - occ / rd->ao_rays;
+    }
+    double diff = fabs(dot3(n, Lt));
+    double k = rd->ka * AO + rd->kd * V * diff;
+    ps->nhit++;
+    if (rd->opaque) {
+        for (int c = 0; c < 3; c++) ps->C[c] = tf[c] * k;
+        ps->A = 1.0;
+        ps->done = 1;
+        return;
+    }
+    double w = (1.0 - ps->A) * alpha;
+    for (int c = 0; c < 3; c++) ps->C[c] += w * tf[c] * k;
+    ps->A += w;
+    float t1 = 1.0f - ps->A32;
+    float t2 = t1 * tf[3];
+    ps->A32 = ps->A32 + t2;
+    if (ps->A32 >= rd->ert_alpha) ps->done = 1;
+}
+
+static void flag_sorted_ties(const orc_voxset *vs, const hit *hs, int nh, int *tie) {
+    for (int i = 0; i + 1 < nh; i++)
+        if (hs[i + 1].t - hs[i].t < hs[i].eps + hs[i + 1].eps &&
+            !same_geometry(&vs->seg[hs[i].k], &vs->seg[hs[i + 1].k]))
+            *tie |= TIE_SORT;
+}
+
+/* One ray by DDA traversal (Sec. 4). */
+static void trace_dda(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *rd,
+                      const double *O, const double *D, const double *Lt, pixstate *ps,
+                      hit **buf, int *bufcap) {
+    const int32_t *R = vs->grid.res;
+    double tnear = -1e300, tfar = 1e300;
+    for (int a = 0; a < 3; a++) {
+        if (D[a] != 0.0) {
+            double t1 = (0.0 - O[a]) / D[a], t2 = ((double)R[a] - O[a]) / D[a];
+            tnear = fmax(tnear, fmin(t1, t2));
+            tfar = fmin(tfar, fmax(t1, t2));
+        } else if (O[a] < 0.0 || O[a] > R[a]) {
+            return;
+        }
+    }
+    if (tnear < 0.0) tnear = 0.0;
+    if (fabs(tfar - tnear) < 1e-5) ps->tie |= TIE_SLAB;
+    if (!(tnear < tfar)) return;
+    int64_t v[3], step[3];
+    double tmax[3];
+    for (int a = 0; a < 3; a++) {
+        double p = O[a] + tnear * D[a];
+        int64_t vi = (int64_t)floor(p);
+        if (vi < 0) vi = 0;
+        if (vi > R[a] - 1) vi = R[a] - 1;
+        v[a] = vi;
+        step[a] = D[a] > 0.0 ? 1 : (D[a] < 0.0 ? -1 : 0);
+    }
+    for (int a = 0; a < 3; a++)
+        tmax[a] = step[a] == 0 ? 1e300
+                : ((double)(step[a] > 0 ? v[a] + 1 : v[a]) - O[a]) / D[a];
+    double t0 = tnear;
+    const double r = rd->radius;
+    while (!ps->done) {
+        int ax = 0;
+        for (int a = 1; a < 3; a++) if (tmax[a] < tmax[ax]) ax = a;
+        double t1 = tmax[ax];
+        int64_t vid = v[0] + (int64_t)R[0] * (v[1] + (int64_t)R[1] * v[2]);
+        uint32_t beg = vs->offset[vid], end = vs->offset[vid + 1];
+        ps->nvox++;
+        if (end > beg) {
+            ps->nrec += end - beg;
+            if ((int)(end - beg) > *bufcap) {
+                *bufcap = (int)(end - beg);
+                *buf = (hit *)realloc(*buf, sizeof(hit) * (size_t)*bufcap);
+            }
+            int nh = 0;
+            for (uint32_t k = beg; k < end; k++) {
+                double a[3], b[3], tc, t, sens;
+                seg_world(vs, &vs->seg[k], a, b);
+                double dist = line_segment_distance(O, D, a, b, &tc);
+                if (fabs(dist - r) < EPS_G && tc > t0 - 1.0 && tc < t1 + 1.0) ps->tie |= TIE_GRAZE;
+                if (!capsule_entry_s(O, D, a, b, r, &t, &sens)) continue;
+                double eps = EPS_T + ERR_Q * sens;
+                if (fabs(t - t0) < eps || fabs(t - t1) < eps) ps->tie |= TIE_OWNER;
+                if (t >= t0 && t < t1) {
+                    (*buf)[nh].t = t; (*buf)[nh].eps = eps; (*buf)[nh].k = k;
+                    nh++;
+                }
+            }
+            qsort(*buf, (size_t)nh, sizeof(hit), hit_cmp);
+            flag_sorted_ties(vs, *buf, nh, &ps->tie);
+            for (int i = 0; i < nh && !ps->done; i++) shade_composite(vs, L, rd, O, D, Lt, &(*buf)[i], ps);
+        }
+        if (ps->done) break;
+        t0 = t1;
+        v[ax] += step[ax];
+        if (v[ax] < 0 || v[ax] >= R[ax]) break;
+        tmax[ax] = ((double)(step[ax] > 0 ? v[ax] + 1 : v[ax]) - O[ax]) / D[ax];
+    }
+}
+
+/* One ray by brute force: every capsule of every voxel, kept iff its entry
+ * point lies in the voxel that stores it; globally sorted by depth. */
+static void trace_brute(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *rd,
+                        const double *O, const double *D, const double *Lt, pixstate *ps) {
+    const int32_t *R = vs->grid.res;
+    const double r = rd->radius;
+    int64_t cap = 64, nh = 0;
+    hit *hs = (hit *)malloc(sizeof(hit) * (size_t)cap);
+    for (int64_t vid = 0; vid < vs->nvox; vid++) {
+        uint32_t beg = vs->offset[vid], end = vs->offset[vid + 1];
+        if (beg == end) continue;
+        int64_t vx = vid % R[0], vy = (vid / R[0]) % R[1], vz = vid / ((int64_t)R[0] * R[1]);
+        int64_t vv[3] = {vx, vy, vz};
+        for (uint32_t k = beg; k < end; k++) {
+            double a[3], b[3], t, sens, tc;
+            seg_world(vs, &vs->seg[k], a, b);
+            double dist = line_segment_distance(O, D, a, b, &tc);
+            if (fabs(dist - r) < EPS_G) {
+                /* only matters if the grazing point is near this voxel */
+                double P[3] = {O[0] + tc * D[0], O[1] + tc * D[1], O[2] + tc * D[2]};
+                int near = 1;
+                for (int c = 0; c < 3; c++)
+                    if (P[c] < vv[c] - 1.0 || P[c] > vv[c] + 2.0) near = 0;
+                if (near) ps->tie |= TIE_GRAZE;
+            }
+            if (!capsule_entry_s(O, D, a, b, r, &t, &sens)) continue;
+            double eps = EPS_T + ERR_Q * sens;
+            double P[3] = {O[0] + t * D[0], O[1] + t * D[1], O[2] + t * D[2]};
+            int own = 1;
+            double margin = 1e300;
+            for (int c = 0; c < 3; c++) {
+                if (P[c] < vv[c] || P[c] >= vv[c] + 1) own = 0;
+                if (D[c] != 0.0) {
+                    margin = fmin(margin, fabs(P[c] - vv[c]) / fabs(D[c]));
+                    margin = fmin(margin, fabs(P[c] - (vv[c] + 1)) / fabs(D[c]));
+                }
+            }
+            if (margin < eps) ps->tie |= TIE_OWNER;
+            if (!own) continue;
+            if (nh == cap) { cap *= 2; hs = (hit *)realloc(hs, sizeof(hit) * (size_t)cap); }
+            hs[nh].t = t; hs[nh].eps = eps; hs[nh].k = k;
+            nh++;
+        }
+    }
+    qsort(hs, (size_t)nh, sizeof(hit), hit_cmp);
+    flag_sorted_ties(vs, hs, (int)nh, &ps->tie);
+    for (int64_t i = 0; i < nh && !ps->done; i++) shade_composite(vs, L, rd, O, D, Lt, &hs[i], ps);
+    free(hs);
+}
+
+int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
+               const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
+               double *rgba, uint8_t *tie, uint64_t *counters, int nthreads) {
+    if ((rd->shadows || rd->ao) && !L) return ORC_EINVAL;
+    if (view->width < 1 || view->height < 1 || !(rd->radius > 0.0f)) return ORC_EINVAL;
+    cam32 cam;
+    cam_setup(view, &cam);
+    double Lt[3];
+    {
+        double ld[3] = {view->light_dir[0], view->light_dir[1], view->light_dir[2]};
+        norm3(ld);
+        /* toward the light, rounded to float32 like the library's copy */
+        for (int a = 0; a < 3; a++) Lt[a] = (double)(float)(-ld[a]);
+    }
+    uint64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel reduction(+ : c0, c1, c2, c3)
+#endif
+    {
+        hit *buf = NULL;
+        int bufcap = 0;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t p = 0; p < npix; p++) {
+            float o32[3], d32[3];
+            cam_ray(&cam, pix[2 * p], pix[2 * p + 1], o32, d32);
+            double O[3] = {o32[0], o32[1], o32[2]}, D[3] = {d32[0], d32[1], d32[2]};
+            pixstate ps;
+            memset(&ps, 0, sizeof ps);
+            if (mode == ORC_RENDER_BRUTE) trace_brute(vs, L, rd, O, D, Lt, &ps);
+            else trace_dda(vs, L, rd, O, D, Lt, &ps, &buf, &bufcap);
+            for (int c = 0; c < 3; c++) rgba[4 * p + c] = ps.C[c] + (1.0 - ps.A) * rd->bg[c];
+            rgba[4 * p + 3] = ps.A;
+            if (tie) tie[p] = (uint8_t)ps.tie;
+            c0 += ps.nvox; c1 += ps.nrec; c2 += ps.nsamp; c3 += ps.nhit;
+        }
+        free(buf);
+    }
+    if (counters) { counters[0] = c0; counters[1] = c1; counters[2] = c2; counters[3] = c3; }
+    return ORC_OK;
+}
