@@ -382,6 +382,9 @@ def test_silhouette_width_is_two_radii(orc):
     px = 2 * dist * math.tan(math.radians(fov / 2)) / H
     for col in (10, 50, 90):
         assert abs(cov[:, col].sum() - 2 * r / px) <= 2.0
+        # the tube axis sits at the bin centre the camera looks at: the image centre row
+        rows = np.nonzero(cov[:, col])[0]
+        assert abs(rows.mean() - (H - 1) / 2) <= 0.5
     assert cov.any(1).sum() == cov[:, 50].sum()
 
 
