@@ -1,0 +1,196 @@
+/*
+ * lvr — voxel-based ray casting of large 3D line sets on one GB300 GPU.
+ *
+ * C ABI of the CUDA library (liblvr.so). Method: Kanzler, Rautenhaus,
+ * Westermann, "A Voxel-based Rendering Pipeline for Large 3D Line Sets"
+ * (arXiv 1801.01155). Section numbers below refer to that paper.
+ *
+ * Conventions
+ *  - Every entry point returns an lvr_status; on failure lvr_last_error()
+ *    gives a message owned by the context, valid until its next call.
+ *  - Pointer arguments marked "host or device" may point to either; the
+ *    library detects which (cudaPointerGetAttributes) and stages host data
+ *    through its own device buffers. Everything else is host memory.
+ *  - Inputs are owned by the caller and are only read, and only until the
+ *    call returns (device inputs: until the work queued on the context's
+ *    stream has consumed them). Handles (lvr_lineset, lvr_lod,
+ *    lvr_ao_model) are owned by the library and released by their
+ *    lvr_free_* call, which must come before lvr_destroy of their context.
+ *    Output buffers are owned by the caller.
+ *  - Work is queued on the context's CUDA stream in call order. Calls that
+ *    return host-visible results (sizes, exports into host memory)
+ *    synchronise that stream. Arguments are validated before any work is
+ *    queued; conditions found on the device (a bad vertex, a count
+ *    overflow) make the call that finds them fail.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef LVR_H
+#define LVR_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LVR_API_VERSION 1
+
+typedef enum lvr_status {
+    LVR_OK = 0,
+    LVR_EINVAL = 1,     /* bad argument or input data */
+    LVR_ENOMEM = 2,     /* device or host allocation failed */
+    LVR_ECUDA = 3,      /* CUDA runtime error */
+    LVR_EOVERFLOW = 4,  /* more than 2^32 - 1 segments */
+    LVR_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    LVR_EDEVICE = 6     /* no usable sm_103 device */
+} lvr_status;
+
+typedef struct lvr_ctx lvr_ctx;
+typedef struct lvr_lineset lvr_lineset;
+typedef struct lvr_lod lvr_lod;
+typedef struct lvr_ao_model lvr_ao_model;
+
+/* Library version (LVR_API_VERSION). */
+int lvr_version(void);
+
+/* Create a context on CUDA device `device`, queuing work on `cuda_stream`
+ * (a cudaStream_t; NULL: the context creates and owns a stream). */
+lvr_status lvr_create(int device, void *cuda_stream, lvr_ctx **out);
+void lvr_destroy(lvr_ctx *ctx);
+const char *lvr_last_error(const lvr_ctx *ctx);
+/* Wait for all work queued on the context's stream. */
+lvr_status lvr_sync(lvr_ctx *ctx);
+
+/* ------------------------------------------------------------------ voxelisation
+ * Sec. 3.1-3.3. Input curves are polylines with optional per-vertex
+ * attributes. Each edge is clipped at the voxel faces in order of
+ * occurrence; each pair of consecutive face points forms one linear segment
+ * in the voxel between them, and the pieces before a curve's first and after
+ * its last face point are dropped (Sec. 3.1). Face points are quantised to
+ * the centres of an N x N subdivision of their face and encoded by a 3-bit
+ * face id and the bin indices (Sec. 3.2). Segments are stored per voxel,
+ * contiguously, behind an offset table (Sec. 3.3); within a voxel they are
+ * ordered by (curve index, position along the curve).
+ *
+ * Grid transform: p = fl32(fl32(v - origin) * scale) per component; every
+ * decision after that is exact integer arithmetic on round(p * 2^16).
+ * Vertices must map to |p| < 2^14 voxels and be finite (else LVR_EINVAL).
+ */
+typedef struct lvr_grid_desc {
+    int32_t res[3];      /* voxels per axis (each 1..4096, product < 2^32) */
+    int32_t bins;        /* N, sub-squares per face edge: power of two, 2..128 */
+    int32_t fit;         /* 1: fit the grid to the vertices' bounding box,
+                            keeping its aspect ratio (Sec. 3.1): res[0] voxels
+                            along the longest extent; origin, scale and the
+                            other res[] are outputs written back here */
+    float   origin[3];   /* world point mapped to grid coordinate 0 */
+    float   scale;       /* grid units (voxels) per world unit, > 0 */
+    float   attr_min;    /* attribute range mapped to 0..65535 (16-bit codes, */
+    float   attr_max;    /*   one byte kept per segment); max <= min: all 0 */
+} lvr_grid_desc;
+
+/* xyz: host or device float32 [n_vertices * 3]; attr: host or device float32
+ * [n_vertices] or NULL; curve_offsets: host or device int64 [n_curves + 1],
+ * curve c = vertices [curve_offsets[c], curve_offsets[c+1]), starting at 0,
+ * non-decreasing, ending at n_vertices. `grid` is read (and, in fit mode,
+ * written). On success *out owns the voxel model. */
+lvr_status lvr_voxelize(lvr_ctx *ctx, const float *xyz, const float *attr,
+                        const int64_t *curve_offsets, int64_t n_curves, int64_t n_vertices,
+                        lvr_grid_desc *grid, lvr_lineset **out);
+
+typedef struct lvr_lineset_info {
+    int32_t res[3];
+    int32_t bins;
+    float   origin[3];
+    float   scale;
+    int64_t n_voxels;
+    int64_t n_segments;
+    int64_t bytes;        /* device bytes held by the handle */
+} lvr_lineset_info;
+lvr_status lvr_lineset_info_get(const lvr_lineset *ls, lvr_lineset_info *info);
+
+/* Decoded copy of the voxel model (for tests and tools). Any pointer may be
+ * NULL. offset: uint32 [n_voxels + 1]; fields: uint8 [n_segments * 8] =
+ * face_in, u_in, v_in, face_out, u_out, v_out, attribute byte, continues-
+ * previous flag; curve, ordinal: uint32 [n_segments]. Host or device. */
+lvr_status lvr_export_lineset(lvr_ctx *ctx, const lvr_lineset *ls, uint32_t *offset,
+                              uint8_t *fields, uint32_t *curve, uint32_t *ordinal);
+void lvr_free_lineset(lvr_lineset *ls);
+
+/* ------------------------------------------------------------------ density LoD
+ * Sec. 3.4, Eq. 1: per voxel rho = sum over its segments of length * sigma,
+ * sigma = sigma256[attribute byte] (host float32 [256], the transfer
+ * function's opacity); then 2^3 pooling into `levels` levels (1..4),
+ * dims ceil(d / 2). Each level stores sums: segment count (uint32), summed
+ * length and summed length * sigma (float32); the density sampled at level
+ * l is dens_l / 8^l, the paper's 2^3 average. */
+lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int levels,
+                         const float *sigma256, lvr_lod **out);
+typedef struct lvr_lod_info {
+    int32_t levels;
+    int32_t dims[4][3];
+} lvr_lod_info;
+lvr_status lvr_lod_info_get(const lvr_lod *lod, lvr_lod_info *info);
+/* Copy one level out; any pointer may be NULL; host or device; each
+ * dims[level] product elements. */
+lvr_status lvr_export_lod(lvr_ctx *ctx, const lvr_lod *lod, int level, uint32_t *cnt,
+                          float *len, float *dens);
+void lvr_free_lod(lvr_lod *lod);
+
+/* ------------------------------------------------------------------ rendering
+ * Secs. 4-5. One ray per pixel (pinhole camera, pixel centres, row 0 at the
+ * top) is traversed through the grid by 3D-DDA; the segments stored in each
+ * visited non-empty voxel are intersected as tubes of radius `radius`
+ * closed by spheres at their end points (Sec. 4.1); a voxel keeps the hits
+ * whose entry point lies inside it and sorts them by depth (Sec. 4). Each
+ * hit is shaded at its entry point (ambient + diffuse with the tube normal,
+ * Sec. 5) and blended front to back with the transfer function's opacity
+ * until the accumulated opacity reaches `ert_alpha` (Sec. 5.1); opaque mode
+ * keeps the first hit. Optional soft shadows march the density LoD toward
+ * a directional light, sampling coarser levels with distance (Sec. 5.2);
+ * optional ambient occlusion marches `ao_rays` hemisphere rays around the
+ * normal up to `ao_radius` voxels (Sec. 5.3). Output pixel =
+ * (C + (1 - A) * bg, A).
+ *
+ * Primary rays are float32 quantities built by a fixed sequence of float32
+ * operations from the camera (see the implementation); light and camera
+ * basis vectors are computed in float64 and rounded to float32.
+ */
+typedef struct lvr_view {
+    float   eye[3];        /* camera position, grid (voxel) coordinates */
+    float   at[3];         /* look-at point */
+    float   up[3];         /* up hint */
+    float   fovy_deg;      /* vertical field of view */
+    int32_t width, height; /* full image size */
+    int32_t crop[4];       /* x0, y0, w, h of the rendered rectangle; w = 0: full image */
+    float   light_dir[3];  /* direction in which the light travels */
+} lvr_view;
+
+typedef struct lvr_render_desc {
+    float   radius;        /* tube radius, voxel units, > 0 */
+    float   tf_rgba[1024]; /* transfer function: RGBA per attribute byte */
+    int32_t opaque;        /* 1: alpha = 1, first hit only (Sec. 5) */
+    float   ert_alpha;     /* early ray termination threshold (> 1: off) */
+    int32_t shadows;       /* 1: soft shadows (needs a LoD) */
+    int32_t ao_mode;       /* 0 off, 1 traced (density-marched, needs a LoD),
+                              2 learned surrogate (needs an lvr_ao_model) */
+    int32_t ao_rays;       /* hemisphere rays per hit, 1..32 (16 typical) */
+    float   ao_radius;     /* radius of influence, voxels (15 typical) */
+    float   ka, kd;        /* ambient / diffuse weights (0.3 / 0.7 typical) */
+    float   bg[3];         /* background colour */
+    int32_t tile_w, tile_h;/* ray tile of one warp: 8x4 (0,0 = default), 4x8, 16x2, 32x1 */
+} lvr_render_desc;
+
+/* rgba: host or device float32 [h * w * 4] for the crop rectangle (row-major,
+ * row 0 = top of the crop). counters: NULL, or host or device uint64 [4]
+ * receiving voxels visited, records tested, LoD trilinear samples and
+ * composited hits over the whole rectangle (costs one extra reduction).
+ * `lod` may be NULL unless shadows or traced AO are on; `ao` may be NULL
+ * unless ao_mode == 2. */
+lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
+                      const lvr_view *view, const lvr_render_desc *desc,
+                      const lvr_ao_model *ao, float *rgba, uint64_t *counters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

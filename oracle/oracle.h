@@ -130,9 +130,12 @@ typedef struct orc_rdesc {
 /* counters[0..3]: voxels visited, records tested, LoD trilinear samples,
  * composited hits (summed over the listed pixels). */
 enum { ORC_RENDER_DDA = 0, ORC_RENDER_BRUTE = 1 };
+/* tie: per-pixel bit mask of near-tie decisions (may be NULL); margin: per
+ * pixel, the smallest decision margin in units of its tie threshold (< 1
+ * exactly when tie != 0; may be NULL). */
 int orc_render(const orc_voxset *vs, const orc_lod *lod, const orc_view *view,
                const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
-               double *rgba, uint8_t *tie, uint64_t *counters, int nthreads);
+               double *rgba, uint8_t *tie, double *margin, uint64_t *counters, int nthreads);
 
 /* ---- pieces exposed for pin tests ---- */
 /* Primary ray of pixel (i, j) under the single-precision ray contract (reading R0). */

@@ -60,7 +60,7 @@ def lib():
         L.orc_lod_free.argtypes = [vp]
         L.orc_lod_dims.argtypes = [vp, C.c_int, vp]
         L.orc_lod_export.argtypes = [vp, C.c_int, vp, vp, vp]
-        L.orc_render.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int, vp, vp, vp, C.c_int]
+        L.orc_render.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int, vp, vp, vp, vp, C.c_int]
         L.orc_primary_ray.argtypes = [vp, i32, i32, vp, vp]
         L.orc_capsule_entry.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
         L.orc_march.argtypes = [vp, vp, vp, C.c_double]
@@ -243,17 +243,22 @@ def pixel_grid(x0, y0, w, h):
     return np.stack([ii.reshape(-1), jj.reshape(-1)], 1).astype(np.int32)
 
 
-def render(vs: VoxSet, lod: Lod | None, view: View, rd: RDesc, pix, mode="dda", nthreads=0):
+def render(vs: VoxSet, lod: Lod | None, view: View, rd: RDesc, pix, mode="dda", nthreads=0,
+           margins=False):
     """Render the listed pixels (int32 (n, 2) of (i, j)); returns rgba (n,4) f64,
-    tie flags (n,) u8 and counters [voxels, records, lod samples, hits]."""
+    tie flags (n,) u8 and counters [voxels, records, lod samples, hits]; with
+    margins=True also the per-pixel smallest normalised decision margin."""
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
     n = len(pix)
     rgba = np.empty((n, 4), np.float64)
     tie = np.empty(n, np.uint8)
+    mg = np.empty(n, np.float64) if margins else None
     cnt = np.zeros(4, np.uint64)
     m = 1 if mode == "brute" else 0
     _check(lib().orc_render(vs.handle, lod.handle if lod is not None else None, C.byref(view),
-                            C.byref(rd), _p(pix), n, m, _p(rgba), _p(tie), _p(cnt), int(nthreads)))
+                            C.byref(rd), _p(pix), n, m, _p(rgba), _p(tie), _p(mg), _p(cnt), int(nthreads)))
+    if margins:
+        return rgba, tie, cnt, mg
     return rgba, tie, cnt
 
 

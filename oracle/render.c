@@ -43,9 +43,9 @@
 #define TIE_FRAME 16
 #define TIE_SLAB  32
 
-static const double EPS_G = 5e-6;     /* |distance - radius| at a silhouette */
-static const double EPS_T = 5e-6;     /* entry parameter vs voxel faces / other hits */
-static const double ERR_Q = 2e-7;     /* float32 error scale of a quadratic's root term */
+static const double EPS_G = 7.5e-7;   /* |distance - radius| at a silhouette */
+static const double EPS_T = 7.5e-7;   /* entry parameter vs voxel faces / other hits */
+static const double ERR_Q = 7.5e-8;   /* float32 error of a squared distance, scaling the root term */
 static const double EPS_F = 1e-5;     /* AO frame switch */
 static const double FRAME_MIN = 1e-3; /* tangent shorter than this: axis fallback */
 
@@ -182,13 +182,19 @@ static int sphere_entry(const double *o, const double *d, const double *c, doubl
     return 1;
 }
 
+/* Which surface a capsule entry lies on: its lateral body, or one of the
+ * end spheres (then `c` is the sphere centre). `ymargin` is how far the body
+ * candidate's axial coordinate lies from the end planes, i.e. how close the
+ * body / sphere choice came to going the other way. */
+typedef struct { double t, sens, c[3], ymargin; int part; } entry;
+
 /* Capsule entry: the capsule is the union of the finite cylinder and the two
  * end spheres, so its first entry is the smallest of: the lateral entry into
  * the infinite cylinder when that point lies between the end planes, and the
- * entries into the two spheres. *sens = 1 / (|d_perp| g), g the half chord,
+ * entries into the two spheres. sens = 1 / (|d_perp| g), g the half chord,
  * scales the float32 error of the root. */
 static int capsule_entry_s(const double *o, const double *d, const double *a, const double *b,
-                           double r, double *t_out, double *sens) {
+                           double r, entry *E) {
     double tc;
     if (line_segment_distance(o, d, a, b, &tc) > r) return 0;
     /* ray origin inside the capsule: no entering intersection ahead */
@@ -201,7 +207,7 @@ static int capsule_entry_s(const double *o, const double *d, const double *a, co
         if (dot3(q, q) <= r * r) return 0;
     }
     int found = 0;
-    double best = 0.0, bsens = 0.0;
+    double ymargin = 1e300;
     double ba[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
     double L2 = dot3(ba, ba);
     if (L2 > 0.0) {
@@ -217,33 +223,41 @@ static int capsule_entry_s(const double *o, const double *d, const double *a, co
             if (disc >= 0.0) {
                 double t = (-B - sqrt(disc)) / A;
                 double y = mw + t * dw;             /* axial coordinate of the entry point */
+                ymargin = fmin(fabs(y), fabs(y - L));
                 if (y >= 0.0 && y <= L) {
                     found = 1;
-                    best = t;
+                    E->t = t;
+                    E->part = 0;
                     double s = sqrt(A), g = sqrt(disc) / s;
-                    bsens = 1.0 / fmax(s * g, 1e-12);
+                    E->sens = 1.0 / fmax(s * g, 1e-12);
                 }
             }
         }
     }
-    double ts, g;
-    if (sphere_entry(o, d, a, r, &ts, &g) && (!found || ts < best)) {
-        found = 1; best = ts; bsens = 1.0 / fmax(g, 1e-12);
+    const double *cs[2] = {a, b};
+    for (int k = 0; k < 2; k++) {
+        double ts, g;
+        if (sphere_entry(o, d, cs[k], r, &ts, &g) && (!found || ts < E->t)) {
+            found = 1;
+            E->t = ts;
+            E->part = 1 + k;
+            E->sens = 1.0 / fmax(g, 1e-12);
+            for (int c = 0; c < 3; c++) E->c[c] = cs[k][c];
+        }
     }
-    if (sphere_entry(o, d, b, r, &ts, &g) && (!found || ts < best)) {
-        found = 1; best = ts; bsens = 1.0 / fmax(g, 1e-12);
-    }
-    if (!found || !(best > 0.0)) return 0;
-    *t_out = best;
-    *sens = bsens;
+    E->ymargin = ymargin;
+    if (!found || !(E->t > 0.0)) return 0;
     return 1;
 }
 
 int orc_capsule_entry(const double o[3], const double d[3], const double a[3],
                       const double b[3], double r, double *t, double *dist) {
-    double tc, sens;
+    double tc;
+    entry E;
     *dist = line_segment_distance(o, d, a, b, &tc);
-    return capsule_entry_s(o, d, a, b, r, t, &sens);
+    if (!capsule_entry_s(o, d, a, b, r, &E)) return 0;
+    *t = E.t;
+    return 1;
 }
 
 /* ------------------------------------------------------------------ LoD marches */
@@ -320,11 +334,11 @@ double orc_march(const orc_lod *L, const double p[3], const double dir[3], doubl
 /* Reading S3: spherical-Fibonacci directions on the hemisphere around n, in
  * the frame whose tangent is the tube axis projected onto the tangent plane
  * (fallback: the world axis least aligned with n). */
-static void ao_dirs_t(const double *n, const double *u, int k, double *dirs, int *tie) {
+static void ao_dirs_t(const double *n, const double *u, int k, double *dirs, double *fmargin) {
     double un = dot3(u, n);
     double T[3] = {u[0] - un * n[0], u[1] - un * n[1], u[2] - un * n[2]};
     double m = sqrt(dot3(T, T));
-    if (fabs(m - FRAME_MIN) < EPS_F) *tie |= TIE_FRAME;
+    *fmargin = fabs(m - FRAME_MIN) / EPS_F;
     if (m >= FRAME_MIN) {
         T[0] /= m; T[1] /= m; T[2] /= m;
     } else {
@@ -332,7 +346,7 @@ static void ao_dirs_t(const double *n, const double *u, int k, double *dirs, int
         int e = 0;
         for (int a = 1; a < 3; a++) if (an[a] < an[e]) e = a;
         for (int a = 0; a < 3; a++)
-            if (a != e && fabs(an[a] - an[e]) < EPS_F) *tie |= TIE_FRAME;
+            if (a != e) *fmargin = fmin(*fmargin, fabs(an[a] - an[e]) / EPS_F);
         double E[3] = {0, 0, 0};
         E[e] = 1.0;
         double en = dot3(E, n);
@@ -352,8 +366,8 @@ static void ao_dirs_t(const double *n, const double *u, int k, double *dirs, int
 }
 
 void orc_ao_dirs(const double n[3], const double u[3], int k, double *dirs) {
-    int tie = 0;
-    ao_dirs_t(n, u, k, dirs, &tie);
+    double fm;
+    ao_dirs_t(n, u, k, dirs, &fm);
 }
 
 /* ------------------------------------------------------------------ per-pixel state */
@@ -362,10 +376,16 @@ typedef struct {
     float A32;          /* the termination decision, in float32 */
     int done;
     int tie;
+    double margin;      /* smallest decision margin, in units of its tie threshold */
     uint64_t nvox, nrec, nsamp, nhit;
 } pixstate;
 
-typedef struct { double t, eps; int64_t k; } hit;
+static void note(pixstate *ps, double m, int bit) {
+    if (m < ps->margin) ps->margin = m;
+    if (m < 1.0) ps->tie |= bit;
+}
+
+typedef struct { double t, eps; int64_t k; entry e; } hit;
 
 static int hit_cmp(const void *x, const void *y) {
     const hit *a = (const hit *)x, *b = (const hit *)y;
@@ -401,7 +421,9 @@ static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rd
         double u[3] = {ba[0], ba[1], ba[2]};
         if (L2 > 0.0) { double l = sqrt(L2); u[0] /= l; u[1] /= l; u[2] /= l; }
         double *dirs = (double *)malloc(sizeof(double) * 3 * (size_t)rd->ao_rays);
-        ao_dirs_t(n, u, rd->ao_rays, dirs, &ps->tie);
+        double fm;
+        ao_dirs_t(n, u, rd->ao_rays, dirs, &fm);
+        note(ps, fm, TIE_FRAME);
         double occ = 0.0;
         for (int i = 0; i < rd->ao_rays; i++)
             occ += fmin(1.0, march(L, P, dirs + 3 * i, rd->ao_radius, &ps->nsamp));
@@ -426,11 +448,19 @@ static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rd
     if (ps->A32 >= rd->ert_alpha) ps->done = 1;
 }
 
-static void flag_sorted_ties(const orc_voxset *vs, const hit *hs, int nh, int *tie) {
-    for (int i = 0; i + 1 < nh; i++)
-        if (hs[i + 1].t - hs[i].t < hs[i].eps + hs[i + 1].eps &&
-            !same_geometry(&vs->seg[hs[i].k], &vs->seg[hs[i + 1].k]))
-            *tie |= TIE_SORT;
+/* Two hits closer in depth than their error bounds may swap under float32 -
+ * unless they are one surface: two capsules entered through the same joint
+ * sphere give bit-identical roots on both sides and keep index order. */
+static const double YMARGIN = 1e-4;
+static void flag_sorted_ties(const orc_voxset *vs, const hit *hs, int nh, pixstate *ps) {
+    for (int i = 0; i + 1 < nh; i++) {
+        const hit *x = &hs[i], *y = &hs[i + 1];
+        if (same_geometry(&vs->seg[x->k], &vs->seg[y->k])) continue;
+        if (x->e.part && y->e.part && x->e.c[0] == y->e.c[0] && x->e.c[1] == y->e.c[1] &&
+            x->e.c[2] == y->e.c[2] && x->e.ymargin > YMARGIN && y->e.ymargin > YMARGIN)
+            continue;
+        note(ps, (y->t - x->t) / (x->eps + y->eps), TIE_SORT);
+    }
 }
 
 /* One ray by DDA traversal (Sec. 4). */
@@ -449,7 +479,7 @@ static void trace_dda(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *r
         }
     }
     if (tnear < 0.0) tnear = 0.0;
-    if (fabs(tfar - tnear) < 1e-5) ps->tie |= TIE_SLAB;
+    note(ps, fabs(tfar - tnear) / 1e-5, TIE_SLAB);
     if (!(tnear < tfar)) return;
     int64_t v[3], step[3];
     double tmax[3];
@@ -481,20 +511,21 @@ static void trace_dda(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *r
             }
             int nh = 0;
             for (uint32_t k = beg; k < end; k++) {
-                double a[3], b[3], tc, t, sens;
+                double a[3], b[3], tc;
+                entry E;
                 seg_world(vs, &vs->seg[k], a, b);
                 double dist = line_segment_distance(O, D, a, b, &tc);
-                if (fabs(dist - r) < EPS_G && tc > t0 - 1.0 && tc < t1 + 1.0) ps->tie |= TIE_GRAZE;
-                if (!capsule_entry_s(O, D, a, b, r, &t, &sens)) continue;
-                double eps = EPS_T + ERR_Q * sens;
-                if (fabs(t - t0) < eps || fabs(t - t1) < eps) ps->tie |= TIE_OWNER;
+                if (tc > t0 - 0.01 && tc < t1 + 0.01) note(ps, fabs(dist - r) / EPS_G, TIE_GRAZE);
+                if (!capsule_entry_s(O, D, a, b, r, &E)) continue;
+                double t = E.t, eps = EPS_T + ERR_Q * E.sens;
+                note(ps, fmin(fabs(t - t0), fabs(t - t1)) / eps, TIE_OWNER);
                 if (t >= t0 && t < t1) {
-                    (*buf)[nh].t = t; (*buf)[nh].eps = eps; (*buf)[nh].k = k;
+                    (*buf)[nh].t = t; (*buf)[nh].eps = eps; (*buf)[nh].k = k; (*buf)[nh].e = E;
                     nh++;
                 }
             }
             qsort(*buf, (size_t)nh, sizeof(hit), hit_cmp);
-            flag_sorted_ties(vs, *buf, nh, &ps->tie);
+            flag_sorted_ties(vs, *buf, nh, ps);
             for (int i = 0; i < nh && !ps->done; i++) shade_composite(vs, L, rd, O, D, Lt, &(*buf)[i], ps);
         }
         if (ps->done) break;
@@ -519,19 +550,20 @@ static void trace_brute(const orc_voxset *vs, const orc_lod *L, const orc_rdesc 
         int64_t vx = vid % R[0], vy = (vid / R[0]) % R[1], vz = vid / ((int64_t)R[0] * R[1]);
         int64_t vv[3] = {vx, vy, vz};
         for (uint32_t k = beg; k < end; k++) {
-            double a[3], b[3], t, sens, tc;
+            double a[3], b[3], tc;
+            entry E;
             seg_world(vs, &vs->seg[k], a, b);
             double dist = line_segment_distance(O, D, a, b, &tc);
-            if (fabs(dist - r) < EPS_G) {
-                /* only matters if the grazing point is near this voxel */
+            {
+                /* only matters if the grazing point is in this voxel */
                 double P[3] = {O[0] + tc * D[0], O[1] + tc * D[1], O[2] + tc * D[2]};
                 int near = 1;
                 for (int c = 0; c < 3; c++)
-                    if (P[c] < vv[c] - 1.0 || P[c] > vv[c] + 2.0) near = 0;
-                if (near) ps->tie |= TIE_GRAZE;
+                    if (P[c] < vv[c] - 0.01 || P[c] > vv[c] + 1.01) near = 0;
+                if (near) note(ps, fabs(dist - r) / EPS_G, TIE_GRAZE);
             }
-            if (!capsule_entry_s(O, D, a, b, r, &t, &sens)) continue;
-            double eps = EPS_T + ERR_Q * sens;
+            if (!capsule_entry_s(O, D, a, b, r, &E)) continue;
+            double t = E.t, eps = EPS_T + ERR_Q * E.sens;
             double P[3] = {O[0] + t * D[0], O[1] + t * D[1], O[2] + t * D[2]};
             int own = 1;
             double margin = 1e300;
@@ -542,22 +574,22 @@ static void trace_brute(const orc_voxset *vs, const orc_lod *L, const orc_rdesc 
                     margin = fmin(margin, fabs(P[c] - (vv[c] + 1)) / fabs(D[c]));
                 }
             }
-            if (margin < eps) ps->tie |= TIE_OWNER;
+            note(ps, margin / eps, TIE_OWNER);
             if (!own) continue;
             if (nh == cap) { cap *= 2; hs = (hit *)realloc(hs, sizeof(hit) * (size_t)cap); }
-            hs[nh].t = t; hs[nh].eps = eps; hs[nh].k = k;
+            hs[nh].t = t; hs[nh].eps = eps; hs[nh].k = k; hs[nh].e = E;
             nh++;
         }
     }
     qsort(hs, (size_t)nh, sizeof(hit), hit_cmp);
-    flag_sorted_ties(vs, hs, (int)nh, &ps->tie);
+    flag_sorted_ties(vs, hs, (int)nh, ps);
     for (int64_t i = 0; i < nh && !ps->done; i++) shade_composite(vs, L, rd, O, D, Lt, &hs[i], ps);
     free(hs);
 }
 
 int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
                const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
-               double *rgba, uint8_t *tie, uint64_t *counters, int nthreads) {
+               double *rgba, uint8_t *tie, double *margin, uint64_t *counters, int nthreads) {
     if ((rd->shadows || rd->ao) && !L) return ORC_EINVAL;
     if (view->width < 1 || view->height < 1 || !(rd->radius > 0.0f)) return ORC_EINVAL;
     cam32 cam;
@@ -586,11 +618,13 @@ int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
             double O[3] = {o32[0], o32[1], o32[2]}, D[3] = {d32[0], d32[1], d32[2]};
             pixstate ps;
             memset(&ps, 0, sizeof ps);
+            ps.margin = 1e300;
             if (mode == ORC_RENDER_BRUTE) trace_brute(vs, L, rd, O, D, Lt, &ps);
             else trace_dda(vs, L, rd, O, D, Lt, &ps, &buf, &bufcap);
             for (int c = 0; c < 3; c++) rgba[4 * p + c] = ps.C[c] + (1.0 - ps.A) * rd->bg[c];
             rgba[4 * p + 3] = ps.A;
             if (tie) tie[p] = (uint8_t)ps.tie;
+            if (margin) margin[p] = ps.margin;
             c0 += ps.nvox; c1 += ps.nrec; c2 += ps.nsamp; c3 += ps.nhit;
         }
         free(buf);

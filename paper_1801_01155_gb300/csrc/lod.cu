@@ -1,0 +1,156 @@
+// Density LoD (Sec. 3.4, Eq. 1): per voxel rho = sum length * sigma over its
+// segments, then 2^3 pooling. Levels store sums (count, length, length*sigma);
+// the density sampled at level l is dens_l / 8^l.
+//
+// Segment lengths are exact: endpoints are face-bin centres, integer in
+// units of 1/(2N), so length = sqrt(I) / (2N) with I < 2^24 an integer;
+// float32 sqrt of I is correctly rounded and the division by 2N is exact.
+// Sums run in the canonical segment order (level 0) and in the fixed child
+// order z, y, x (coarser levels), so results are deterministic.
+#include "lvr_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void face_point_2n(uint32_t face, uint32_t u, uint32_t v, int twoN, int q[3]) {
+    const int ax = (int)(face >> 1);
+    const int side = (face & 1u) ? twoN : 0;
+    const int cu = 2 * (int)u + 1, cv = 2 * (int)v + 1;
+    q[0] = ax == 0 ? side : cu;
+    q[1] = ax == 1 ? side : (ax == 0 ? cu : cv);
+    q[2] = ax == 2 ? side : cv;
+}
+
+__global__ void __launch_bounds__(256)
+lod_level0_kernel(const uint32_t *__restrict__ offset, const uint64_t *__restrict__ rec, int64_t nvox,
+                  int N, const float *__restrict__ sigma_g, uint32_t *cnt, float *len, float *dens) {
+    __shared__ float sigma[256];
+    sigma[threadIdx.x] = sigma_g[threadIdx.x];
+    __syncthreads();
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    const uint32_t beg = offset[v], end = offset[v + 1];
+    const int twoN = 2 * N;
+    const float inv2N = 1.0f / (float)twoN;      // power of two: exact
+    float L = 0.0f, R = 0.0f;
+    for (uint32_t i = beg; i < end; i++) {
+        const uint64_t r = __ldg(rec + i);
+        int a[3], b[3];
+        face_point_2n(rec_face_in(r), rec_u_in(r), rec_v_in(r), twoN, a);
+        face_point_2n(rec_face_out(r), rec_u_out(r), rec_v_out(r), twoN, b);
+        const int I = (b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) +
+                      (b[2] - a[2]) * (b[2] - a[2]);
+        const float l = __fmul_rn(__fsqrt_rn((float)I), inv2N);
+        L = __fadd_rn(L, l);
+        R = __fmaf_rn(l, sigma[rec_attr(r)], R);
+    }
+    cnt[v] = end - beg;
+    len[v] = L;
+    dens[v] = R;
+}
+
+__global__ void __launch_bounds__(256)
+lod_pool_kernel(int cx, int cy, int cz, const uint32_t *__restrict__ ccnt, const float *__restrict__ clen,
+                const float *__restrict__ cdens, int px, int py, int pz, uint32_t *pcnt, float *plen,
+                float *pdens) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t np = (int64_t)px * py * pz;
+    if (p >= np) return;
+    const int x = (int)(p % px), y = (int)((p / px) % py), z = (int)(p / ((int64_t)px * py));
+    uint32_t c = 0;
+    float L = 0.0f, R = 0.0f;
+    for (int dz = 0; dz < 2; dz++)
+        for (int dy = 0; dy < 2; dy++)
+            for (int dx = 0; dx < 2; dx++) {
+                const int X = 2 * x + dx, Y = 2 * y + dy, Z = 2 * z + dz;
+                if (X >= cx || Y >= cy || Z >= cz) continue;
+                const int64_t i = X + (int64_t)cx * (Y + (int64_t)cy * Z);
+                c += ccnt[i];
+                L = __fadd_rn(L, clen[i]);
+                R = __fadd_rn(R, cdens[i]);
+            }
+    pcnt[p] = c;
+    plen[p] = L;
+    pdens[p] = R;
+}
+
+}  // namespace
+
+extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int levels,
+                                    const float *sigma256, lvr_lod **out) {
+    if (!ctx) return LVR_EINVAL;
+    if (!ls || !out || !sigma256) return set_err(ctx, LVR_EINVAL, "lvr_build_lod: null argument");
+    *out = nullptr;
+    if (levels < 1 || levels > 4) return set_err(ctx, LVR_EINVAL, "levels must be in [1,4]");
+    for (int i = 0; i < 256; i++)
+        if (!(sigma256[i] >= 0.0f) || !(sigma256[i] < 1e30f))
+            return set_err(ctx, LVR_EINVAL, "sigma must be finite and >= 0");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    lvr_lod *L = new lvr_lod();
+    L->ctx = ctx;
+    L->levels = levels;
+    lvr_status st = LVR_OK;
+    for (int l = 0; l < levels && st == LVR_OK; l++) {
+        for (int a = 0; a < 3; a++) L->dims[l][a] = l == 0 ? ls->res[a] : (L->dims[l - 1][a] + 1) / 2;
+        const size_t n = (size_t)L->dims[l][0] * L->dims[l][1] * L->dims[l][2];
+        if ((st = dev_alloc(ctx, (void **)&L->cnt[l], n * 4)) != LVR_OK) break;
+        if ((st = dev_alloc(ctx, (void **)&L->len[l], n * 4)) != LVR_OK) break;
+        st = dev_alloc(ctx, (void **)&L->dens[l], n * 4);
+    }
+    if (st == LVR_OK) st = ensure_stage_in(ctx, 1024);
+    if (st != LVR_OK) {
+        lvr_free_lod(L);
+        return st;
+    }
+    float *dsig = (float *)ctx->stage_in;
+    cudaError_t e = cudaMemcpyAsync(dsig, sigma256, 1024, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        lod_level0_kernel<<<grid1d(ls->nvox, 256), 256, 0, s>>>(ls->offset, ls->rec, ls->nvox, ls->bins,
+                                                                 dsig, L->cnt[0], L->len[0], L->dens[0]);
+        for (int l = 1; l < levels; l++) {
+            const int32_t *c = L->dims[l - 1], *p = L->dims[l];
+            const int64_t np = (int64_t)p[0] * p[1] * p[2];
+            lod_pool_kernel<<<grid1d(np, 256), 256, 0, s>>>(c[0], c[1], c[2], L->cnt[l - 1], L->len[l - 1],
+                                                             L->dens[l - 1], p[0], p[1], p[2], L->cnt[l],
+                                                             L->len[l], L->dens[l]);
+        }
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        lvr_free_lod(L);
+        return cuda_err(ctx, e, "lvr_build_lod");
+    }
+    *out = L;
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_lod_info_get(const lvr_lod *lod, lvr_lod_info *info) {
+    if (!lod || !info) return LVR_EINVAL;
+    info->levels = lod->levels;
+    for (int l = 0; l < 4; l++)
+        for (int a = 0; a < 3; a++) info->dims[l][a] = l < lod->levels ? lod->dims[l][a] : 0;
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_export_lod(lvr_ctx *ctx, const lvr_lod *lod, int level, uint32_t *cnt,
+                                     float *len, float *dens) {
+    if (!ctx) return LVR_EINVAL;
+    if (!lod || level < 0 || level >= lod->levels) return set_err(ctx, LVR_EINVAL, "bad LoD level");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t n = (size_t)lod->dims[level][0] * lod->dims[level][1] * lod->dims[level][2];
+    lvr_status st = copy_out(ctx, cnt, lod->cnt[level], n * 4);
+    if (st == LVR_OK) st = copy_out(ctx, len, lod->len[level], n * 4);
+    if (st == LVR_OK) st = copy_out(ctx, dens, lod->dens[level], n * 4);
+    return st;
+}
+
+extern "C" void lvr_free_lod(lvr_lod *lod) {
+    if (!lod) return;
+    cudaSetDevice(lod->ctx->device);
+    for (int l = 0; l < 4; l++) {
+        dev_free(lod->ctx, lod->cnt[l]);
+        dev_free(lod->ctx, lod->len[l]);
+        dev_free(lod->ctx, lod->dens[l]);
+    }
+    delete lod;
+}

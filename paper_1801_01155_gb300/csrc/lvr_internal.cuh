@@ -1,0 +1,110 @@
+// Internal types and helpers of the lvr CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lvr.h"
+
+// ------------------------------------------------------------------ status words
+// Bits a kernel may raise in the context's device status word.
+enum : uint32_t {
+    ST_BAD_VERTEX = 1u << 0,    // vertex not finite or outside +-2^14 voxels
+    ST_BAD_ATTR = 1u << 1,      // attribute not finite
+    ST_BAD_OFFSETS = 1u << 2,   // curve offsets not monotone / out of range
+    ST_OVERFLOW = 1u << 3,      // more than 2^32 - 1 segments
+    ST_INTERNAL = 1u << 4,      // internal consistency check failed
+};
+
+// ------------------------------------------------------------------ handles
+struct lvr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    uint32_t *d_status = nullptr;          // device status word
+    unsigned long long *d_u64 = nullptr;   // small device counters [8]
+    void *h_pinned = nullptr;              // pinned readback area (256 B)
+    // grow-only device scratch, reused across calls
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // grow-only device staging for host inputs / outputs
+    void *stage_in = nullptr;
+    size_t stage_in_bytes = 0;
+    void *stage_out = nullptr;
+    size_t stage_out_bytes = 0;
+};
+
+struct lvr_lineset {
+    lvr_ctx *ctx = nullptr;
+    int32_t res[3] = {0, 0, 0};
+    int32_t bins = 0;
+    float origin[3] = {0, 0, 0};
+    float scale = 0;
+    int64_t nvox = 0;
+    int64_t nseg = 0;
+    uint32_t *offset = nullptr;   // [nvox + 1]
+    uint64_t *rec = nullptr;      // [nseg] packed segment records
+    uint64_t *key = nullptr;      // [nseg] (curve << 32) | ordinal
+};
+
+struct lvr_lod {
+    lvr_ctx *ctx = nullptr;
+    int levels = 0;
+    int32_t dims[4][3] = {};
+    uint32_t *cnt[4] = {};
+    float *len[4] = {};
+    float *dens[4] = {};
+};
+
+// ------------------------------------------------------------------ packed record
+// 64-bit segment record (Sec. 3.2 / Sec. 6.2 encoding, widened to one word):
+//   bits  0- 2 face_in   3- 9 u_in   10-16 v_in
+//   bits 17-19 face_out 20-26 u_out  27-33 v_out
+//   bits 34-41 attribute byte, bit 42 continues-previous, bits 43-47 local id
+//   (curve index mod 32, the paper's 5-bit local line id); 48-63 zero.
+__host__ __device__ inline uint64_t rec_pack(uint32_t fi, uint32_t ui, uint32_t vi, uint32_t fo,
+                                             uint32_t uo, uint32_t vo, uint32_t attr,
+                                             uint32_t cont, uint32_t lid) {
+    return (uint64_t)fi | ((uint64_t)ui << 3) | ((uint64_t)vi << 10) | ((uint64_t)fo << 17) |
+           ((uint64_t)uo << 20) | ((uint64_t)vo << 27) | ((uint64_t)attr << 34) |
+           ((uint64_t)cont << 42) | ((uint64_t)(lid & 31u) << 43);
+}
+__host__ __device__ inline uint32_t rec_face_in(uint64_t r) { return (uint32_t)(r & 7u); }
+__host__ __device__ inline uint32_t rec_u_in(uint64_t r) { return (uint32_t)((r >> 3) & 127u); }
+__host__ __device__ inline uint32_t rec_v_in(uint64_t r) { return (uint32_t)((r >> 10) & 127u); }
+__host__ __device__ inline uint32_t rec_face_out(uint64_t r) { return (uint32_t)((r >> 17) & 7u); }
+__host__ __device__ inline uint32_t rec_u_out(uint64_t r) { return (uint32_t)((r >> 20) & 127u); }
+__host__ __device__ inline uint32_t rec_v_out(uint64_t r) { return (uint32_t)((r >> 27) & 127u); }
+__host__ __device__ inline uint32_t rec_attr(uint64_t r) { return (uint32_t)((r >> 34) & 255u); }
+__host__ __device__ inline uint32_t rec_cont(uint64_t r) { return (uint32_t)((r >> 42) & 1u); }
+
+// ------------------------------------------------------------------ host helpers
+lvr_status set_err(lvr_ctx *ctx, lvr_status st, const char *fmt, ...);
+lvr_status cuda_err(lvr_ctx *ctx, cudaError_t e, const char *what);
+#define LVR_CUDA(ctx, call)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call); \
+    } while (0)
+
+bool is_device_ptr(const void *p);
+// Device copy of a host-or-device input (host data staged into ctx buffers).
+lvr_status stage_input(lvr_ctx *ctx, const void *p, size_t bytes, size_t slot_offset,
+                       const void **dev);
+lvr_status ensure_scratch(lvr_ctx *ctx, size_t bytes);
+lvr_status ensure_stage_in(lvr_ctx *ctx, size_t bytes);
+lvr_status ensure_stage_out(lvr_ctx *ctx, size_t bytes);
+lvr_status dev_alloc(lvr_ctx *ctx, void **p, size_t bytes);
+void dev_free(lvr_ctx *ctx, void *p);
+// Copy `bytes` from device `src` into host-or-device `dst` (sync if host).
+lvr_status copy_out(lvr_ctx *ctx, void *dst, const void *src, size_t bytes);
+
+inline unsigned grid1d(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 0x7fffffff) g = 0x7fffffff;
+    return (unsigned)g;
+}

@@ -1,0 +1,301 @@
+"""ctypes binding of liblvr.so (C ABI in include/lvr.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. The functions carry the C names (``lvr_voxelize``,
+``lvr_build_lod``, ``lvr_render``, ...). Array arguments may be torch
+tensors (CUDA or CPU) or numpy arrays; the library stages host memory
+itself. Handles are wrapped so that they are freed with their Python
+object. If the library has not been built this module raises on import:
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblvr.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"`")
+
+_L = C.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EDEVICE = range(7)
+_NAMES = {0: "LVR_OK", 1: "LVR_EINVAL", 2: "LVR_ENOMEM", 3: "LVR_ECUDA", 4: "LVR_EOVERFLOW",
+          5: "LVR_ETIMEOUT", 6: "LVR_EDEVICE"}
+
+
+class LVRError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("res", C.c_int32 * 3), ("bins", C.c_int32), ("fit", C.c_int32),
+                ("origin", C.c_float * 3), ("scale", C.c_float),
+                ("attr_min", C.c_float), ("attr_max", C.c_float)]
+
+
+class LineSetInfo(C.Structure):
+    _fields_ = [("res", C.c_int32 * 3), ("bins", C.c_int32), ("origin", C.c_float * 3),
+                ("scale", C.c_float), ("n_voxels", C.c_int64), ("n_segments", C.c_int64),
+                ("bytes", C.c_int64)]
+
+
+class LodInfo(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("dims", (C.c_int32 * 3) * 4)]
+
+
+class View(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("at", C.c_float * 3), ("up", C.c_float * 3),
+                ("fovy_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("crop", C.c_int32 * 4), ("light_dir", C.c_float * 3)]
+
+
+class RenderDesc(C.Structure):
+    _fields_ = [("radius", C.c_float), ("tf_rgba", C.c_float * 1024), ("opaque", C.c_int32),
+                ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao_mode", C.c_int32),
+                ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
+                ("kd", C.c_float), ("bg", C.c_float * 3), ("tile_w", C.c_int32),
+                ("tile_h", C.c_int32)]
+
+
+_vp, _i64, _i32 = C.c_void_p, C.c_int64, C.c_int32
+_SIGS = {
+    "lvr_version": ([], C.c_int),
+    "lvr_create": ([C.c_int, _vp, C.POINTER(_vp)], C.c_int),
+    "lvr_destroy": ([_vp], None),
+    "lvr_last_error": ([_vp], C.c_char_p),
+    "lvr_sync": ([_vp], C.c_int),
+    "lvr_voxelize": ([_vp, _vp, _vp, _vp, _i64, _i64, C.POINTER(GridDesc), C.POINTER(_vp)], C.c_int),
+    "lvr_lineset_info_get": ([_vp, C.POINTER(LineSetInfo)], C.c_int),
+    "lvr_export_lineset": ([_vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "lvr_free_lineset": ([_vp], None),
+    "lvr_build_lod": ([_vp, _vp, C.c_int, _vp, C.POINTER(_vp)], C.c_int),
+    "lvr_lod_info_get": ([_vp, C.POINTER(LodInfo)], C.c_int),
+    "lvr_export_lod": ([_vp, _vp, C.c_int, _vp, _vp, _vp], C.c_int),
+    "lvr_free_lod": ([_vp], None),
+    "lvr_render": ([_vp, _vp, _vp, C.POINTER(View), C.POINTER(RenderDesc), _vp, _vp, _vp], C.c_int),
+}
+for _n, (_a, _r) in _SIGS.items():
+    _f = getattr(_L, _n)
+    _f.argtypes = _a
+    _f.restype = _r
+
+ABI_SYMBOLS = tuple(_SIGS)
+
+
+def _ptr(x):
+    """Raw address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("arrays passed to lvr must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to lvr must be contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _check(ctx, rc):
+    if rc != OK:
+        msg = _L.lvr_last_error(ctx).decode() if ctx else ""
+        raise LVRError(rc, msg)
+
+
+# ---------------------------------------------------------------- handles
+class Context:
+    """lvr_ctx on a CUDA device; ``stream`` is a torch.cuda.Stream or raw handle."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = _vp()
+        raw = None
+        if stream is not None:
+            raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = _L.lvr_create(int(device), raw, C.byref(h))
+        if rc != OK:
+            raise LVRError(rc, "lvr_create failed")
+        self.handle = h
+        self.device = device
+        self.stream = stream
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _L.lvr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+    def sync(self):
+        _check(self.handle, _L.lvr_sync(self.handle))
+
+
+class LineSet:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.handle = ctx, h
+
+    def info(self) -> LineSetInfo:
+        inf = LineSetInfo()
+        _check(self.ctx.handle, _L.lvr_lineset_info_get(self.handle, C.byref(inf)))
+        return inf
+
+    def free(self):
+        if getattr(self, "handle", None):
+            _L.lvr_free_lineset(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.handle:
+            self.free()
+
+
+class Lod:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.handle = ctx, h
+
+    def info(self) -> LodInfo:
+        inf = LodInfo()
+        _check(self.ctx.handle, _L.lvr_lod_info_get(self.handle, C.byref(inf)))
+        return inf
+
+    def free(self):
+        if getattr(self, "handle", None):
+            _L.lvr_free_lod(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.handle:
+            self.free()
+
+
+# ---------------------------------------------------------------- C-named calls
+def lvr_version() -> int:
+    return _L.lvr_version()
+
+
+def lvr_create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def lvr_sync(ctx: Context):
+    ctx.sync()
+
+
+def grid_desc(res, bins, origin=(0.0, 0.0, 0.0), scale=1.0, attr_min=0.0, attr_max=0.0,
+              fit=False) -> GridDesc:
+    g = GridDesc()
+    r = (res, res, res) if np.isscalar(res) else tuple(res)
+    g.res[:] = [int(x) for x in r]
+    g.bins = int(bins)
+    g.fit = int(bool(fit))
+    g.origin[:] = [float(x) for x in origin]
+    g.scale = float(scale)
+    g.attr_min = float(attr_min)
+    g.attr_max = float(attr_max)
+    return g
+
+
+def lvr_voxelize(ctx: Context, xyz, attr, curve_offsets, grid: GridDesc) -> LineSet:
+    """xyz float32 (nv,3), attr float32 (nv,) or None, curve_offsets int64 (nc+1,)."""
+    nv = int(xyz.shape[0]) if xyz is not None else 0
+    nc = int(curve_offsets.shape[0]) - 1
+    h = _vp()
+    _check(ctx.handle, _L.lvr_voxelize(ctx.handle, _ptr(xyz), _ptr(attr), _ptr(curve_offsets), nc, nv,
+                                       C.byref(grid), C.byref(h)))
+    return LineSet(ctx, h)
+
+
+def lvr_export_lineset(ctx: Context, ls: LineSet, offset=None, fields=None, curve=None, ordinal=None):
+    _check(ctx.handle, _L.lvr_export_lineset(ctx.handle, ls.handle, _ptr(offset), _ptr(fields),
+                                             _ptr(curve), _ptr(ordinal)))
+
+
+def export_lineset_numpy(ctx: Context, ls: LineSet) -> dict:
+    inf = ls.info()
+    off = np.empty(inf.n_voxels + 1, np.uint32)
+    fields = np.empty((inf.n_segments, 8), np.uint8)
+    curve = np.empty(inf.n_segments, np.uint32)
+    ordn = np.empty(inf.n_segments, np.uint32)
+    lvr_export_lineset(ctx, ls, off, fields, curve, ordn)
+    return dict(offset=off, fields=fields, curve=curve, ordinal=ordn)
+
+
+def lvr_free_lineset(ls: LineSet):
+    ls.free()
+
+
+def lvr_build_lod(ctx: Context, ls: LineSet, levels: int, sigma256) -> Lod:
+    sigma256 = np.ascontiguousarray(np.asarray(sigma256, np.float32))
+    assert sigma256.shape == (256,)
+    h = _vp()
+    _check(ctx.handle, _L.lvr_build_lod(ctx.handle, ls.handle, int(levels), _ptr(sigma256), C.byref(h)))
+    return Lod(ctx, h)
+
+
+def lvr_export_lod(ctx: Context, lod: Lod, level: int, cnt=None, len_=None, dens=None):
+    _check(ctx.handle, _L.lvr_export_lod(ctx.handle, lod.handle, int(level), _ptr(cnt), _ptr(len_), _ptr(dens)))
+
+
+def export_lod_numpy(ctx: Context, lod: Lod, level: int) -> dict:
+    d = tuple(lod.info().dims[level])
+    n = d[0] * d[1] * d[2]
+    cnt = np.empty(n, np.uint32)
+    ln = np.empty(n, np.float32)
+    dn = np.empty(n, np.float32)
+    lvr_export_lod(ctx, lod, level, cnt, ln, dn)
+    return dict(cnt=cnt, len=ln, dens=dn, dims=d)
+
+
+def lvr_free_lod(lod: Lod):
+    lod.free()
+
+
+def make_view(eye, at, up, fovy_deg, width, height, light_dir, crop=None) -> View:
+    v = View()
+    v.eye[:] = [float(x) for x in eye]
+    v.at[:] = [float(x) for x in at]
+    v.up[:] = [float(x) for x in up]
+    v.fovy_deg = float(fovy_deg)
+    v.width = int(width)
+    v.height = int(height)
+    v.crop[:] = [int(x) for x in (crop or (0, 0, 0, 0))]
+    v.light_dir[:] = [float(x) for x in light_dir]
+    return v
+
+
+def make_desc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao_mode=0, ao_rays=16,
+              ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), tile=(0, 0)) -> RenderDesc:
+    d = RenderDesc()
+    d.radius = float(radius)
+    tf = np.ascontiguousarray(np.asarray(tf, np.float32)).reshape(-1)
+    assert tf.size == 1024
+    C.memmove(d.tf_rgba, tf.ctypes.data, 4096)
+    d.opaque = int(bool(opaque))
+    d.ert_alpha = float(ert_alpha)
+    d.shadows = int(bool(shadows))
+    d.ao_mode = int(ao_mode)
+    d.ao_rays = int(ao_rays)
+    d.ao_radius = float(ao_radius)
+    d.ka = float(ka)
+    d.kd = float(kd)
+    d.bg[:] = [float(x) for x in bg]
+    d.tile_w, d.tile_h = int(tile[0]), int(tile[1])
+    return d
+
+
+def lvr_render(ctx: Context, ls: LineSet, lod: Lod | None, view: View, desc: RenderDesc, rgba,
+               ao_model=None, counters=None):
+    """rgba: float32 (h, w, 4) for the crop (torch CUDA tensor or host array)."""
+    _check(ctx.handle, _L.lvr_render(ctx.handle, ls.handle, lod.handle if lod is not None else None,
+                                     C.byref(view), C.byref(desc),
+                                     ao_model.handle if ao_model is not None else None,
+                                     _ptr(rgba), _ptr(counters)))
+    return rgba

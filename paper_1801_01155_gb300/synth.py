@@ -131,19 +131,43 @@ def make_streamlines(n_lines: int, n_vertices: int, seed: int,
     seeds = field.rng.random((n_lines, 3))
     xyz = np.empty((n_lines, n_vertices, 3), np.float32)
     attr = np.empty((n_lines, n_vertices), np.float32)
-    for c0 in range(0, n_lines, chunk):
-        x = seeds[c0:c0 + chunk].astype(np.float64)
-        for i in range(n_vertices):
-            u = field.velocity(x)
-            xyz[c0:c0 + chunk, i] = x
-            attr[c0:c0 + chunk, i] = np.sqrt((u * u).sum(1))
-            if i + 1 == n_vertices:
-                break
-            k1 = u
-            k2 = field.velocity(x + 0.5 * dt * k1)
-            k3 = field.velocity(x + 0.5 * dt * k2)
-            k4 = field.velocity(x + dt * k3)
-            x = x + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    try:            # vectorised over lines with torch's CPU threads when available
+        import torch
+        K = torch.from_numpy(field.k.T.astype(np.float64))
+        AMP = torch.from_numpy(field.amp)
+        PHI = torch.from_numpy(field.phi)
+        two_pi = 2.0 * math.pi
+
+        def vel(x):
+            return torch.cos(torch.addmm(PHI, x, K, alpha=two_pi)) @ AMP
+
+        for c0 in range(0, n_lines, chunk):
+            x = torch.from_numpy(seeds[c0:c0 + chunk].copy())
+            for i in range(n_vertices):
+                u = vel(x)
+                xyz[c0:c0 + chunk, i] = x.numpy()
+                attr[c0:c0 + chunk, i] = torch.sqrt((u * u).sum(1)).numpy()
+                if i + 1 == n_vertices:
+                    break
+                k1 = u
+                k2 = vel(x + (0.5 * dt) * k1)
+                k3 = vel(x + (0.5 * dt) * k2)
+                k4 = vel(x + dt * k3)
+                x = x + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    except ImportError:
+        for c0 in range(0, n_lines, chunk):
+            x = seeds[c0:c0 + chunk].astype(np.float64)
+            for i in range(n_vertices):
+                u = field.velocity(x)
+                xyz[c0:c0 + chunk, i] = x
+                attr[c0:c0 + chunk, i] = np.sqrt((u * u).sum(1))
+                if i + 1 == n_vertices:
+                    break
+                k1 = u
+                k2 = field.velocity(x + 0.5 * dt * k1)
+                k3 = field.velocity(x + 0.5 * dt * k2)
+                k4 = field.velocity(x + dt * k3)
+                x = x + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
     offsets = np.arange(0, (n_lines + 1) * n_vertices, n_vertices, dtype=np.int64)
     ls = LineSet(xyz.reshape(-1, 3), attr.reshape(-1), offsets, seed)
     if path:

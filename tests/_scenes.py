@@ -1,0 +1,74 @@
+"""Shared test scenes: one seeded input feeds both the CUDA path and the oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_1801_01155_gb300 import synth
+
+TOL = 2e-3          # RGBA, absolute per channel
+TIE_CAP = 1e-3      # fraction of pixels allowed to be flagged as near-ties
+
+_CACHE = {}
+
+
+def streamlines(n, nv, seed):
+    key = (n, nv, seed)
+    if key not in _CACHE:
+        _CACHE[key] = synth.make_streamlines(n, nv, seed)
+    return _CACHE[key]
+
+
+def grid_args(ls, R, N, origin=(0.0, 0.0, 0.0), scale=None):
+    scale = float(R) if scale is None else float(scale)
+    return dict(res=R, bins=N, origin=origin, scale=scale,
+                attr_min=float(ls.attr.min()), attr_max=float(ls.attr.max()))
+
+
+def gpu_lineset(lvr, ctx, ls, dev, **g):
+    import torch
+    xyz = torch.from_numpy(ls.xyz).to(dev)
+    attr = torch.from_numpy(ls.attr).to(dev)
+    offs = torch.from_numpy(ls.offsets).to(dev)
+    return lvr.lvr_voxelize(ctx, xyz, attr, offs, lvr.grid_desc(**g))
+
+
+def oracle_lineset(O, ls, **g):
+    return O.VoxSet(ls.xyz, ls.attr, ls.offsets, O.make_grid(**g))
+
+
+def compare_lineset(lvr, ctx, gls, ovs):
+    e = lvr.export_lineset_numpy(ctx, gls)
+    o = ovs.export()
+    assert e["offset"].shape == o["offset"].shape
+    np.testing.assert_array_equal(e["offset"], o["offset"])
+    np.testing.assert_array_equal(e["fields"], o["fields"])
+    np.testing.assert_array_equal(e["curve"], o["curve"])
+    np.testing.assert_array_equal(e["ordinal"], o["ordinal"])
+    return len(o["curve"])
+
+
+def views(cam, crop=None):
+    """(library view, oracle view, pixel list) for a synth camera dict."""
+    from oracle import oracle as O
+    from paper_1801_01155_gb300 import lvr
+    W, H = cam["width"], cam["height"]
+    lv = lvr.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"], crop=crop)
+    ov = O.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"])
+    if crop:
+        pix = O.pixel_grid(*crop)
+    else:
+        pix = O.pixel_grid(0, 0, W, H)
+    return lv, ov, pix
+
+
+def check_image(got, ref, tie, tol=TOL, cap=TIE_CAP, what=""):
+    """Element-wise parity outside flagged pixels; flagged fraction capped."""
+    got = np.asarray(got, np.float64).reshape(-1, 4)
+    ok = tie == 0
+    frac = 1.0 - ok.mean()
+    err = np.abs(got - ref)
+    worst = err[ok].max() if ok.any() else 0.0
+    nbad = int((err[ok].max(1) > tol).sum())
+    assert nbad == 0, f"{what}: {nbad} non-tie pixels off by > {tol} (worst {worst:.3e})"
+    assert frac <= cap, f"{what}: {frac:.4%} tie pixels > {cap:.2%}"
+    return worst, frac

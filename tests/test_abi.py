@@ -1,0 +1,59 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares.
+
+No compute calls: this runs without a GPU.
+"""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(lvr_[a-z0-9_]+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1801_01155_gb300 import lvr
+    return lvr
+
+
+def test_headers_declare_the_boundary():
+    names = declared()
+    for n in ("lvr_voxelize", "lvr_build_lod", "lvr_render", "lvr_create", "lvr_destroy"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = lib.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = sorted(declared() - exported)
+    assert not missing, f"declared but not exported: {missing}"
+    for n in declared():
+        assert hasattr(lib._L, n)
+
+
+def test_binding_covers_the_header(lib):
+    assert set(lib.ABI_SYMBOLS) <= declared()
+    assert declared() <= set(lib.ABI_SYMBOLS), sorted(declared() - set(lib.ABI_SYMBOLS))
+    assert lib.lvr_version() == 1
+
+
+def test_structs_match_header_sizes(lib):
+    import ctypes as C
+    assert C.sizeof(lib.GridDesc) == 4 * 3 + 4 + 4 + 12 + 4 + 8
+    assert C.sizeof(lib.View) == 12 * 3 + 4 + 8 + 16 + 12
+    assert C.sizeof(lib.RenderDesc) == 4 + 4096 + 4 + 4 + 4 + 4 + 4 + 4 + 8 + 12 + 8

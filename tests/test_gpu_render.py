@@ -1,0 +1,255 @@
+"""CUDA ray-caster against the FP64 oracle (Secs. 4-5).
+
+RGBA must agree within 2e-3 per channel outside near-tie pixels, which the
+oracle flags (silhouettes, voxel-face ownership, depth order) and which are
+capped at 0.1 % of the pixels.
+"""
+import numpy as np
+import pytest
+
+from paper_1801_01155_gb300 import synth
+from tests import _scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from oracle import oracle as O
+    from paper_1801_01155_gb300 import lvr
+    dev = torch.device("cuda:0")
+    ctx = lvr.Context(0, torch.cuda.Stream(dev))
+    return lvr, O, ctx, dev
+
+
+class Scene:
+    def __init__(self, env, n, nv, seed, R, N=32, levels=3, alpha=(0.05, 0.3)):
+        lvr, O, ctx, dev = env
+        self.ls = S.streamlines(n, nv, seed)
+        g = S.grid_args(self.ls, R, N)
+        self.R = R
+        self.tf = synth.tf_ramp(*alpha)
+        self.gls = S.gpu_lineset(lvr, ctx, self.ls, dev, **g)
+        self.ovs = S.oracle_lineset(O, self.ls, **g)
+        sig = synth.sigma_lut(self.tf)
+        self.glod = lvr.lvr_build_lod(ctx, self.gls, levels, sig)
+        self.olod = O.Lod(self.ovs, levels, sig)
+
+    def render(self, env, cam, crop=None, radius=0.15, tile=(0, 0), counters=False, **kw):
+        import torch
+        lvr, O, ctx, dev = env
+        lv, ov, pix = S.views(cam, crop)
+        w, h = (crop[2], crop[3]) if crop else (cam["width"], cam["height"])
+        out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+        cnt = torch.zeros(4, dtype=torch.int64, device=dev) if counters else None
+        okw = {k: v for k, v in kw.items() if k != "ao_mode"}
+        if kw.get("ao_mode"):
+            okw["ao"] = True
+        desc = lvr.make_desc(radius, self.tf, tile=tile, **kw)
+        lvr.lvr_render(ctx, self.gls, self.glod, lv, desc, out, counters=cnt)
+        ctx.sync()
+        rd = O.make_rdesc(radius, self.tf, **okw)
+        ref, tie, ocnt = O.render(self.ovs, self.olod, ov, rd, pix)
+        got = out.cpu().numpy().reshape(-1, 4)
+        return got, ref, tie, (cnt.cpu().numpy() if counters else None), ocnt
+
+
+@pytest.fixture(scope="module")
+def c1(env):
+    return Scene(env, 500, 64, 0, 32, alpha=(1.0, 1.0))
+
+
+@pytest.fixture(scope="module")
+def c1t(env):
+    return Scene(env, 500, 64, 0, 32)
+
+
+@pytest.fixture(scope="module")
+def c2(env):
+    return Scene(env, 100_000, 200, 1, 256)
+
+
+def test_c1_opaque_full_image(env, c1):
+    """Config 1: 500 x 64 streamlines, 32^3, r = 0.2, opaque, 128 x 128."""
+    cam = synth.orbit_view((32, 32, 32), 128, 128)
+    got, ref, tie, gc, oc = c1.render(env, cam, radius=0.2, opaque=True, counters=True)
+    S.check_image(got, ref, tie, what="c1 opaque")
+    assert (ref[:, 3] > 0).mean() > 0.3
+    # the same voxels and records are read (float32 may pass a voxel edge on
+    # the other side, so allow a few extra or fewer)
+    np.testing.assert_allclose(gc, oc.astype(np.float64), rtol=2e-3)
+
+
+def test_c3_illumination_small(env, c1t):
+    """Config 3 at reduced size: c1 set + 3-level LoD, transparent, soft
+    shadows and 16 traced AO rays per hit."""
+    cam = synth.orbit_view((32, 32, 32), 192, 108)
+    got, ref, tie, gc, oc = c1t.render(env, cam, radius=0.2, ert_alpha=0.99, shadows=True, ao_mode=1,
+                                       counters=True)
+    S.check_image(got, ref, tie, what="c3 small")
+    # traversal counters match the oracle's within the tie pixels' share
+    np.testing.assert_allclose(gc, oc.astype(np.float64), rtol=2e-3)
+
+
+def test_c3_full_frame_sampled(env, c1t):
+    """Config 3 at 1920 x 1080, launched as the benchmark launches it; the
+    oracle checks a sample of 3000 pixels."""
+    import torch
+    lvr, O, ctx, dev = env
+    cam = synth.orbit_view((32, 32, 32), 1920, 1080)
+    lv, ov, _ = S.views(cam)
+    out = torch.empty((1080, 1920, 4), dtype=torch.float32, device=dev)
+    lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, lvr.make_desc(0.2, c1t.tf, ert_alpha=0.99, shadows=True, ao_mode=1), out)
+    ctx.sync()
+    rng = np.random.default_rng(0)
+    pix = np.stack([rng.integers(0, 1920, 3000), rng.integers(0, 1080, 3000)], 1).astype(np.int32)
+    ref, tie, _ = O.render(c1t.ovs, c1t.olod, ov, O.make_rdesc(0.2, c1t.tf, ert_alpha=0.99, shadows=True, ao=True), pix)
+    got = out.cpu().numpy()[pix[:, 1], pix[:, 0]]
+    S.check_image(got, ref, tie, cap=3e-3, what="c3 sampled")
+
+
+def test_c2_crop_transparent(env, c2):
+    """Config 2: 100k x 200 streamlines, 256^3, r = 0.15, alpha 0.05-0.3,
+    termination at 0.99, 1920 x 1080 view; the central 256 x 256 crop."""
+    cam = synth.orbit_view((256, 256, 256), 1920, 1080)
+    got, ref, tie, gc, oc = c2.render(env, cam, crop=(832, 412, 256, 256), ert_alpha=0.99, counters=True)
+    S.check_image(got, ref, tie, what="c2 crop")
+    assert (ref[:, 3] > 0.9).mean() > 0.5
+    np.testing.assert_allclose(gc, oc.astype(np.float64), rtol=2e-3)
+
+
+def test_c2_crop_shadows_ao(env, c2):
+    """The benchmark workload (config 2 set, transparent, soft shadows, 16 AO
+    rays) on a 128 x 128 crop."""
+    cam = synth.orbit_view((256, 256, 256), 1920, 1080)
+    got, ref, tie, gc, oc = c2.render(env, cam, crop=(896, 476, 128, 128), ert_alpha=0.99, shadows=True,
+                                      ao_mode=1, counters=True)
+    S.check_image(got, ref, tie, what="c2 crop AO")
+    np.testing.assert_allclose(gc, oc.astype(np.float64), rtol=2e-3)
+
+
+def test_c2_full_frame_sampled(env, c2):
+    """Full 1080p frame of the benchmark workload in the benchmark's launch
+    configuration; 2000 sampled pixels checked by the oracle."""
+    import torch
+    lvr, O, ctx, dev = env
+    cam = synth.orbit_view((256, 256, 256), 1920, 1080)
+    lv, ov, _ = S.views(cam)
+    out = torch.empty((1080, 1920, 4), dtype=torch.float32, device=dev)
+    desc = lvr.make_desc(0.15, c2.tf, ert_alpha=0.99, shadows=True, ao_mode=1)
+    lvr.lvr_render(ctx, c2.gls, c2.glod, lv, desc, out)
+    ctx.sync()
+    rng = np.random.default_rng(1)
+    pix = np.stack([rng.integers(0, 1920, 2000), rng.integers(0, 1080, 2000)], 1).astype(np.int32)
+    ref, tie, _ = O.render(c2.ovs, c2.olod, ov, O.make_rdesc(0.15, c2.tf, ert_alpha=0.99, shadows=True, ao=True), pix)
+    got = out.cpu().numpy()[pix[:, 1], pix[:, 0]]
+    S.check_image(got, ref, tie, cap=3e-3, what="c2 sampled")
+
+
+def test_tile_shapes_bit_identical(env, c1t):
+    import torch
+    lvr, O, ctx, dev = env
+    cam = synth.orbit_view((32, 32, 32), 100, 70)
+    lv, _, _ = S.views(cam)
+    imgs = []
+    for tile in ((8, 4), (4, 8), (16, 2), (32, 1)):
+        out = torch.empty((70, 100, 4), dtype=torch.float32, device=dev)
+        lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, lvr.make_desc(0.2, c1t.tf, shadows=True, ao_mode=1, tile=tile), out)
+        ctx.sync()
+        imgs.append(out.cpu().numpy())
+    for im in imgs[1:]:
+        np.testing.assert_array_equal(im, imgs[0])
+
+
+def test_host_output_and_crops_agree(env, c1t):
+    """Host output buffers, and crops (including ragged ones at the image
+    edge), reproduce the same pixels as a full device render."""
+    import torch
+    lvr, O, ctx, dev = env
+    cam = synth.orbit_view((32, 32, 32), 77, 53)
+    lv, _, _ = S.views(cam)
+    desc = lvr.make_desc(0.2, c1t.tf, shadows=True, ao_mode=1)
+    full = torch.empty((53, 77, 4), dtype=torch.float32, device=dev)
+    lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, desc, full)
+    ctx.sync()
+    host = np.empty((53, 77, 4), np.float32)
+    lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, desc, host)
+    np.testing.assert_array_equal(host, full.cpu().numpy())
+    for crop in ((0, 0, 13, 7), (60, 40, 17, 13), (5, 50, 72, 3)):
+        lvc, _, _ = S.views(cam, crop)
+        part = np.empty((crop[3], crop[2], 4), np.float32)
+        lvr.lvr_render(ctx, c1t.gls, c1t.glod, lvc, desc, part)
+        np.testing.assert_array_equal(part, full.cpu().numpy()[crop[1]:crop[1] + crop[3], crop[0]:crop[0] + crop[2]])
+
+
+def test_edge_cases(env, c1t):
+    """Camera inside the grid, rays that miss the grid, an empty line set."""
+    import torch
+    lvr, O, ctx, dev = env
+    inside = dict(eye=np.array([16.3, 15.2, 17.1], np.float32), at=np.array([30.0, 2.0, 5.0], np.float32),
+                  up=np.array([0, 1, 0], np.float32), fovy_deg=70.0, width=64, height=48,
+                  light_dir=np.array([0.2, -1, 0.1], np.float32))
+    got, ref, tie, _, _ = c1t.render(env, inside, radius=0.2, ert_alpha=0.99, shadows=True, ao_mode=1)
+    S.check_image(got, ref, tie, cap=5e-3, what="camera inside")
+    away = dict(inside, eye=np.array([100.0, 100.0, 100.0], np.float32), at=np.array([200.0, 100, 100], np.float32))
+    got, ref, tie, _, _ = c1t.render(env, away, radius=0.2)
+    np.testing.assert_array_equal(got, np.tile([1, 1, 1, 0], (64 * 48, 1)).astype(np.float32))
+    empty = lvr.lvr_voxelize(ctx, np.zeros((0, 3), np.float32), None, np.zeros(1, np.int64),
+                             lvr.grid_desc(16, 8, scale=16.0))
+    cam = synth.orbit_view((16, 16, 16), 32, 32)
+    lv, _, _ = S.views(cam)
+    out = np.empty((32, 32, 4), np.float32)
+    lvr.lvr_render(ctx, empty, None, lv, lvr.make_desc(0.2, c1t.tf, bg=(0.2, 0.3, 0.4)), out)
+    np.testing.assert_array_equal(out.reshape(-1, 4), np.tile([0.2, 0.3, 0.4, 0], (1024, 1)).astype(np.float32))
+
+
+def test_many_hits_in_one_voxel(env):
+    """More hits per voxel than the shared-memory list holds: the overflow path
+    must keep depth order. 60 parallel lines through a 3-voxel row, seen
+    along the lines with wide tubes and no early termination."""
+    import torch
+    lvr, O, ctx, dev = env
+    rng = np.random.default_rng(9)
+    n = 60
+    xyz = np.zeros((n, 2, 3), np.float32)
+    xyz[:, 0, 0], xyz[:, 1, 0] = 0.2, 2.8
+    xyz[:, :, 1] = (0.1 + 0.8 * rng.random(n))[:, None]
+    xyz[:, :, 2] = (0.1 + 0.8 * rng.random(n))[:, None]
+    attr = np.repeat(rng.random(n).astype(np.float32), 2)
+    offs = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+    g = dict(res=(3, 1, 1), bins=64, scale=1.0, attr_min=0.0, attr_max=1.0)
+    gl = lvr.lvr_voxelize(ctx, xyz.reshape(-1, 3), attr, offs, lvr.grid_desc(**g))
+    ov = O.VoxSet(xyz.reshape(-1, 3), attr, offs, O.make_grid(**g))
+    tf = synth.tf_ramp(0.02, 0.05)
+    cam = dict(eye=np.array([1.5, 0.5, 6.0], np.float32), at=np.array([1.5, 0.5, 0.5], np.float32),
+               up=np.array([0, 1, 0], np.float32), fovy_deg=12.0, width=48, height=32,
+               light_dir=np.array([0.3, -1, -0.2], np.float32))
+    lv, ovw, pix = S.views(cam)
+    out = np.empty((32, 48, 4), np.float32)
+    lvr.lvr_render(ctx, gl, None, lv, lvr.make_desc(0.3, tf, ert_alpha=2.0), out)
+    ref, tie, cnt = O.render(ov, None, ovw, O.make_rdesc(0.3, tf, ert_alpha=2.0), pix)
+    assert cnt[3] / len(pix) > 10
+    S.check_image(out, ref, tie, cap=2e-2, what="overflow path")
+
+
+def test_invalid_render_arguments(env, c1t):
+    lvr, O, ctx, dev = env
+    cam = synth.orbit_view((32, 32, 32), 16, 16)
+    lv, _, _ = S.views(cam)
+    out = np.empty((16, 16, 4), np.float32)
+    bad = [
+        (lvr.make_desc(0.0, c1t.tf), c1t.glod, lv),
+        (lvr.make_desc(0.2, c1t.tf, shadows=True), None, lv),
+        (lvr.make_desc(0.2, c1t.tf, ao_mode=1, ao_rays=0), c1t.glod, lv),
+        (lvr.make_desc(0.2, c1t.tf, ao_mode=1, ao_rays=33), c1t.glod, lv),
+        (lvr.make_desc(0.2, c1t.tf, tile=(5, 5)), c1t.glod, lv),
+        (lvr.make_desc(0.2, c1t.tf), c1t.glod, S.views(cam, (10, 10, 8, 8))[0]),
+    ]
+    for desc, lod, view in bad:
+        with pytest.raises(lvr.LVRError) as ei:
+            lvr.lvr_render(ctx, c1t.gls, lod, view, desc, out)
+        assert ei.value.code == lvr.EINVAL
