@@ -144,41 +144,47 @@ static int same_geometry(const orc_seg *x, const orc_seg *y) {
            x->v_out == y->v_out;
 }
 
-/* Distance from the line o + t d (|d| = 1) to the segment [a, b]; *tc = line
- * parameter of the closest approach. */
+/* Distance from the line o + t d to the segment [a, b]; *tc = line parameter
+ * of the closest approach. The direction need not be unit: primary rays
+ * carry a float32 direction whose length differs from 1 by ~1e-7. */
 static double line_segment_distance(const double *o, const double *d, const double *a,
                                     const double *b, double *tc) {
     double ba[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
     double ao[3] = {a[0] - o[0], a[1] - o[1], a[2] - o[2]};
-    double L2 = dot3(ba, ba), k = dot3(d, ba);
+    double L2 = dot3(ba, ba), dd = dot3(d, d), k = dot3(d, ba);
     double h = 0.0;
     if (L2 > 0.0) {
-        double det = L2 - k * k;                 /* |d|^2 L2 - (d.ba)^2 */
-        if (det > 1e-14 * L2) {
+        double det = dd * L2 - k * k;
+        if (det > 1e-14 * dd * L2) {
             /* minimise |o + t d - a - h ba|^2 over t, h */
             double e = dot3(d, ao), f = dot3(ba, ao);
-            h = (k * e - f) / det;
+            h = (k * e - dd * f) / det;
         }
         if (h < 0.0) h = 0.0;
         if (h > 1.0) h = 1.0;
     }
     double c[3] = {a[0] + h * ba[0], a[1] + h * ba[1], a[2] + h * ba[2]};
     double co[3] = {c[0] - o[0], c[1] - o[1], c[2] - o[2]};
-    double t = dot3(co, d);
+    double t = dot3(co, d) / dd;
     double p[3] = {o[0] + t * d[0] - c[0], o[1] + t * d[1] - c[1], o[2] + t * d[2] - c[2]};
     *tc = t;
     return sqrt(dot3(p, p));
 }
 
-/* Smaller root of |o + t d - c|^2 = r^2 (|d| = 1); returns 0 if none. */
+/* Smaller root of |o + t d - c|^2 = r^2, solved around the closest approach
+ * t_c = -(o - c).d / |d|^2: the squared distance of the centre from the line
+ * is taken from the perpendicular vector itself, which does not cancel even
+ * for an origin hundreds of radii away. *g = half chord length. */
 static int sphere_entry(const double *o, const double *d, const double *c, double r,
                         double *t, double *g) {
     double oc[3] = {o[0] - c[0], o[1] - c[1], o[2] - c[2]};
-    double b = dot3(oc, d), cc = dot3(oc, oc) - r * r;
-    double h = b * b - cc;                        /* r^2 - (distance centre-to-line)^2 */
+    double dd = dot3(d, d);
+    double tc = -dot3(oc, d) / dd;
+    double q[3] = {oc[0] + tc * d[0], oc[1] + tc * d[1], oc[2] + tc * d[2]};
+    double h = r * r - dot3(q, q);
     if (h < 0.0) return 0;
-    *t = -b - sqrt(h);
     *g = sqrt(h);
+    *t = tc - *g / sqrt(dd);
     return 1;
 }
 
@@ -217,18 +223,21 @@ static int capsule_entry_s(const double *o, const double *d, const double *a, co
         double dw = dot3(d, w), mw = dot3(oa, w);
         double dp[3] = {d[0] - dw * w[0], d[1] - dw * w[1], d[2] - dw * w[2]};
         double mp[3] = {oa[0] - mw * w[0], oa[1] - mw * w[1], oa[2] - mw * w[2]};
-        double A = dot3(dp, dp), B = dot3(dp, mp), C = dot3(mp, mp) - r * r;
+        /* |mp + t dp| = r, around the closest approach to the axis */
+        double A = dot3(dp, dp);
         if (A > 0.0) {
-            double disc = B * B - A * C;
-            if (disc >= 0.0) {
-                double t = (-B - sqrt(disc)) / A;
+            double tca = -dot3(dp, mp) / A;
+            double q[3] = {mp[0] + tca * dp[0], mp[1] + tca * dp[1], mp[2] + tca * dp[2]};
+            double h = r * r - dot3(q, q);
+            if (h >= 0.0) {
+                double s = sqrt(A), g = sqrt(h);
+                double t = tca - g / s;
                 double y = mw + t * dw;             /* axial coordinate of the entry point */
                 ymargin = fmin(fabs(y), fabs(y - L));
                 if (y >= 0.0 && y <= L) {
                     found = 1;
                     E->t = t;
                     E->part = 0;
-                    double s = sqrt(A), g = sqrt(disc) / s;
                     E->sens = 1.0 / fmax(s * g, 1e-12);
                 }
             }

@@ -280,6 +280,28 @@ def test_capsule_misses_and_caps(orc):
     assert not orc.capsule_entry([0.4, 0.0, 5.0], [0, 0, 1.0], a, b, r)[0]
 
 
+def test_capsule_far_origin_float32_direction(orc):
+    """Primary rays start hundreds of voxels away with a float32 direction
+    whose length is 1 only to ~1e-7. Closed form for a ray aimed 400 units
+    along d at a sphere (zero-length segment) offset 0.1 perpendicular to d:
+    |o + t d - c|^2 = (t - 400)^2 |d|^2 + 0.01, so t = 400 - sqrt(r^2 - 0.01) / |d|."""
+    d32 = np.array([0.6, 0.0, 0.8], np.float64) * (1 + 3e-7)
+    d = d32.astype(np.float32).astype(np.float64)          # |d| != 1
+    o = np.array([0.25, -0.5, -300.0])
+    c = o + 400.0 * d + np.array([0.0, 0.1, 0.0])          # (0,1,0) is exactly normal to d
+    r = 0.15
+    hit, t, dist = orc.capsule_entry(o, d, c, c, r)
+    nd = math.sqrt(d[0] ** 2 + d[2] ** 2)
+    assert hit and t == pytest.approx(400.0 - math.sqrt(r * r - 0.01) / nd, abs=1e-9)
+    assert dist == pytest.approx(0.1, abs=1e-9)
+    # the same through the body of a long tube along y (perpendicular to d)
+    hit, t, dist = orc.capsule_entry(o, d, c - [0, 2.0, 0], c + [0, 2.0, 0], r)
+    assert hit and t == pytest.approx(400.0 - r / nd, abs=1e-9)
+    # and a near miss by 1e-6 is a miss
+    cm = o + 400.0 * d + np.array([0.0, r + 1e-6, 0.0])
+    assert not orc.capsule_entry(o, d, cm, cm, r)[0]
+
+
 # ------------------------------------------------------------ primary rays (reading R0)
 def test_primary_ray_geometry(orc):
     eye, at = np.array([10.0, 20.0, 30.0]), np.array([1.0, 2.0, 3.0])
