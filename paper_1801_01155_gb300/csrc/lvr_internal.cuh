@@ -35,6 +35,7 @@ struct lvr_ctx {
     size_t stage_in_bytes = 0;
     void *stage_out = nullptr;
     size_t stage_out_bytes = 0;
+    int render_blocks = 0;                 // persistent render grid (SMs x resident blocks)
 };
 
 struct lvr_lineset {

@@ -4,18 +4,33 @@
 // termination, and density-LoD marches for soft shadows and ambient
 // occlusion.
 //
+// Execution. A persistent kernel: every warp pulls warp-sized pixel tiles
+// (8x4 by default) from a device counter. Per tile the warp alternates two
+// phases until all its rays are finished:
+//   A. traversal (one ray per lane): DDA, capsule tests, per-voxel sort and
+//      front-to-back weighting. The compositing weight of a hit depends only
+//      on the opacities in front of it, never on its lighting, so each hit's
+//      weight, position, normal and tube direction are final here; they go
+//      to the lane's shared-memory hit slots (KS per lane). A lane stops when
+//      its slots are full (it resumes inside the same voxel later) or when
+//      its ray is finished.
+//   B. lighting (whole warp): the warp's collected hits are dealt out to the
+//      32 lanes, which march the shadow ray and the AO rays of their hits in
+//      one flattened loop, one density sample per iteration, so the warp
+//      stays converged while marches of different lengths interleave. Each
+//      hit's lit contribution is written back to its slot, and the owning
+//      lane adds its slots in depth order.
+//
 // Precision. All device arithmetic is float32. The primary ray is a float32
 // quantity built by a fixed sequence of correctly rounded operations. The
-// ray's position is kept in voxel-local coordinates: the box entry point is
-// computed once in float-float (error-free product and sum), and from then
-// on the ray state is the voxel index plus a local position in [0,1]^3, so
-// every intersection is solved with operands of magnitude about 1 instead
-// of the camera distance. Tube-axis distances use cross products, which do
-// not cancel.
+// ray state is a voxel index plus a local position; for every non-empty
+// voxel the local origin is recomputed from the global ray in float-float
+// (error-free product and sum), so intersections are solved with operands of
+// magnitude ~1. Tube and sphere entries are solved around the closest
+// approach, which does not cancel.
 //
-// Ownership. A voxel keeps a hit iff its entry point lies inside the voxel:
-// in local coordinates, iff the entry parameter s satisfies
-// 0 <= s < s_exit. Ties between faces step in axis order x, y, z.
+// Ownership. A voxel keeps a hit iff its entry point lies inside the voxel
+// (in local coordinates, in [0,1)^3). DDA ties step in axis order x, y, z.
 #include <math.h>
 #include <string.h>
 
@@ -24,8 +39,9 @@
 namespace {
 
 constexpr int RT = 128;       // threads per block (4 warps)
-constexpr int HMAX = 8;       // hits per voxel staged in shared memory per ray
+constexpr int KS = 4;         // hit slots per lane per lighting round
 constexpr int MAX_AO = 32;
+constexpr unsigned FULL = 0xffffffffu;
 
 struct RenderParams {
     const uint32_t *offset;
@@ -39,16 +55,17 @@ struct RenderParams {
     float lod_lo, lod_hi[3];      // support of the density field (level-0 voxels)
     float F[3], R[3], U[3], th, tw, eye[3];
     int32_t W, H, x0, y0, cw, ch;
-    int32_t tile_w, tile_h;
+    int32_t tile_w, tile_h, tiles_x, ntiles;
     float Lt[3];                  // toward the light, unit
     int32_t opaque;
     float ert;
-    int32_t shadows, ao, ao_rays;
+    int32_t shadows, ao, ao_rays, nrays;
     float ao_radius, ka, kd, bg[3];
     float aod[MAX_AO][3];         // hemisphere directions in the (T, B, n) frame
     float tf[1024];
     float4 *out;
     unsigned long long *counters;
+    unsigned *tile_counter;
 };
 
 struct Vec { float x, y, z; };
@@ -61,6 +78,7 @@ __device__ __forceinline__ Vec cross(Vec a, Vec b) {
 __device__ __forceinline__ Vec axpy(float s, Vec d, Vec p) {
     return {fmaf(s, d.x, p.x), fmaf(s, d.y, p.y), fmaf(s, d.z, p.z)};
 }
+__device__ __forceinline__ Vec scale(Vec a, float s) { return {a.x * s, a.y * s, a.z * s}; }
 
 // Face point (Sec. 3.2): face id -> axis and side, bins -> sub-square centres.
 __device__ __forceinline__ Vec face_point(uint32_t face, uint32_t u, uint32_t v, float invN) {
@@ -70,9 +88,9 @@ __device__ __forceinline__ Vec face_point(uint32_t face, uint32_t u, uint32_t v,
     return {ax == 0 ? side : cu, ax == 1 ? side : (ax == 0 ? cu : cv), ax == 2 ? side : cv};
 }
 
-// First entry of ray p + s D (|D| = 1) into the sphere |x - c| = r; INF if
-// none. Closest-approach form: the squared distance of the centre from the
-// ray is taken from the perpendicular vector itself, which does not cancel.
+// First entry of ray p + s D into the sphere |x - c| = r; INF if none.
+// Closest-approach form: the squared distance of the centre from the ray is
+// taken from the perpendicular vector itself, which does not cancel.
 __device__ __forceinline__ float sphere_entry(Vec p, Vec D, Vec c, float r2) {
     const Vec oc = sub(p, c);
     const float sc = -dot(oc, D);
@@ -93,7 +111,7 @@ __device__ __forceinline__ float capsule_entry(Vec p, Vec D, Vec a, Vec b, float
     const float L2 = dot(ba, ba);
     if (L2 > 0.0f) {
         const float L = sqrtf(L2), iL = 1.0f / L;
-        const Vec w = mk(ba.x * iL, ba.y * iL, ba.z * iL);
+        const Vec w = scale(ba, iL);
         const Vec oa = sub(p, a);
         const float dw = dot(D, w), ow = dot(oa, w);
         const Vec Dp = axpy(-dw, w, D), Op = axpy(-ow, w, oa);
@@ -123,6 +141,18 @@ __device__ __forceinline__ float sample_level(const RenderParams &P, int l, Vec 
     const float fx = qx - fx0, fy = qy - fy0, fz = qz - fz0;
     const int dx = P.ldims[l][0], dy = P.ldims[l][1], dz = P.ldims[l][2];
     const float *__restrict__ d = P.dens[l];
+    if ((unsigned)ix < (unsigned)(dx - 1) && (unsigned)iy < (unsigned)(dy - 1) && (unsigned)iz < (unsigned)(dz - 1)) {
+        // all eight corners inside: one base index, three strides
+        const unsigned sy = (unsigned)dx, sz = (unsigned)dx * (unsigned)dy;
+        const float *c = d + ((unsigned)ix + sy * ((unsigned)iy + (unsigned)dy * (unsigned)iz));
+        const float v000 = __ldg(c), v100 = __ldg(c + 1), v010 = __ldg(c + sy), v110 = __ldg(c + sy + 1);
+        const float v001 = __ldg(c + sz), v101 = __ldg(c + sz + 1), v011 = __ldg(c + sz + sy),
+                    v111 = __ldg(c + sz + sy + 1);
+        const float x00 = fmaf(fx, v100 - v000, v000), x10 = fmaf(fx, v110 - v010, v010);
+        const float x01 = fmaf(fx, v101 - v001, v001), x11 = fmaf(fx, v111 - v011, v011);
+        const float y0 = fmaf(fy, x10 - x00, x00), y1 = fmaf(fy, x11 - x01, x01);
+        return fmaf(fz, y1 - y0, y0);
+    }
     float acc = 0.0f;
 #pragma unroll
     for (int c = 0; c < 8; c++) {
@@ -134,109 +164,6 @@ __device__ __forceinline__ float sample_level(const RenderParams &P, int l, Vec 
         }
     }
     return acc;
-}
-
-// Density march (Secs. 5.2, 5.3): samples at s = 1, 2, 4, ... with step 2^l
-// at level l = floor(log2 s) (capped); optical depth O += rho_l * 2^l with
-// rho_l = dens_l / 8^l; stops at O >= 1, beyond max_dist (if >= 0), or when
-// the sample leaves the support of the density field.
-__device__ float march(const RenderParams &P, Vec p, Vec d, float max_dist, unsigned &nsamp) {
-    float O = 0.0f;
-    int s = 1;
-    const int top = P.levels - 1;
-    for (;;) {
-        if (max_dist >= 0.0f && (float)s > max_dist) break;
-        const Vec x = axpy((float)s, d, p);
-        if (x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] ||
-            x.y > P.lod_hi[1] || x.z > P.lod_hi[2])
-            break;
-        int l = 31 - __clz(s);
-        l = l < top ? l : top;
-        const float w = __int_as_float((127 - 2 * l) << 23);   // 2^l / 8^l
-        O = fmaf(sample_level(P, l, x), w, O);
-        nsamp++;
-        if (O >= 1.0f) break;
-        s += 1 << l;
-    }
-    return O;
-}
-
-struct RayState {
-    float Cr, Cg, Cb, A;
-    bool done;
-    unsigned nvox, nrec, nsamp, nhit;
-};
-
-// Shade one hit at local parameter t of voxel (vx,vy,vz) and composite it.
-__device__ void shade_hit(const RenderParams &P, const float4 *s_tf, uint64_t r, float t, Vec p, Vec D,
-                          int vx, int vy, int vz, RayState &S) {
-    const Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
-    const Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
-    const Vec Pl = axpy(t, D, p);
-    const Vec ba = sub(b, a);
-    const float L2 = dot(ba, ba);
-    float h = 0.0f;
-    if (L2 > 0.0f) h = fminf(fmaxf(dot(sub(Pl, a), ba) / L2, 0.0f), 1.0f);
-    Vec n = sub(Pl, axpy(h, ba, a));
-    const float nl = rsqrtf(dot(n, n));
-    n = mk(n.x * nl, n.y * nl, n.z * nl);
-    const float4 c = s_tf[rec_attr(r)];
-    const float alpha = P.opaque ? 1.0f : c.w;
-    const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
-    const Vec Pg = mk((float)vx + Pl.x, (float)vy + Pl.y, (float)vz + Pl.z);
-    float V = 1.0f, AO = 1.0f;
-    if (P.shadows) V = 1.0f - fminf(1.0f, march(P, Pg, Lt, -1.0f, S.nsamp));
-    if (P.ao) {
-        Vec u = mk(0.0f, 0.0f, 0.0f);
-        if (L2 > 0.0f) {
-            const float il = 1.0f / sqrtf(L2);
-            u = mk(ba.x * il, ba.y * il, ba.z * il);
-        }
-        const float un = dot(u, n);
-        Vec T = mk(u.x - un * n.x, u.y - un * n.y, u.z - un * n.z);
-        const float m = sqrtf(dot(T, T));
-        if (m >= 1e-3f) {
-            T = mk(T.x / m, T.y / m, T.z / m);
-        } else {
-            const float ax = fabsf(n.x), ay = fabsf(n.y), az = fabsf(n.z);
-            int e = 0;
-            float best = ax;
-            if (ay < best) { e = 1; best = ay; }
-            if (az < best) { e = 2; }
-            const float ne = e == 0 ? n.x : (e == 1 ? n.y : n.z);
-            T = mk((e == 0 ? 1.0f : 0.0f) - ne * n.x, (e == 1 ? 1.0f : 0.0f) - ne * n.y,
-                   (e == 2 ? 1.0f : 0.0f) - ne * n.z);
-            const float tl = rsqrtf(dot(T, T));
-            T = mk(T.x * tl, T.y * tl, T.z * tl);
-        }
-        const Vec B = cross(n, T);
-        float occ = 0.0f;
-        for (int i = 0; i < P.ao_rays; i++) {
-            const float dx = P.aod[i][0], dy = P.aod[i][1], dz = P.aod[i][2];
-            const Vec d = mk(fmaf(T.x, dx, fmaf(B.x, dy, n.x * dz)), fmaf(T.y, dx, fmaf(B.y, dy, n.y * dz)),
-                             fmaf(T.z, dx, fmaf(B.z, dy, n.z * dz)));
-            occ += fminf(1.0f, march(P, Pg, d, P.ao_radius, S.nsamp));
-        }
-        AO = 1.0f - occ / (float)P.ao_rays;
-    }
-    const float k = fmaf(P.ka, AO, P.kd * V * fabsf(dot(n, Lt)));
-    S.nhit++;
-    if (P.opaque) {
-        S.Cr = c.x * k;
-        S.Cg = c.y * k;
-        S.Cb = c.z * k;
-        S.A = 1.0f;
-        S.done = true;
-        return;
-    }
-    // front-to-back blending (Sec. 5.1); the opacity update is rounded step by
-    // step so the termination test is reproducible: A <- A + (1 - A) * alpha
-    const float w = __fmul_rn(__fsub_rn(1.0f, S.A), alpha);
-    S.Cr = fmaf(w, c.x * k, S.Cr);
-    S.Cg = fmaf(w, c.y * k, S.Cg);
-    S.Cb = fmaf(w, c.z * k, S.Cb);
-    S.A = __fadd_rn(S.A, w);
-    if (S.A >= P.ert) S.done = true;
 }
 
 // A voxel owns a hit iff the entry point p + t D lies in its [0,1)^3 and in
@@ -253,166 +180,392 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__global__ void __launch_bounds__(RT)
-render_kernel(const __grid_constant__ RenderParams P) {
-    __shared__ float4 s_tf[256];
-    __shared__ float s_ht[HMAX][RT];
-    __shared__ uint32_t s_hk[HMAX][RT];
-    for (int i = threadIdx.x; i < 256; i += RT)
-        s_tf[i] = make_float4(P.tf[4 * i], P.tf[4 * i + 1], P.tf[4 * i + 2], P.tf[4 * i + 3]);
-    __syncthreads();
+__device__ __forceinline__ bool key_after(float t, uint32_t k, float lt, uint32_t lk) {
+    return t > lt || (t == lt && k > lk);
+}
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int px = blockIdx.x * (2 * P.tile_w) + (warp & 1) * P.tile_w + lane % P.tile_w;
-    const int py = blockIdx.y * (2 * P.tile_h) + (warp >> 1) * P.tile_h + lane / P.tile_w;
-    if (px >= P.cw || py >= P.ch) return;
-    const int i = P.x0 + px, j = P.y0 + py;
+// Shared memory of one block: transfer function, per-lane sorted hit staging
+// and per-lane hit slots (field-major, lane-minor: conflict-free).
+enum { F_PX, F_PY, F_PZ, F_NX, F_NY, F_NZ, F_UX, F_UY, F_UZ, F_CR, F_CG, F_CB, NF };
+struct Smem {
+    float4 tf[256];
+    float st[KS][RT];             // staged (t, k) of the current voxel, ascending
+    uint32_t sk[KS][RT];
+    float slot[NF][KS][RT];
+    uint8_t item[4][32 * KS];     // per warp: (owner lane, slot) of each collected hit
+};
 
-    // primary ray: float32 contract, each step correctly rounded
-    const float sx = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * i + 1), (float)P.W), 1.0f), P.tw);
-    const float sy = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * j + 1), (float)P.H), 1.0f), P.th);
-    float d[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) d[a] = __fsub_rn(__fadd_rn(P.F[a], __fmul_rn(sx, P.R[a])), __fmul_rn(sy, P.U[a]));
-    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
-    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
-    const Vec D = mk(__fmul_rn(d[0], inv), __fmul_rn(d[1], inv), __fmul_rn(d[2], inv));
-    const float Da[3] = {D.x, D.y, D.z};
+struct Ray {
+    Vec D;
+    float invD[3];
+    int v[3];
+    float pl[3];
+    float T;                      // ray parameter at the current voxel's entry
+    float A, Cr, Cg, Cb;
+    float rt;                     // resume key inside the current voxel
+    uint32_t rk;
+    bool resume;
+    bool done;
+};
 
-    RayState S = {0.0f, 0.0f, 0.0f, 0.0f, false, 0u, 0u, 0u, 0u};
-    // slab test: only the entry parameter is needed, approximately
-    float tnear = 0.0f, tfar = INFINITY;
-    bool miss = false;
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        if (Da[a] != 0.0f) {
-            const float ia = 1.0f / Da[a];
-            const float t1 = (0.0f - P.eye[a]) * ia, t2 = ((float)P.res[a] - P.eye[a]) * ia;
-            tnear = fmaxf(tnear, fminf(t1, t2));
-            tfar = fminf(tfar, fmaxf(t1, t2));
-        } else if (P.eye[a] < 0.0f || P.eye[a] > (float)P.res[a]) {
-            miss = true;
-        }
-    }
-    if (!miss && tnear < tfar) {
-        // entry point in float-float, split into voxel index + local position
-        int v[3];
-        float pl[3];
+// Phase A for one lane: traverse until KS hits are collected or the ray ends.
+__device__ int traverse(const RenderParams &P, Smem &sm, Ray &ray, int tid, unsigned &nvox, unsigned &nrec,
+                        unsigned &nhit) {
+    int used = 0;
+    const float Da[3] = {ray.D.x, ray.D.y, ray.D.z};
+    while (!ray.done && used < KS) {
+        float se = INFINITY;
+        int ax = 0;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const float ph = __fmul_rn(tnear, Da[a]);
-            const float pe = __fmaf_rn(tnear, Da[a], -ph);
-            float sh, se;
-            two_sum(P.eye[a], ph, sh, se);
-            const float lo = __fadd_rn(se, pe);
-            float fl = floorf(sh);
-            float f = __fadd_rn(__fsub_rn(sh, fl), lo);
-            if (f < 0.0f) { fl -= 1.0f; f += 1.0f; }
-            else if (f >= 1.0f) { fl += 1.0f; f -= 1.0f; }
-            int vi = (int)fl;
-            if (vi < 0) { f += (float)vi; vi = 0; }
-            if (vi > P.res[a] - 1) { f += (float)(vi - (P.res[a] - 1)); vi = P.res[a] - 1; }
-            v[a] = vi;
-            pl[a] = f;
+            const float e = Da[a] > 0.0f ? (1.0f - ray.pl[a]) * ray.invD[a]
+                                        : (Da[a] < 0.0f ? (0.0f - ray.pl[a]) * ray.invD[a] : INFINITY);
+            if (e < se) { se = e; ax = a; }
         }
-        const float invD[3] = {Da[0] != 0.0f ? 1.0f / Da[0] : INFINITY, Da[1] != 0.0f ? 1.0f / Da[1] : INFINITY,
-                               Da[2] != 0.0f ? 1.0f / Da[2] : INFINITY};
-        const float r2 = P.r2;
-        float T = tnear;              // ray parameter at the current voxel's entry
-        float(*ht)[RT] = s_ht;
-        uint32_t(*hk)[RT] = s_hk;
-        for (;;) {
-            // exit parameter of the current voxel, ties in axis order x, y, z
-            float se = INFINITY;
-            int ax = 0;
+        se = fmaxf(se, 0.0f);
+        const uint32_t vid = (uint32_t)ray.v[0] + (uint32_t)P.res[0] * ((uint32_t)ray.v[1] + (uint32_t)P.res[1] * (uint32_t)ray.v[2]);
+        const uint32_t beg = __ldg(P.offset + vid), end = __ldg(P.offset + vid + 1);
+        if (!ray.resume) {
+            nvox++;
+            nrec += end - beg;
+        }
+        if (end > beg) {
+            // accurate local origin: eye + T D - v in float-float, rounded once
+            float po[3];
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                float e = Da[a] > 0.0f ? (1.0f - pl[a]) * invD[a] : (Da[a] < 0.0f ? (0.0f - pl[a]) * invD[a] : INFINITY);
-                if (e < se) { se = e; ax = a; }
+                const float ph = __fmul_rn(ray.T, Da[a]);
+                const float pe = __fmaf_rn(ray.T, Da[a], -ph);
+                float sh, s2;
+                two_sum(P.eye[a], ph, sh, s2);
+                po[a] = __fadd_rn(__fsub_rn(sh, (float)ray.v[a]), __fadd_rn(s2, pe));
             }
-            se = fmaxf(se, 0.0f);
-            const uint32_t vid = (uint32_t)v[0] + (uint32_t)P.res[0] * ((uint32_t)v[1] + (uint32_t)P.res[1] * (uint32_t)v[2]);
-            const uint32_t beg = __ldg(P.offset + vid), end = __ldg(P.offset + vid + 1);
-            S.nvox++;
-            if (end > beg) {
-                S.nrec += end - beg;
-                // accurate local origin: eye + T D - v in float-float, rounded once
-                float po[3];
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    const float ph = __fmul_rn(T, Da[a]);
-                    const float pe = __fmaf_rn(T, Da[a], -ph);
-                    float sh, s2;
-                    two_sum(P.eye[a], ph, sh, s2);
-                    po[a] = __fadd_rn(__fsub_rn(sh, (float)v[a]), __fadd_rn(s2, pe));
-                }
-                const Vec p = mk(po[0], po[1], po[2]);
-                int nh = 0;
-                for (uint32_t k = beg; k < end; k++) {
-                    const uint64_t r = __ldg(P.rec + k);
-                    const Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
-                    const Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
-                    const float t = capsule_entry(p, D, a, b, r2);
-                    if (!owned(p, D, t, -T)) continue;
-                    // bounded insertion: keep the HMAX smallest (t, k), in order
-                    if (nh < HMAX || t < ht[HMAX - 1][tid]) {
-                        int q = nh < HMAX ? nh : HMAX - 1;
-                        while (q > 0 && t < ht[q - 1][tid]) {
-                            ht[q][tid] = ht[q - 1][tid];
-                            hk[q][tid] = hk[q - 1][tid];
-                            q--;
-                        }
-                        ht[q][tid] = t;
-                        hk[q][tid] = k;
+            const Vec p = mk(po[0], po[1], po[2]);
+            const int room = KS - used;
+            int nh = 0;
+            for (uint32_t k = beg; k < end; k++) {
+                const uint64_t r = __ldg(P.rec + k);
+                const Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
+                const Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
+                const float t = capsule_entry(p, ray.D, a, b, P.r2);
+                if (!owned(p, ray.D, t, -ray.T)) continue;
+                if (ray.resume && !key_after(t, k, ray.rt, ray.rk)) continue;
+                // bounded insertion: keep the `room` smallest (t, k), ascending
+                if (nh < room || t < sm.st[room - 1][tid]) {
+                    int q = nh < room ? nh : room - 1;
+                    while (q > 0 && t < sm.st[q - 1][tid]) {
+                        sm.st[q][tid] = sm.st[q - 1][tid];
+                        sm.sk[q][tid] = sm.sk[q - 1][tid];
+                        q--;
                     }
-                    nh++;
+                    sm.st[q][tid] = t;
+                    sm.sk[q][tid] = k;
                 }
-                const int nl = nh < HMAX ? nh : HMAX;
-                for (int q = 0; q < nl && !S.done; q++)
-                    shade_hit(P, s_tf, __ldg(P.rec + hk[q][tid]), ht[q][tid], p, D, v[0], v[1], v[2], S);
-                if (nh > HMAX && !S.done) {
-                    // more hits than staged: select the next (t, k) one at a time
-                    float lt = ht[HMAX - 1][tid];
-                    uint32_t lk = hk[HMAX - 1][tid];
-                    while (!S.done) {
-                        float bt = INFINITY;
-                        uint32_t bk = 0xffffffffu;
-                        for (uint32_t k = beg; k < end; k++) {
-                            const uint64_t r = __ldg(P.rec + k);
-                            const Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
-                            const Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
-                            const float t = capsule_entry(p, D, a, b, r2);
-                            if (!owned(p, D, t, -T)) continue;
-                            const bool after = t > lt || (t == lt && k > lk);
-                            const bool before = t < bt || (t == bt && k < bk);
-                            if (after && before) { bt = t; bk = k; }
-                        }
-                        if (bk == 0xffffffffu) break;
-                        shade_hit(P, s_tf, __ldg(P.rec + bk), bt, p, D, v[0], v[1], v[2], S);
-                        lt = bt;
-                        lk = bk;
+                nh++;
+            }
+            const int take = nh < room ? nh : room;
+            for (int q = 0; q < take; q++) {
+                const float t = sm.st[q][tid];
+                const uint32_t k = sm.sk[q][tid];
+                const uint64_t r = __ldg(P.rec + k);
+                const Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
+                const Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
+                const Vec Pl = axpy(t, ray.D, p);
+                const Vec ba = sub(b, a);
+                const float L2 = dot(ba, ba);
+                float h = 0.0f;
+                Vec u = mk(0.0f, 0.0f, 0.0f);
+                if (L2 > 0.0f) {
+                    h = fminf(fmaxf(dot(sub(Pl, a), ba) / L2, 0.0f), 1.0f);
+                    u = scale(ba, 1.0f / sqrtf(L2));
+                }
+                Vec n = sub(Pl, axpy(h, ba, a));
+                n = scale(n, rsqrtf(dot(n, n)));
+                const float4 c = sm.tf[rec_attr(r)];
+                // front-to-back weight (Sec. 5.1); the opacity update is rounded
+                // step by step so the termination test is reproducible:
+                // A <- A + (1 - A) * alpha
+                float w;
+                if (P.opaque) {
+                    w = 1.0f;
+                    ray.A = 1.0f;
+                    ray.done = true;
+                } else {
+                    w = __fmul_rn(__fsub_rn(1.0f, ray.A), c.w);
+                    ray.A = __fadd_rn(ray.A, w);
+                    if (ray.A >= P.ert) ray.done = true;
+                }
+                if (P.nrays == 0) {
+                    const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
+                    const float kk = fmaf(P.kd, fabsf(dot(n, Lt)), P.ka);
+                    ray.Cr = fmaf(w * c.x, kk, ray.Cr);
+                    ray.Cg = fmaf(w * c.y, kk, ray.Cg);
+                    ray.Cb = fmaf(w * c.z, kk, ray.Cb);
+                } else {
+                    sm.slot[F_PX][used][tid] = (float)ray.v[0] + Pl.x;
+                    sm.slot[F_PY][used][tid] = (float)ray.v[1] + Pl.y;
+                    sm.slot[F_PZ][used][tid] = (float)ray.v[2] + Pl.z;
+                    sm.slot[F_NX][used][tid] = n.x;
+                    sm.slot[F_NY][used][tid] = n.y;
+                    sm.slot[F_NZ][used][tid] = n.z;
+                    sm.slot[F_UX][used][tid] = u.x;
+                    sm.slot[F_UY][used][tid] = u.y;
+                    sm.slot[F_UZ][used][tid] = u.z;
+                    sm.slot[F_CR][used][tid] = w * c.x;
+                    sm.slot[F_CG][used][tid] = w * c.y;
+                    sm.slot[F_CB][used][tid] = w * c.z;
+                    used++;
+                }
+                ray.rt = t;
+                ray.rk = k;
+                nhit++;
+                if (ray.done) break;
+            }
+            if (ray.done) break;
+            if (take < nh) {              // slots full inside this voxel: resume here
+                ray.resume = true;
+                break;
+            }
+        }
+        ray.resume = false;
+        // step into the neighbour across face `ax`
+        ray.T = __fadd_rn(ray.T, se);
+#pragma unroll
+        for (int a = 0; a < 3; a++) ray.pl[a] = fmaf(se, Da[a], ray.pl[a]);
+        const int sg = Da[ax] > 0.0f ? 1 : -1;
+        ray.v[ax] += sg;
+        ray.pl[ax] = sg > 0 ? 0.0f : 1.0f;
+        if (ray.v[ax] < 0 || ray.v[ax] >= P.res[ax]) ray.done = true;
+    }
+    return used;
+}
+
+// Hit frame for the AO hemisphere (reading S3): tangent = tube direction
+// projected onto the tangent plane; fallback: the world axis least aligned
+// with n.
+__device__ __forceinline__ Vec ao_tangent(Vec n, Vec u) {
+    const float un = dot(u, n);
+    Vec T = axpy(-un, n, u);
+    const float m = sqrtf(dot(T, T));
+    if (m >= 1e-3f) return scale(T, 1.0f / m);
+    const float ax = fabsf(n.x), ay = fabsf(n.y), az = fabsf(n.z);
+    int e = 0;
+    float best = ax;
+    if (ay < best) { e = 1; best = ay; }
+    if (az < best) { e = 2; }
+    const float ne = e == 0 ? n.x : (e == 1 ? n.y : n.z);
+    T = mk((e == 0 ? 1.0f : 0.0f) - ne * n.x, (e == 1 ? 1.0f : 0.0f) - ne * n.y, (e == 2 ? 1.0f : 0.0f) - ne * n.z);
+    return scale(T, rsqrtf(dot(T, T)));
+}
+
+struct HitLight {
+    Vec P, n, T, B, dir;
+    int r;                 // current ray: 0 .. nrays-1 (shadow first if enabled)
+    int s;                 // march distance in voxels
+    float O, occ, V;
+};
+
+__device__ __forceinline__ Vec ray_dir(const RenderParams &P, const HitLight &h, int r) {
+    if (P.shadows && r == 0) return mk(P.Lt[0], P.Lt[1], P.Lt[2]);
+    const int i = r - (P.shadows ? 1 : 0);
+    const float dx = P.aod[i][0], dy = P.aod[i][1], dz = P.aod[i][2];
+    return mk(fmaf(h.T.x, dx, fmaf(h.B.x, dy, h.n.x * dz)), fmaf(h.T.y, dx, fmaf(h.B.y, dy, h.n.y * dz)),
+              fmaf(h.T.z, dx, fmaf(h.B.z, dy, h.n.z * dz)));
+}
+
+__device__ __forceinline__ void load_hit(const RenderParams &P, const Smem &sm, int owner, int q, HitLight &h) {
+    h.P = mk(sm.slot[F_PX][q][owner], sm.slot[F_PY][q][owner], sm.slot[F_PZ][q][owner]);
+    h.n = mk(sm.slot[F_NX][q][owner], sm.slot[F_NY][q][owner], sm.slot[F_NZ][q][owner]);
+    if (P.ao) {
+        h.T = ao_tangent(h.n, mk(sm.slot[F_UX][q][owner], sm.slot[F_UY][q][owner], sm.slot[F_UZ][q][owner]));
+        h.B = cross(h.n, h.T);
+    }
+    h.r = 0;
+    h.s = 1;
+    h.O = 0.0f;
+    h.occ = 0.0f;
+    h.V = 1.0f;
+    h.dir = ray_dir(P, h, 0);
+}
+
+// Phase B: the warp's hits, dealt out to lanes; shadow and AO marches
+// (Secs. 5.2, 5.3, readings S2 / S3) in one flattened loop of density
+// samples. Samples at s = 1, 2, 4, ... with step 2^l at level
+// l = floor(log2 s) (capped); O += rho_l * 2^l with rho_l = dens_l / 8^l;
+// a ray ends at O >= 1, beyond the AO radius, or when the sample leaves the
+// support of the density field.
+__device__ void light_hits(const RenderParams &P, Smem &sm, int warp, int lane, int total, unsigned &nsamp) {
+    int g = lane;
+    HitLight h;
+    if (g < total) {
+        const int it = sm.item[warp][g];
+        load_hit(P, sm, warp * 32 + (it >> 3), it & 7, h);
+    }
+    const int top = P.levels - 1;
+    while (__any_sync(FULL, g < total)) {
+        if (g < total) {
+            bool end_ray = false;
+            const bool is_ao = !(P.shadows && h.r == 0);
+            if (is_ao && (float)h.s > P.ao_radius) {
+                end_ray = true;
+            } else {
+                const Vec x = axpy((float)h.s, h.dir, h.P);
+                if (x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] ||
+                    x.y > P.lod_hi[1] || x.z > P.lod_hi[2]) {
+                    end_ray = true;
+                } else {
+                    int l = 31 - __clz(h.s);
+                    l = l < top ? l : top;
+                    const float wl = __int_as_float((127 - 2 * l) << 23);   // 2^l / 8^l
+                    h.O = fmaf(sample_level(P, l, x), wl, h.O);
+                    nsamp++;
+                    if (h.O >= 1.0f) end_ray = true;
+                    else h.s += 1 << l;
+                }
+            }
+            if (end_ray) {
+                const float o = fminf(1.0f, h.O);
+                if (is_ao) h.occ += o;
+                else h.V = 1.0f - o;
+                h.r++;
+                h.s = 1;
+                h.O = 0.0f;
+                if (h.r < P.nrays) {
+                    h.dir = ray_dir(P, h, h.r);
+                } else {
+                    // lit contribution of this hit: w * rgb * (ka * AO + kd * V * |n.L|)
+                    const int it = sm.item[warp][g];
+                    const int owner = warp * 32 + (it >> 3), q = it & 7;
+                    const float AO = P.ao ? 1.0f - h.occ / (float)P.ao_rays : 1.0f;
+                    const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
+                    const float kk = fmaf(P.ka, AO, P.kd * h.V * fabsf(dot(h.n, Lt)));
+                    sm.slot[F_CR][q][owner] *= kk;
+                    sm.slot[F_CG][q][owner] *= kk;
+                    sm.slot[F_CB][q][owner] *= kk;
+                    g += 32;
+                    if (g < total) {
+                        const int it2 = sm.item[warp][g];
+                        load_hit(P, sm, warp * 32 + (it2 >> 3), it2 & 7, h);
                     }
                 }
             }
-            if (S.done) break;
-            T = __fadd_rn(T, se);
-            // step into the neighbour across face `ax`
-#pragma unroll
-            for (int a = 0; a < 3; a++) pl[a] = fmaf(se, Da[a], pl[a]);
-            const int sg = Da[ax] > 0.0f ? 1 : -1;
-            v[ax] += sg;
-            pl[ax] = sg > 0 ? 0.0f : 1.0f;
-            if (v[ax] < 0 || v[ax] >= P.res[ax]) break;
         }
     }
-    const float4 o = make_float4(fmaf(1.0f - S.A, P.bg[0], S.Cr), fmaf(1.0f - S.A, P.bg[1], S.Cg),
-                                 fmaf(1.0f - S.A, P.bg[2], S.Cb), S.A);
-    P.out[(int64_t)py * P.cw + px] = o;
+}
+
+__global__ void __launch_bounds__(RT, 4)
+render_kernel(const __grid_constant__ RenderParams P) {
+    __shared__ Smem sm;
+    for (int i = threadIdx.x; i < 256; i += RT)
+        sm.tf[i] = make_float4(P.tf[4 * i], P.tf[4 * i + 1], P.tf[4 * i + 2], P.tf[4 * i + 3]);
+    __syncthreads();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned nvox = 0, nrec = 0, nsamp = 0, nhit = 0;
+
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(P.tile_counter, 1u);
+        tile = __shfl_sync(FULL, tile, 0);
+        if (tile >= (unsigned)P.ntiles) break;
+        const int px = (int)(tile % (unsigned)P.tiles_x) * P.tile_w + lane % P.tile_w;
+        const int py = (int)(tile / (unsigned)P.tiles_x) * P.tile_h + lane / P.tile_w;
+        const bool valid = px < P.cw && py < P.ch;
+        Ray ray;
+        ray.A = ray.Cr = ray.Cg = ray.Cb = 0.0f;
+        ray.done = !valid;
+        ray.resume = false;
+        ray.rt = 0.0f;
+        ray.rk = 0;
+        ray.T = 0.0f;
+        if (valid) {
+            const int i = P.x0 + px, j = P.y0 + py;
+            // primary ray: float32 contract, each step correctly rounded
+            const float sx = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * i + 1), (float)P.W), 1.0f), P.tw);
+            const float sy = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * j + 1), (float)P.H), 1.0f), P.th);
+            float d[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                d[a] = __fsub_rn(__fadd_rn(P.F[a], __fmul_rn(sx, P.R[a])), __fmul_rn(sy, P.U[a]));
+            const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
+            const float inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
+            ray.D = mk(__fmul_rn(d[0], inv), __fmul_rn(d[1], inv), __fmul_rn(d[2], inv));
+            const float Da[3] = {ray.D.x, ray.D.y, ray.D.z};
+            // slab test: only the entry parameter is needed, approximately
+            float tnear = 0.0f, tfar = INFINITY;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                if (Da[a] != 0.0f) {
+                    const float ia = 1.0f / Da[a];
+                    const float t1 = (0.0f - P.eye[a]) * ia, t2 = ((float)P.res[a] - P.eye[a]) * ia;
+                    tnear = fmaxf(tnear, fminf(t1, t2));
+                    tfar = fminf(tfar, fmaxf(t1, t2));
+                } else if (P.eye[a] < 0.0f || P.eye[a] > (float)P.res[a]) {
+                    tnear = INFINITY;
+                }
+            }
+            if (!(tnear < tfar)) {
+                ray.done = true;
+            } else {
+                // entry point in float-float, split into voxel index + local position
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const float ph = __fmul_rn(tnear, Da[a]);
+                    const float pe = __fmaf_rn(tnear, Da[a], -ph);
+                    float sh, s2;
+                    two_sum(P.eye[a], ph, sh, s2);
+                    const float lo = __fadd_rn(s2, pe);
+                    float fl = floorf(sh);
+                    float f = __fadd_rn(__fsub_rn(sh, fl), lo);
+                    if (f < 0.0f) { fl -= 1.0f; f += 1.0f; }
+                    else if (f >= 1.0f) { fl += 1.0f; f -= 1.0f; }
+                    int vi = (int)fl;
+                    if (vi < 0) { f += (float)vi; vi = 0; }
+                    if (vi > P.res[a] - 1) { f += (float)(vi - (P.res[a] - 1)); vi = P.res[a] - 1; }
+                    ray.v[a] = vi;
+                    ray.pl[a] = f;
+                    ray.invD[a] = Da[a] != 0.0f ? 1.0f / Da[a] : INFINITY;
+                }
+                ray.T = tnear;
+            }
+        }
+        // alternate traversal and lighting until every ray of the tile is finished
+        for (;;) {
+            const int used = traverse(P, sm, ray, tid, nvox, nrec, nhit);
+            if (P.nrays > 0) {
+                // list the warp's hits: (owner lane, slot), lane-major
+                int pre = used;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, pre, o);
+                    if (lane >= o) pre += y;
+                }
+                const int total = __shfl_sync(FULL, pre, 31);
+                pre -= used;
+                for (int q = 0; q < used; q++) sm.item[warp][pre + q] = (uint8_t)((lane << 3) | q);
+                __syncwarp();
+                if (total > 0) {
+                    light_hits(P, sm, warp, lane, total, nsamp);
+                    __syncwarp();
+                    for (int q = 0; q < used; q++) {
+                        ray.Cr += sm.slot[F_CR][q][tid];
+                        ray.Cg += sm.slot[F_CG][q][tid];
+                        ray.Cb += sm.slot[F_CB][q][tid];
+                    }
+                }
+                __syncwarp();
+            }
+            if (__all_sync(FULL, ray.done)) break;
+        }
+        if (valid) {
+            const float4 o = make_float4(fmaf(1.0f - ray.A, P.bg[0], ray.Cr), fmaf(1.0f - ray.A, P.bg[1], ray.Cg),
+                                         fmaf(1.0f - ray.A, P.bg[2], ray.Cb), ray.A);
+            P.out[(int64_t)py * P.cw + px] = o;
+        }
+    }
     if (P.counters) {
-        const unsigned mask = __activemask();
-        const unsigned c0 = __reduce_add_sync(mask, S.nvox), c1 = __reduce_add_sync(mask, S.nrec),
-                       c2 = __reduce_add_sync(mask, S.nsamp), c3 = __reduce_add_sync(mask, S.nhit);
-        if (lane == __ffs(mask) - 1) {
+        const unsigned c0 = __reduce_add_sync(FULL, nvox), c1 = __reduce_add_sync(FULL, nrec),
+                       c2 = __reduce_add_sync(FULL, nsamp), c3 = __reduce_add_sync(FULL, nhit);
+        if (lane == 0) {
             atomicAdd(P.counters + 0, (unsigned long long)c0);
             atomicAdd(P.counters + 1, (unsigned long long)c1);
             atomicAdd(P.counters + 2, (unsigned long long)c2);
@@ -448,7 +601,7 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
     (void)ao;
     const bool need_lod = desc->shadows || desc->ao_mode == 1;
     if (need_lod && !lod) return set_err(ctx, LVR_EINVAL, "shadows / traced AO need a LoD");
-    if (desc->ao_mode == 1 && (desc->ao_rays < 1 || desc->ao_rays > 32))
+    if (desc->ao_mode == 1 && (desc->ao_rays < 1 || desc->ao_rays > MAX_AO))
         return set_err(ctx, LVR_EINVAL, "ao_rays must be in [1,32]");
     if (lod && (lod->dims[0][0] != ls->res[0] || lod->dims[0][1] != ls->res[1] || lod->dims[0][2] != ls->res[2]))
         return set_err(ctx, LVR_EINVAL, "LoD does not belong to this line set");
@@ -485,11 +638,11 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
     r[0] = f[1] * up[2] - f[2] * up[1];
     r[1] = f[2] * up[0] - f[0] * up[2];
     r[2] = f[0] * up[1] - f[1] * up[0];
+    if (!(fabs(r[0]) + fabs(r[1]) + fabs(r[2]) > 0.0)) return set_err(ctx, LVR_EINVAL, "degenerate camera");
     norm3(r);
     u[0] = r[1] * f[2] - r[2] * f[1];
     u[1] = r[2] * f[0] - r[0] * f[2];
     u[2] = r[0] * f[1] - r[1] * f[0];
-    if (!(fabs(r[0]) + fabs(r[1]) + fabs(r[2]) > 0.0)) return set_err(ctx, LVR_EINVAL, "degenerate camera");
     const double tanh_ = tan((double)view->fovy_deg * M_PI / 360.0);
     for (int a = 0; a < 3; a++) {
         P.F[a] = (float)f[a];
@@ -501,6 +654,8 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
     P.tw = (float)(tanh_ * (double)view->width / (double)view->height);
     P.W = view->width; P.H = view->height; P.x0 = x0; P.y0 = y0; P.cw = cw; P.ch = ch;
     P.tile_w = tw; P.tile_h = th;
+    P.tiles_x = (cw + tw - 1) / tw;
+    P.ntiles = P.tiles_x * ((ch + th - 1) / th);
     double ld[3] = {view->light_dir[0], view->light_dir[1], view->light_dir[2]};
     norm3(ld);
     for (int a = 0; a < 3; a++) P.Lt[a] = (float)(-ld[a]);
@@ -508,7 +663,8 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
     P.ert = desc->ert_alpha;
     P.shadows = desc->shadows ? 1 : 0;
     P.ao = desc->ao_mode == 1 ? 1 : 0;
-    P.ao_rays = desc->ao_rays;
+    P.ao_rays = P.ao ? desc->ao_rays : 0;
+    P.nrays = P.shadows + P.ao_rays;
     P.ao_radius = desc->ao_radius;
     P.ka = desc->ka;
     P.kd = desc->kd;
@@ -534,7 +690,16 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
         P.counters = host_cnt ? (unsigned long long *)ctx->d_u64 : (unsigned long long *)counters;
         LVR_CUDA(ctx, cudaMemsetAsync(P.counters, 0, 32, s));
     }
-    dim3 grid((cw + 2 * tw - 1) / (2 * tw), (ch + 2 * th - 1) / (2 * th));
+    P.tile_counter = ctx->d_status + 1;
+    LVR_CUDA(ctx, cudaMemsetAsync(P.tile_counter, 0, 4, s));
+    if (!ctx->render_blocks) {
+        int sms = 0, per_sm = 0;
+        LVR_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        LVR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel, RT, 0));
+        ctx->render_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int need = (P.ntiles + RT / 32 - 1) / (RT / 32);
+    const int grid = need < ctx->render_blocks ? need : ctx->render_blocks;
     render_kernel<<<grid, RT, 0, s>>>(P);
     LVR_CUDA(ctx, cudaGetLastError());
     if (host_out) LVR_CUDA(ctx, cudaMemcpyAsync(rgba, P.out, out_bytes, cudaMemcpyDeviceToHost, s));
