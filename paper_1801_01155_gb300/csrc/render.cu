@@ -14,12 +14,12 @@
 //      to the lane's shared-memory hit slots (KS per lane). A lane stops when
 //      its slots are full (it resumes inside the same voxel later) or when
 //      its ray is finished.
-//   B. lighting (whole warp): the warp's collected hits are dealt out to the
-//      32 lanes, which march the shadow ray and the AO rays of their hits in
-//      one flattened loop, one density sample per iteration, so the warp
-//      stays converged while marches of different lengths interleave. Each
-//      hit's lit contribution is written back to its slot, and the owning
-//      lane adds its slots in depth order.
+//   B. lighting (whole warp): the warp's collected hits are lit together:
+//      shadow rays one lane per hit; the AO rays of one hit on a group of
+//      adjacent lanes, which sample the same neighbourhood at the same
+//      distances (good cache locality, little divergence), their occlusion
+//      summed by a fixed butterfly. Each hit's lit contribution is written
+//      back to its slot, and the owning lane adds its slots in depth order.
 //
 // Precision. All device arithmetic is float32. The primary ray is a float32
 // quantity built by a fixed sequence of correctly rounded operations. The
@@ -186,7 +186,7 @@ __device__ __forceinline__ bool key_after(float t, uint32_t k, float lt, uint32_
 
 // Shared memory of one block: transfer function, per-lane sorted hit staging
 // and per-lane hit slots (field-major, lane-minor: conflict-free).
-enum { F_PX, F_PY, F_PZ, F_NX, F_NY, F_NZ, F_UX, F_UY, F_UZ, F_CR, F_CG, F_CB, NF };
+enum { F_PX, F_PY, F_PZ, F_NX, F_NY, F_NZ, F_UX, F_UY, F_UZ, F_CR, F_CG, F_CB, F_AO, F_V, NF };
 struct Smem {
     float4 tf[256];
     float st[KS][RT];             // staged (t, k) of the current voxel, ascending
@@ -332,10 +332,14 @@ __device__ int traverse(const RenderParams &P, Smem &sm, Ray &ray, int tid, unsi
         ray.T = __fadd_rn(ray.T, se);
 #pragma unroll
         for (int a = 0; a < 3; a++) ray.pl[a] = fmaf(se, Da[a], ray.pl[a]);
-        const int sg = Da[ax] > 0.0f ? 1 : -1;
-        ray.v[ax] += sg;
-        ray.pl[ax] = sg > 0 ? 0.0f : 1.0f;
-        if (ray.v[ax] < 0 || ray.v[ax] >= P.res[ax]) ray.done = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {       // constant indices keep the state in registers
+            if (a != ax) continue;
+            const int sg = Da[a] > 0.0f ? 1 : -1;
+            ray.v[a] += sg;
+            ray.pl[a] = sg > 0 ? 0.0f : 1.0f;
+            if (ray.v[a] < 0 || ray.v[a] >= P.res[a]) ray.done = true;
+        }
     }
     return used;
 }
@@ -358,98 +362,85 @@ __device__ __forceinline__ Vec ao_tangent(Vec n, Vec u) {
     return scale(T, rsqrtf(dot(T, T)));
 }
 
-struct HitLight {
-    Vec P, n, T, B, dir;
-    int r;                 // current ray: 0 .. nrays-1 (shadow first if enabled)
-    int s;                 // march distance in voxels
-    float O, occ, V;
-};
-
-__device__ __forceinline__ Vec ray_dir(const RenderParams &P, const HitLight &h, int r) {
-    if (P.shadows && r == 0) return mk(P.Lt[0], P.Lt[1], P.Lt[2]);
-    const int i = r - (P.shadows ? 1 : 0);
-    const float dx = P.aod[i][0], dy = P.aod[i][1], dz = P.aod[i][2];
-    return mk(fmaf(h.T.x, dx, fmaf(h.B.x, dy, h.n.x * dz)), fmaf(h.T.y, dx, fmaf(h.B.y, dy, h.n.y * dz)),
-              fmaf(h.T.z, dx, fmaf(h.B.z, dy, h.n.z * dz)));
-}
-
-__device__ __forceinline__ void load_hit(const RenderParams &P, const Smem &sm, int owner, int q, HitLight &h) {
-    h.P = mk(sm.slot[F_PX][q][owner], sm.slot[F_PY][q][owner], sm.slot[F_PZ][q][owner]);
-    h.n = mk(sm.slot[F_NX][q][owner], sm.slot[F_NY][q][owner], sm.slot[F_NZ][q][owner]);
-    if (P.ao) {
-        h.T = ao_tangent(h.n, mk(sm.slot[F_UX][q][owner], sm.slot[F_UY][q][owner], sm.slot[F_UZ][q][owner]));
-        h.B = cross(h.n, h.T);
-    }
-    h.r = 0;
-    h.s = 1;
-    h.O = 0.0f;
-    h.occ = 0.0f;
-    h.V = 1.0f;
-    h.dir = ray_dir(P, h, 0);
-}
-
-// Phase B: the warp's hits, dealt out to lanes; shadow and AO marches
-// (Secs. 5.2, 5.3, readings S2 / S3) in one flattened loop of density
-// samples. Samples at s = 1, 2, 4, ... with step 2^l at level
-// l = floor(log2 s) (capped); O += rho_l * 2^l with rho_l = dens_l / 8^l;
-// a ray ends at O >= 1, beyond the AO radius, or when the sample leaves the
-// support of the density field.
-__device__ void light_hits(const RenderParams &P, Smem &sm, int warp, int lane, int total, unsigned &nsamp) {
-    int g = lane;
-    HitLight h;
-    if (g < total) {
-        const int it = sm.item[warp][g];
-        load_hit(P, sm, warp * 32 + (it >> 3), it & 7, h);
-    }
+// Density march (Secs. 5.2, 5.3, readings S2 / S3): samples at s = 1, 2, 4,
+// ... with step 2^l at level l = floor(log2 s) (capped); O += rho_l * 2^l
+// with rho_l = dens_l / 8^l; the ray ends at O >= 1, beyond max_dist (if
+// >= 0), or when the sample leaves the support of the density field.
+__device__ __forceinline__ float march(const RenderParams &P, Vec p, Vec d, float max_dist, unsigned &nsamp) {
     const int top = P.levels - 1;
-    while (__any_sync(FULL, g < total)) {
-        if (g < total) {
-            bool end_ray = false;
-            const bool is_ao = !(P.shadows && h.r == 0);
-            if (is_ao && (float)h.s > P.ao_radius) {
-                end_ray = true;
-            } else {
-                const Vec x = axpy((float)h.s, h.dir, h.P);
-                if (x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] ||
-                    x.y > P.lod_hi[1] || x.z > P.lod_hi[2]) {
-                    end_ray = true;
-                } else {
-                    int l = 31 - __clz(h.s);
-                    l = l < top ? l : top;
-                    const float wl = __int_as_float((127 - 2 * l) << 23);   // 2^l / 8^l
-                    h.O = fmaf(sample_level(P, l, x), wl, h.O);
-                    nsamp++;
-                    if (h.O >= 1.0f) end_ray = true;
-                    else h.s += 1 << l;
-                }
+    float O = 0.0f;
+    int s = 1;
+    for (;;) {
+        if (max_dist >= 0.0f && (float)s > max_dist) break;
+        const Vec x = axpy((float)s, d, p);
+        if (x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
+            x.z > P.lod_hi[2])
+            break;
+        int l = 31 - __clz(s);
+        l = l < top ? l : top;
+        const float wl = __int_as_float((127 - 2 * l) << 23);   // 2^l / 8^l
+        O = fmaf(sample_level(P, l, x), wl, O);
+        nsamp++;
+        if (O >= 1.0f) break;
+        s += 1 << l;
+    }
+    return O;
+}
+
+__device__ __forceinline__ int slot_owner(const Smem &sm, int warp, int g) { return warp * 32 + (sm.item[warp][g] >> 3); }
+__device__ __forceinline__ int slot_index(const Smem &sm, int warp, int g) { return sm.item[warp][g] & 7; }
+
+// Phase B: light the warp's collected hits.
+//  - Shadows: one lane per hit, a march toward the light (Sec. 5.2).
+//  - AO: the ao_rays hemisphere rays of one hit run on a group of adjacent
+//    lanes (group = next power of two >= ao_rays), so a group samples one
+//    neighbourhood at the same distances; occlusion is summed over the group
+//    with a fixed butterfly, so the result does not depend on the schedule.
+//  - Each hit's weighted colour is then scaled by ka * AO + kd * V * |n.L|.
+__device__ void light_hits(const RenderParams &P, Smem &sm, int warp, int lane, int total, unsigned &nsamp) {
+    const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
+    if (P.shadows) {
+        for (int g = lane; g < total; g += 32) {
+            const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
+            const Vec Pg = mk(sm.slot[F_PX][q][o], sm.slot[F_PY][q][o], sm.slot[F_PZ][q][o]);
+            sm.slot[F_V][q][o] = 1.0f - fminf(1.0f, march(P, Pg, Lt, -1.0f, nsamp));
+        }
+    }
+    if (P.ao) {
+        int G = 1;
+        while (G < P.ao_rays) G <<= 1;
+        const int per = 32 / G, sub = lane / G, ray = lane % G;
+        for (int m = 0; m < total; m += per) {
+            const int g = m + sub;
+            float o = 0.0f;
+            if (g < total && ray < P.ao_rays) {
+                const int ow = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
+                const Vec Pg = mk(sm.slot[F_PX][q][ow], sm.slot[F_PY][q][ow], sm.slot[F_PZ][q][ow]);
+                const Vec n = mk(sm.slot[F_NX][q][ow], sm.slot[F_NY][q][ow], sm.slot[F_NZ][q][ow]);
+                const Vec T = ao_tangent(n, mk(sm.slot[F_UX][q][ow], sm.slot[F_UY][q][ow], sm.slot[F_UZ][q][ow]));
+                const Vec B = cross(n, T);
+                const float dx = P.aod[ray][0], dy = P.aod[ray][1], dz = P.aod[ray][2];
+                const Vec d = mk(fmaf(T.x, dx, fmaf(B.x, dy, n.x * dz)), fmaf(T.y, dx, fmaf(B.y, dy, n.y * dz)),
+                                 fmaf(T.z, dx, fmaf(B.z, dy, n.z * dz)));
+                o = fminf(1.0f, march(P, Pg, d, P.ao_radius, nsamp));
             }
-            if (end_ray) {
-                const float o = fminf(1.0f, h.O);
-                if (is_ao) h.occ += o;
-                else h.V = 1.0f - o;
-                h.r++;
-                h.s = 1;
-                h.O = 0.0f;
-                if (h.r < P.nrays) {
-                    h.dir = ray_dir(P, h, h.r);
-                } else {
-                    // lit contribution of this hit: w * rgb * (ka * AO + kd * V * |n.L|)
-                    const int it = sm.item[warp][g];
-                    const int owner = warp * 32 + (it >> 3), q = it & 7;
-                    const float AO = P.ao ? 1.0f - h.occ / (float)P.ao_rays : 1.0f;
-                    const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
-                    const float kk = fmaf(P.ka, AO, P.kd * h.V * fabsf(dot(h.n, Lt)));
-                    sm.slot[F_CR][q][owner] *= kk;
-                    sm.slot[F_CG][q][owner] *= kk;
-                    sm.slot[F_CB][q][owner] *= kk;
-                    g += 32;
-                    if (g < total) {
-                        const int it2 = sm.item[warp][g];
-                        load_hit(P, sm, warp * 32 + (it2 >> 3), it2 & 7, h);
-                    }
-                }
+            for (int x = G >> 1; x > 0; x >>= 1) o += __shfl_xor_sync(FULL, o, x);
+            if (ray == 0 && g < total) {
+                const int ow = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
+                sm.slot[F_AO][q][ow] = 1.0f - o / (float)P.ao_rays;
             }
         }
+    }
+    __syncwarp();
+    for (int g = lane; g < total; g += 32) {
+        const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
+        const Vec n = mk(sm.slot[F_NX][q][o], sm.slot[F_NY][q][o], sm.slot[F_NZ][q][o]);
+        const float AO = P.ao ? sm.slot[F_AO][q][o] : 1.0f;
+        const float V = P.shadows ? sm.slot[F_V][q][o] : 1.0f;
+        const float kk = fmaf(P.ka, AO, P.kd * V * fabsf(dot(n, Lt)));
+        sm.slot[F_CR][q][o] *= kk;
+        sm.slot[F_CG][q][o] *= kk;
+        sm.slot[F_CB][q][o] *= kk;
     }
 }
 
