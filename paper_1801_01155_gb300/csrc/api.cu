@@ -105,6 +105,14 @@ extern "C" lvr_status lvr_create(int device, void *cuda_stream, lvr_ctx **out) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess || prop.major < 10) return LVR_EDEVICE;
     if (cudaSetDevice(device) != cudaSuccess) return LVR_EDEVICE;
+    // keep freed stream-ordered allocations in this process's pool instead of
+    // returning them to the driver at every synchronisation: line sets and
+    // LoDs are allocated and freed once per frame
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     lvr_ctx *ctx = new lvr_ctx();
     ctx->device = device;
     if (cuda_stream) {
