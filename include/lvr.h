@@ -116,6 +116,44 @@ lvr_status lvr_export_lineset(lvr_ctx *ctx, const lvr_lineset *ls, uint32_t *off
                               uint8_t *fields, uint32_t *curve, uint32_t *ordinal);
 void lvr_free_lineset(lvr_lineset *ls);
 
+/* ------------------------------------------------------------------ allocation-free voxelisation
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: code that runs where cudaMalloc is not
+ * allowed or not wanted (a real-time loop with a fixed memory budget, a
+ * host application whose allocator owns all device memory, a plug-in that
+ * receives its buffers from the host program). It computes what
+ * lvr_voxelize computes, into buffers the caller owns, and allocates
+ * nothing: its temporary storage is one static device array of 16 MiB
+ * plus 4 KiB, reserved on every GPU that loads the library until the
+ * process exits, which limits grids to LVR_STATIC_MAX_VOXELS voxels
+ * (128^3).
+ *
+ * All pointers are device pointers (host pointers: LVR_EINVAL; nothing is
+ * staged). grid->fit must be 0. offset: uint32 [voxels + 1]; records and
+ * keys: uint64 [capacity] receive the segments, voxel-major and by (curve,
+ * position along the curve) within a voxel. Record bits: 0-2 entry face
+ * (0=-x,1=+x,2=-y,3=+y,4=-z,5=+z), 3-9 / 10-16 entry bins on the two other
+ * axes in increasing axis order, 17-19 exit face, 20-26 / 27-33 exit bins,
+ * 34-41 attribute byte, 42 continues-previous flag, 43-47 curve index mod
+ * 32. Key = (curve << 32) | position along the curve. *n_segments receives
+ * the segment count; if it exceeds `capacity` the call returns
+ * LVR_EOVERFLOW after counting and writes no segments (retry with a larger
+ * buffer). Work runs on `cuda_stream` (a cudaStream_t, NULL: legacy default
+ * stream) of the current device; the call waits for the count.
+ *
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture. Every call on a device shares the one array, which keeps the
+ * previous call's contents (the call clears what must start at zero):
+ * calls that overlap on the GPU (from several streams or host threads)
+ * race and must be serialised by the caller. Errors are reported by the
+ * status code only. */
+#define LVR_STATIC_MAX_VOXELS 2097152u
+lvr_status lvr_voxelize_static(const float *xyz, const float *attr, const int64_t *curve_offsets,
+                               int64_t n_curves, int64_t n_vertices, const lvr_grid_desc *grid,
+                               uint32_t *offset, uint64_t *records, uint64_t *keys, int64_t capacity,
+                               int64_t *n_segments, void *cuda_stream);
+
 /* ------------------------------------------------------------------ density LoD
  * Sec. 3.4, Eq. 1: per voxel rho = sum over its segments of length * sigma,
  * sigma = sigma256[attribute byte] (host float32 [256], the transfer

@@ -18,6 +18,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "lvr_internal.cuh"
 
 namespace {
@@ -590,5 +592,128 @@ extern "C" lvr_status lvr_voxelize(lvr_ctx *ctx, const float *xyz, const float *
         LVR_CUDA(ctx, cudaGetLastError());
     }
     *out = ls;
+    return LVR_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free variant
+// lvr_voxelize_static: the same voxeliser for callers that must not allocate
+// device memory (see include/lvr.h). Its scratch lives in one file-scope
+// device array, reserved on every device that loads the library until the
+// process exits. Host code never uses the array's name as an address: the
+// device address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+
+constexpr uint32_t STATIC_MAX_VOXELS = LVR_STATIC_MAX_VOXELS;
+constexpr size_t STATIC_TILES = (STATIC_MAX_VOXELS + SCAN_TILE - 1) / SCAN_TILE;
+// layout (bytes): counts [MAXV] u32 | long list [MAXV] u32 | tile sums [TILES] u64 |
+//                 total u64 | status u32 | long count u32
+constexpr size_t ST_OFF_LONG = (size_t)STATIC_MAX_VOXELS * 4;
+constexpr size_t ST_OFF_TILES = ST_OFF_LONG + (size_t)STATIC_MAX_VOXELS * 4;
+constexpr size_t ST_OFF_TOTAL = ST_OFF_TILES + STATIC_TILES * 8;
+constexpr size_t ST_OFF_STATUS = ST_OFF_TOTAL + 8;
+constexpr size_t ST_OFF_LCOUNT = ST_OFF_STATUS + 4;
+constexpr size_t STATIC_BYTES = ST_OFF_LCOUNT + 4;
+
+__device__ __align__(256) unsigned char g_static_scratch[STATIC_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+void *g_static_addr[MAX_DEVICES] = {};
+std::mutex g_static_mu;
+
+// Device address of the scratch array on the current device (looked up once).
+cudaError_t static_scratch(int dev, unsigned char **out) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = (unsigned char *)g_static_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" lvr_status lvr_voxelize_static(const float *xyz, const float *attr, const int64_t *curve_offsets,
+                                          int64_t n_curves, int64_t n_vertices, const lvr_grid_desc *g,
+                                          uint32_t *offset, uint64_t *records, uint64_t *keys,
+                                          int64_t capacity, int64_t *n_segments, void *cuda_stream) {
+    if (!g || !curve_offsets || !offset || !n_segments || capacity < 0) return LVR_EINVAL;
+    if ((capacity > 0 || n_curves > 0) && (!records || !keys)) return LVR_EINVAL;
+    *n_segments = 0;
+    if (n_curves < 0 || n_vertices < 0 || n_curves > 0xffffffffLL) return LVR_EINVAL;
+    if (n_curves == 0 && n_vertices != 0) return LVR_EINVAL;
+    if (n_vertices > 0 && !xyz) return LVR_EINVAL;
+    if (g->fit || !valid_bins(g->bins)) return LVR_EINVAL;
+    for (int a = 0; a < 3; a++)
+        if (g->res[a] < 1 || g->res[a] > 4096) return LVR_EINVAL;
+    if (!(g->scale > 0.0f) || !isfinite(g->scale)) return LVR_EINVAL;
+    const int64_t nvox = (int64_t)g->res[0] * g->res[1] * g->res[2];
+    if (nvox > (int64_t)STATIC_MAX_VOXELS) return LVR_EINVAL;
+    // every buffer must already be on the device: nothing is staged
+    const void *ptrs[6] = {xyz, attr, curve_offsets, offset, records, keys};
+    for (const void *p : ptrs)
+        if (p && !is_device_ptr(p)) return LVR_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return LVR_EDEVICE;
+    unsigned char *base = nullptr;
+    if (static_scratch(dev, &base) != cudaSuccess) return LVR_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint32_t *cnt = (uint32_t *)base;
+    uint32_t *long_list = (uint32_t *)(base + ST_OFF_LONG);
+    unsigned long long *tiles = (unsigned long long *)(base + ST_OFF_TILES);
+    unsigned long long *total = (unsigned long long *)(base + ST_OFF_TOTAL);
+    uint32_t *status = (uint32_t *)(base + ST_OFF_STATUS);
+    uint32_t *long_count = (uint32_t *)(base + ST_OFF_LCOUNT);
+
+    VoxParams P;
+    P.xyz = xyz;
+    P.offs = curve_offsets;
+    P.nc = n_curves;
+    P.nv = n_vertices;
+    for (int a = 0; a < 3; a++) {
+        P.o[a] = g->origin[a];
+        P.res[a] = g->res[a];
+    }
+    P.s = g->scale;
+    P.N = g->bins;
+    P.amin = g->attr_min;
+    P.aspan = g->attr_max - g->attr_min;
+    P.attr = (attr && g->attr_max > g->attr_min) ? attr : nullptr;
+    P.status = status;
+
+    // the array keeps the previous call's contents: clear what must start at zero
+    if (cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(total, 0, 16, s) != cudaSuccess)
+        return LVR_ECUDA;
+    if (n_curves > 0) vox_curves_kernel<false><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, total);
+    if (cudaGetLastError() != cudaSuccess) return LVR_ECUDA;
+    unsigned long long h_total = 0;
+    uint32_t h_status = 0;
+    if (cudaMemcpyAsync(&h_total, total, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LVR_ECUDA;
+    if (h_status & (ST_BAD_OFFSETS | ST_BAD_VERTEX | ST_BAD_ATTR)) return LVR_EINVAL;
+    if (h_status & ST_INTERNAL) return LVR_ECUDA;
+    if (h_total > 0xffffffffull) return LVR_EOVERFLOW;
+    *n_segments = (int64_t)h_total;
+    if ((int64_t)h_total > capacity) return LVR_EOVERFLOW;
+
+    const int64_t ntiles = (nvox + SCAN_TILE - 1) / SCAN_TILE;
+    scan_reduce_kernel<<<(unsigned)ntiles, SCAN_T, 0, s>>>(cnt, nvox, tiles);
+    scan_tiles_kernel<<<1, 1024, 0, s>>>(tiles, ntiles, offset + nvox, status);
+    scan_down_kernel<<<(unsigned)ntiles, SCAN_T, 0, s>>>(cnt, nvox, tiles, offset);
+    if (h_total > 0) {
+        if (cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s) != cudaSuccess ||
+            cudaMemsetAsync(long_count, 0, 4, s) != cudaSuccess)
+            return LVR_ECUDA;
+        vox_curves_kernel<true><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, offset, records, keys, total);
+        sort_small_kernel<<<grid1d(nvox, 256), 256, 0, s>>>(offset, nvox, records, keys, long_list, long_count);
+        sort_long_kernel<<<304, 256, 2 * SMEM_LIST * sizeof(uint64_t), s>>>(offset, records, keys, long_list,
+                                                                           long_count);
+    }
+    if (cudaGetLastError() != cudaSuccess) return LVR_ECUDA;
     return LVR_OK;
 }

@@ -80,7 +80,10 @@ _SIGS = {
     "lvr_export_lod": ([_vp, _vp, C.c_int, _vp, _vp, _vp], C.c_int),
     "lvr_free_lod": ([_vp], None),
     "lvr_render": ([_vp, _vp, _vp, C.POINTER(View), C.POINTER(RenderDesc), _vp, _vp, _vp], C.c_int),
+    "lvr_voxelize_static": ([_vp, _vp, _vp, _i64, _i64, C.POINTER(GridDesc), _vp, _vp, _vp, _i64,
+                             C.POINTER(_i64), _vp], C.c_int),
 }
+STATIC_MAX_VOXELS = 2097152
 for _n, (_a, _r) in _SIGS.items():
     _f = getattr(_L, _n)
     _f.argtypes = _a
@@ -299,3 +302,28 @@ def lvr_render(ctx: Context, ls: LineSet, lod: Lod | None, view: View, desc: Ren
                                      ao_model.handle if ao_model is not None else None,
                                      _ptr(rgba), _ptr(counters)))
     return rgba
+
+
+def lvr_voxelize_static(xyz, attr, curve_offsets, grid: GridDesc, offset, records, keys, stream=None) -> int:
+    """Allocation-free voxelisation into caller-owned device tensors.
+
+    For callers that cannot allocate device memory: the library's scratch is
+    a static device array (grids up to STATIC_MAX_VOXELS voxels). offset:
+    uint32-sized [voxels + 1]; records / keys: 64-bit [capacity]. Returns the
+    segment count; raises LVRError(LVR_EOVERFLOW) with .n_segments set when
+    the capacity is too small. Calls that overlap on the GPU race.
+    """
+    nv = int(xyz.shape[0]) if xyz is not None else 0
+    nc = int(curve_offsets.shape[0]) - 1
+    cap = int(records.shape[0]) if records is not None else 0
+    n = _i64(0)
+    raw = None
+    if stream is not None:
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = _L.lvr_voxelize_static(_ptr(xyz), _ptr(attr), _ptr(curve_offsets), nc, nv, C.byref(grid),
+                                _ptr(offset), _ptr(records), _ptr(keys), cap, C.byref(n), raw)
+    if rc != OK:
+        err = LVRError(rc, "lvr_voxelize_static failed")
+        err.n_segments = n.value
+        raise err
+    return n.value
