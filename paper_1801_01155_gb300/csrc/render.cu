@@ -11,9 +11,11 @@
 //      front-to-back weighting. The compositing weight of a hit depends only
 //      on the opacities in front of it, never on its lighting, so each hit's
 //      weight, position, normal and tube direction are final here; they go
-//      to the lane's shared-memory hit slots (KS per lane). A lane stops when
-//      its slots are full (it resumes inside the same voxel later) or when
-//      its ray is finished.
+//      to the lane's shared-memory hit slots (KS per lane). The warp steps
+//      its lanes voxel by voxel until it holds ROUND_TARGET hits, or every
+//      lane is full or finished; a full lane resumes inside the same voxel in
+//      the next round. Lighting in small rounds keeps lanes in dense regions
+//      from idling while a lane in a sparse region looks for hits.
 //   B. lighting (whole warp): the warp's collected hits are lit together:
 //      shadow rays one lane per hit; the AO rays of one hit on a group of
 //      adjacent lanes, which sample the same neighbourhood at the same
@@ -40,6 +42,7 @@ namespace {
 
 constexpr int RT = 128;       // threads per block (4 warps)
 constexpr int KS = 4;         // hit slots per lane per lighting round
+constexpr unsigned ROUND_TARGET = 16;   // a warp lights its hits once it holds this many
 constexpr int MAX_AO = 32;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -209,11 +212,10 @@ struct Ray {
 };
 
 // Phase A for one lane: traverse until KS hits are collected or the ray ends.
-__device__ int traverse(const RenderParams &P, Smem &sm, Ray &ray, int tid, unsigned &nvox, unsigned &nrec,
-                        unsigned &nhit) {
-    int used = 0;
+__device__ __forceinline__ void voxel_step(const RenderParams &P, Smem &sm, Ray &ray, int tid, unsigned &nvox,
+                                           unsigned &nrec, unsigned &nhit, int &used) {
     const float Da[3] = {ray.D.x, ray.D.y, ray.D.z};
-    while (!ray.done && used < KS) {
+    do {
         float se = INFINITY;
         int ax = 0;
 #pragma unroll
@@ -340,6 +342,20 @@ __device__ int traverse(const RenderParams &P, Smem &sm, Ray &ray, int tid, unsi
             ray.pl[a] = sg > 0 ? 0.0f : 1.0f;
             if (ray.v[a] < 0 || ray.v[a] >= P.res[a]) ray.done = true;
         }
+    } while (false);
+}
+
+__device__ int traverse(const RenderParams &P, Smem &sm, Ray &ray, int tid, unsigned &nvox, unsigned &nrec,
+                        unsigned &nhit) {
+    int used = 0;
+    if (P.nrays == 0) {
+        while (!ray.done) voxel_step(P, sm, ray, tid, nvox, nrec, nhit, used);
+        return 0;
+    }
+    for (;;) {
+        if (!ray.done && used < KS) voxel_step(P, sm, ray, tid, nvox, nrec, nhit, used);
+        const unsigned tot = __reduce_add_sync(FULL, (unsigned)used);
+        if (tot >= ROUND_TARGET || __all_sync(FULL, ray.done || used >= KS)) break;
     }
     return used;
 }
@@ -444,7 +460,7 @@ __device__ void light_hits(const RenderParams &P, Smem &sm, int warp, int lane, 
     }
 }
 
-__global__ void __launch_bounds__(RT, 4)
+__global__ void __launch_bounds__(RT, 6)
 render_kernel(const __grid_constant__ RenderParams P) {
     __shared__ Smem sm;
     for (int i = threadIdx.x; i < 256; i += RT)
