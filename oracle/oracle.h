@@ -120,11 +120,12 @@ typedef struct orc_rdesc {
     int32_t opaque;             /* 1: alpha = 1, first hit only */
     float   ert_alpha;          /* early termination threshold (>= 1: never) */
     int32_t shadows;            /* soft shadow cone march */
-    int32_t ao;                 /* traced (density-marched) ambient occlusion */
+    int32_t ao;                 /* 1: traced (density-marched) AO; 2: learned surrogate */
     int32_t ao_rays;            /* hemisphere rays per hit */
     float   ao_radius;          /* radius of influence, voxels */
     float   ka, kd;             /* ambient and diffuse weights */
     float   bg[3];              /* background colour */
+    const float *ao_params;     /* learned AO parameters (ao == 2), see orc_ao_mlp */
 } orc_rdesc;
 
 /* counters[0..3]: voxels visited, records tested, LoD trilinear samples,
@@ -151,6 +152,13 @@ double orc_march(const orc_lod *lod, const double p[3], const double dir[3], dou
 double orc_sample(const orc_lod *lod, int level, const double x[3]);
 /* Hemisphere directions around normal n with tangent hint u (reading S3). */
 void orc_ao_dirs(const double n[3], const double u[3], int k, double *dirs);
+
+/* ---- learned AO surrogate (reading L1; aomlp.c) ---- */
+int    orc_ao_nparams(void);
+double orc_bf16(double x);
+void   orc_ao_tangent(const double a[3], const double b[3], double t[3]);
+void   orc_ao_features(const orc_lod *lod, int64_t voxel, const double t[3], double *x256);
+double orc_ao_mlp(const float *params, const double *x256);
 
 #ifdef __cplusplus
 }

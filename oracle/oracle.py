@@ -30,7 +30,7 @@ class RDesc(C.Structure):
     _fields_ = [("radius", C.c_float), ("tf", C.c_float * 1024), ("opaque", C.c_int32),
                 ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao", C.c_int32),
                 ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
-                ("kd", C.c_float), ("bg", C.c_float * 3)]
+                ("kd", C.c_float), ("bg", C.c_float * 3), ("ao_params", C.c_void_p)]
 
 
 def _p(a):
@@ -68,6 +68,13 @@ def lib():
         L.orc_sample.argtypes = [vp, C.c_int, vp]
         L.orc_sample.restype = C.c_double
         L.orc_ao_dirs.argtypes = [vp, vp, C.c_int, vp]
+        L.orc_ao_nparams.restype = C.c_int
+        L.orc_bf16.argtypes = [C.c_double]
+        L.orc_bf16.restype = C.c_double
+        L.orc_ao_tangent.argtypes = [vp, vp, vp]
+        L.orc_ao_features.argtypes = [vp, i64, vp, vp]
+        L.orc_ao_mlp.argtypes = [vp, vp]
+        L.orc_ao_mlp.restype = C.c_double
         _lib = L
     return _lib
 
@@ -220,7 +227,8 @@ def make_view(eye, at, up, fovy_deg, width, height, light_dir) -> View:
 
 
 def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False,
-               ao_rays=16, ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0)) -> RDesc:
+               ao_rays=16, ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), ao_params=None) -> RDesc:
+    """ao: False/0 off, True/1 traced, 2 learned (ao_params: float32 [ao_nparams()])."""
     d = RDesc()
     d.radius = float(radius)
     tf = np.ascontiguousarray(tf, np.float32).reshape(-1)
@@ -235,6 +243,12 @@ def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False
     d.ka = float(ka)
     d.kd = float(kd)
     d.bg[:] = [float(x) for x in bg]
+    if ao_params is not None:
+        ao_params = np.ascontiguousarray(ao_params, np.float32)
+        assert ao_params.size == ao_nparams()
+        d._keep = ao_params                       # keep the buffer alive with the struct
+        d.ao_params = ao_params.ctypes.data
+        d.ao = 2
     return d
 
 
@@ -287,3 +301,60 @@ def ao_dirs(n, u, k=16):
 
 def num_threads() -> int:
     return len(os.sched_getaffinity(0))
+
+
+# ---------------------------------------------------------------- learned AO (reading L1)
+def ao_nparams() -> int:
+    return lib().orc_ao_nparams()
+
+
+def bf16(x: float) -> float:
+    return lib().orc_bf16(float(x))
+
+
+def ao_tangent(a, b):
+    a = np.ascontiguousarray(a, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    t = np.empty(3)
+    lib().orc_ao_tangent(_p(a), _p(b), _p(t))
+    return t
+
+
+def ao_features(lod: "Lod", voxel: int, t):
+    t = np.ascontiguousarray(t, np.float64)
+    x = np.empty(256)
+    lib().orc_ao_features(lod.handle, int(voxel), _p(t), _p(x))
+    return x
+
+
+def ao_mlp(params, x) -> float:
+    params = np.ascontiguousarray(params, np.float32)
+    x = np.ascontiguousarray(x, np.float64)
+    return lib().orc_ao_mlp(_p(params), _p(x))
+
+
+class _OrcLodStruct(C.Structure):
+    _fields_ = [("levels", C.c_int), ("dims", (C.c_int32 * 3) * 4), ("cnt", C.c_void_p * 4),
+                ("len", C.c_void_p * 4), ("dens", C.c_void_p * 4)]
+
+
+class HandLod:
+    """A one-level orc_lod over given count / length arrays [z][y][x] (for
+    closed-form checks of the feature gather)."""
+
+    def __init__(self, cnt, len_):
+        self._cnt = np.ascontiguousarray(cnt, np.uint32)
+        self._len = np.ascontiguousarray(len_, np.float64)
+        self._dens = np.zeros_like(self._len)
+        nz, ny, nx = self._cnt.shape
+        s = _OrcLodStruct()
+        s.levels = 1
+        s.dims[0][0], s.dims[0][1], s.dims[0][2] = nx, ny, nz
+        s.cnt[0] = self._cnt.ctypes.data
+        s.len[0] = self._len.ctypes.data
+        s.dens[0] = self._dens.ctypes.data
+        self._s = s
+
+    @property
+    def handle(self):
+        return C.cast(C.pointer(self._s), C.c_void_p)

@@ -426,7 +426,12 @@ static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rd
 
     double V = 1.0, AO = 1.0;
     if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
-    if (rd->ao && L && rd->ao_rays > 0) {
+    if (rd->ao == 2 && L && rd->ao_params) {
+        double t[3], x[256];
+        orc_ao_tangent(a, b, t);
+        orc_ao_features(L, s->voxel, t, x);
+        AO = orc_ao_mlp(rd->ao_params, x);
+    } else if (rd->ao && L && rd->ao_rays > 0) {
         double u[3] = {ba[0], ba[1], ba[2]};
         if (L2 > 0.0) { double l = sqrt(L2); u[0] /= l; u[1] /= l; u[2] /= l; }
         double *dirs = (double *)malloc(sizeof(double) * 3 * (size_t)rd->ao_rays);
