@@ -222,11 +222,106 @@ typedef struct lvr_render_desc {
  * row 0 = top of the crop). counters: NULL, or host or device uint64 [4]
  * receiving voxels visited, records tested, LoD trilinear samples and
  * composited hits over the whole rectangle (costs one extra reduction).
- * `lod` may be NULL unless shadows or traced AO are on; `ao` may be NULL
- * unless ao_mode == 2. */
+ * `lod` may be NULL unless shadows or AO are on; `ao` may be NULL unless
+ * ao_mode == 2, where the call evaluates the model's per-voxel layer-1 term
+ * for `lod` once and caches it in the model (the model is therefore not
+ * const; a model must not be used by two overlapping calls). */
 lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
                       const lvr_view *view, const lvr_render_desc *desc,
-                      const lvr_ao_model *ao, float *rgba, uint64_t *counters);
+                      lvr_ao_model *ao, float *rgba, uint64_t *counters);
+
+/* ------------------------------------------------------------------ learned ambient occlusion
+ * The paper has no counterpart: a small network that predicts the traced
+ * AO of Sec. 5.3 (ao_mode 1) at a hit, used by lvr_render with ao_mode 2
+ * in place of the 16 marched AO rays.
+ *
+ * Model: 256 inputs, three hidden layers of 64 with ReLU, one sigmoid
+ * output. Inputs: the hit segment's unit direction (entry -> exit) with
+ * its first non-zero component made positive (3); for the 5^3 level-0
+ * voxels around the hit voxel (dz, dy, dx in -2..2, x fastest)
+ * log1p(segment count) and log1p(summed segment length), zero outside the
+ * grid (250); three zeros. Parameters: float32 [lvr_ao_nparams()] =
+ * W1 [64][256], b1 [64], W2 [64][64], b2 [64], W3 [64][64], b3 [64],
+ * W4 [64], b4 (row-major [out][in]), used as bfloat16 (round to nearest
+ * even) in every product, with bfloat16 inputs and hidden activations and
+ * float32 sums; the neighbourhood part of layer 1 is summed per voxel and
+ * rounded to bfloat16 before the direction part and b1 are added. */
+int lvr_ao_nparams(void);
+/* params: host float32 [lvr_ao_nparams()], copied; must be finite. */
+lvr_status lvr_ao_model_create(lvr_ctx *ctx, const float *params, lvr_ao_model **out);
+/* Current parameters into host or device float32 [lvr_ao_nparams()]. */
+lvr_status lvr_ao_model_params(lvr_ctx *ctx, const lvr_ao_model *m, float *params);
+void lvr_free_ao_model(lvr_ao_model *m);
+
+/* Model output for n hits: voxel int32 [n] (level-0 linear index
+ * x + X (y + Y z), in [0, voxels): LVR_EINVAL otherwise when host memory is
+ * given; NaN output for that hit when device memory is given), dir float32
+ * [n][3] (segment direction, any length, normalised as d / sqrt(d.d) in
+ * float32; zero gives a zero direction feature), ao float32 [n]. Host or
+ * device buffers. The same device code as the fused inference in
+ * lvr_render. */
+lvr_status lvr_ao_infer(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, int64_t n,
+                        const int32_t *voxel, const float *dir, float *ao);
+/* The model inputs of n hits as bfloat16 bit patterns, X uint16 [n][256];
+ * device buffers only; voxel ids as for lvr_ao_infer (out of range: an
+ * all-zero row). */
+lvr_status lvr_ao_features(lvr_ctx *ctx, const lvr_lod *lod, int64_t n, const int32_t *voxel,
+                           const float *dir, uint16_t *X);
+/* Training samples of one view with traced AO (desc's ao_rays, ao_radius,
+ * radius, transfer function, opaque and ert_alpha; shadows and ao_mode are
+ * ignored). Per pixel of the crop rectangle the ray is composited as usual
+ * and the hit of index k = h(seed, pixel) mod depth along it (0 = first) is
+ * recorded, if the ray reaches it: voxel int32 (-1: none), dir float32 [3]
+ * (unit entry -> exit direction of the hit segment), ao float32 (traced AO
+ * factor). h is the lowbias32 integer hash of seed ^ (pixel * 0x9e3779b9),
+ * pixel = row * crop width + column. Device buffers. */
+lvr_status lvr_ao_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
+                          const lvr_view *view, const lvr_render_desc *desc, int32_t depth,
+                          uint32_t seed, int32_t *voxel, float *dir, float *ao);
+
+/* Learned against traced AO over every hit the image composites: renders
+ * like lvr_render with ao_mode 2 (rgba may be NULL; host or device) and
+ * also traces desc->ao_rays AO rays at each hit. Shadows are off. */
+typedef struct lvr_ao_error {
+    uint64_t hits;          /* composited hits */
+    double   mean_abs;      /* mean |learned - traced| */
+    double   p99_abs;       /* 99th percentile of |learned - traced|, upper edge of a 1/4096 bin */
+    double   max_abs;
+    double   mean_traced, mean_learned;
+} lvr_ao_error;
+lvr_status lvr_ao_judge(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
+                        const lvr_view *view, const lvr_render_desc *desc, lvr_ao_model *ao,
+                        float *rgba, lvr_ao_error *err);
+/* One step on a batch of n rows (1..2^20; device X bf16 bits [n][256],
+ * device y float32 [n]): forward, mean squared error, backward, and, if
+ * lr > 0, one Adam update (beta 0.9 / 0.999, eps 1e-8, bias-corrected)
+ * of the float32 masters. loss (host, may be NULL): the batch MSE before
+ * the update. grads (host or device float32 [lvr_ao_nparams()], may be
+ * NULL): d MSE / d parameter, computed with the bf16 operands of the
+ * forward pass (straight-through rounding). */
+lvr_status lvr_ao_train_step(lvr_ctx *ctx, lvr_ao_model *m, int64_t n, const uint16_t *X,
+                             const float *y, float lr, float *loss, float *grads);
+
+typedef struct lvr_ao_train_desc {
+    int64_t  n_samples;    /* samples over all sets, split evenly (>= 64) */
+    int32_t  epochs;       /* passes over the samples */
+    int32_t  batch;        /* rows per Adam step, multiple of 64, <= 65536 */
+    float    lr;           /* Adam step size */
+    uint64_t seed;         /* initial weights and sampling views */
+    int32_t  view_size;    /* square sampling views, pixels (8..4096) */
+    int32_t  depth;        /* hit index range of the samples (lvr_ao_samples) */
+    const lvr_render_desc *render;   /* sampling render: radius, TF, ERT, AO rays / radius */
+} lvr_ao_train_desc;
+/* Trains a model on traced AO: for each line set (with its LoD), seeded
+ * orbit views (40 degree field of view, distance 1.8 x half the grid
+ * diagonal) are sampled with lvr_ao_samples until the set's share of
+ * samples is collected; their inputs are built, the weights initialised
+ * uniformly in +-1/sqrt(fan_in) (zero for the padding inputs) and `epochs`
+ * passes of minibatch Adam run over a per-epoch stride permutation of the
+ * samples. *out receives the model; final_mse (host, may be NULL) its mean
+ * squared error over all samples (training forward pass). */
+lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets, const lvr_lod *const *lods,
+                        int nsets, const lvr_ao_train_desc *td, lvr_ao_model **out, float *final_mse);
 
 #ifdef __cplusplus
 }

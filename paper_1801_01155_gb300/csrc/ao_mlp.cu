@@ -1,0 +1,809 @@
+// Learned AO surrogate: model handle, per-voxel terms, batched inference,
+// training samples and the trainer (forward / backward / Adam). Layout and
+// arithmetic of the model: see ao_mlp.cuh. Tensor cores via mma.sync
+// m16n8k16 (bf16 inputs, f32 accumulation) in every contraction.
+#include <math.h>
+#include <string.h>
+
+#include <numeric>
+#include <vector>
+
+#include "ao_mlp.cuh"
+#include "lvr_internal.cuh"
+
+using namespace aomlp;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+// ------------------------------------------------------------------ parameter copies
+// bf16 weight copies, the layer-1 direction table [f] = (bf16 W1[f][0..2], b1[f])
+// and bf16-rounded W4, refreshed after every change of the masters.
+__global__ void refresh_kernel(const float *__restrict__ p, bf16 *w1b, bf16 *w2b, bf16 *w3b, float *w1t,
+                               float *w4b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NH * NIN; i += gridDim.x * blockDim.x) {
+        w1b[i] = __float2bfloat16_rn(p[OW1 + i]);
+        if (i < NH * NH) {
+            w2b[i] = __float2bfloat16_rn(p[OW2 + i]);
+            w3b[i] = __float2bfloat16_rn(p[OW3 + i]);
+        }
+        if (i < NH) {
+            w1t[4 * i + 0] = bf16_round(p[OW1 + i * NIN + 0]);
+            w1t[4 * i + 1] = bf16_round(p[OW1 + i * NIN + 1]);
+            w1t[4 * i + 2] = bf16_round(p[OW1 + i * NIN + 2]);
+            w1t[4 * i + 3] = p[OB1 + i];
+            w4b[i] = bf16_round(p[OW4 + i]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ features
+// Per voxel: (bf16 log1p(count), bf16 log1p(summed length)) packed in 32 bits.
+__global__ void logf_kernel(const uint32_t *__restrict__ cnt, const float *__restrict__ len, int64_t n,
+                            uint32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = pack_bf16x2(log1pf((float)cnt[i]), log1pf(len[i]));
+}
+
+// Neighbourhood inputs 3..252 of voxel (vx, vy, vz) into row[3..252];
+// `lane` / `nl` split the 125 neighbours over cooperating threads.
+__device__ __forceinline__ void gather_nbhd(const uint32_t *__restrict__ logf, int dx, int dy, int dz, int vx, int vy,
+                                            int vz, bf16 *row, int lane, int nl) {
+    for (int n = lane; n < 125; n += nl) {
+        const int ox = n % 5 - 2, oy = (n / 5) % 5 - 2, oz = n / 25 - 2;
+        const int X = vx + ox, Y = vy + oy, Z = vz + oz;
+        uint32_t v = 0;
+        if ((unsigned)X < (unsigned)dx && (unsigned)Y < (unsigned)dy && (unsigned)Z < (unsigned)dz)
+            v = __ldg(logf + (X + (int64_t)dx * (Y + (int64_t)dy * Z)));
+        const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&v);
+        row[3 + 2 * n] = pr.x;
+        row[4 + 2 * n] = pr.y;
+    }
+}
+
+constexpr int VT_ROW = NIN + 8;   // padded smem row (bank-conflict-free fragments)
+
+// Layer-1 voxel term for every voxel: vterm[v][f] = bf16(sum_{k>=3} W1[f][k] x_v[k]).
+// One warp per 16 voxels: gather the 16 x 256 input tile into shared memory,
+// then 8 n-tiles x 16 k-steps of mma.
+__global__ void __launch_bounds__(128)
+vterm_kernel(const uint32_t *__restrict__ logf, int dx, int dy, int dz, const bf16 *__restrict__ w1b, bf16 *vterm) {
+    __shared__ __align__(16) bf16 tile[4][16][VT_ROW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t nvox = (int64_t)dx * dy * dz;
+    bf16(*A)[VT_ROW] = tile[warp];
+    for (int64_t base = ((int64_t)blockIdx.x * 4 + warp) * 16; base < nvox; base += (int64_t)gridDim.x * 64) {
+        // zero direction and padding columns, gather the neighbourhoods (two lanes per voxel)
+        const int r = lane >> 1;
+        const int64_t v = base + r;
+        bf16 *row = A[r];
+        if ((lane & 1) == 0) {
+            row[0] = row[1] = row[2] = __float2bfloat16_rn(0.0f);
+            row[253] = row[254] = row[255] = __float2bfloat16_rn(0.0f);
+        }
+        if (v < nvox) {
+            const int vx = (int)(v % dx), vy = (int)((v / dx) % dy), vz = (int)(v / ((int64_t)dx * dy));
+            gather_nbhd(logf, dx, dy, dz, vx, vy, vz, row, lane & 1, 2);
+        } else {
+            for (int k = 3 + (lane & 1); k < 253; k += 2) row[k] = __float2bfloat16_rn(0.0f);
+        }
+        __syncwarp();
+        float acc[8][4];
+#pragma unroll
+        for (int n = 0; n < 8; n++) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
+#pragma unroll 4
+        for (int k = 0; k < NIN / 16; k++) {
+            uint32_t a[4];
+            const uint32_t *r0 = reinterpret_cast<const uint32_t *>(&A[g][k * 16]);
+            const uint32_t *r1 = reinterpret_cast<const uint32_t *>(&A[g + 8][k * 16]);
+            a[0] = r0[t];
+            a[1] = r1[t];
+            a[2] = r0[t + 4];
+            a[3] = r1[t + 4];
+#pragma unroll
+            for (int n = 0; n < 8; n++) {
+                const uint32_t *wr = reinterpret_cast<const uint32_t *>(w1b + (n * 8 + g) * NIN + k * 16);
+                mma16816(acc[n], a, __ldg(wr + t), __ldg(wr + t + 4));
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < 8; n++) {
+            if (base + g < nvox)
+                reinterpret_cast<uint32_t *>(vterm + (base + g) * NH + n * 8)[t] = pack_bf16x2(acc[n][0], acc[n][1]);
+            if (base + g + 8 < nvox)
+                reinterpret_cast<uint32_t *>(vterm + (base + g + 8) * NH + n * 8)[t] = pack_bf16x2(acc[n][2], acc[n][3]);
+        }
+        __syncwarp();
+    }
+}
+
+// Training inputs: x = (bf16 direction, neighbourhood, 0 0 0) for each sample.
+__global__ void features_kernel(const uint32_t *__restrict__ logf, int dx, int dy, int dz, int64_t n,
+                                const int32_t *__restrict__ vox, const float *__restrict__ dir, bf16 *X) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        bf16 *row = X + i * NIN;
+        const int32_t v = vox[i];
+        if (v < 0 || (int64_t)v >= (int64_t)dx * dy * dz) {   // out of range: all-zero row
+            for (int k = lane; k < NIN; k += 32) row[k] = __float2bfloat16_rn(0.0f);
+            continue;
+        }
+        if (lane == 0) {
+            float u[3], t[3];
+            unit_direction(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2], u);
+            tangent_feature(u[0], u[1], u[2], t);
+            row[0] = __float2bfloat16_rn(t[0]);
+            row[1] = __float2bfloat16_rn(t[1]);
+            row[2] = __float2bfloat16_rn(t[2]);
+            row[253] = row[254] = row[255] = __float2bfloat16_rn(0.0f);
+        }
+        const int vx = v % dx, vy = (v / dx) % dy, vz = v / (dx * dy);
+        gather_nbhd(logf, dx, dy, dz, vx, vy, vz, row, lane, 32);
+    }
+}
+
+// Learned AO of n samples (voxel, raw segment direction): the same device code
+// as the ray caster's fused inference. One warp per 16 samples.
+__global__ void __launch_bounds__(128)
+infer_kernel(Net net, const bf16 *__restrict__ vterm, int64_t nvox, int64_t n, const int32_t *__restrict__ vox,
+             const float *__restrict__ dir, float *ao) {
+    __shared__ __align__(16) bf16 tile[4][16][NH];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bf16(*h)[NH] = tile[warp];
+    for (int64_t base = ((int64_t)blockIdx.x * 4 + warp) * 16; base < n; base += (int64_t)gridDim.x * 64) {
+        const int r = lane >> 1;
+        const int64_t i = base + r;
+        if (i < n && vox[i] >= 0 && vox[i] < nvox) {
+            float u[3], t[3];
+            unit_direction(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2], u);
+            tangent_feature(u[0], u[1], u[2], t);
+            layer1_half(net, vterm + (int64_t)vox[i] * NH, t, (lane & 1) * 32, h[r]);
+        } else {
+            for (int k = (lane & 1) * 32; k < (lane & 1) * 32 + 32; k++) h[r][k] = __float2bfloat16_rn(0.0f);
+        }
+        __syncwarp();
+        float lo, hi;
+        layers234(net, &h[0][0], lo, hi);
+        if ((lane & 3) == 0) {   // out-of-range voxel ids give NaN
+            const int g = lane >> 2;
+            if (base + g < n) ao[base + g] = vox[base + g] >= 0 && vox[base + g] < nvox ? lo : __int_as_float(0x7fc00000);
+            if (base + g + 8 < n)
+                ao[base + g + 8] = vox[base + g + 8] >= 0 && vox[base + g + 8] < nvox ? hi : __int_as_float(0x7fc00000);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ trainer
+// C[z] = op(A) x op(B) over the k-range of split z (f32 partials).
+// A_COL: op(A)[m][k] = A[k * lda + m], else A[m * lda + k].
+// B_KN:  op(B)[k][n] = B[k * ldb + n], else B[n * ldb + k].
+constexpr int GT = 64, GK = 32, GKP = GK + 8;
+template <bool A_COL, bool B_KN>
+__global__ void __launch_bounds__(128)
+gemm_kernel(int M, int N, int K, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, float *C,
+            int kchunk) {
+    __shared__ __align__(16) bf16 sa[GT][GKP];
+    __shared__ __align__(16) bf16 sb[GT][GKP];
+    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT, z = blockIdx.z;
+    const int kb = z * kchunk, ke = min(K, kb + kchunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const bf16 zero = __float2bfloat16_rn(0.0f);
+    float acc[8][4];
+#pragma unroll
+    for (int n = 0; n < 8; n++) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
+    for (int k0 = kb; k0 < ke; k0 += GK) {
+        for (int i = tid; i < GT * GK; i += 128) {
+            int m, k;
+            if (A_COL) { m = i % GT; k = i / GT; } else { k = i % GK; m = i / GK; }
+            const int gm = m0 + m, gk = k0 + k;
+            sa[m][k] = (gm < M && gk < ke) ? (A_COL ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk]) : zero;
+            int nn, kk;
+            if (B_KN) { nn = i % GT; kk = i / GT; } else { kk = i % GK; nn = i / GK; }
+            const int gn = n0 + nn, gk2 = k0 + kk;
+            sb[nn][kk] = (gn < N && gk2 < ke) ? (B_KN ? B[(int64_t)gk2 * ldb + gn] : B[(int64_t)gn * ldb + gk2]) : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < GK; ks += 16) {
+            uint32_t a[4];
+            const uint32_t *r0 = reinterpret_cast<const uint32_t *>(&sa[warp * 16 + g][ks]);
+            const uint32_t *r1 = reinterpret_cast<const uint32_t *>(&sa[warp * 16 + g + 8][ks]);
+            a[0] = r0[t];
+            a[1] = r1[t];
+            a[2] = r0[t + 4];
+            a[3] = r1[t + 4];
+#pragma unroll
+            for (int n = 0; n < 8; n++) {
+                const uint32_t *br = reinterpret_cast<const uint32_t *>(&sb[n * 8 + g][ks]);
+                mma16816(acc[n], a, br[t], br[t + 4]);
+            }
+        }
+        __syncthreads();
+    }
+    float *Cz = C + (int64_t)z * M * N;
+#pragma unroll
+    for (int n = 0; n < 8; n++) {
+        const int gm = m0 + warp * 16 + g, gn = n0 + n * 8 + 2 * t;
+        if (gm < M && gn < N) { Cz[(int64_t)gm * N + gn] = acc[n][0]; if (gn + 1 < N) Cz[(int64_t)gm * N + gn + 1] = acc[n][1]; }
+        if (gm + 8 < M && gn < N) { Cz[(int64_t)(gm + 8) * N + gn] = acc[n][2]; if (gn + 1 < N) Cz[(int64_t)(gm + 8) * N + gn + 1] = acc[n][3]; }
+    }
+}
+
+// out[i] = sum_z part[z][i] (fixed order), i < n
+__global__ void sum_splits_kernel(const float *__restrict__ part, int splits, int64_t n, float *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int z = 0; z < splits; z++) s += part[(int64_t)z * n + i];
+        out[i] = s;
+    }
+}
+
+// Z [R][64] += bias, H = bf16(ReLU(Z)).
+__global__ void act_kernel(float *Z, const float *__restrict__ bias, int64_t R, bf16 *H) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R * NH; i += (int64_t)gridDim.x * blockDim.x) {
+        const float z = Z[i] + bias[i % NH];
+        Z[i] = z;
+        H[i] = __float2bfloat16_rn(fmaxf(z, 0.0f));
+    }
+}
+
+constexpr int EB = 256;   // rows per block of the row-wise kernels
+
+// Output layer and MSE: y = sigmoid(H3 . w4 + b4), dz4 = 2 (y - t) / R * y (1 - y);
+// per-block partial sums of (y - t)^2, dz4 and dz4 * H3[:, j] (for b4 and W4).
+__global__ void __launch_bounds__(EB)
+out_kernel(const bf16 *__restrict__ H3, const float *__restrict__ w4b, const float *__restrict__ b4,
+           const float *__restrict__ target, int64_t R, float *dz4, float *part /*[blocks][66]*/, float *pred) {
+    __shared__ float red[EB];
+    const int64_t r = blockIdx.x * (int64_t)EB + threadIdx.x;
+    float d = 0.0f, e2 = 0.0f;
+    if (r < R) {
+        float z = __ldg(b4);
+        for (int j = 0; j < NH; j++) z = fmaf(__bfloat162float(H3[r * NH + j]), w4b[j], z);
+        const float y = 1.0f / (1.0f + expf(-z));
+        if (pred) pred[r] = y;
+        const float e = y - (target ? target[r] : 0.0f);
+        e2 = e * e;
+        d = 2.0f * e / (float)R * y * (1.0f - y);
+        dz4[r] = d;
+    }
+    // block sums: [0] loss, [1] dz4, [2 + j] dz4 * H3[:, j]
+    for (int c = 0; c < 2 + NH; c++) {
+        float v = c == 0 ? e2 : (c == 1 ? d : (r < R ? d * __bfloat162float(H3[r * NH + c - 2]) : 0.0f));
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int s = EB / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * (2 + NH) + c] = red[0];
+        __syncthreads();
+    }
+}
+
+// dZ = dH (f32) masked by Z > 0, as bf16; per-block column sums of the f32 dZ
+// (bias gradient). For the last hidden layer dH = dz4 w4^T (outer product).
+__global__ void __launch_bounds__(EB)
+back_act_kernel(const float *__restrict__ dH, const float *__restrict__ dz4, const float *__restrict__ w4b,
+                const float *__restrict__ Z, int64_t R, bf16 *dZb, float *part /*[blocks][64]*/) {
+    __shared__ float red[EB / 64][NH + 1];
+    const int j = threadIdx.x % NH, sub = threadIdx.x / NH;
+    float s = 0.0f;
+    for (int64_t r = blockIdx.x * (int64_t)(EB / 64) * 16 + sub; r < min(R, (int64_t)(blockIdx.x + 1) * (EB / 64) * 16);
+         r += EB / 64) {
+        const int64_t i = r * NH + j;
+        const float dh = dH ? dH[i] : dz4[r] * w4b[j];
+        const float d = Z[i] > 0.0f ? dh : 0.0f;
+        dZb[i] = __float2bfloat16_rn(d);
+        s += d;
+    }
+    red[sub][j] = s;
+    __syncthreads();
+    if (sub == 0) {
+        float tsum = 0.0f;
+        for (int q = 0; q < EB / 64; q++) tsum += red[q][j];
+        part[blockIdx.x * NH + j] = tsum;
+    }
+}
+
+// sum_b part[b][c] for c < ncols into out[c] (fixed order)
+__global__ void colsum_kernel(const float *__restrict__ part, int nb, int ncols, int stride, float *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    float s = 0.0f;
+    for (int b = 0; b < nb; b++) s += part[(int64_t)b * stride + c];
+    out[c] = s;
+}
+
+__global__ void adam_kernel(float *p, const float *__restrict__ gr, float *m, float *v, int n, float lr, float c1,
+                            float c2) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float g = gr[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * g, vi = b2 * v[i] + (1.0f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// rows of the batch: X[b] = Xall[idx(b)], y[b] = yall[idx(b)], idx = (start + b) * P mod n
+__global__ void gather_rows_kernel(const bf16 *__restrict__ Xall, const float *__restrict__ yall, int64_t n,
+                                   int64_t start, int64_t P, int rows, bf16 *X, float *y) {
+    const int b = blockIdx.x;
+    if (b >= rows) return;
+    const int64_t src = (int64_t)(((uint64_t)(start + b) * (uint64_t)P) % (uint64_t)n);   // < 2^63
+    const uint4 *s = reinterpret_cast<const uint4 *>(Xall + src * NIN);
+    uint4 *d = reinterpret_cast<uint4 *>(X + (int64_t)b * NIN);
+    for (int q = threadIdx.x; q < NIN / 8; q += blockDim.x) d[q] = s[q];
+    if (threadIdx.x == 0) y[b] = yall[src];
+}
+
+// deterministic compaction of first-hit samples (voxel >= 0), one block
+__global__ void __launch_bounds__(1024)
+compact_samples_kernel(const int32_t *__restrict__ vox, const float *__restrict__ dir, const float *__restrict__ ao,
+                       int64_t n, int64_t cap, int32_t *ovox, float *odir, float *oao, int32_t *oset, int set,
+                       unsigned long long *count) {
+    __shared__ int wsum[32];
+    __shared__ unsigned long long base;
+    if (threadIdx.x == 0) base = *count;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < n; c0 += 1024) {
+        const int64_t i = c0 + threadIdx.x;
+        const int keep = i < n && vox[i] >= 0;
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) wsum[w] = __popc(ball);
+        __syncthreads();
+        int pre = 0, tot = 0;
+        for (int q = 0; q < 32; q++) { if (q < w) pre += wsum[q]; tot += wsum[q]; }
+        const unsigned long long at = base + pre + __popc(ball & ((1u << lane) - 1u));
+        if (keep && at < (unsigned long long)cap) {
+            ovox[at] = vox[i];
+            odir[3 * at] = dir[3 * i];
+            odir[3 * at + 1] = dir[3 * i + 1];
+            odir[3 * at + 2] = dir[3 * i + 2];
+            oao[at] = ao[i];
+            oset[at] = set;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base < (unsigned long long)cap ? base : (unsigned long long)cap;
+}
+
+}  // namespace
+
+Net ao_net(const lvr_ao_model *m) {
+    Net n;
+    n.w2 = (const bf16 *)m->w2b;
+    n.w3 = (const bf16 *)m->w3b;
+    n.w1t = m->w1t;
+    n.b2 = m->params + OB2;
+    n.b3 = m->params + OB3;
+    n.w4 = m->w4b;
+    n.b4 = m->params + OB4;
+    return n;
+}
+
+namespace {
+
+lvr_status refresh(lvr_ctx *ctx, lvr_ao_model *m) {
+    refresh_kernel<<<64, 256, 0, ctx->stream>>>(m->params, (bf16 *)m->w1b, (bf16 *)m->w2b, (bf16 *)m->w3b, m->w1t,
+                                                m->w4b);
+    m->bound_gen = 0;   // voxel terms depend on W1
+    LVR_CUDA(ctx, cudaGetLastError());
+    return LVR_OK;
+}
+
+lvr_status model_alloc(lvr_ctx *ctx, lvr_ao_model **out) {
+    lvr_ao_model *m = new lvr_ao_model();
+    m->ctx = ctx;
+    lvr_status st;
+    if ((st = dev_alloc(ctx, (void **)&m->params, NPARAM * 4)) != LVR_OK ||
+        (st = dev_alloc(ctx, &m->w1b, NH * NIN * 2)) != LVR_OK || (st = dev_alloc(ctx, &m->w2b, NH * NH * 2)) != LVR_OK ||
+        (st = dev_alloc(ctx, &m->w3b, NH * NH * 2)) != LVR_OK || (st = dev_alloc(ctx, (void **)&m->w1t, NH * 16)) != LVR_OK ||
+        (st = dev_alloc(ctx, (void **)&m->w4b, NH * 4)) != LVR_OK) {
+        lvr_free_ao_model(m);
+        return st;
+    }
+    *out = m;
+    return LVR_OK;
+}
+
+// Trainer scratch for one batch of R rows.
+struct Work {
+    bf16 *X, *H1, *H2, *H3, *dZ1, *dZ2, *dZ3;
+    float *y, *Z1, *Z2, *Z3, *dH, *dz4, *part, *split, *pred;
+    int splits;
+};
+
+lvr_status work_alloc(lvr_ctx *ctx, int R, Work &w, std::vector<void *> &keep) {
+    w.splits = R >= 4096 ? 32 : (R >= 1024 ? 8 : 1);
+    const size_t rb = (size_t)(R < 64 ? 64 : R);   // dH doubles as the 65-float output-layer scratch
+    const size_t nblk = (rb + EB - 1) / EB + (rb + 63) / 64 + 8;
+    struct { void **p; size_t b; } req[] = {
+        {(void **)&w.X, rb * NIN * 2}, {(void **)&w.H1, rb * NH * 2}, {(void **)&w.H2, rb * NH * 2},
+        {(void **)&w.H3, rb * NH * 2}, {(void **)&w.dZ1, rb * NH * 2}, {(void **)&w.dZ2, rb * NH * 2},
+        {(void **)&w.dZ3, rb * NH * 2}, {(void **)&w.y, rb * 4}, {(void **)&w.Z1, rb * NH * 4},
+        {(void **)&w.Z2, rb * NH * 4}, {(void **)&w.Z3, rb * NH * 4}, {(void **)&w.dH, rb * NH * 4},
+        {(void **)&w.dz4, rb * 4}, {(void **)&w.part, nblk * (NH + 2) * 4},
+        {(void **)&w.split, (size_t)w.splits * NH * NIN * 4}, {(void **)&w.pred, rb * 4}};
+    for (auto &q : req) {
+        lvr_status st = dev_alloc(ctx, q.p, q.b);
+        if (st != LVR_OK) return st;
+        keep.push_back(*q.p);
+    }
+    return LVR_OK;
+}
+
+void gemm(cudaStream_t s, bool acol, bool bkn, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
+          float *C, int splits, float *split_buf) {
+    const int kchunk = ((K + splits - 1) / splits + GK - 1) / GK * GK;
+    const int nz = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, nz);
+    float *dst = nz > 1 ? split_buf : C;
+    if (!acol && !bkn) gemm_kernel<false, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, dst, kchunk);
+    else if (!acol && bkn) gemm_kernel<false, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, dst, kchunk);
+    else if (acol && bkn) gemm_kernel<true, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, dst, kchunk);
+    else gemm_kernel<true, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, dst, kchunk);
+    if (nz > 1) sum_splits_kernel<<<grid1d((int64_t)M * N, 256), 256, 0, s>>>(split_buf, nz, (int64_t)M * N, C);
+}
+
+// One forward (and, if `grads`, backward) pass over the R rows in w.X / w.y.
+// Returns per-block loss partial sums in w.part (column 0).
+void pass(cudaStream_t s, const lvr_ao_model *m, int R, Work &w, float *grads) {
+    const float *p = m->params;
+    const bf16 *w1b = (const bf16 *)m->w1b, *w2b = (const bf16 *)m->w2b, *w3b = (const bf16 *)m->w3b;
+    const unsigned ge = grid1d((int64_t)R * NH, 256) > 4096 ? 4096 : grid1d((int64_t)R * NH, 256);
+    // forward: Z = H W^T + b, H' = bf16(ReLU(Z))
+    gemm(s, false, false, R, NH, NIN, w.X, NIN, w1b, NIN, w.Z1, 1, nullptr);
+    act_kernel<<<ge, 256, 0, s>>>(w.Z1, p + OB1, R, w.H1);
+    gemm(s, false, false, R, NH, NH, w.H1, NH, w2b, NH, w.Z2, 1, nullptr);
+    act_kernel<<<ge, 256, 0, s>>>(w.Z2, p + OB2, R, w.H2);
+    gemm(s, false, false, R, NH, NH, w.H2, NH, w3b, NH, w.Z3, 1, nullptr);
+    act_kernel<<<ge, 256, 0, s>>>(w.Z3, p + OB3, R, w.H3);
+    const int nb = (R + EB - 1) / EB;
+    out_kernel<<<nb, EB, 0, s>>>(w.H3, m->w4b, p + OB4, w.y, R, w.dz4, w.part, w.pred);
+    if (!grads) return;
+    // output layer gradients: db4, dW4
+    colsum_kernel<<<1, 128, 0, s>>>(w.part + 1, nb, 1 + NH, 2 + NH, w.dH);   // scratch: [db4, dW4...]
+    cudaMemcpyAsync(grads + OB4, w.dH, 4, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(grads + OW4, w.dH + 1, NH * 4, cudaMemcpyDeviceToDevice, s);
+    const int nb64 = (R + 63) / 64;
+    float *bpart = w.part + (size_t)nb * (2 + NH);
+    // layer 3: dZ3 = (dz4 w4) * [Z3 > 0]; dW3 = dZ3^T H2; db3
+    back_act_kernel<<<nb64, EB, 0, s>>>(nullptr, w.dz4, m->w4b, w.Z3, R, w.dZ3, bpart);
+    colsum_kernel<<<1, 64, 0, s>>>(bpart, nb64, NH, NH, grads + OB3);
+    gemm(s, true, true, NH, NH, R, w.dZ3, NH, w.H2, NH, grads + OW3, w.splits, w.split);
+    // layer 2: dH2 = dZ3 W3; dZ2 = dH2 * [Z2 > 0]; dW2 = dZ2^T H1
+    gemm(s, false, true, R, NH, NH, w.dZ3, NH, w3b, NH, w.dH, 1, nullptr);
+    back_act_kernel<<<nb64, EB, 0, s>>>(w.dH, nullptr, nullptr, w.Z2, R, w.dZ2, bpart);
+    colsum_kernel<<<1, 64, 0, s>>>(bpart, nb64, NH, NH, grads + OB2);
+    gemm(s, true, true, NH, NH, R, w.dZ2, NH, w.H1, NH, grads + OW2, w.splits, w.split);
+    // layer 1: dH1 = dZ2 W2; dZ1; dW1 = dZ1^T X
+    gemm(s, false, true, R, NH, NH, w.dZ2, NH, w2b, NH, w.dH, 1, nullptr);
+    back_act_kernel<<<nb64, EB, 0, s>>>(w.dH, nullptr, nullptr, w.Z1, R, w.dZ1, bpart);
+    colsum_kernel<<<1, 64, 0, s>>>(bpart, nb64, NH, NH, grads + OB1);
+    gemm(s, true, true, NH, NIN, R, w.dZ1, NH, w.X, NIN, grads + OW1, w.splits, w.split);
+}
+
+lvr_status adam_step(lvr_ctx *ctx, lvr_ao_model *m, float lr) {
+    if (!m->adam_m) {
+        lvr_status st;
+        if ((st = dev_alloc(ctx, (void **)&m->adam_m, NPARAM * 4)) != LVR_OK) return st;
+        if ((st = dev_alloc(ctx, (void **)&m->adam_v, NPARAM * 4)) != LVR_OK) return st;
+        LVR_CUDA(ctx, cudaMemsetAsync(m->adam_m, 0, NPARAM * 4, ctx->stream));
+        LVR_CUDA(ctx, cudaMemsetAsync(m->adam_v, 0, NPARAM * 4, ctx->stream));
+        m->adam_t = 0;
+    }
+    m->adam_t++;
+    const float c1 = 1.0f - powf(0.9f, (float)m->adam_t), c2 = 1.0f - powf(0.999f, (float)m->adam_t);
+    adam_kernel<<<64, 256, 0, ctx->stream>>>(m->params, m->grads, m->adam_m, m->adam_v, NPARAM, lr, c1, c2);
+    return refresh(ctx, m);
+}
+
+float host_loss(lvr_ctx *ctx, const Work &w, int R) {
+    const int nb = (R + EB - 1) / EB;
+    std::vector<float> part((size_t)nb * (2 + NH));
+    cudaMemcpyAsync(part.data(), w.part, part.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    double s = 0.0;
+    for (int b = 0; b < nb; b++) s += part[(size_t)b * (2 + NH)];
+    return (float)(s / R);
+}
+
+// splitmix64: counter-based generator for initial weights and sampling views
+uint64_t mix64(uint64_t x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+double unit(uint64_t seed, uint64_t i) { return (mix64(seed * 0x100000001b3ull + i) >> 11) * (1.0 / 9007199254740992.0); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ binding the voxel term
+lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod) {
+    if (m->bound_gen == lod->gen && m->vterm) return LVR_OK;
+    const int dx = lod->dims[0][0], dy = lod->dims[0][1], dz = lod->dims[0][2];
+    const int64_t nvox = (int64_t)dx * dy * dz;
+    const size_t lb = (size_t)nvox * 4, vb = (size_t)nvox * NH * 2;
+    if (m->logf_bytes < lb) {
+        dev_free(ctx, m->logf);
+        m->logf = nullptr;
+        m->logf_bytes = 0;
+        lvr_status st = dev_alloc(ctx, &m->logf, lb);
+        if (st != LVR_OK) return st;
+        m->logf_bytes = lb;
+    }
+    if (m->vterm_bytes < vb) {
+        dev_free(ctx, m->vterm);
+        m->vterm = nullptr;
+        m->vterm_bytes = 0;
+        lvr_status st = dev_alloc(ctx, &m->vterm, vb);
+        if (st != LVR_OK) return st;
+        m->vterm_bytes = vb;
+    }
+    logf_kernel<<<grid1d(nvox, 256) > 8192 ? 8192 : grid1d(nvox, 256), 256, 0, ctx->stream>>>(
+        lod->cnt[0], lod->len[0], nvox, (uint32_t *)m->logf);
+    const int64_t tiles = (nvox + 63) / 64;
+    vterm_kernel<<<(unsigned)(tiles > 65535 * 4 ? 65535 * 4 : tiles), 128, 0, ctx->stream>>>(
+        (const uint32_t *)m->logf, dx, dy, dz, (const bf16 *)m->w1b, (bf16 *)m->vterm);
+    LVR_CUDA(ctx, cudaGetLastError());
+    m->bound_gen = lod->gen;
+    return LVR_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" int lvr_ao_nparams(void) { return NPARAM; }
+
+extern "C" lvr_status lvr_ao_model_create(lvr_ctx *ctx, const float *params, lvr_ao_model **out) {
+    if (!ctx) return LVR_EINVAL;
+    if (!params || !out) return set_err(ctx, LVR_EINVAL, "lvr_ao_model_create: null argument");
+    *out = nullptr;
+    for (int i = 0; i < NPARAM; i++)
+        if (!isfinite(params[i])) return set_err(ctx, LVR_EINVAL, "parameters must be finite");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    lvr_ao_model *m;
+    lvr_status st = model_alloc(ctx, &m);
+    if (st != LVR_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(m->params, params, NPARAM * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+        lvr_free_ao_model(m);
+        return cuda_err(ctx, e, "lvr_ao_model_create");
+    }
+    if ((st = refresh(ctx, m)) != LVR_OK) {
+        lvr_free_ao_model(m);
+        return st;
+    }
+    LVR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // params came from caller memory
+    *out = m;
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_ao_model_params(lvr_ctx *ctx, const lvr_ao_model *m, float *params) {
+    if (!ctx) return LVR_EINVAL;
+    if (!m || !params) return set_err(ctx, LVR_EINVAL, "lvr_ao_model_params: null argument");
+    return copy_out(ctx, params, m->params, NPARAM * 4);
+}
+
+extern "C" void lvr_free_ao_model(lvr_ao_model *m) {
+    if (!m) return;
+    lvr_ctx *ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w1t, m->w4b, m->logf, m->vterm};
+    for (void *p : ps) dev_free(ctx, p);
+    delete m;
+}
+
+extern "C" lvr_status lvr_ao_infer(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, int64_t n,
+                                   const int32_t *voxel, const float *dir, float *ao) {
+    if (!ctx) return LVR_EINVAL;
+    if (!m || !lod || n < 0 || (n > 0 && (!voxel || !dir || !ao))) return set_err(ctx, LVR_EINVAL, "lvr_ao_infer: bad argument");
+    if (n == 0) return LVR_OK;
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t nvox = (int64_t)lod->dims[0][0] * lod->dims[0][1] * lod->dims[0][2];
+    const size_t bv = (size_t)n * 4, bd = (size_t)n * 12;
+    lvr_status st;
+    if ((st = ensure_stage_in(ctx, bv + bd + 512)) != LVR_OK) return st;
+    const void *dv, *dd;
+    if ((st = stage_input(ctx, voxel, bv, 0, &dv)) != LVR_OK) return st;
+    if ((st = stage_input(ctx, dir, bd, (bv + 255) & ~(size_t)255, &dd)) != LVR_OK) return st;
+    // voxel ids are checked on the host copy when host memory was given; on the
+    // device an id out of range gives NaN
+    if (!is_device_ptr(voxel))
+        for (int64_t i = 0; i < n; i++)
+            if (voxel[i] < 0 || voxel[i] >= nvox) return set_err(ctx, LVR_EINVAL, "voxel id out of range");
+    if ((st = ao_bind(ctx, m, lod)) != LVR_OK) return st;
+    const bool host_out = !is_device_ptr(ao);
+    float *dout = ao;
+    if (host_out) {
+        if ((st = ensure_stage_out(ctx, (size_t)n * 4)) != LVR_OK) return st;
+        dout = (float *)ctx->stage_out;
+    }
+    const int64_t tiles = (n + 63) / 64;
+    infer_kernel<<<(unsigned)(tiles > 65535 ? 65535 : tiles), 128, 0, ctx->stream>>>(
+        ao_net(m), (const bf16 *)m->vterm, nvox, n, (const int32_t *)dv, (const float *)dd, dout);
+    LVR_CUDA(ctx, cudaGetLastError());
+    if (host_out) return copy_out(ctx, ao, dout, (size_t)n * 4);
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_ao_features(lvr_ctx *ctx, const lvr_lod *lod, int64_t n, const int32_t *voxel,
+                                      const float *dir, uint16_t *X) {
+    if (!ctx) return LVR_EINVAL;
+    if (!lod || n < 0 || (n > 0 && (!voxel || !dir || !X))) return set_err(ctx, LVR_EINVAL, "lvr_ao_features: bad argument");
+    if (n == 0) return LVR_OK;
+    if (!is_device_ptr(voxel) || !is_device_ptr(dir) || !is_device_ptr(X))
+        return set_err(ctx, LVR_EINVAL, "lvr_ao_features takes device buffers");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int dx = lod->dims[0][0], dy = lod->dims[0][1], dz = lod->dims[0][2];
+    const int64_t nvox = (int64_t)dx * dy * dz;
+    lvr_status st = ensure_scratch(ctx, (size_t)nvox * 4);
+    if (st != LVR_OK) return st;
+    logf_kernel<<<grid1d(nvox, 256) > 8192 ? 8192 : grid1d(nvox, 256), 256, 0, ctx->stream>>>(
+        lod->cnt[0], lod->len[0], nvox, (uint32_t *)ctx->scratch);
+    features_kernel<<<grid1d(n * 32, 256) > 65535 ? 65535 : grid1d(n * 32, 256), 256, 0, ctx->stream>>>(
+        (const uint32_t *)ctx->scratch, dx, dy, dz, n, voxel, dir, (bf16 *)X);
+    LVR_CUDA(ctx, cudaGetLastError());
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_ao_train_step(lvr_ctx *ctx, lvr_ao_model *m, int64_t n, const uint16_t *X, const float *y,
+                                        float lr, float *loss, float *grads) {
+    if (!ctx) return LVR_EINVAL;
+    if (!m || n < 1 || n > (1 << 20) || !X || !y) return set_err(ctx, LVR_EINVAL, "lvr_ao_train_step: bad argument");
+    if (!is_device_ptr(X) || !is_device_ptr(y)) return set_err(ctx, LVR_EINVAL, "lvr_ao_train_step takes device X, y");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    lvr_status st;
+    if (!m->grads && (st = dev_alloc(ctx, (void **)&m->grads, NPARAM * 4)) != LVR_OK) return st;
+    Work w;
+    std::vector<void *> keep;
+    if ((st = work_alloc(ctx, (int)n, w, keep)) != LVR_OK) {
+        for (void *p : keep) dev_free(ctx, p);
+        return st;
+    }
+    cudaMemcpyAsync(w.X, X, (size_t)n * NIN * 2, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(w.y, y, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    pass(s, m, (int)n, w, m->grads);
+    if (loss) *loss = host_loss(ctx, w, (int)n);
+    if (grads) st = copy_out(ctx, grads, m->grads, NPARAM * 4);
+    if (st == LVR_OK && lr > 0.0f) st = adam_step(ctx, m, lr);
+    for (void *p : keep) dev_free(ctx, p);
+    LVR_CUDA(ctx, cudaGetLastError());
+    return st;
+}
+
+// hit samples of one view with traced AO (render.cu)
+lvr_status render_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
+                          const lvr_render_desc *desc, int32_t depth, uint32_t seed, int32_t *vox, float *dir,
+                          float *ao);
+
+extern "C" lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets, const lvr_lod *const *lods, int nsets,
+                                   const lvr_ao_train_desc *td, lvr_ao_model **out, float *final_mse) {
+    if (!ctx) return LVR_EINVAL;
+    if (!sets || !lods || nsets < 1 || !td || !out) return set_err(ctx, LVR_EINVAL, "lvr_train_ao: null argument");
+    *out = nullptr;
+    if (td->n_samples < 64 || td->epochs < 1 || td->batch < 64 || td->batch % 64 || td->batch > (1 << 16) ||
+        !(td->lr > 0.0f) || td->view_size < 8 || td->view_size > 4096 || !td->render || td->depth < 1)
+        return set_err(ctx, LVR_EINVAL, "lvr_train_ao: bad training description");
+    for (int i = 0; i < nsets; i++)
+        if (!sets[i] || !lods[i]) return set_err(ctx, LVR_EINVAL, "null line set or LoD");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    lvr_status st;
+    const int64_t N = td->n_samples;
+    const int V = td->view_size;
+    // sample buffers
+    int32_t *svox = nullptr, *sset = nullptr, *pvox = nullptr;
+    float *sdir = nullptr, *sao = nullptr, *pdir = nullptr, *pao = nullptr;
+    bf16 *Xall = nullptr;
+    unsigned long long *cnt = ctx->d_u64 + 4;
+    std::vector<void *> keep;
+    auto A = [&](void **p, size_t b) { st = dev_alloc(ctx, p, b); if (st == LVR_OK) keep.push_back(*p); return st == LVR_OK; };
+    auto cleanup = [&]() { for (void *p : keep) dev_free(ctx, p); };
+    if (!A((void **)&svox, N * 4) || !A((void **)&sset, N * 4) || !A((void **)&sdir, N * 12) || !A((void **)&sao, N * 4) ||
+        !A((void **)&pvox, (size_t)V * V * 4) || !A((void **)&pdir, (size_t)V * V * 12) || !A((void **)&pao, (size_t)V * V * 4) ||
+        !A((void **)&Xall, (size_t)N * NIN * 2)) {
+        cleanup();
+        return st;
+    }
+    // 1. samples: hits at random depth with traced AO from seeded orbit views of every set
+    const lvr_render_desc &rd = *td->render;
+    LVR_CUDA(ctx, cudaMemsetAsync(cnt, 0, 8, s));
+    for (int set = 0; set < nsets; set++) {
+        const int64_t goal = N * (set + 1) / nsets;
+        unsigned long long have = 0;
+        for (int v = 0; v < 4096; v++) {
+            LVR_CUDA(ctx, cudaMemcpyAsync(&have, cnt, 8, cudaMemcpyDeviceToHost, s));
+            LVR_CUDA(ctx, cudaStreamSynchronize(s));
+            if ((int64_t)have >= goal) break;
+            const lvr_lineset *ls = sets[set];
+            const double c[3] = {ls->res[0] / 2.0, ls->res[1] / 2.0, ls->res[2] / 2.0};
+            const double half = 0.5 * sqrt((double)ls->res[0] * ls->res[0] + (double)ls->res[1] * ls->res[1] +
+                                           (double)ls->res[2] * ls->res[2]);
+            const uint64_t key = ((uint64_t)set << 20) | (uint64_t)v;
+            const double az = 2.0 * M_PI * unit(td->seed, 2 * key), el = -0.6 + 1.5 * unit(td->seed, 2 * key + 1);
+            lvr_view vw;
+            memset(&vw, 0, sizeof vw);
+            const double d[3] = {cos(el) * cos(az), sin(el), cos(el) * sin(az)};
+            for (int a = 0; a < 3; a++) {
+                vw.eye[a] = (float)(c[a] + 1.8 * half * d[a]);
+                vw.at[a] = (float)c[a];
+            }
+            vw.up[1] = 1.0f;
+            vw.fovy_deg = 40.0f;
+            vw.width = vw.height = V;
+            vw.light_dir[1] = -1.0f;
+            const uint32_t vseed = (uint32_t)mix64(td->seed ^ (key * 0x2545f4914f6cdd1dull));
+            if ((st = render_samples(ctx, ls, lods[set], &vw, &rd, td->depth, vseed, pvox, pdir, pao)) != LVR_OK) {
+                cleanup();
+                return st;
+            }
+            compact_samples_kernel<<<1, 1024, 0, s>>>(pvox, pdir, pao, (int64_t)V * V, goal, svox, sdir, sao, sset, set, cnt);
+            LVR_CUDA(ctx, cudaGetLastError());
+        }
+        if ((int64_t)have < goal) {
+            cleanup();
+            return set_err(ctx, LVR_EINVAL, "line set %d: too few hits to collect samples", set);
+        }
+        // 2. features of this set's samples (its own LoD)
+        const int64_t lo = N * set / nsets;
+        const lvr_lod *lod = lods[set];
+        const int dx = lod->dims[0][0], dy = lod->dims[0][1], dz = lod->dims[0][2];
+        const int64_t nvox = (int64_t)dx * dy * dz;
+        if ((st = ensure_scratch(ctx, (size_t)nvox * 4)) != LVR_OK) { cleanup(); return st; }
+        logf_kernel<<<grid1d(nvox, 256) > 8192 ? 8192 : grid1d(nvox, 256), 256, 0, s>>>(lod->cnt[0], lod->len[0], nvox,
+                                                                                         (uint32_t *)ctx->scratch);
+        const int64_t ns = goal - lo;
+        features_kernel<<<grid1d(ns * 32, 256) > 65535 ? 65535 : grid1d(ns * 32, 256), 256, 0, s>>>(
+            (const uint32_t *)ctx->scratch, dx, dy, dz, ns, svox + lo, sdir + 3 * lo, Xall + lo * NIN);
+        LVR_CUDA(ctx, cudaGetLastError());
+    }
+    // 3. model: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases
+    std::vector<float> p0(NPARAM);
+    for (int i = 0; i < NPARAM; i++) {
+        const int fan = i < OW2 ? NIN : NH;
+        p0[i] = (float)((2.0 * unit(td->seed ^ 0x5eedull, (uint64_t)i) - 1.0) / sqrt((double)fan));
+    }
+    for (int k = 253; k < NIN; k++)
+        for (int f = 0; f < NH; f++) p0[OW1 + f * NIN + k] = 0.0f;   // padding inputs
+    lvr_ao_model *m;
+    if ((st = lvr_ao_model_create(ctx, p0.data(), &m)) != LVR_OK) { cleanup(); return st; }
+    if ((st = dev_alloc(ctx, (void **)&m->grads, NPARAM * 4)) != LVR_OK) { lvr_free_ao_model(m); cleanup(); return st; }
+    // 4. epochs of Adam over minibatches; rows in a stride permutation per epoch
+    const int R = td->batch;
+    Work w;
+    if ((st = work_alloc(ctx, R, w, keep)) != LVR_OK) { lvr_free_ao_model(m); cleanup(); return st; }
+    const int64_t steps = (N + R - 1) / R;
+    static const int64_t primes[] = {1000003, 2000003, 3000017, 4000037, 5000011, 6000011, 7000003, 8000009};
+    for (int ep = 0; ep < td->epochs; ep++) {
+        int64_t P = primes[ep % 8];
+        while (std::gcd(P, N) != 1) P += 2;
+        for (int64_t it = 0; it < steps; it++) {
+            gather_rows_kernel<<<R, 32, 0, s>>>(Xall, sao, N, it * R + ep * 7919, P, R, w.X, w.y);
+            pass(s, m, R, w, m->grads);
+            if ((st = adam_step(ctx, m, td->lr)) != LVR_OK) { lvr_free_ao_model(m); cleanup(); return st; }
+        }
+        LVR_CUDA(ctx, cudaGetLastError());
+    }
+    // 5. final mean squared error over all samples (forward only)
+    double se = 0.0;
+    for (int64_t b = 0; b < N; b += R) {
+        const int rows = (int)(N - b < R ? N - b : R);
+        gather_rows_kernel<<<rows, 32, 0, s>>>(Xall, sao, N, b, 1, rows, w.X, w.y);
+        pass(s, m, rows, w, nullptr);
+        se += (double)host_loss(ctx, w, rows) * rows;
+    }
+    if (final_mse) *final_mse = (float)(se / N);
+    cleanup();
+    LVR_CUDA(ctx, cudaStreamSynchronize(s));
+    *out = m;
+    return LVR_OK;
+}

@@ -86,8 +86,10 @@ extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int lev
             return set_err(ctx, LVR_EINVAL, "sigma must be finite and >= 0");
     LVR_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
+    static uint64_t next_gen = 0;
     lvr_lod *L = new lvr_lod();
     L->ctx = ctx;
+    L->gen = __atomic_add_fetch(&next_gen, 1, __ATOMIC_RELAXED);
     L->levels = levels;
     lvr_status st = LVR_OK;
     for (int l = 0; l < levels && st == LVR_OK; l++) {

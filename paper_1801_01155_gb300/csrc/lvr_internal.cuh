@@ -35,7 +35,7 @@ struct lvr_ctx {
     size_t stage_in_bytes = 0;
     void *stage_out = nullptr;
     size_t stage_out_bytes = 0;
-    int render_blocks = 0;                 // persistent render grid (SMs x resident blocks)
+    int render_blocks[4] = {0, 0, 0, 0};   // persistent render grid per kernel variant (SMs x resident blocks)
 };
 
 struct lvr_lineset {
@@ -53,12 +53,33 @@ struct lvr_lineset {
 
 struct lvr_lod {
     lvr_ctx *ctx = nullptr;
+    uint64_t gen = 0;             // unique per LoD built in this process
     int levels = 0;
     int32_t dims[4][3] = {};
     uint32_t *cnt[4] = {};
     float *len[4] = {};
     float *dens[4] = {};
 };
+
+struct lvr_ao_model {
+    lvr_ctx *ctx = nullptr;
+    float *params = nullptr;      // float32 masters, layout of ao_mlp.cuh
+    float *grads = nullptr;       // training: gradient of the last step
+    float *adam_m = nullptr, *adam_v = nullptr;
+    int64_t adam_t = 0;
+    void *w1b = nullptr, *w2b = nullptr, *w3b = nullptr;   // bf16 copies
+    float *w1t = nullptr, *w4b = nullptr;
+    // voxel term of the LoD the model was last bound to
+    uint64_t bound_gen = 0;
+    void *logf = nullptr;         // bf16x2 per voxel: log1p(count), log1p(length)
+    size_t logf_bytes = 0;
+    void *vterm = nullptr;        // bf16 [voxels][64]
+    size_t vterm_bytes = 0;
+};
+
+// Bind `m` to `lod`: (re)compute the per-voxel log features and layer-1
+// voxel term if the model was bound to another LoD (ao_mlp.cu).
+lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod);
 
 // ------------------------------------------------------------------ packed record
 // 64-bit segment record (Sec. 3.2 / Sec. 6.2 encoding, widened to one word):

@@ -36,6 +36,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
+#include "ao_mlp.cuh"
 #include "lvr_internal.cuh"
 
 namespace {
@@ -66,9 +69,24 @@ struct RenderParams {
     float ao_radius, ka, kd, bg[3];
     float aod[MAX_AO][3];         // hemisphere directions in the (T, B, n) frame
     float tf[1024];
-    float4 *out;
+    float4 *out;                  // may be null (sample mode)
     unsigned long long *counters;
     unsigned *tile_counter;
+    // learned AO (ao_mode 2)
+    int32_t learned;
+    aomlp::Net net;
+    const __nv_bfloat16 *vterm;
+    // sample mode: per pixel the hit of index `target` (hash of seed and
+    // pixel, mod depth) along the composited ray: voxel (-1: none), segment
+    // direction, traced AO
+    int32_t *samp_vox;
+    float *samp_dir, *samp_ao;
+    uint32_t samp_seed;
+    int32_t samp_depth;
+    // judge mode: learned vs traced AO statistics (see lvr_ao_judge)
+    unsigned long long *judge;    // [4]: hits, sum |e|, sum traced, sum learned (x 2^32)
+    unsigned *judge_max;          // max |e| as float bits
+    unsigned *judge_hist;         // [JH] histogram of |e|
 };
 
 struct Vec { float x, y, z; };
@@ -187,15 +205,27 @@ __device__ __forceinline__ bool key_after(float t, uint32_t k, float lt, uint32_
     return t > lt || (t == lt && k > lk);
 }
 
+// Kernel variants: image with traced or no AO; image with learned AO; hit
+// samples (voxel, direction, traced AO) for the learned-AO trainer; image with
+// learned AO that also traces AO at every hit and records the difference.
+enum { MODE_IMAGE = 0, MODE_LEARNED = 1, MODE_SAMPLES = 2, MODE_JUDGE = 3 };
+constexpr int JH = 4096;          // judge histogram bins over |e| in [0, 1]
+
 // Shared memory of one block: transfer function, per-lane sorted hit staging
-// and per-lane hit slots (field-major, lane-minor: conflict-free).
-enum { F_PX, F_PY, F_PZ, F_NX, F_NY, F_NZ, F_UX, F_UY, F_UZ, F_CR, F_CG, F_CB, F_AO, F_V, NF };
+// and per-lane hit slots (field-major, lane-minor: conflict-free). The hit's
+// voxel id (last field) is kept only by the variants that need it, so the
+// image variant stays within six resident blocks per SM.
+enum { F_PX, F_PY, F_PZ, F_NX, F_NY, F_NZ, F_UX, F_UY, F_UZ, F_CR, F_CG, F_CB, F_AO, F_V, F_VID, NF };
+template <int MODE>
 struct Smem {
+    static constexpr int kMode = MODE;
+    static constexpr bool kVid = MODE != MODE_IMAGE;
     float4 tf[256];
     float st[KS][RT];             // staged (t, k) of the current voxel, ascending
     uint32_t sk[KS][RT];
-    float slot[NF][KS][RT];
+    float slot[kVid ? NF : NF - 1][KS][RT];
     uint8_t item[4][32 * KS];     // per warp: (owner lane, slot) of each collected hit
+    __align__(16) __nv_bfloat16 htile[MODE == MODE_LEARNED || MODE == MODE_JUDGE ? 4 * 16 * 64 : 8];   // per warp: 16 x 64
 };
 
 struct Ray {
@@ -209,10 +239,12 @@ struct Ray {
     uint32_t rk;
     bool resume;
     bool done;
+    int hidx, target;             // sample mode: index of the next hit, index to record
 };
 
 // Phase A for one lane: traverse until KS hits are collected or the ray ends.
-__device__ __forceinline__ void voxel_step(const RenderParams &P, Smem &sm, Ray &ray, int tid, unsigned &nvox,
+template <class SM>
+__device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &ray, int tid, unsigned &nvox,
                                            unsigned &nrec, unsigned &nhit, int &used) {
     const float Da[3] = {ray.D.x, ray.D.y, ray.D.z};
     do {
@@ -297,13 +329,19 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, Smem &sm, Ray 
                     ray.A = __fadd_rn(ray.A, w);
                     if (ray.A >= P.ert) ray.done = true;
                 }
+                bool store = true;
+                if constexpr (SM::kMode == MODE_SAMPLES) {   // only the target hit, then stop
+                    store = ray.hidx == ray.target;
+                    ray.hidx++;
+                    if (store) ray.done = true;
+                }
                 if (P.nrays == 0) {
                     const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
                     const float kk = fmaf(P.kd, fabsf(dot(n, Lt)), P.ka);
                     ray.Cr = fmaf(w * c.x, kk, ray.Cr);
                     ray.Cg = fmaf(w * c.y, kk, ray.Cg);
                     ray.Cb = fmaf(w * c.z, kk, ray.Cb);
-                } else {
+                } else if (store) {
                     sm.slot[F_PX][used][tid] = (float)ray.v[0] + Pl.x;
                     sm.slot[F_PY][used][tid] = (float)ray.v[1] + Pl.y;
                     sm.slot[F_PZ][used][tid] = (float)ray.v[2] + Pl.z;
@@ -313,6 +351,7 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, Smem &sm, Ray 
                     sm.slot[F_UX][used][tid] = u.x;
                     sm.slot[F_UY][used][tid] = u.y;
                     sm.slot[F_UZ][used][tid] = u.z;
+                    if constexpr (SM::kVid) sm.slot[F_VID][used][tid] = __uint_as_float(vid);
                     sm.slot[F_CR][used][tid] = w * c.x;
                     sm.slot[F_CG][used][tid] = w * c.y;
                     sm.slot[F_CB][used][tid] = w * c.z;
@@ -345,7 +384,8 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, Smem &sm, Ray 
     } while (false);
 }
 
-__device__ int traverse(const RenderParams &P, Smem &sm, Ray &ray, int tid, unsigned &nvox, unsigned &nrec,
+template <class SM>
+__device__ int traverse(const RenderParams &P, SM &sm, Ray &ray, int tid, unsigned &nvox, unsigned &nrec,
                         unsigned &nhit) {
     int used = 0;
     if (P.nrays == 0) {
@@ -403,8 +443,10 @@ __device__ __forceinline__ float march(const RenderParams &P, Vec p, Vec d, floa
     return O;
 }
 
-__device__ __forceinline__ int slot_owner(const Smem &sm, int warp, int g) { return warp * 32 + (sm.item[warp][g] >> 3); }
-__device__ __forceinline__ int slot_index(const Smem &sm, int warp, int g) { return sm.item[warp][g] & 7; }
+template <class SM>
+__device__ __forceinline__ int slot_owner(const SM &sm, int warp, int g) { return warp * 32 + (sm.item[warp][g] >> 3); }
+template <class SM>
+__device__ __forceinline__ int slot_index(const SM &sm, int warp, int g) { return sm.item[warp][g] & 7; }
 
 // Phase B: light the warp's collected hits.
 //  - Shadows: one lane per hit, a march toward the light (Sec. 5.2).
@@ -413,7 +455,9 @@ __device__ __forceinline__ int slot_index(const Smem &sm, int warp, int g) { ret
 //    neighbourhood at the same distances; occlusion is summed over the group
 //    with a fixed butterfly, so the result does not depend on the schedule.
 //  - Each hit's weighted colour is then scaled by ka * AO + kd * V * |n.L|.
-__device__ void light_hits(const RenderParams &P, Smem &sm, int warp, int lane, int total, unsigned &nsamp) {
+template <int MODE>
+__device__ void light_hits(const RenderParams &P, Smem<MODE> &sm, int warp, int lane, int total, unsigned &nsamp,
+                           unsigned long long js[4], float &jmax) {
     const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
     if (P.shadows) {
         for (int g = lane; g < total; g += 32) {
@@ -422,7 +466,35 @@ __device__ void light_hits(const RenderParams &P, Smem &sm, int warp, int lane, 
             sm.slot[F_V][q][o] = 1.0f - fminf(1.0f, march(P, Pg, Lt, -1.0f, nsamp));
         }
     }
-    if (P.ao) {
+    if constexpr (MODE == MODE_LEARNED || MODE == MODE_JUDGE) {
+        // learned AO (Sec. 5.3 surrogate): 16 hits per step; two lanes build a
+        // hit's layer-1 row from its voxel term, then layers 2..4 on tensor
+        // cores. The judge keeps it in F_V (no shadows there) beside the traced AO.
+        constexpr int FL = MODE == MODE_JUDGE ? F_V : F_AO;
+        __nv_bfloat16 *h = sm.htile + warp * 16 * 64;
+        for (int g0 = 0; g0 < total; g0 += 16) {
+            const int r = lane >> 1, gi = g0 + r;
+            if (gi < total) {
+                const int o = slot_owner(sm, warp, gi), q = slot_index(sm, warp, gi);
+                float t[3];
+                aomlp::tangent_feature(sm.slot[F_UX][q][o], sm.slot[F_UY][q][o], sm.slot[F_UZ][q][o], t);
+                const uint32_t vid = __float_as_uint(sm.slot[F_VID][q][o]);
+                aomlp::layer1_half(P.net, P.vterm + (size_t)vid * 64, t, (lane & 1) * 32, h + r * 64);
+            } else {
+                for (int k = (lane & 1) * 32; k < (lane & 1) * 32 + 32; k++) h[r * 64 + k] = __float2bfloat16_rn(0.0f);
+            }
+            __syncwarp();
+            float lo, hi;
+            aomlp::layers234(P.net, h, lo, hi);
+            if ((lane & 3) == 0) {
+                const int g = lane >> 2;
+                if (g0 + g < total) sm.slot[FL][slot_index(sm, warp, g0 + g)][slot_owner(sm, warp, g0 + g)] = lo;
+                if (g0 + g + 8 < total) sm.slot[FL][slot_index(sm, warp, g0 + g + 8)][slot_owner(sm, warp, g0 + g + 8)] = hi;
+            }
+            __syncwarp();
+        }
+    }
+    if (MODE != MODE_LEARNED && P.ao) {
         int G = 1;
         while (G < P.ao_rays) G <<= 1;
         const int per = 32 / G, sub = lane / G, ray = lane % G;
@@ -451,8 +523,21 @@ __device__ void light_hits(const RenderParams &P, Smem &sm, int warp, int lane, 
     for (int g = lane; g < total; g += 32) {
         const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
         const Vec n = mk(sm.slot[F_NX][q][o], sm.slot[F_NY][q][o], sm.slot[F_NZ][q][o]);
-        const float AO = P.ao ? sm.slot[F_AO][q][o] : 1.0f;
-        const float V = P.shadows ? sm.slot[F_V][q][o] : 1.0f;
+        float AO, V;
+        if constexpr (MODE == MODE_JUDGE) {
+            const float tr = sm.slot[F_AO][q][o], le = sm.slot[F_V][q][o], e = fabsf(le - tr);
+            js[0] += 1ull;
+            js[1] += (unsigned long long)(e * 4294967296.0f);
+            js[2] += (unsigned long long)(tr * 4294967296.0f);
+            js[3] += (unsigned long long)(le * 4294967296.0f);
+            jmax = fmaxf(jmax, e);
+            atomicAdd(P.judge_hist + (e < 1.0f ? (int)(e * (float)JH) : JH - 1), 1u);   // NaN: last bin
+            AO = le;
+            V = 1.0f;
+        } else {
+            AO = (P.ao || MODE == MODE_LEARNED) ? sm.slot[F_AO][q][o] : 1.0f;
+            V = P.shadows ? sm.slot[F_V][q][o] : 1.0f;
+        }
         const float kk = fmaf(P.ka, AO, P.kd * V * fabsf(dot(n, Lt)));
         sm.slot[F_CR][q][o] *= kk;
         sm.slot[F_CG][q][o] *= kk;
@@ -460,14 +545,17 @@ __device__ void light_hits(const RenderParams &P, Smem &sm, int warp, int lane, 
     }
 }
 
-__global__ void __launch_bounds__(RT, 6)
+template <int MODE>
+__global__ void __launch_bounds__(RT, MODE == MODE_LEARNED || MODE == MODE_JUDGE ? 4 : 6)
 render_kernel(const __grid_constant__ RenderParams P) {
-    __shared__ Smem sm;
+    __shared__ Smem<MODE> sm;
     for (int i = threadIdx.x; i < 256; i += RT)
         sm.tf[i] = make_float4(P.tf[4 * i], P.tf[4 * i + 1], P.tf[4 * i + 2], P.tf[4 * i + 3]);
     __syncthreads();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned nvox = 0, nrec = 0, nsamp = 0, nhit = 0;
+    unsigned long long js[4] = {0ull, 0ull, 0ull, 0ull};
+    float jmax = 0.0f;
 
     for (;;) {
         unsigned tile = 0;
@@ -478,6 +566,14 @@ render_kernel(const __grid_constant__ RenderParams P) {
         const int py = (int)(tile / (unsigned)P.tiles_x) * P.tile_h + lane / P.tile_w;
         const bool valid = px < P.cw && py < P.ch;
         Ray ray;
+        ray.hidx = ray.target = 0;
+        if (MODE == MODE_SAMPLES && valid) {
+            const int64_t pix = (int64_t)py * P.cw + px;
+            P.samp_vox[pix] = -1;
+            uint32_t hsh = P.samp_seed ^ (uint32_t)pix * 0x9e3779b9u;   // integer hash (lowbias32)
+            hsh ^= hsh >> 16; hsh *= 0x7feb352du; hsh ^= hsh >> 15; hsh *= 0x846ca68bu; hsh ^= hsh >> 16;
+            ray.target = (int)(hsh % (uint32_t)P.samp_depth);
+        }
         ray.A = ray.Cr = ray.Cg = ray.Cb = 0.0f;
         ray.done = !valid;
         ray.resume = false;
@@ -551,19 +647,29 @@ render_kernel(const __grid_constant__ RenderParams P) {
                 for (int q = 0; q < used; q++) sm.item[warp][pre + q] = (uint8_t)((lane << 3) | q);
                 __syncwarp();
                 if (total > 0) {
-                    light_hits(P, sm, warp, lane, total, nsamp);
+                    light_hits(P, sm, warp, lane, total, nsamp, js, jmax);
                     __syncwarp();
                     for (int q = 0; q < used; q++) {
                         ray.Cr += sm.slot[F_CR][q][tid];
                         ray.Cg += sm.slot[F_CG][q][tid];
                         ray.Cb += sm.slot[F_CB][q][tid];
                     }
+                    if constexpr (MODE == MODE_SAMPLES) {   // the one stored hit
+                      if (used > 0) {
+                        const int64_t pix = (int64_t)py * P.cw + px;
+                        P.samp_vox[pix] = (int32_t)__float_as_uint(sm.slot[F_VID][0][tid]);
+                        P.samp_dir[3 * pix] = sm.slot[F_UX][0][tid];
+                        P.samp_dir[3 * pix + 1] = sm.slot[F_UY][0][tid];
+                        P.samp_dir[3 * pix + 2] = sm.slot[F_UZ][0][tid];
+                        P.samp_ao[pix] = sm.slot[F_AO][0][tid];
+                      }
+                    }
                 }
                 __syncwarp();
             }
             if (__all_sync(FULL, ray.done)) break;
         }
-        if (valid) {
+        if (valid && P.out) {
             const float4 o = make_float4(fmaf(1.0f - ray.A, P.bg[0], ray.Cr), fmaf(1.0f - ray.A, P.bg[1], ray.Cg),
                                          fmaf(1.0f - ray.A, P.bg[2], ray.Cb), ray.A);
             P.out[(int64_t)py * P.cw + px] = o;
@@ -579,6 +685,17 @@ render_kernel(const __grid_constant__ RenderParams P) {
             atomicAdd(P.counters + 3, (unsigned long long)c3);
         }
     }
+    if constexpr (MODE == MODE_JUDGE) {
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            for (int o = 16; o > 0; o >>= 1) js[c] += __shfl_xor_sync(FULL, js[c], o);
+        for (int o = 16; o > 0; o >>= 1) jmax = fmaxf(jmax, __shfl_xor_sync(FULL, jmax, o));
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) atomicAdd(P.judge + c, js[c]);
+            atomicMax(P.judge_max, __float_as_uint(jmax));
+        }
+    }
 }
 
 }  // namespace
@@ -589,11 +706,11 @@ static void norm3(double *a) {
     a[0] /= l; a[1] /= l; a[2] /= l;
 }
 
-extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
-                                 const lvr_view *view, const lvr_render_desc *desc,
-                                 const lvr_ao_model *ao, float *rgba, uint64_t *counters) {
-    if (!ctx) return LVR_EINVAL;
-    if (!ls || !view || !desc || !rgba) return set_err(ctx, LVR_EINVAL, "lvr_render: null argument");
+// Validates the arguments and fills the launch parameters (all but outputs).
+// `judge`: learned AO for the image plus traced AO at every hit (ao_rays).
+static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
+                        const lvr_render_desc *desc, lvr_ao_model *ao, RenderParams &P, bool judge = false) {
+    if (!ls || !view || !desc) return set_err(ctx, LVR_EINVAL, "lvr_render: null argument");
     if (view->width < 1 || view->height < 1) return set_err(ctx, LVR_EINVAL, "image size must be >= 1");
     int x0 = 0, y0 = 0, cw = view->width, ch = view->height;
     if (view->crop[2] > 0) {
@@ -604,21 +721,17 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
     if (!(desc->radius > 0.0f) || !(desc->radius < 1e3f)) return set_err(ctx, LVR_EINVAL, "radius must be > 0");
     if (!(view->fovy_deg > 0.0f && view->fovy_deg < 180.0f)) return set_err(ctx, LVR_EINVAL, "fovy out of (0,180)");
     if (desc->ao_mode < 0 || desc->ao_mode > 2) return set_err(ctx, LVR_EINVAL, "bad ao_mode");
-    if (desc->ao_mode == 2) return set_err(ctx, LVR_EINVAL, "learned AO model not available in this build");
-    (void)ao;
-    const bool need_lod = desc->shadows || desc->ao_mode == 1;
-    if (need_lod && !lod) return set_err(ctx, LVR_EINVAL, "shadows / traced AO need a LoD");
-    if (desc->ao_mode == 1 && (desc->ao_rays < 1 || desc->ao_rays > MAX_AO))
+    if (desc->ao_mode == 2 && !ao) return set_err(ctx, LVR_EINVAL, "learned AO needs a model");
+    const bool need_lod = desc->shadows || desc->ao_mode != 0;
+    if (need_lod && !lod) return set_err(ctx, LVR_EINVAL, "shadows / AO need a LoD");
+    if ((desc->ao_mode == 1 || judge) && (desc->ao_rays < 1 || desc->ao_rays > MAX_AO))
         return set_err(ctx, LVR_EINVAL, "ao_rays must be in [1,32]");
     if (lod && (lod->dims[0][0] != ls->res[0] || lod->dims[0][1] != ls->res[1] || lod->dims[0][2] != ls->res[2]))
         return set_err(ctx, LVR_EINVAL, "LoD does not belong to this line set");
     int tw = desc->tile_w, th = desc->tile_h;
     if (tw == 0 && th == 0) { tw = 8; th = 4; }
     if (tw * th != 32 || tw < 1 || th < 1) return set_err(ctx, LVR_EINVAL, "tile must have 32 pixels");
-    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t s = ctx->stream;
 
-    RenderParams P;
     memset(&P, 0, sizeof P);
     P.offset = ls->offset;
     P.rec = ls->rec;
@@ -669,9 +782,11 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
     P.opaque = desc->opaque ? 1 : 0;
     P.ert = desc->ert_alpha;
     P.shadows = desc->shadows ? 1 : 0;
-    P.ao = desc->ao_mode == 1 ? 1 : 0;
+    P.ao = desc->ao_mode == 1 || judge ? 1 : 0;
     P.ao_rays = P.ao ? desc->ao_rays : 0;
-    P.nrays = P.shadows + P.ao_rays;
+    P.learned = desc->ao_mode == 2 ? 1 : 0;
+    if (judge) P.shadows = 0;   // the judge keeps the learned AO where the visibility would go
+    P.nrays = P.shadows + P.ao_rays + P.learned;
     P.ao_radius = desc->ao_radius;
     P.ka = desc->ka;
     P.kd = desc->kd;
@@ -686,31 +801,147 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
         }
     }
     memcpy(P.tf, desc->tf_rgba, sizeof P.tf);
+    if (P.learned) {
+        lvr_status st = ao_bind(ctx, ao, lod);
+        if (st != LVR_OK) return st;
+        P.net = ao_net(ao);
+        P.vterm = (const __nv_bfloat16 *)ao->vterm;
+    }
+    return LVR_OK;
+}
 
-    const size_t out_bytes = (size_t)cw * ch * 16;
+static lvr_status launch(lvr_ctx *ctx, RenderParams &P) {
+    cudaStream_t s = ctx->stream;
+    P.tile_counter = ctx->d_status + 1;
+    LVR_CUDA(ctx, cudaMemsetAsync(P.tile_counter, 0, 4, s));
+    const int mode = P.judge ? MODE_JUDGE : (P.learned ? MODE_LEARNED : (P.samp_vox ? MODE_SAMPLES : MODE_IMAGE));
+    void (*const kern[4])(RenderParams) = {render_kernel<MODE_IMAGE>, render_kernel<MODE_LEARNED>,
+                                           render_kernel<MODE_SAMPLES>, render_kernel<MODE_JUDGE>};
+    int &blocks = ctx->render_blocks[mode];
+    if (!blocks) {
+        int sms = 0, per_sm = 0;
+        LVR_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        LVR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[mode], RT, 0));
+        blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int need = (P.ntiles + RT / 32 - 1) / (RT / 32);
+    const int grid = need < blocks ? need : blocks;
+    kern[mode]<<<grid, RT, 0, s>>>(P);
+    LVR_CUDA(ctx, cudaGetLastError());
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
+                                 const lvr_view *view, const lvr_render_desc *desc,
+                                 lvr_ao_model *ao, float *rgba, uint64_t *counters) {
+    if (!ctx) return LVR_EINVAL;
+    if (!rgba) return set_err(ctx, LVR_EINVAL, "lvr_render: null output");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    RenderParams P;
+    lvr_status st = setup(ctx, ls, lod, view, desc, ao, P);
+    if (st != LVR_OK) return st;
+    cudaStream_t s = ctx->stream;
+    const size_t out_bytes = (size_t)P.cw * P.ch * 16;
     const bool host_out = !is_device_ptr(rgba);
     const bool host_cnt = counters && !is_device_ptr(counters);
-    lvr_status st = LVR_OK;
     if (host_out && (st = ensure_stage_out(ctx, out_bytes)) != LVR_OK) return st;
     P.out = host_out ? (float4 *)ctx->stage_out : (float4 *)rgba;
     if (counters) {
         P.counters = host_cnt ? (unsigned long long *)ctx->d_u64 : (unsigned long long *)counters;
         LVR_CUDA(ctx, cudaMemsetAsync(P.counters, 0, 32, s));
     }
-    P.tile_counter = ctx->d_status + 1;
-    LVR_CUDA(ctx, cudaMemsetAsync(P.tile_counter, 0, 4, s));
-    if (!ctx->render_blocks) {
-        int sms = 0, per_sm = 0;
-        LVR_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-        LVR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel, RT, 0));
-        ctx->render_blocks = sms * (per_sm > 0 ? per_sm : 1);
-    }
-    const int need = (P.ntiles + RT / 32 - 1) / (RT / 32);
-    const int grid = need < ctx->render_blocks ? need : ctx->render_blocks;
-    render_kernel<<<grid, RT, 0, s>>>(P);
-    LVR_CUDA(ctx, cudaGetLastError());
+    if ((st = launch(ctx, P)) != LVR_OK) return st;
     if (host_out) LVR_CUDA(ctx, cudaMemcpyAsync(rgba, P.out, out_bytes, cudaMemcpyDeviceToHost, s));
     if (host_cnt) LVR_CUDA(ctx, cudaMemcpyAsync(counters, P.counters, 32, cudaMemcpyDeviceToHost, s));
     if (host_out || host_cnt) LVR_CUDA(ctx, cudaStreamSynchronize(s));
+    return LVR_OK;
+}
+
+// Hit samples of one view for the learned-AO trainer: per pixel of the crop
+// (device buffers) the hit of index hash(seed, pixel) mod depth along the ray,
+// composited as `desc` says, with traced AO: voxel (-1: none), unit segment
+// direction (entry -> exit) and traced AO.
+lvr_status render_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
+                          const lvr_render_desc *desc, int32_t depth, uint32_t seed, int32_t *vox, float *dir,
+                          float *ao) {
+    if (depth < 1) return set_err(ctx, LVR_EINVAL, "sample depth must be >= 1");
+    RenderParams P;
+    lvr_render_desc d = *desc;
+    d.ao_mode = 1;
+    d.shadows = 0;
+    lvr_status st = setup(ctx, ls, lod, view, &d, nullptr, P);
+    if (st != LVR_OK) return st;
+    P.samp_vox = vox;
+    P.samp_dir = dir;
+    P.samp_ao = ao;
+    P.samp_seed = seed;
+    P.samp_depth = depth;
+    return launch(ctx, P);
+}
+
+extern "C" lvr_status lvr_ao_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
+                                     const lvr_render_desc *desc, int32_t depth, uint32_t seed, int32_t *voxel,
+                                     float *dir, float *ao) {
+    if (!ctx) return LVR_EINVAL;
+    if (!voxel || !dir || !ao) return set_err(ctx, LVR_EINVAL, "lvr_ao_samples: null output");
+    if (!is_device_ptr(voxel) || !is_device_ptr(dir) || !is_device_ptr(ao))
+        return set_err(ctx, LVR_EINVAL, "lvr_ao_samples takes device buffers");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    return render_samples(ctx, ls, lod, view, desc, depth, seed, voxel, dir, ao);
+}
+
+extern "C" lvr_status lvr_ao_judge(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
+                                   const lvr_render_desc *desc, lvr_ao_model *ao, float *rgba, lvr_ao_error *err) {
+    if (!ctx) return LVR_EINVAL;
+    if (!err || !ao) return set_err(ctx, LVR_EINVAL, "lvr_ao_judge: null argument");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    RenderParams P;
+    lvr_render_desc d = *desc;
+    d.ao_mode = 2;
+    lvr_status st = setup(ctx, ls, lod, view, &d, ao, P, true);
+    if (st != LVR_OK) return st;
+    cudaStream_t s = ctx->stream;
+    const size_t out_bytes = (size_t)P.cw * P.ch * 16;
+    const bool host_out = rgba && !is_device_ptr(rgba);
+    if (host_out && (st = ensure_stage_out(ctx, out_bytes)) != LVR_OK) return st;
+    P.out = host_out ? (float4 *)ctx->stage_out : (float4 *)rgba;
+    unsigned *hist = nullptr;
+    if ((st = dev_alloc(ctx, (void **)&hist, JH * 4 + 64)) != LVR_OK) return st;
+    P.judge_hist = hist;
+    P.judge = (unsigned long long *)(hist + JH);
+    P.judge_max = hist + JH + 8;
+    cudaError_t e = cudaMemsetAsync(hist, 0, JH * 4 + 64, s);
+    if (e == cudaSuccess) {
+        st = launch(ctx, P);
+        e = cudaGetLastError();
+    }
+    std::vector<unsigned> h(JH + 16);
+    if (st == LVR_OK && e == cudaSuccess) e = cudaMemcpyAsync(h.data(), hist, JH * 4 + 64, cudaMemcpyDeviceToHost, s);
+    if (st == LVR_OK && e == cudaSuccess && host_out) e = cudaMemcpyAsync(rgba, P.out, out_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(ctx, hist);
+    if (st != LVR_OK) return st;
+    if (e != cudaSuccess) return cuda_err(ctx, e, "lvr_ao_judge");
+    unsigned long long js[4];
+    memcpy(js, h.data() + JH, sizeof js);
+    unsigned mx = h[JH + 8];
+    memset(err, 0, sizeof *err);
+    err->hits = js[0];
+    if (js[0]) {
+        const double sc = 1.0 / 4294967296.0 / (double)js[0];
+        err->mean_abs = (double)js[1] * sc;
+        err->mean_traced = (double)js[2] * sc;
+        err->mean_learned = (double)js[3] * sc;
+        float m;
+        memcpy(&m, &mx, 4);
+        err->max_abs = m;
+        const unsigned long long want = (js[0] * 99 + 99) / 100;   // ceil(0.99 hits)
+        unsigned long long acc = 0;
+        for (int b = 0; b < JH; b++) {
+            acc += h[b];
+            if (acc >= want) { err->p99_abs = (double)(b + 1) / JH; break; }
+        }
+        if (err->p99_abs > err->max_abs) err->p99_abs = err->max_abs;
+    }
     return LVR_OK;
 }

@@ -64,6 +64,20 @@ class RenderDesc(C.Structure):
                 ("tile_h", C.c_int32)]
 
 
+class AoTrainDesc(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("epochs", C.c_int32), ("batch", C.c_int32),
+                ("lr", C.c_float), ("seed", C.c_uint64), ("view_size", C.c_int32),
+                ("depth", C.c_int32), ("render", C.POINTER(RenderDesc))]
+
+
+class AoError(C.Structure):
+    _fields_ = [("hits", C.c_uint64), ("mean_abs", C.c_double), ("p99_abs", C.c_double),
+                ("max_abs", C.c_double), ("mean_traced", C.c_double), ("mean_learned", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp, _i64, _i32 = C.c_void_p, C.c_int64, C.c_int32
 _SIGS = {
     "lvr_version": ([], C.c_int),
@@ -82,6 +96,19 @@ _SIGS = {
     "lvr_render": ([_vp, _vp, _vp, C.POINTER(View), C.POINTER(RenderDesc), _vp, _vp, _vp], C.c_int),
     "lvr_voxelize_static": ([_vp, _vp, _vp, _i64, _i64, C.POINTER(GridDesc), _vp, _vp, _vp, _i64,
                              C.POINTER(_i64), _vp], C.c_int),
+    "lvr_ao_nparams": ([], C.c_int),
+    "lvr_ao_model_create": ([_vp, _vp, C.POINTER(_vp)], C.c_int),
+    "lvr_ao_model_params": ([_vp, _vp, _vp], C.c_int),
+    "lvr_free_ao_model": ([_vp], None),
+    "lvr_ao_infer": ([_vp, _vp, _vp, _i64, _vp, _vp, _vp], C.c_int),
+    "lvr_ao_features": ([_vp, _vp, _i64, _vp, _vp, _vp], C.c_int),
+    "lvr_ao_samples": ([_vp, _vp, _vp, C.POINTER(View), C.POINTER(RenderDesc), _i32, C.c_uint32, _vp, _vp,
+                        _vp], C.c_int),
+    "lvr_ao_judge": ([_vp, _vp, _vp, C.POINTER(View), C.POINTER(RenderDesc), _vp, _vp, C.POINTER(AoError)],
+                     C.c_int),
+    "lvr_ao_train_step": ([_vp, _vp, _i64, _vp, _vp, C.c_float, C.POINTER(C.c_float), _vp], C.c_int),
+    "lvr_train_ao": ([_vp, _vp, _vp, C.c_int, C.POINTER(AoTrainDesc), C.POINTER(_vp),
+                      C.POINTER(C.c_float)], C.c_int),
 }
 STATIC_MAX_VOXELS = 2097152
 for _n, (_a, _r) in _SIGS.items():
@@ -172,6 +199,27 @@ class Lod:
     def free(self):
         if getattr(self, "handle", None):
             _L.lvr_free_lod(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.handle:
+            self.free()
+
+
+class AoModel:
+    """lvr_ao_model: learned AO surrogate parameters on the device."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.handle = ctx, h
+
+    def params(self) -> np.ndarray:
+        out = np.empty(lvr_ao_nparams(), np.float32)
+        _check(self.ctx.handle, _L.lvr_ao_model_params(self.ctx.handle, self.handle, _ptr(out)))
+        return out
+
+    def free(self):
+        if getattr(self, "handle", None):
+            _L.lvr_free_ao_model(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -327,3 +375,81 @@ def lvr_voxelize_static(xyz, attr, curve_offsets, grid: GridDesc, offset, record
         err.n_segments = n.value
         raise err
     return n.value
+
+
+# ---------------------------------------------------------------- learned AO
+def lvr_ao_nparams() -> int:
+    return int(_L.lvr_ao_nparams())
+
+
+def lvr_ao_model_create(ctx: Context, params) -> AoModel:
+    """params: host float32 [lvr_ao_nparams()]."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.shape != (lvr_ao_nparams(),):
+        raise ValueError("params must have lvr_ao_nparams() entries")
+    h = _vp()
+    _check(ctx.handle, _L.lvr_ao_model_create(ctx.handle, _ptr(p), C.byref(h)))
+    return AoModel(ctx, h)
+
+
+def lvr_free_ao_model(m: AoModel):
+    m.free()
+
+
+def lvr_ao_infer(ctx: Context, m: AoModel, lod: Lod, voxel, dir_, ao):
+    """voxel int32 [n], dir float32 [n, 3], ao float32 [n] (host or device)."""
+    n = int(voxel.shape[0])
+    _check(ctx.handle, _L.lvr_ao_infer(ctx.handle, m.handle, lod.handle, n, _ptr(voxel), _ptr(dir_), _ptr(ao)))
+    return ao
+
+
+def lvr_ao_features(ctx: Context, lod: Lod, voxel, dir_, X):
+    """X: device int16/uint16-sized [n, 256] receiving bfloat16 bit patterns."""
+    n = int(voxel.shape[0])
+    _check(ctx.handle, _L.lvr_ao_features(ctx.handle, lod.handle, n, _ptr(voxel), _ptr(dir_), _ptr(X)))
+    return X
+
+
+def lvr_ao_samples(ctx: Context, ls: LineSet, lod: Lod, view: View, desc: RenderDesc, depth: int, seed: int,
+                   voxel, dir_, ao):
+    """Device voxel int32 [h*w], dir float32 [h*w, 3], ao float32 [h*w]: per pixel the
+    hit of index hash(seed, pixel) mod depth with its traced AO (voxel -1: none)."""
+    _check(ctx.handle, _L.lvr_ao_samples(ctx.handle, ls.handle, lod.handle, C.byref(view), C.byref(desc),
+                                         int(depth), int(seed) & 0xFFFFFFFF, _ptr(voxel), _ptr(dir_), _ptr(ao)))
+
+
+def lvr_ao_judge(ctx: Context, ls: LineSet, lod: Lod, view: View, desc: RenderDesc, m: AoModel,
+                 rgba=None) -> dict:
+    """Learned vs traced AO over every composited hit of the view (see include/lvr.h)."""
+    err = AoError()
+    _check(ctx.handle, _L.lvr_ao_judge(ctx.handle, ls.handle, lod.handle, C.byref(view), C.byref(desc),
+                                       m.handle, _ptr(rgba), C.byref(err)))
+    return err.as_dict()
+
+
+def lvr_ao_train_step(ctx: Context, m: AoModel, X, y, lr: float = 0.0, grads=None) -> float:
+    """One forward/backward (and Adam step if lr > 0) on device X [n, 256] bf16 bits, y [n]."""
+    loss = C.c_float(0.0)
+    _check(ctx.handle, _L.lvr_ao_train_step(ctx.handle, m.handle, int(X.shape[0]), _ptr(X), _ptr(y),
+                                            float(lr), C.byref(loss), _ptr(grads)))
+    return loss.value
+
+
+def lvr_train_ao(ctx: Context, sets, lods, desc: AoTrainDesc):
+    """Train a model on traced AO of the given line sets; returns (AoModel, final MSE)."""
+    n = len(sets)
+    hs = (_vp * n)(*[s.handle for s in sets])
+    hl = (_vp * n)(*[l.handle for l in lods])
+    h = _vp()
+    mse = C.c_float(0.0)
+    _check(ctx.handle, _L.lvr_train_ao(ctx.handle, hs, hl, n, C.byref(desc), C.byref(h), C.byref(mse)))
+    return AoModel(ctx, h), mse.value
+
+
+def ao_train_desc(n_samples, epochs, batch, lr, seed, render: RenderDesc, view_size=256, depth=32) -> AoTrainDesc:
+    d = AoTrainDesc()
+    d.n_samples, d.epochs, d.batch, d.lr, d.seed = int(n_samples), int(epochs), int(batch), float(lr), int(seed)
+    d.view_size, d.depth = int(view_size), int(depth)
+    d._render = render                       # keep the referenced struct alive
+    d.render = C.pointer(render)
+    return d

@@ -57,3 +57,28 @@ def test_structs_match_header_sizes(lib):
     assert C.sizeof(lib.GridDesc) == 4 * 3 + 4 + 4 + 12 + 4 + 8
     assert C.sizeof(lib.View) == 12 * 3 + 4 + 8 + 16 + 12
     assert C.sizeof(lib.RenderDesc) == 4 + 4096 + 4 + 4 + 4 + 4 + 4 + 4 + 8 + 12 + 8
+
+
+STRUCTS = {"lvr_grid_desc": "GridDesc", "lvr_lineset_info": "LineSetInfo", "lvr_lod_info": "LodInfo",
+           "lvr_view": "View", "lvr_render_desc": "RenderDesc", "lvr_ao_train_desc": "AoTrainDesc",
+           "lvr_ao_error": "AoError"}
+
+
+def test_struct_layouts_match_the_c_compiler(lib, tmp_path):
+    """Every binding struct has the size and field offsets gcc gives the header's struct."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lvr.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS.items():
+        lines.append(f'printf("{pyname} size %zu\\n", sizeof({cname}));')
+        for f, _ in getattr(lib, pyname)._fields_:
+            lines.append(f'printf("{pyname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        pyname, what, val = line.split()
+        cls = getattr(lib, pyname)
+        got = __import__("ctypes").sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert got == int(val), (pyname, what, got, val)
