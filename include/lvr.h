@@ -233,19 +233,23 @@ lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
 /* ------------------------------------------------------------------ learned ambient occlusion
  * The paper has no counterpart: a small network that predicts the traced
  * AO of Sec. 5.3 (ao_mode 1) at a hit, used by lvr_render with ao_mode 2
- * in place of the 16 marched AO rays.
+ * in place of the marched AO rays.
  *
- * Model: 256 inputs, three hidden layers of 64 with ReLU, one sigmoid
- * output. Inputs: the hit segment's unit direction (entry -> exit) with
- * its first non-zero component made positive (3); for the 5^3 level-0
- * voxels around the hit voxel (dz, dy, dx in -2..2, x fastest)
- * log1p(segment count) and log1p(summed segment length), zero outside the
- * grid (250); three zeros. Parameters: float32 [lvr_ao_nparams()] =
- * W1 [64][256], b1 [64], W2 [64][64], b2 [64], W3 [64][64], b3 [64],
- * W4 [64], b4 (row-major [out][in]), used as bfloat16 (round to nearest
- * even) in every product, with bfloat16 inputs and hidden activations and
- * float32 sums; the neighbourhood part of layer 1 is summed per voxel and
- * rounded to bfloat16 before the direction part and b1 are added. */
+ * Model: 400 inputs, three hidden layers of 64 with ReLU, one sigmoid
+ * output. Per-hit inputs 0..14: the hit segment's unit direction (entry ->
+ * exit) with its first non-zero component made positive (3), the unit
+ * tube normal at the hit (3), and for l = 0, 1, 2 the hit point's offset
+ * inside the level-l LoD cell of its voxel v, p / 2^l - floor(v / 2^l) -
+ * 1/2 per axis (9); input 15 is zero. Per-voxel inputs 16..390: for l = 0,
+ * 1, 2 the 5^3 level-l cells around v's cell (dz, dy, dx in -2..2, x
+ * fastest), log1p(8 rho), rho = dens_l / 8^l the density the AO march
+ * samples, zero outside the level; inputs 391..399 are zero. The LoD needs
+ * at least 3 levels. Parameters: float32 [lvr_ao_nparams()] = W1 [64][400],
+ * b1 [64], W2 [64][64], b2 [64], W3 [64][64], b3 [64], W4 [64], b4
+ * (row-major [out][in]), used as bfloat16 (round to nearest even) in every
+ * product, with bfloat16 inputs and hidden activations and float32 sums;
+ * the per-voxel part of layer 1 is summed per voxel and rounded to
+ * bfloat16 before the per-hit part and b1 are added. */
 int lvr_ao_nparams(void);
 /* params: host float32 [lvr_ao_nparams()], copied; must be finite. */
 lvr_status lvr_ao_model_create(lvr_ctx *ctx, const float *params, lvr_ao_model **out);
@@ -257,27 +261,32 @@ void lvr_free_ao_model(lvr_ao_model *m);
  * x + X (y + Y z), in [0, voxels): LVR_EINVAL otherwise when host memory is
  * given; NaN output for that hit when device memory is given), dir float32
  * [n][3] (segment direction, any length, normalised as d / sqrt(d.d) in
- * float32; zero gives a zero direction feature), ao float32 [n]. Host or
- * device buffers. The same device code as the fused inference in
- * lvr_render. */
+ * float32; zero gives a zero direction input), pos float32 [n][3] (hit
+ * point, grid coordinates, inside the voxel), normal float32 [n][3] (unit),
+ * ao float32 [n]. Host or device buffers. The same device code as the fused
+ * inference in lvr_render. */
 lvr_status lvr_ao_infer(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, int64_t n,
-                        const int32_t *voxel, const float *dir, float *ao);
-/* The model inputs of n hits as bfloat16 bit patterns, X uint16 [n][256];
- * device buffers only; voxel ids as for lvr_ao_infer (out of range: an
- * all-zero row). */
+                        const int32_t *voxel, const float *dir, const float *pos,
+                        const float *normal, float *ao);
+/* The model inputs of n hits as bfloat16 bit patterns, X uint16 [n][400];
+ * device buffers only; arguments as for lvr_ao_infer (a voxel id out of
+ * range gives an all-zero row). */
 lvr_status lvr_ao_features(lvr_ctx *ctx, const lvr_lod *lod, int64_t n, const int32_t *voxel,
-                           const float *dir, uint16_t *X);
+                           const float *dir, const float *pos, const float *normal, uint16_t *X);
 /* Training samples of one view with traced AO (desc's ao_rays, ao_radius,
  * radius, transfer function, opaque and ert_alpha; shadows and ao_mode are
  * ignored). Per pixel of the crop rectangle the ray is composited as usual
  * and the hit of index k = h(seed, pixel) mod depth along it (0 = first) is
  * recorded, if the ray reaches it: voxel int32 (-1: none), dir float32 [3]
  * (unit entry -> exit direction of the hit segment), ao float32 (traced AO
- * factor). h is the lowbias32 integer hash of seed ^ (pixel * 0x9e3779b9),
- * pixel = row * crop width + column. Device buffers. */
+ * factor); optionally (both or neither may be NULL) pos float32 [3] (hit
+ * point, grid coordinates) and normal float32 [3] (unit tube normal there).
+ * h is the lowbias32 integer hash of seed ^ (pixel * 0x9e3779b9), pixel =
+ * row * crop width + column. Device buffers. */
 lvr_status lvr_ao_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
                           const lvr_view *view, const lvr_render_desc *desc, int32_t depth,
-                          uint32_t seed, int32_t *voxel, float *dir, float *ao);
+                          uint32_t seed, int32_t *voxel, float *dir, float *ao, float *pos,
+                          float *normal);
 
 /* Learned against traced AO over every hit the image composites: renders
  * like lvr_render with ao_mode 2 (rgba may be NULL; host or device) and
@@ -292,7 +301,7 @@ typedef struct lvr_ao_error {
 lvr_status lvr_ao_judge(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
                         const lvr_view *view, const lvr_render_desc *desc, lvr_ao_model *ao,
                         float *rgba, lvr_ao_error *err);
-/* One step on a batch of n rows (1..2^20; device X bf16 bits [n][256],
+/* One step on a batch of n rows (1..2^20; device X bf16 bits [n][400],
  * device y float32 [n]): forward, mean squared error, backward, and, if
  * lr > 0, one Adam update (beta 0.9 / 0.999, eps 1e-8, bias-corrected)
  * of the float32 masters. loss (host, may be NULL): the batch MSE before
@@ -318,8 +327,9 @@ typedef struct lvr_ao_train_desc {
  * samples is collected; their inputs are built, the weights initialised
  * uniformly in +-1/sqrt(fan_in) (zero for the padding inputs) and `epochs`
  * passes of minibatch Adam run over a per-epoch stride permutation of the
- * samples. *out receives the model; final_mse (host, may be NULL) its mean
- * squared error over all samples (training forward pass). */
+ * samples, the step size decaying from lr to 0 along a half cosine. *out
+ * receives the model; final_mse (host, may be NULL) its mean squared error
+ * over all samples (training forward pass). */
 lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets, const lvr_lod *const *lods,
                         int nsets, const lvr_ao_train_desc *td, lvr_ao_model **out, float *final_mse);
 

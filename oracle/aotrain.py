@@ -5,8 +5,8 @@ Not part of the paper: the surrogate stands in for the traced density AO of
 Sec. 5.3. Float64 numpy, written from the model definition (reading L1 in
 aomlp.c) and the chain rule:
 
-Training forward pass (the model with bfloat16 operands; the neighbourhood
-part of layer 1 is not rounded separately here, unlike inference):
+Training forward pass (the model with bfloat16 operands; the per-voxel part
+of layer 1 is not rounded separately here, unlike inference):
     Z1 = q(X) q(W1)^T + b1,  H1 = q(ReLU(Z1))
     Z2 = H1 q(W2)^T + b2,    H2 = q(ReLU(Z2))
     Z3 = H2 q(W3)^T + b3,    H3 = q(ReLU(Z3))
@@ -30,7 +30,8 @@ from __future__ import annotations
 
 import numpy as np
 
-NIN, NH = 256, 64
+NIN, NH = 400, 64
+NHIT, VOFF = 15, 16          # per-hit inputs 0..14; per-voxel inputs from 16
 OW1 = 0
 OB1 = OW1 + NH * NIN
 OW2 = OB1 + NH
@@ -78,7 +79,7 @@ def loss(p, X, t, rnd=True) -> float:
 
 
 def loss_and_grad(p, X, t, rnd=True):
-    """(loss, gradient float64 [NPARAM]) of the batch (X [R][256], t [R])."""
+    """(loss, gradient float64 [NPARAM]) of the batch (X [R][NIN], t [R])."""
     q = bf16 if rnd else (lambda a: np.asarray(a, np.float64))
     W1, b1, W2, b2, W3, b3, W4, b4 = unpack(p)
     f = forward(p, X, rnd)

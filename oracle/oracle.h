@@ -155,10 +155,14 @@ void orc_ao_dirs(const double n[3], const double u[3], int k, double *dirs);
 
 /* ---- learned AO surrogate (reading L1; aomlp.c) ---- */
 int    orc_ao_nparams(void);
+int    orc_ao_ninputs(void);
 double orc_bf16(double x);
 void   orc_ao_tangent(const double a[3], const double b[3], double t[3]);
-void   orc_ao_features(const orc_lod *lod, int64_t voxel, const double t[3], double *x256);
-double orc_ao_mlp(const float *params, const double *x256);
+/* x: [orc_ao_ninputs()]; t tangent, n unit normal, p hit point (grid
+ * coordinates); returns -1 if the LoD has fewer than 3 levels. */
+int    orc_ao_features(const orc_lod *lod, int64_t voxel, const double t[3], const double n[3],
+                       const double p[3], double *x);
+double orc_ao_mlp(const float *params, const double *x);
 
 #ifdef __cplusplus
 }

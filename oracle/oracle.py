@@ -69,10 +69,12 @@ def lib():
         L.orc_sample.restype = C.c_double
         L.orc_ao_dirs.argtypes = [vp, vp, C.c_int, vp]
         L.orc_ao_nparams.restype = C.c_int
+        L.orc_ao_ninputs.restype = C.c_int
         L.orc_bf16.argtypes = [C.c_double]
         L.orc_bf16.restype = C.c_double
         L.orc_ao_tangent.argtypes = [vp, vp, vp]
-        L.orc_ao_features.argtypes = [vp, i64, vp, vp]
+        L.orc_ao_features.argtypes = [vp, i64, vp, vp, vp, vp]
+        L.orc_ao_features.restype = C.c_int
         L.orc_ao_mlp.argtypes = [vp, vp]
         L.orc_ao_mlp.restype = C.c_double
         _lib = L
@@ -320,10 +322,16 @@ def ao_tangent(a, b):
     return t
 
 
-def ao_features(lod: "Lod", voxel: int, t):
-    t = np.ascontiguousarray(t, np.float64)
-    x = np.empty(256)
-    lib().orc_ao_features(lod.handle, int(voxel), _p(t), _p(x))
+def ao_ninputs() -> int:
+    return lib().orc_ao_ninputs()
+
+
+def ao_features(lod: "Lod", voxel: int, t, n, p):
+    """Model inputs of a hit in `voxel`: tangent t, unit normal n, hit point p."""
+    t, n, p = (np.ascontiguousarray(a, np.float64) for a in (t, n, p))
+    x = np.empty(ao_ninputs())
+    if lib().orc_ao_features(lod.handle, int(voxel), _p(t), _p(n), _p(p), _p(x)) != 0:
+        raise ValueError("the learned AO model needs a LoD of >= 3 levels")
     return x
 
 
@@ -339,20 +347,21 @@ class _OrcLodStruct(C.Structure):
 
 
 class HandLod:
-    """A one-level orc_lod over given count / length arrays [z][y][x] (for
-    closed-form checks of the feature gather)."""
+    """An orc_lod over given per-level density sums [z][y][x] (counts and
+    lengths zero), for closed-form checks of the feature gather."""
 
-    def __init__(self, cnt, len_):
-        self._cnt = np.ascontiguousarray(cnt, np.uint32)
-        self._len = np.ascontiguousarray(len_, np.float64)
-        self._dens = np.zeros_like(self._len)
-        nz, ny, nx = self._cnt.shape
+    def __init__(self, dens_levels):
+        self._keep = []
         s = _OrcLodStruct()
-        s.levels = 1
-        s.dims[0][0], s.dims[0][1], s.dims[0][2] = nx, ny, nz
-        s.cnt[0] = self._cnt.ctypes.data
-        s.len[0] = self._len.ctypes.data
-        s.dens[0] = self._dens.ctypes.data
+        s.levels = len(dens_levels)
+        for l, d in enumerate(dens_levels):
+            d = np.ascontiguousarray(d, np.float64)
+            nz, ny, nx = d.shape
+            c = np.zeros(d.shape, np.uint32)
+            ln = np.zeros(d.shape)
+            self._keep += [d, c, ln]
+            s.dims[l][0], s.dims[l][1], s.dims[l][2] = nx, ny, nz
+            s.cnt[l], s.len[l], s.dens[l] = c.ctypes.data, ln.ctypes.data, d.ctypes.data
         self._s = s
 
     @property

@@ -427,10 +427,10 @@ static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rd
     double V = 1.0, AO = 1.0;
     if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
     if (rd->ao == 2 && L && rd->ao_params) {
-        double t[3], x[256];
+        double t[3], x[512];
         orc_ao_tangent(a, b, t);
-        orc_ao_features(L, s->voxel, t, x);
-        AO = orc_ao_mlp(rd->ao_params, x);
+        if (orc_ao_features(L, s->voxel, t, n, P, x) == 0) AO = orc_ao_mlp(rd->ao_params, x);
+        else AO = NAN;
     } else if (rd->ao && L && rd->ao_rays > 0) {
         double u[3] = {ba[0], ba[1], ba[2]};
         if (L2 > 0.0) { double l = sqrt(L2); u[0] /= l; u[1] /= l; u[2] /= l; }

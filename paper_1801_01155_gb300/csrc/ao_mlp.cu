@@ -17,82 +17,76 @@ typedef __nv_bfloat16 bf16;
 namespace {
 
 // ------------------------------------------------------------------ parameter copies
-// bf16 weight copies, the layer-1 direction table [f] = (bf16 W1[f][0..2], b1[f])
-// and bf16-rounded W4, refreshed after every change of the masters.
-__global__ void refresh_kernel(const float *__restrict__ p, bf16 *w1b, bf16 *w2b, bf16 *w3b, float *w1t,
-                               float *w4b) {
+// bf16 weight copies and bf16-rounded W4, refreshed after every change of
+// the masters.
+__global__ void refresh_kernel(const float *__restrict__ p, bf16 *w1b, bf16 *w2b, bf16 *w3b, float *w4b) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NH * NIN; i += gridDim.x * blockDim.x) {
         w1b[i] = __float2bfloat16_rn(p[OW1 + i]);
         if (i < NH * NH) {
             w2b[i] = __float2bfloat16_rn(p[OW2 + i]);
             w3b[i] = __float2bfloat16_rn(p[OW3 + i]);
         }
-        if (i < NH) {
-            w1t[4 * i + 0] = bf16_round(p[OW1 + i * NIN + 0]);
-            w1t[4 * i + 1] = bf16_round(p[OW1 + i * NIN + 1]);
-            w1t[4 * i + 2] = bf16_round(p[OW1 + i * NIN + 2]);
-            w1t[4 * i + 3] = p[OB1 + i];
-            w4b[i] = bf16_round(p[OW4 + i]);
-        }
+        if (i < NH) w4b[i] = bf16_round(p[OW4 + i]);
     }
 }
 
-// ------------------------------------------------------------------ features
-// Per voxel: (bf16 log1p(count), bf16 log1p(summed length)) packed in 32 bits.
-__global__ void logf_kernel(const uint32_t *__restrict__ cnt, const float *__restrict__ len, int64_t n,
-                            uint32_t *out) {
+// ------------------------------------------------------------------ inputs
+// Per-voxel input values of one LoD level: bf16(log1p(8 dens_l / 8^l)).
+__global__ void logd_kernel(const float *__restrict__ dens, int64_t n, float inv8l, bf16 *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = pack_bf16x2(log1pf((float)cnt[i]), log1pf(len[i]));
+        out[i] = __float2bfloat16_rn(log1pf(8.0f * (dens[i] * inv8l)));
 }
 
-// Neighbourhood inputs 3..252 of voxel (vx, vy, vz) into row[3..252];
-// `lane` / `nl` split the 125 neighbours over cooperating threads.
-__device__ __forceinline__ void gather_nbhd(const uint32_t *__restrict__ logf, int dx, int dy, int dz, int vx, int vy,
-                                            int vz, bf16 *row, int lane, int nl) {
-    for (int n = lane; n < 125; n += nl) {
-        const int ox = n % 5 - 2, oy = (n / 5) % 5 - 2, oz = n / 25 - 2;
-        const int X = vx + ox, Y = vy + oy, Z = vz + oz;
-        uint32_t v = 0;
-        if ((unsigned)X < (unsigned)dx && (unsigned)Y < (unsigned)dy && (unsigned)Z < (unsigned)dz)
-            v = __ldg(logf + (X + (int64_t)dx * (Y + (int64_t)dy * Z)));
-        const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&v);
-        row[3 + 2 * n] = pr.x;
-        row[4 + 2 * n] = pr.y;
+// The three levels' input values and dimensions.
+struct Logd {
+    const bf16 *d[3];
+    int dims[3][3];
+};
+
+// Per-voxel inputs 16..390 of voxel v into row[0..374]: for each level the
+// 5^3 cells around v's cell, x fastest; `lane` / `nl` split the work.
+__device__ __forceinline__ void gather_voxel_inputs(const Logd &L, int vx, int vy, int vz, bf16 *row, int lane,
+                                                    int nl) {
+    for (int i = lane; i < NVIN; i += nl) {
+        const int l = i / 125, n = i - 125 * l;
+        const int X = (vx >> l) + n % 5 - 2, Y = (vy >> l) + (n / 5) % 5 - 2, Z = (vz >> l) + n / 25 - 2;
+        bf16 v = __float2bfloat16_rn(0.0f);
+        if ((unsigned)X < (unsigned)L.dims[l][0] && (unsigned)Y < (unsigned)L.dims[l][1] &&
+            (unsigned)Z < (unsigned)L.dims[l][2])
+            v = L.d[l][X + (int64_t)L.dims[l][0] * (Y + (int64_t)L.dims[l][1] * Z)];
+        row[i] = v;
     }
 }
 
-constexpr int VT_ROW = NIN + 8;   // padded smem row (bank-conflict-free fragments)
+constexpr int VT_ROW = VK + 8;   // padded smem row (bank-conflict-free fragments)
 
-// Layer-1 voxel term for every voxel: vterm[v][f] = bf16(sum_{k>=3} W1[f][k] x_v[k]).
-// One warp per 16 voxels: gather the 16 x 256 input tile into shared memory,
-// then 8 n-tiles x 16 k-steps of mma.
-__global__ void __launch_bounds__(128)
-vterm_kernel(const uint32_t *__restrict__ logf, int dx, int dy, int dz, const bf16 *__restrict__ w1b, bf16 *vterm) {
-    __shared__ __align__(16) bf16 tile[4][16][VT_ROW];
+// Layer-1 voxel term for every voxel: vterm[v][f] = bf16(sum_{k>=16} W1[f][k] x_v[k]).
+// One warp per 16 voxels: gather the 16 x 384 input tile into shared memory,
+// then 8 n-tiles x 24 k-steps of mma.
+__global__ void __launch_bounds__(64)
+vterm_kernel(Logd L, const bf16 *__restrict__ w1b, bf16 *vterm) {
+    __shared__ __align__(16) bf16 tile[2][16][VT_ROW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int64_t nvox = (int64_t)dx * dy * dz;
+    const int dx = L.dims[0][0], dy = L.dims[0][1];
+    const int64_t nvox = (int64_t)dx * dy * L.dims[0][2];
     bf16(*A)[VT_ROW] = tile[warp];
-    for (int64_t base = ((int64_t)blockIdx.x * 4 + warp) * 16; base < nvox; base += (int64_t)gridDim.x * 64) {
-        // zero direction and padding columns, gather the neighbourhoods (two lanes per voxel)
-        const int r = lane >> 1;
-        const int64_t v = base + r;
-        bf16 *row = A[r];
-        if ((lane & 1) == 0) {
-            row[0] = row[1] = row[2] = __float2bfloat16_rn(0.0f);
-            row[253] = row[254] = row[255] = __float2bfloat16_rn(0.0f);
-        }
-        if (v < nvox) {
-            const int vx = (int)(v % dx), vy = (int)((v / dx) % dy), vz = (int)(v / ((int64_t)dx * dy));
-            gather_nbhd(logf, dx, dy, dz, vx, vy, vz, row, lane & 1, 2);
-        } else {
-            for (int k = 3 + (lane & 1); k < 253; k += 2) row[k] = __float2bfloat16_rn(0.0f);
+    for (int64_t base = ((int64_t)blockIdx.x * 2 + warp) * 16; base < nvox; base += (int64_t)gridDim.x * 32) {
+        for (int r = 0; r < 16; r++) {
+            const int64_t v = base + r;
+            if (v < nvox) {
+                const int vx = (int)(v % dx), vy = (int)((v / dx) % dy), vz = (int)(v / ((int64_t)dx * dy));
+                gather_voxel_inputs(L, vx, vy, vz, A[r], lane, 32);
+            } else {
+                for (int k = lane; k < NVIN; k += 32) A[r][k] = __float2bfloat16_rn(0.0f);
+            }
+            if (lane < VK - NVIN) A[r][NVIN + lane] = __float2bfloat16_rn(0.0f);
         }
         __syncwarp();
         float acc[8][4];
 #pragma unroll
         for (int n = 0; n < 8; n++) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
 #pragma unroll 4
-        for (int k = 0; k < NIN / 16; k++) {
+        for (int k = 0; k < VK / 16; k++) {
             uint32_t a[4];
             const uint32_t *r0 = reinterpret_cast<const uint32_t *>(&A[g][k * 16]);
             const uint32_t *r1 = reinterpret_cast<const uint32_t *>(&A[g + 8][k * 16]);
@@ -102,7 +96,7 @@ vterm_kernel(const uint32_t *__restrict__ logf, int dx, int dy, int dz, const bf
             a[3] = r1[t + 4];
 #pragma unroll
             for (int n = 0; n < 8; n++) {
-                const uint32_t *wr = reinterpret_cast<const uint32_t *>(w1b + (n * 8 + g) * NIN + k * 16);
+                const uint32_t *wr = reinterpret_cast<const uint32_t *>(w1b + (n * 8 + g) * NIN + VOFF + k * 16);
                 mma16816(acc[n], a, __ldg(wr + t), __ldg(wr + t + 4));
             }
         }
@@ -117,55 +111,64 @@ vterm_kernel(const uint32_t *__restrict__ logf, int dx, int dy, int dz, const bf
     }
 }
 
-// Training inputs: x = (bf16 direction, neighbourhood, 0 0 0) for each sample.
-__global__ void features_kernel(const uint32_t *__restrict__ logf, int dx, int dy, int dz, int64_t n,
-                                const int32_t *__restrict__ vox, const float *__restrict__ dir, bf16 *X) {
+// Per-hit inputs of sample i from its voxel id, raw direction, point and normal.
+__device__ __forceinline__ void sample_hit_inputs(int dx, int dy, int32_t v, const float *dir, const float *pos,
+                                                  const float *nrm, float h[NHIT]) {
+    float u[3];
+    unit_direction(dir[0], dir[1], dir[2], u);
+    hit_inputs(u[0], u[1], u[2], nrm[0], nrm[1], nrm[2], pos[0], pos[1], pos[2], v % dx, (v / dx) % dy, v / (dx * dy),
+               h);
+}
+
+// Training inputs: one warp per sample; an out-of-range voxel id gives an all-zero row.
+__global__ void features_kernel(Logd L, int64_t n, const int32_t *__restrict__ vox, const float *__restrict__ dir,
+                                const float *__restrict__ pos, const float *__restrict__ nrm, bf16 *X) {
     const int lane = threadIdx.x & 31;
+    const int dx = L.dims[0][0], dy = L.dims[0][1];
+    const int64_t nvox = (int64_t)dx * dy * L.dims[0][2];
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         bf16 *row = X + i * NIN;
         const int32_t v = vox[i];
-        if (v < 0 || (int64_t)v >= (int64_t)dx * dy * dz) {   // out of range: all-zero row
+        if (v < 0 || (int64_t)v >= nvox) {
             for (int k = lane; k < NIN; k += 32) row[k] = __float2bfloat16_rn(0.0f);
             continue;
         }
         if (lane == 0) {
-            float u[3], t[3];
-            unit_direction(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2], u);
-            tangent_feature(u[0], u[1], u[2], t);
-            row[0] = __float2bfloat16_rn(t[0]);
-            row[1] = __float2bfloat16_rn(t[1]);
-            row[2] = __float2bfloat16_rn(t[2]);
-            row[253] = row[254] = row[255] = __float2bfloat16_rn(0.0f);
+            float h[NHIT];
+            sample_hit_inputs(dx, dy, v, dir + 3 * i, pos + 3 * i, nrm + 3 * i, h);
+            for (int k = 0; k < NHIT; k++) row[k] = __float2bfloat16_rn(h[k]);
+            row[NHIT] = __float2bfloat16_rn(0.0f);
         }
-        const int vx = v % dx, vy = (v / dx) % dy, vz = v / (dx * dy);
-        gather_nbhd(logf, dx, dy, dz, vx, vy, vz, row, lane, 32);
+        if (lane < NIN - VOFF - NVIN) row[VOFF + NVIN + lane] = __float2bfloat16_rn(0.0f);
+        gather_voxel_inputs(L, v % dx, (v / dx) % dy, v / (dx * dy), row + VOFF, lane, 32);
     }
 }
 
-// Learned AO of n samples (voxel, raw segment direction): the same device code
-// as the ray caster's fused inference. One warp per 16 samples.
+// Learned AO of n samples: the same device code as the ray caster's fused
+// inference. One warp per 16 samples; out-of-range voxel ids give NaN.
 __global__ void __launch_bounds__(128)
-infer_kernel(Net net, const bf16 *__restrict__ vterm, int64_t nvox, int64_t n, const int32_t *__restrict__ vox,
-             const float *__restrict__ dir, float *ao) {
+infer_kernel(Net net, const bf16 *__restrict__ vterm, int dx, int dy, int64_t nvox, int64_t n,
+             const int32_t *__restrict__ vox, const float *__restrict__ dir, const float *__restrict__ pos,
+             const float *__restrict__ nrm, float *ao) {
     __shared__ __align__(16) bf16 tile[4][16][NH];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
     bf16(*h)[NH] = tile[warp];
+    auto ok = [&](int64_t i) { return i < n && vox[i] >= 0 && vox[i] < nvox; };
     for (int64_t base = ((int64_t)blockIdx.x * 4 + warp) * 16; base < n; base += (int64_t)gridDim.x * 64) {
-        const int r = lane >> 1;
-        const int64_t i = base + r;
-        if (i < n && vox[i] >= 0 && vox[i] < nvox) {
-            float u[3], t[3];
-            unit_direction(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2], u);
-            tangent_feature(u[0], u[1], u[2], t);
-            layer1_half(net, vterm + (int64_t)vox[i] * NH, t, (lane & 1) * 32, h[r]);
-        } else {
-            for (int k = (lane & 1) * 32; k < (lane & 1) * 32 + 32; k++) h[r][k] = __float2bfloat16_rn(0.0f);
+        if (lane < 16) {
+            const int64_t i = base + lane;
+            float hx[NHIT];
+            if (ok(i)) sample_hit_inputs(dx, dy, vox[i], dir + 3 * i, pos + 3 * i, nrm + 3 * i, hx);
+            else for (int k = 0; k < NHIT; k++) hx[k] = 0.0f;
+            store_hit_inputs(hx, h[lane]);
         }
         __syncwarp();
+        layer1_tile(net, ok(base + g) ? vterm + (int64_t)vox[base + g] * NH : nullptr,
+                    ok(base + g + 8) ? vterm + (int64_t)vox[base + g + 8] * NH : nullptr, &h[0][0]);
         float lo, hi;
         layers234(net, &h[0][0], lo, hi);
-        if ((lane & 3) == 0) {   // out-of-range voxel ids give NaN
+        if ((lane & 3) == 0) {
             const int g = lane >> 2;
             if (base + g < n) ao[base + g] = vox[base + g] >= 0 && vox[base + g] < nvox ? lo : __int_as_float(0x7fc00000);
             if (base + g + 8 < n)
@@ -344,7 +347,8 @@ __global__ void gather_rows_kernel(const bf16 *__restrict__ Xall, const float *_
 // deterministic compaction of first-hit samples (voxel >= 0), one block
 __global__ void __launch_bounds__(1024)
 compact_samples_kernel(const int32_t *__restrict__ vox, const float *__restrict__ dir, const float *__restrict__ ao,
-                       int64_t n, int64_t cap, int32_t *ovox, float *odir, float *oao, int32_t *oset, int set,
+                       const float *__restrict__ pos, const float *__restrict__ nrm, int64_t n, int64_t cap,
+                       int32_t *ovox, float *odir, float *oao, float *opos, float *onrm, int32_t *oset, int set,
                        unsigned long long *count) {
     __shared__ int wsum[32];
     __shared__ unsigned long long base;
@@ -366,6 +370,10 @@ compact_samples_kernel(const int32_t *__restrict__ vox, const float *__restrict_
             odir[3 * at + 1] = dir[3 * i + 1];
             odir[3 * at + 2] = dir[3 * i + 2];
             oao[at] = ao[i];
+            for (int c = 0; c < 3; c++) {
+                opos[3 * at + c] = pos[3 * i + c];
+                onrm[3 * at + c] = nrm[3 * i + c];
+            }
             oset[at] = set;
         }
         __syncthreads();
@@ -379,9 +387,10 @@ compact_samples_kernel(const int32_t *__restrict__ vox, const float *__restrict_
 
 Net ao_net(const lvr_ao_model *m) {
     Net n;
+    n.w1 = (const bf16 *)m->w1b;
     n.w2 = (const bf16 *)m->w2b;
     n.w3 = (const bf16 *)m->w3b;
-    n.w1t = m->w1t;
+    n.b1 = m->params + OB1;
     n.b2 = m->params + OB2;
     n.b3 = m->params + OB3;
     n.w4 = m->w4b;
@@ -392,8 +401,7 @@ Net ao_net(const lvr_ao_model *m) {
 namespace {
 
 lvr_status refresh(lvr_ctx *ctx, lvr_ao_model *m) {
-    refresh_kernel<<<64, 256, 0, ctx->stream>>>(m->params, (bf16 *)m->w1b, (bf16 *)m->w2b, (bf16 *)m->w3b, m->w1t,
-                                                m->w4b);
+    refresh_kernel<<<64, 256, 0, ctx->stream>>>(m->params, (bf16 *)m->w1b, (bf16 *)m->w2b, (bf16 *)m->w3b, m->w4b);
     m->bound_gen = 0;   // voxel terms depend on W1
     LVR_CUDA(ctx, cudaGetLastError());
     return LVR_OK;
@@ -405,8 +413,7 @@ lvr_status model_alloc(lvr_ctx *ctx, lvr_ao_model **out) {
     lvr_status st;
     if ((st = dev_alloc(ctx, (void **)&m->params, NPARAM * 4)) != LVR_OK ||
         (st = dev_alloc(ctx, &m->w1b, NH * NIN * 2)) != LVR_OK || (st = dev_alloc(ctx, &m->w2b, NH * NH * 2)) != LVR_OK ||
-        (st = dev_alloc(ctx, &m->w3b, NH * NH * 2)) != LVR_OK || (st = dev_alloc(ctx, (void **)&m->w1t, NH * 16)) != LVR_OK ||
-        (st = dev_alloc(ctx, (void **)&m->w4b, NH * 4)) != LVR_OK) {
+        (st = dev_alloc(ctx, &m->w3b, NH * NH * 2)) != LVR_OK || (st = dev_alloc(ctx, (void **)&m->w4b, NH * 4)) != LVR_OK) {
         lvr_free_ao_model(m);
         return st;
     }
@@ -528,32 +535,52 @@ double unit(uint64_t seed, uint64_t i) { return (mix64(seed * 0x100000001b3ull +
 }  // namespace
 
 // ------------------------------------------------------------------ binding the voxel term
+// The three levels' input values of a LoD into `buf` (bf16, levels back to back).
+static lvr_status make_logd(lvr_ctx *ctx, const lvr_lod *lod, void **buf, size_t *bytes, Logd &L) {
+    if (lod->levels < 3) return set_err(ctx, LVR_EINVAL, "learned AO needs a LoD of >= 3 levels");
+    size_t off[3], tot = 0;
+    int64_t cnt[3];
+    for (int l = 0; l < 3; l++) {
+        cnt[l] = (int64_t)lod->dims[l][0] * lod->dims[l][1] * lod->dims[l][2];
+        off[l] = tot;
+        tot += ((size_t)cnt[l] * 2 + 255) & ~(size_t)255;
+        for (int a = 0; a < 3; a++) L.dims[l][a] = lod->dims[l][a];
+    }
+    if (*bytes < tot) {
+        dev_free(ctx, *buf);
+        *buf = nullptr;
+        *bytes = 0;
+        lvr_status st = dev_alloc(ctx, buf, tot);
+        if (st != LVR_OK) return st;
+        *bytes = tot;
+    }
+    for (int l = 0; l < 3; l++) {
+        bf16 *d = (bf16 *)((char *)*buf + off[l]);
+        L.d[l] = d;
+        const unsigned g = grid1d(cnt[l], 256) > 8192 ? 8192 : grid1d(cnt[l], 256);
+        logd_kernel<<<g, 256, 0, ctx->stream>>>(lod->dens[l], cnt[l], 1.0f / (float)(1 << (3 * l)), d);
+    }
+    LVR_CUDA(ctx, cudaGetLastError());
+    return LVR_OK;
+}
+
 lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod) {
     if (m->bound_gen == lod->gen && m->vterm) return LVR_OK;
-    const int dx = lod->dims[0][0], dy = lod->dims[0][1], dz = lod->dims[0][2];
-    const int64_t nvox = (int64_t)dx * dy * dz;
-    const size_t lb = (size_t)nvox * 4, vb = (size_t)nvox * NH * 2;
-    if (m->logf_bytes < lb) {
-        dev_free(ctx, m->logf);
-        m->logf = nullptr;
-        m->logf_bytes = 0;
-        lvr_status st = dev_alloc(ctx, &m->logf, lb);
-        if (st != LVR_OK) return st;
-        m->logf_bytes = lb;
-    }
+    Logd L;
+    lvr_status st = make_logd(ctx, lod, &m->logd, &m->logd_bytes, L);
+    if (st != LVR_OK) return st;
+    const int64_t nvox = (int64_t)lod->dims[0][0] * lod->dims[0][1] * lod->dims[0][2];
+    const size_t vb = (size_t)nvox * NH * 2;
     if (m->vterm_bytes < vb) {
         dev_free(ctx, m->vterm);
         m->vterm = nullptr;
         m->vterm_bytes = 0;
-        lvr_status st = dev_alloc(ctx, &m->vterm, vb);
-        if (st != LVR_OK) return st;
+        if ((st = dev_alloc(ctx, &m->vterm, vb)) != LVR_OK) return st;
         m->vterm_bytes = vb;
     }
-    logf_kernel<<<grid1d(nvox, 256) > 8192 ? 8192 : grid1d(nvox, 256), 256, 0, ctx->stream>>>(
-        lod->cnt[0], lod->len[0], nvox, (uint32_t *)m->logf);
-    const int64_t tiles = (nvox + 63) / 64;
-    vterm_kernel<<<(unsigned)(tiles > 65535 * 4 ? 65535 * 4 : tiles), 128, 0, ctx->stream>>>(
-        (const uint32_t *)m->logf, dx, dy, dz, (const bf16 *)m->w1b, (bf16 *)m->vterm);
+    const int64_t tiles = (nvox + 31) / 32;
+    vterm_kernel<<<(unsigned)(tiles > 65535 * 8 ? 65535 * 8 : tiles), 64, 0, ctx->stream>>>(L, (const bf16 *)m->w1b,
+                                                                                              (bf16 *)m->vterm);
     LVR_CUDA(ctx, cudaGetLastError());
     m->bound_gen = lod->gen;
     return LVR_OK;
@@ -596,24 +623,29 @@ extern "C" void lvr_free_ao_model(lvr_ao_model *m) {
     if (!m) return;
     lvr_ctx *ctx = m->ctx;
     cudaSetDevice(ctx->device);
-    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w1t, m->w4b, m->logf, m->vterm};
+    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w4b, m->logd, m->vterm};
     for (void *p : ps) dev_free(ctx, p);
     delete m;
 }
 
 extern "C" lvr_status lvr_ao_infer(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, int64_t n,
-                                   const int32_t *voxel, const float *dir, float *ao) {
+                                   const int32_t *voxel, const float *dir, const float *pos, const float *normal,
+                                   float *ao) {
     if (!ctx) return LVR_EINVAL;
-    if (!m || !lod || n < 0 || (n > 0 && (!voxel || !dir || !ao))) return set_err(ctx, LVR_EINVAL, "lvr_ao_infer: bad argument");
+    if (!m || !lod || n < 0 || (n > 0 && (!voxel || !dir || !pos || !normal || !ao)))
+        return set_err(ctx, LVR_EINVAL, "lvr_ao_infer: bad argument");
     if (n == 0) return LVR_OK;
     LVR_CUDA(ctx, cudaSetDevice(ctx->device));
-    const int64_t nvox = (int64_t)lod->dims[0][0] * lod->dims[0][1] * lod->dims[0][2];
-    const size_t bv = (size_t)n * 4, bd = (size_t)n * 12;
+    const int dx = lod->dims[0][0], dy = lod->dims[0][1];
+    const int64_t nvox = (int64_t)dx * dy * lod->dims[0][2];
+    const size_t bv = ((size_t)n * 4 + 255) & ~(size_t)255, b3 = ((size_t)n * 12 + 255) & ~(size_t)255;
     lvr_status st;
-    if ((st = ensure_stage_in(ctx, bv + bd + 512)) != LVR_OK) return st;
-    const void *dv, *dd;
-    if ((st = stage_input(ctx, voxel, bv, 0, &dv)) != LVR_OK) return st;
-    if ((st = stage_input(ctx, dir, bd, (bv + 255) & ~(size_t)255, &dd)) != LVR_OK) return st;
+    if ((st = ensure_stage_in(ctx, bv + 3 * b3)) != LVR_OK) return st;
+    const void *dv, *dd, *dp, *dn;
+    if ((st = stage_input(ctx, voxel, (size_t)n * 4, 0, &dv)) != LVR_OK) return st;
+    if ((st = stage_input(ctx, dir, (size_t)n * 12, bv, &dd)) != LVR_OK) return st;
+    if ((st = stage_input(ctx, pos, (size_t)n * 12, bv + b3, &dp)) != LVR_OK) return st;
+    if ((st = stage_input(ctx, normal, (size_t)n * 12, bv + 2 * b3, &dn)) != LVR_OK) return st;
     // voxel ids are checked on the host copy when host memory was given; on the
     // device an id out of range gives NaN
     if (!is_device_ptr(voxel))
@@ -628,30 +660,35 @@ extern "C" lvr_status lvr_ao_infer(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod 
     }
     const int64_t tiles = (n + 63) / 64;
     infer_kernel<<<(unsigned)(tiles > 65535 ? 65535 : tiles), 128, 0, ctx->stream>>>(
-        ao_net(m), (const bf16 *)m->vterm, nvox, n, (const int32_t *)dv, (const float *)dd, dout);
+        ao_net(m), (const bf16 *)m->vterm, dx, dy, nvox, n, (const int32_t *)dv, (const float *)dd,
+        (const float *)dp, (const float *)dn, dout);
     LVR_CUDA(ctx, cudaGetLastError());
     if (host_out) return copy_out(ctx, ao, dout, (size_t)n * 4);
     return LVR_OK;
 }
 
 extern "C" lvr_status lvr_ao_features(lvr_ctx *ctx, const lvr_lod *lod, int64_t n, const int32_t *voxel,
-                                      const float *dir, uint16_t *X) {
+                                      const float *dir, const float *pos, const float *normal, uint16_t *X) {
     if (!ctx) return LVR_EINVAL;
-    if (!lod || n < 0 || (n > 0 && (!voxel || !dir || !X))) return set_err(ctx, LVR_EINVAL, "lvr_ao_features: bad argument");
+    if (!lod || n < 0 || (n > 0 && (!voxel || !dir || !pos || !normal || !X)))
+        return set_err(ctx, LVR_EINVAL, "lvr_ao_features: bad argument");
     if (n == 0) return LVR_OK;
-    if (!is_device_ptr(voxel) || !is_device_ptr(dir) || !is_device_ptr(X))
+    if (!is_device_ptr(voxel) || !is_device_ptr(dir) || !is_device_ptr(pos) || !is_device_ptr(normal) ||
+        !is_device_ptr(X))
         return set_err(ctx, LVR_EINVAL, "lvr_ao_features takes device buffers");
     LVR_CUDA(ctx, cudaSetDevice(ctx->device));
-    const int dx = lod->dims[0][0], dy = lod->dims[0][1], dz = lod->dims[0][2];
-    const int64_t nvox = (int64_t)dx * dy * dz;
-    lvr_status st = ensure_scratch(ctx, (size_t)nvox * 4);
-    if (st != LVR_OK) return st;
-    logf_kernel<<<grid1d(nvox, 256) > 8192 ? 8192 : grid1d(nvox, 256), 256, 0, ctx->stream>>>(
-        lod->cnt[0], lod->len[0], nvox, (uint32_t *)ctx->scratch);
-    features_kernel<<<grid1d(n * 32, 256) > 65535 ? 65535 : grid1d(n * 32, 256), 256, 0, ctx->stream>>>(
-        (const uint32_t *)ctx->scratch, dx, dy, dz, n, voxel, dir, (bf16 *)X);
-    LVR_CUDA(ctx, cudaGetLastError());
-    return LVR_OK;
+    void *buf = nullptr;
+    size_t bytes = 0;
+    Logd L;
+    lvr_status st = make_logd(ctx, lod, &buf, &bytes, L);
+    if (st == LVR_OK) {
+        const unsigned g = grid1d(n * 32, 256) > 65535 ? 65535 : grid1d(n * 32, 256);
+        features_kernel<<<g, 256, 0, ctx->stream>>>(L, n, voxel, dir, pos, normal, (bf16 *)X);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_err(ctx, e, "lvr_ao_features");
+    }
+    dev_free(ctx, buf);
+    return st;
 }
 
 extern "C" lvr_status lvr_ao_train_step(lvr_ctx *ctx, lvr_ao_model *m, int64_t n, const uint16_t *X, const float *y,
@@ -683,7 +720,7 @@ extern "C" lvr_status lvr_ao_train_step(lvr_ctx *ctx, lvr_ao_model *m, int64_t n
 // hit samples of one view with traced AO (render.cu)
 lvr_status render_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
                           const lvr_render_desc *desc, int32_t depth, uint32_t seed, int32_t *vox, float *dir,
-                          float *ao);
+                          float *ao, float *pos, float *nrm);
 
 extern "C" lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets, const lvr_lod *const *lods, int nsets,
                                    const lvr_ao_train_desc *td, lvr_ao_model **out, float *final_mse) {
@@ -702,15 +739,23 @@ extern "C" lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets,
     const int V = td->view_size;
     // sample buffers
     int32_t *svox = nullptr, *sset = nullptr, *pvox = nullptr;
-    float *sdir = nullptr, *sao = nullptr, *pdir = nullptr, *pao = nullptr;
+    float *sdir = nullptr, *sao = nullptr, *spos = nullptr, *snrm = nullptr;
+    float *pdir = nullptr, *pao = nullptr, *ppos = nullptr, *pnrm = nullptr;
     bf16 *Xall = nullptr;
+    void *logd = nullptr;
+    size_t logd_bytes = 0;
     unsigned long long *cnt = ctx->d_u64 + 4;
     std::vector<void *> keep;
     auto A = [&](void **p, size_t b) { st = dev_alloc(ctx, p, b); if (st == LVR_OK) keep.push_back(*p); return st == LVR_OK; };
-    auto cleanup = [&]() { for (void *p : keep) dev_free(ctx, p); };
+    auto cleanup = [&]() {
+        for (void *p : keep) dev_free(ctx, p);
+        dev_free(ctx, logd);
+    };
+    const size_t VV = (size_t)V * V;
     if (!A((void **)&svox, N * 4) || !A((void **)&sset, N * 4) || !A((void **)&sdir, N * 12) || !A((void **)&sao, N * 4) ||
-        !A((void **)&pvox, (size_t)V * V * 4) || !A((void **)&pdir, (size_t)V * V * 12) || !A((void **)&pao, (size_t)V * V * 4) ||
-        !A((void **)&Xall, (size_t)N * NIN * 2)) {
+        !A((void **)&spos, N * 12) || !A((void **)&snrm, N * 12) || !A((void **)&pvox, VV * 4) ||
+        !A((void **)&pdir, VV * 12) || !A((void **)&pao, VV * 4) || !A((void **)&ppos, VV * 12) ||
+        !A((void **)&pnrm, VV * 12) || !A((void **)&Xall, (size_t)N * NIN * 2)) {
         cleanup();
         return st;
     }
@@ -742,11 +787,12 @@ extern "C" lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets,
             vw.width = vw.height = V;
             vw.light_dir[1] = -1.0f;
             const uint32_t vseed = (uint32_t)mix64(td->seed ^ (key * 0x2545f4914f6cdd1dull));
-            if ((st = render_samples(ctx, ls, lods[set], &vw, &rd, td->depth, vseed, pvox, pdir, pao)) != LVR_OK) {
+            if ((st = render_samples(ctx, ls, lods[set], &vw, &rd, td->depth, vseed, pvox, pdir, pao, ppos, pnrm)) != LVR_OK) {
                 cleanup();
                 return st;
             }
-            compact_samples_kernel<<<1, 1024, 0, s>>>(pvox, pdir, pao, (int64_t)V * V, goal, svox, sdir, sao, sset, set, cnt);
+            compact_samples_kernel<<<1, 1024, 0, s>>>(pvox, pdir, pao, ppos, pnrm, (int64_t)VV, goal, svox, sdir, sao,
+                                                      spos, snrm, sset, set, cnt);
             LVR_CUDA(ctx, cudaGetLastError());
         }
         if ((int64_t)have < goal) {
@@ -755,15 +801,11 @@ extern "C" lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets,
         }
         // 2. features of this set's samples (its own LoD)
         const int64_t lo = N * set / nsets;
-        const lvr_lod *lod = lods[set];
-        const int dx = lod->dims[0][0], dy = lod->dims[0][1], dz = lod->dims[0][2];
-        const int64_t nvox = (int64_t)dx * dy * dz;
-        if ((st = ensure_scratch(ctx, (size_t)nvox * 4)) != LVR_OK) { cleanup(); return st; }
-        logf_kernel<<<grid1d(nvox, 256) > 8192 ? 8192 : grid1d(nvox, 256), 256, 0, s>>>(lod->cnt[0], lod->len[0], nvox,
-                                                                                         (uint32_t *)ctx->scratch);
+        Logd L;
+        if ((st = make_logd(ctx, lods[set], &logd, &logd_bytes, L)) != LVR_OK) { cleanup(); return st; }
         const int64_t ns = goal - lo;
         features_kernel<<<grid1d(ns * 32, 256) > 65535 ? 65535 : grid1d(ns * 32, 256), 256, 0, s>>>(
-            (const uint32_t *)ctx->scratch, dx, dy, dz, ns, svox + lo, sdir + 3 * lo, Xall + lo * NIN);
+            L, ns, svox + lo, sdir + 3 * lo, spos + 3 * lo, snrm + 3 * lo, Xall + lo * NIN);
         LVR_CUDA(ctx, cudaGetLastError());
     }
     // 3. model: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases
@@ -772,8 +814,10 @@ extern "C" lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets,
         const int fan = i < OW2 ? NIN : NH;
         p0[i] = (float)((2.0 * unit(td->seed ^ 0x5eedull, (uint64_t)i) - 1.0) / sqrt((double)fan));
     }
-    for (int k = 253; k < NIN; k++)
-        for (int f = 0; f < NH; f++) p0[OW1 + f * NIN + k] = 0.0f;   // padding inputs
+    for (int f = 0; f < NH; f++) {   // padding inputs
+        p0[OW1 + f * NIN + NHIT] = 0.0f;
+        for (int k = VOFF + NVIN; k < NIN; k++) p0[OW1 + f * NIN + k] = 0.0f;
+    }
     lvr_ao_model *m;
     if ((st = lvr_ao_model_create(ctx, p0.data(), &m)) != LVR_OK) { cleanup(); return st; }
     if ((st = dev_alloc(ctx, (void **)&m->grads, NPARAM * 4)) != LVR_OK) { lvr_free_ao_model(m); cleanup(); return st; }
@@ -783,13 +827,17 @@ extern "C" lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets,
     if ((st = work_alloc(ctx, R, w, keep)) != LVR_OK) { lvr_free_ao_model(m); cleanup(); return st; }
     const int64_t steps = (N + R - 1) / R;
     static const int64_t primes[] = {1000003, 2000003, 3000017, 4000037, 5000011, 6000011, 7000003, 8000009};
+    const double total = (double)steps * td->epochs;
     for (int ep = 0; ep < td->epochs; ep++) {
         int64_t P = primes[ep % 8];
         while (std::gcd(P, N) != 1) P += 2;
         for (int64_t it = 0; it < steps; it++) {
+            // step size: cosine decay from lr to 0 over all steps
+            const double k = (double)(ep * steps + it) / total;
+            const float lr = (float)(td->lr * 0.5 * (1.0 + cos(M_PI * k)));
             gather_rows_kernel<<<R, 32, 0, s>>>(Xall, sao, N, it * R + ep * 7919, P, R, w.X, w.y);
             pass(s, m, R, w, m->grads);
-            if ((st = adam_step(ctx, m, td->lr)) != LVR_OK) { lvr_free_ao_model(m); cleanup(); return st; }
+            if ((st = adam_step(ctx, m, lr)) != LVR_OK) { lvr_free_ao_model(m); cleanup(); return st; }
         }
         LVR_CUDA(ctx, cudaGetLastError());
     }

@@ -4,16 +4,19 @@
 // (render.cu). Not part of the paper: the surrogate stands in for the traced
 // density AO of Sec. 5.3.
 //
-// Model (inputs 256 = 3 + 250 + 3 padding, three hidden layers of 64, ReLU,
-// sigmoid output). Inputs: the hit segment's direction with its first
-// non-zero component made positive (3), then for the 5^3 level-0 voxels
-// around the hit voxel (dz, dy, dx in -2..2, x fastest) log1p(count) and
-// log1p(summed length), zero outside the grid. Parameters are float32
-// masters used as bfloat16 (nearest even); bf16 enters every product (inputs,
-// weights, hidden activations), sums are float32. The neighbourhood part of
-// layer 1 depends only on the hit voxel: it is evaluated once per voxel and
-// stored as bf16 (the "voxel term"), and the direction part and bias are
-// added per hit.
+// Model: 400 inputs, three hidden layers of 64 with ReLU, sigmoid output.
+// Per-hit inputs 0..14: the hit segment's unit direction with its first
+// non-zero component made positive (3), the unit tube normal (3), and the
+// hit point's offset inside the level-l cell of its voxel for l = 0, 1, 2,
+// p / 2^l - floor(v / 2^l) - 1/2 (9); input 15 is zero. Per-voxel inputs
+// 16..390: for l = 0, 1, 2 the 5^3 level-l cells around the voxel's cell
+// (dz, dy, dx in -2..2, x fastest), log1p(8 rho) with rho = dens_l / 8^l
+// (Eq. 1's density as the AO march samples it), zero outside the level;
+// inputs 391..399 are zero. Parameters are float32 masters used as bfloat16
+// (nearest even); bf16 enters every product (inputs, weights, hidden
+// activations), sums are float32. The per-voxel part of layer 1 depends only
+// on the hit voxel: it is evaluated once per voxel and stored as bf16 (the
+// "voxel term"); the per-hit part and the bias are added per hit.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -21,16 +24,18 @@
 
 namespace aomlp {
 
-constexpr int NIN = 256, NH = 64;
+constexpr int NIN = 400, NH = 64;
+constexpr int NHIT = 15, VOFF = 16, NVIN = 375;   // per-hit inputs; first per-voxel input; per-voxel inputs
+constexpr int VK = NIN - VOFF;                    // per-voxel K of layer 1 (24 mma k-steps)
 constexpr int OW1 = 0, OB1 = OW1 + NH * NIN, OW2 = OB1 + NH, OB2 = OW2 + NH * NH, OW3 = OB2 + NH,
               OB3 = OW3 + NH * NH, OW4 = OB3 + NH, OB4 = OW4 + NH, NPARAM = OB4 + 1;
 
 // Device-side model: bf16 weights (row-major [out][in]) and float biases.
 struct Net {
+    const __nv_bfloat16 *w1;   // [64][400]
     const __nv_bfloat16 *w2;   // [64][64]
     const __nv_bfloat16 *w3;   // [64][64]
-    const float *w1t;          // [64][4]: bf16(W1[f][0..2]) as float, b1[f]
-    const float *b2, *b3;      // [64]
+    const float *b1, *b2, *b3; // [64]
     const float *w4;           // [64], values already rounded to bf16
     const float *b4;           // [1]
 };
@@ -64,13 +69,26 @@ __device__ __forceinline__ void unit_direction(float dx, float dy, float dz, flo
     u[2] = dz * s;
 }
 
-// Direction feature: sign-normalised unit segment direction, bf16-rounded.
-__device__ __forceinline__ void tangent_feature(float ux, float uy, float uz, float t[3]) {
+// Per-hit inputs 0..14 from the unit segment direction u, the unit normal n,
+// the hit point p (grid coordinates) and its voxel v, bf16-rounded.
+__device__ __forceinline__ void hit_inputs(float ux, float uy, float uz, float nx, float ny, float nz, float px,
+                                           float py, float pz, int vx, int vy, int vz, float h[NHIT]) {
     const float s = ux != 0.0f ? (ux > 0.0f ? 1.0f : -1.0f)
                   : (uy != 0.0f ? (uy > 0.0f ? 1.0f : -1.0f) : (uz > 0.0f ? 1.0f : -1.0f));
-    t[0] = bf16_round(s * ux);
-    t[1] = bf16_round(s * uy);
-    t[2] = bf16_round(s * uz);
+    h[0] = bf16_round(s * ux);
+    h[1] = bf16_round(s * uy);
+    h[2] = bf16_round(s * uz);
+    h[3] = bf16_round(nx);
+    h[4] = bf16_round(ny);
+    h[5] = bf16_round(nz);
+    const float p[3] = {px, py, pz};
+    const int v[3] = {vx, vy, vz};
+#pragma unroll
+    for (int l = 0; l < 3; l++) {
+        const float sc = l == 0 ? 1.0f : (l == 1 ? 0.5f : 0.25f);
+#pragma unroll
+        for (int c = 0; c < 3; c++) h[6 + 3 * l + c] = bf16_round(p[c] * sc - (float)(v[c] >> l) - 0.5f);
+    }
 }
 
 // Layers 2..4 for 16 hits of one warp. `h` is the warp's 16 x 64 bf16 layer-1
@@ -136,31 +154,66 @@ __device__ __forceinline__ void layers234(const Net &net, __nv_bfloat16 *h, floa
     ao_hi = 1.0f / (1.0f + __expf(-(hi + b4)));
 }
 
-// Layer-1 activation of one hit for 32 consecutive features f0..f0+31:
-// bf16(ReLU(voxel_term[f] + (b1[f] + W1[f][0..2] . t))) written to `row`.
-__device__ __forceinline__ void layer1_half(const Net &net, const __nv_bfloat16 *vterm, const float t[3], int f0,
-                                            __nv_bfloat16 *row) {
-    const uint4 *vp = reinterpret_cast<const uint4 *>(vterm + f0);
-    const float4 *wt = reinterpret_cast<const float4 *>(net.w1t);
+// Per-hit inputs of one hit as 16 bf16 (input 15 zero) into `row` (16-byte aligned).
+__device__ __forceinline__ void store_hit_inputs(const float h[NHIT], __nv_bfloat16 *row) {
+    uint32_t w[8];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const uint4 v = __ldg(vp + q);
-        const uint32_t words[4] = {v.x, v.y, v.z, v.w};
-        uint32_t out[4];
+    for (int i = 0; i < 7; i++) w[i] = pack_bf16x2(h[2 * i], h[2 * i + 1]);
+    w[7] = pack_bf16x2(h[14], 0.0f);
+    uint4 *d = reinterpret_cast<uint4 *>(row);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// Layer 1 for the 16 hits of one warp on tensor cores. On entry h[r][0..15]
+// (row stride 64) holds hit r's per-hit inputs; vt_lo / vt_hi point to the
+// voxel terms of rows g = lane / 4 and g + 8 (null: zero). The accumulators
+// start at b1 + voxel term and receive the per-hit part in one k-step; on
+// exit h[r][0..63] = bf16(ReLU(z1)).
+__device__ __forceinline__ void layer1_tile(const Net &net, const __nv_bfloat16 *vt_lo, const __nv_bfloat16 *vt_hi,
+                                            __nv_bfloat16 *h) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    uint32_t a[4];
+    const uint32_t *r0 = reinterpret_cast<const uint32_t *>(h + g * NH);
+    const uint32_t *r1 = reinterpret_cast<const uint32_t *>(h + (g + 8) * NH);
+    a[0] = r0[t];
+    a[1] = r1[t];
+    a[2] = r0[t + 4];
+    a[3] = r1[t + 4];
+    float acc[8][4];
 #pragma unroll
-        for (int w = 0; w < 4; w++) {
-            const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&words[w]);
-            float z[2] = {__bfloat162float(pr.x), __bfloat162float(pr.y)};
-#pragma unroll
-            for (int e = 0; e < 2; e++) {
-                const float4 c = __ldg(wt + f0 + q * 8 + w * 2 + e);
-                const float d = fmaf(c.x, t[0], fmaf(c.y, t[1], fmaf(c.z, t[2], c.w)));
-                z[e] = fmaxf(z[e] + d, 0.0f);
-            }
-            out[w] = pack_bf16x2(z[0], z[1]);
+    for (int n = 0; n < 8; n++) {
+        const int f = n * 8 + 2 * t;
+        const float b0 = __ldg(net.b1 + f), b1 = __ldg(net.b1 + f + 1);
+        float lo0 = 0.0f, lo1 = 0.0f, hi0 = 0.0f, hi1 = 0.0f;
+        if (vt_lo) {
+            const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_lo + f));
+            const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&u);
+            lo0 = __bfloat162float(pr.x);
+            lo1 = __bfloat162float(pr.y);
         }
-        *reinterpret_cast<uint4 *>(row + f0 + q * 8) = make_uint4(out[0], out[1], out[2], out[3]);
+        if (vt_hi) {
+            const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_hi + f));
+            const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&u);
+            hi0 = __bfloat162float(pr.x);
+            hi1 = __bfloat162float(pr.y);
+        }
+        acc[n][0] = b0 + lo0;
+        acc[n][1] = b1 + lo1;
+        acc[n][2] = b0 + hi0;
+        acc[n][3] = b1 + hi1;
+        const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w1 + (n * 8 + g) * NIN);
+        mma16816(acc[n], a, __ldg(wr + t), __ldg(wr + t + 4));
     }
+    __syncwarp();
+#pragma unroll
+    for (int n = 0; n < 8; n++) {
+        uint32_t *o0 = reinterpret_cast<uint32_t *>(h + g * NH + n * 8);
+        uint32_t *o1 = reinterpret_cast<uint32_t *>(h + (g + 8) * NH + n * 8);
+        o0[t] = pack_bf16x2(fmaxf(acc[n][0], 0.0f), fmaxf(acc[n][1], 0.0f));
+        o1[t] = pack_bf16x2(fmaxf(acc[n][2], 0.0f), fmaxf(acc[n][3], 0.0f));
+    }
+    __syncwarp();
 }
 
 }  // namespace aomlp

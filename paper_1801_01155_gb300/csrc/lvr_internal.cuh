@@ -68,11 +68,11 @@ struct lvr_ao_model {
     float *adam_m = nullptr, *adam_v = nullptr;
     int64_t adam_t = 0;
     void *w1b = nullptr, *w2b = nullptr, *w3b = nullptr;   // bf16 copies
-    float *w1t = nullptr, *w4b = nullptr;
+    float *w4b = nullptr;
     // voxel term of the LoD the model was last bound to
     uint64_t bound_gen = 0;
-    void *logf = nullptr;         // bf16x2 per voxel: log1p(count), log1p(length)
-    size_t logf_bytes = 0;
+    void *logd = nullptr;         // bf16 per cell of levels 0..2: log1p(8 dens_l / 8^l)
+    size_t logd_bytes = 0;
     void *vterm = nullptr;        // bf16 [voxels][64]
     size_t vterm_bytes = 0;
 };

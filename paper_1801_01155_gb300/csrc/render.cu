@@ -81,6 +81,7 @@ struct RenderParams {
     // direction, traced AO
     int32_t *samp_vox;
     float *samp_dir, *samp_ao;
+    float *samp_pos, *samp_nrm;   // optional: hit point (grid coordinates), unit normal
     uint32_t samp_seed;
     int32_t samp_depth;
     // judge mode: learned vs traced AO statistics (see lvr_ao_judge)
@@ -467,23 +468,38 @@ __device__ void light_hits(const RenderParams &P, Smem<MODE> &sm, int warp, int 
         }
     }
     if constexpr (MODE == MODE_LEARNED || MODE == MODE_JUDGE) {
-        // learned AO (Sec. 5.3 surrogate): 16 hits per step; two lanes build a
-        // hit's layer-1 row from its voxel term, then layers 2..4 on tensor
-        // cores. The judge keeps it in F_V (no shadows there) beside the traced AO.
+        // learned AO (Sec. 5.3 surrogate), 16 hits per step: per-hit inputs
+        // into a shared tile, layer 1 as voxel term + per-hit part, then
+        // layers 2..4, all on tensor cores. The judge keeps it in F_V (no
+        // shadows there) beside the traced AO.
         constexpr int FL = MODE == MODE_JUDGE ? F_V : F_AO;
         __nv_bfloat16 *h = sm.htile + warp * 16 * 64;
+        const uint32_t rx = (uint32_t)P.res[0], ry = (uint32_t)P.res[1];
         for (int g0 = 0; g0 < total; g0 += 16) {
-            const int r = lane >> 1, gi = g0 + r;
-            if (gi < total) {
-                const int o = slot_owner(sm, warp, gi), q = slot_index(sm, warp, gi);
-                float t[3];
-                aomlp::tangent_feature(sm.slot[F_UX][q][o], sm.slot[F_UY][q][o], sm.slot[F_UZ][q][o], t);
-                const uint32_t vid = __float_as_uint(sm.slot[F_VID][q][o]);
-                aomlp::layer1_half(P.net, P.vterm + (size_t)vid * 64, t, (lane & 1) * 32, h + r * 64);
-            } else {
-                for (int k = (lane & 1) * 32; k < (lane & 1) * 32 + 32; k++) h[r * 64 + k] = __float2bfloat16_rn(0.0f);
+            if (lane < 16) {   // per-hit inputs of hit g0 + lane into row lane
+                float hx[aomlp::NHIT];
+                const int gi = g0 + lane;
+                if (gi < total) {
+                    const int o = slot_owner(sm, warp, gi), q = slot_index(sm, warp, gi);
+                    const uint32_t vid = __float_as_uint(sm.slot[F_VID][q][o]);
+                    aomlp::hit_inputs(sm.slot[F_UX][q][o], sm.slot[F_UY][q][o], sm.slot[F_UZ][q][o],
+                                      sm.slot[F_NX][q][o], sm.slot[F_NY][q][o], sm.slot[F_NZ][q][o],
+                                      sm.slot[F_PX][q][o], sm.slot[F_PY][q][o], sm.slot[F_PZ][q][o],
+                                      (int)(vid % rx), (int)((vid / rx) % ry), (int)(vid / (rx * ry)), hx);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < aomlp::NHIT; k++) hx[k] = 0.0f;
+                }
+                aomlp::store_hit_inputs(hx, h + lane * 64);
             }
             __syncwarp();
+            const int gl = g0 + (lane >> 2), gh = gl + 8;
+            const __nv_bfloat16 *vlo = nullptr, *vhi = nullptr;
+            if (gl < total)
+                vlo = P.vterm + (size_t)__float_as_uint(sm.slot[F_VID][slot_index(sm, warp, gl)][slot_owner(sm, warp, gl)]) * 64;
+            if (gh < total)
+                vhi = P.vterm + (size_t)__float_as_uint(sm.slot[F_VID][slot_index(sm, warp, gh)][slot_owner(sm, warp, gh)]) * 64;
+            aomlp::layer1_tile(P.net, vlo, vhi, h);
             float lo, hi;
             aomlp::layers234(P.net, h, lo, hi);
             if ((lane & 3) == 0) {
@@ -662,6 +678,14 @@ render_kernel(const __grid_constant__ RenderParams P) {
                         P.samp_dir[3 * pix + 1] = sm.slot[F_UY][0][tid];
                         P.samp_dir[3 * pix + 2] = sm.slot[F_UZ][0][tid];
                         P.samp_ao[pix] = sm.slot[F_AO][0][tid];
+                        if (P.samp_pos) {
+                            P.samp_pos[3 * pix] = sm.slot[F_PX][0][tid];
+                            P.samp_pos[3 * pix + 1] = sm.slot[F_PY][0][tid];
+                            P.samp_pos[3 * pix + 2] = sm.slot[F_PZ][0][tid];
+                            P.samp_nrm[3 * pix] = sm.slot[F_NX][0][tid];
+                            P.samp_nrm[3 * pix + 1] = sm.slot[F_NY][0][tid];
+                            P.samp_nrm[3 * pix + 2] = sm.slot[F_NZ][0][tid];
+                        }
                       }
                     }
                 }
@@ -722,6 +746,8 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     if (!(view->fovy_deg > 0.0f && view->fovy_deg < 180.0f)) return set_err(ctx, LVR_EINVAL, "fovy out of (0,180)");
     if (desc->ao_mode < 0 || desc->ao_mode > 2) return set_err(ctx, LVR_EINVAL, "bad ao_mode");
     if (desc->ao_mode == 2 && !ao) return set_err(ctx, LVR_EINVAL, "learned AO needs a model");
+    if ((desc->ao_mode == 2 || judge) && lod && lod->levels < 3)
+        return set_err(ctx, LVR_EINVAL, "learned AO needs a LoD of >= 3 levels");
     const bool need_lod = desc->shadows || desc->ao_mode != 0;
     if (need_lod && !lod) return set_err(ctx, LVR_EINVAL, "shadows / AO need a LoD");
     if ((desc->ao_mode == 1 || judge) && (desc->ao_rays < 1 || desc->ao_rays > MAX_AO))
@@ -863,7 +889,7 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
 // direction (entry -> exit) and traced AO.
 lvr_status render_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
                           const lvr_render_desc *desc, int32_t depth, uint32_t seed, int32_t *vox, float *dir,
-                          float *ao) {
+                          float *ao, float *pos, float *nrm) {
     if (depth < 1) return set_err(ctx, LVR_EINVAL, "sample depth must be >= 1");
     RenderParams P;
     lvr_render_desc d = *desc;
@@ -876,18 +902,22 @@ lvr_status render_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lo
     P.samp_ao = ao;
     P.samp_seed = seed;
     P.samp_depth = depth;
+    P.samp_pos = pos && nrm ? pos : nullptr;
+    P.samp_nrm = pos && nrm ? nrm : nullptr;
     return launch(ctx, P);
 }
 
 extern "C" lvr_status lvr_ao_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
                                      const lvr_render_desc *desc, int32_t depth, uint32_t seed, int32_t *voxel,
-                                     float *dir, float *ao) {
+                                     float *dir, float *ao, float *pos, float *normal) {
     if (!ctx) return LVR_EINVAL;
     if (!voxel || !dir || !ao) return set_err(ctx, LVR_EINVAL, "lvr_ao_samples: null output");
-    if (!is_device_ptr(voxel) || !is_device_ptr(dir) || !is_device_ptr(ao))
+    if (!is_device_ptr(voxel) || !is_device_ptr(dir) || !is_device_ptr(ao) || (pos && !is_device_ptr(pos)) ||
+        (normal && !is_device_ptr(normal)))
         return set_err(ctx, LVR_EINVAL, "lvr_ao_samples takes device buffers");
+    if (!pos != !normal) return set_err(ctx, LVR_EINVAL, "lvr_ao_samples: pos and normal go together");
     LVR_CUDA(ctx, cudaSetDevice(ctx->device));
-    return render_samples(ctx, ls, lod, view, desc, depth, seed, voxel, dir, ao);
+    return render_samples(ctx, ls, lod, view, desc, depth, seed, voxel, dir, ao, pos, normal);
 }
 
 extern "C" lvr_status lvr_ao_judge(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,

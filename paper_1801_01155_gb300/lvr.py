@@ -100,10 +100,10 @@ _SIGS = {
     "lvr_ao_model_create": ([_vp, _vp, C.POINTER(_vp)], C.c_int),
     "lvr_ao_model_params": ([_vp, _vp, _vp], C.c_int),
     "lvr_free_ao_model": ([_vp], None),
-    "lvr_ao_infer": ([_vp, _vp, _vp, _i64, _vp, _vp, _vp], C.c_int),
-    "lvr_ao_features": ([_vp, _vp, _i64, _vp, _vp, _vp], C.c_int),
+    "lvr_ao_infer": ([_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "lvr_ao_features": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "lvr_ao_samples": ([_vp, _vp, _vp, C.POINTER(View), C.POINTER(RenderDesc), _i32, C.c_uint32, _vp, _vp,
-                        _vp], C.c_int),
+                        _vp, _vp, _vp], C.c_int),
     "lvr_ao_judge": ([_vp, _vp, _vp, C.POINTER(View), C.POINTER(RenderDesc), _vp, _vp, C.POINTER(AoError)],
                      C.c_int),
     "lvr_ao_train_step": ([_vp, _vp, _i64, _vp, _vp, C.c_float, C.POINTER(C.c_float), _vp], C.c_int),
@@ -396,26 +396,33 @@ def lvr_free_ao_model(m: AoModel):
     m.free()
 
 
-def lvr_ao_infer(ctx: Context, m: AoModel, lod: Lod, voxel, dir_, ao):
-    """voxel int32 [n], dir float32 [n, 3], ao float32 [n] (host or device)."""
+AO_NINPUTS = 400
+
+
+def lvr_ao_infer(ctx: Context, m: AoModel, lod: Lod, voxel, dir_, pos, normal, ao):
+    """voxel int32 [n], dir / pos / normal float32 [n, 3], ao float32 [n] (host or device)."""
     n = int(voxel.shape[0])
-    _check(ctx.handle, _L.lvr_ao_infer(ctx.handle, m.handle, lod.handle, n, _ptr(voxel), _ptr(dir_), _ptr(ao)))
+    _check(ctx.handle, _L.lvr_ao_infer(ctx.handle, m.handle, lod.handle, n, _ptr(voxel), _ptr(dir_), _ptr(pos),
+                                       _ptr(normal), _ptr(ao)))
     return ao
 
 
-def lvr_ao_features(ctx: Context, lod: Lod, voxel, dir_, X):
-    """X: device int16/uint16-sized [n, 256] receiving bfloat16 bit patterns."""
+def lvr_ao_features(ctx: Context, lod: Lod, voxel, dir_, pos, normal, X):
+    """X: device int16/uint16-sized [n, AO_NINPUTS] receiving bfloat16 bit patterns."""
     n = int(voxel.shape[0])
-    _check(ctx.handle, _L.lvr_ao_features(ctx.handle, lod.handle, n, _ptr(voxel), _ptr(dir_), _ptr(X)))
+    _check(ctx.handle, _L.lvr_ao_features(ctx.handle, lod.handle, n, _ptr(voxel), _ptr(dir_), _ptr(pos),
+                                          _ptr(normal), _ptr(X)))
     return X
 
 
 def lvr_ao_samples(ctx: Context, ls: LineSet, lod: Lod, view: View, desc: RenderDesc, depth: int, seed: int,
-                   voxel, dir_, ao):
-    """Device voxel int32 [h*w], dir float32 [h*w, 3], ao float32 [h*w]: per pixel the
-    hit of index hash(seed, pixel) mod depth with its traced AO (voxel -1: none)."""
+                   voxel, dir_, ao, pos=None, normal=None):
+    """Device voxel int32 [h*w], dir float32 [h*w, 3], ao float32 [h*w] (and optional
+    pos, normal float32 [h*w, 3]): per pixel the hit of index hash(seed, pixel) mod
+    depth with its traced AO (voxel -1: none)."""
     _check(ctx.handle, _L.lvr_ao_samples(ctx.handle, ls.handle, lod.handle, C.byref(view), C.byref(desc),
-                                         int(depth), int(seed) & 0xFFFFFFFF, _ptr(voxel), _ptr(dir_), _ptr(ao)))
+                                         int(depth), int(seed) & 0xFFFFFFFF, _ptr(voxel), _ptr(dir_), _ptr(ao),
+                                         _ptr(pos), _ptr(normal)))
 
 
 def lvr_ao_judge(ctx: Context, ls: LineSet, lod: Lod, view: View, desc: RenderDesc, m: AoModel,

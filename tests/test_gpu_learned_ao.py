@@ -55,15 +55,18 @@ def random_params(seed, scale=3.0):
     from oracle import aotrain as T
     rng = np.random.default_rng(seed)
     p = np.empty(T.NPARAM)
-    p[:T.OW2] = rng.uniform(-1, 1, T.OW2) * scale / 16.0
+    p[:T.OW2] = rng.uniform(-1, 1, T.OW2) * scale / 20.0
     p[T.OW2:] = rng.uniform(-1, 1, T.NPARAM - T.OW2) * scale / 8.0
-    p[T.OW1:T.OB1].reshape(64, 256)[:, 253:] = 0.0
+    W1 = p[T.OW1:T.OB1].reshape(64, 400)
+    W1[:, 15] = 0.0
+    W1[:, 391:] = 0.0
     return p.astype(np.float32)
 
 
 def hit_queries(st, n, seed):
-    """Voxels (mostly non-empty, some empty, corners) and directions (random,
-    axis-aligned, zero, negative first components)."""
+    """Voxels (mostly non-empty, some empty, the corners), directions (random,
+    axis-aligned, zero, negative first components), points inside the voxel
+    and unit normals."""
     rng = np.random.default_rng(seed)
     cnt = st.olod.export(0)["cnt"]
     nz = np.flatnonzero(cnt)
@@ -71,7 +74,23 @@ def hit_queries(st, n, seed):
     vox[:2] = [0, cnt.size - 1]
     d = rng.standard_normal((n, 3))
     d[2:8] = [[1, 0, 0], [0, -1, 0], [0, 0, 2.5], [0, 0, 0], [-1, 2, 0], [0, -3, 4]]
-    return vox, d.astype(np.float32)
+    R = st.R
+    v = np.stack([vox % R, (vox // R) % R, vox // (R * R)], 1)
+    pos = v + rng.uniform(0.0, 1.0, (n, 3))
+    pos[8] = v[8]                                   # a voxel corner
+    nrm = rng.standard_normal((n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    return vox, d.astype(np.float32), pos.astype(np.float32), nrm.astype(np.float32)
+
+
+def oracle_inputs(O, st, vox, d, pos, nrm):
+    return np.stack([O.ao_features(st.olod, int(v), O.ao_tangent([0, 0, 0], dd), nn, pp)
+                     for v, dd, pp, nn in zip(vox, d.astype(np.float64), pos.astype(np.float64),
+                                              nrm.astype(np.float64))])
+
+
+def _dev(torch, dev, *arrs):
+    return [torch.from_numpy(a).to(dev) for a in arrs]
 
 
 def bf16_margin_flags(x, rel):
@@ -89,25 +108,26 @@ def test_features_match_oracle(env, c1t):
     import torch
     from oracle import aotrain as T
     lvr, O, ctx, dev = env
-    vox, d = hit_queries(c1t, 3000, 1)
-    X = torch.empty((len(vox), 256), dtype=torch.int16, device=dev)
-    lvr.lvr_ao_features(ctx, c1t.glod, torch.from_numpy(vox).to(dev), torch.from_numpy(d).to(dev), X)
+    q = hit_queries(c1t, 3000, 1)
+    X = torch.empty((len(q[0]), 400), dtype=torch.int16, device=dev)
+    lvr.lvr_ao_features(ctx, c1t.glod, *_dev(torch, dev, *q), X)
     ctx.sync()
     got = X.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
     got = got.view(np.float32).astype(np.float64)
-    ref = np.stack([O.ao_features(c1t.olod, int(v), O.ao_tangent([0, 0, 0], dd)) for v, dd in zip(vox, d)])
+    ref = oracle_inputs(O, c1t, *q)
     want = T.bf16(ref)
-    # margins: float32 length sums (n * 2^-24), log1pf and the float32 unit direction (~2^-22)
-    cnt = c1t.olod.export(0)["cnt"]
+    # margins: per-hit inputs from float32 directions and points (~2^-21
+    # relative); densities are float32 sums over up to a few hundred
+    # segments, pooled twice, then log1pf (~2^-17)
     flag = bf16_margin_flags(ref, 2.0 ** -19)
-    flag[:, 4:253:2] |= bf16_margin_flags(ref[:, 4:253:2], 64 * 2.0 ** -24)
+    flag[:, 16:391] |= bf16_margin_flags(ref[:, 16:391], 2.0 ** -17)
     bad = (got != want) & ~flag
     assert not bad.any(), f"{bad.sum()} inputs differ, first at {np.argwhere(bad)[:3]}"
     near = (got != want) & flag
     ulp = np.abs(T.bf16(np.abs(want) * (1 + 2.0 ** -7)) - np.abs(want))
     assert np.all(np.abs(got - want)[near] <= ulp[near] + 1e-300)
-    assert flag.mean() < 0.01
-    assert cnt.size and (got[:, 3:253] != 0).any()
+    assert flag.mean() < 0.01, flag.mean()
+    assert (got[:, 16:391] != 0).mean() > 0.2
 
 
 def test_infer_matches_oracle(env, c1t):
@@ -115,19 +135,18 @@ def test_infer_matches_oracle(env, c1t):
     lvr, O, ctx, dev = env
     p = random_params(7)
     m = lvr.lvr_ao_model_create(ctx, p)
-    vox, d = hit_queries(c1t, 4000, 2)
-    ao = torch.empty(len(vox), dtype=torch.float32, device=dev)
-    lvr.lvr_ao_infer(ctx, m, c1t.glod, torch.from_numpy(vox).to(dev), torch.from_numpy(d).to(dev), ao)
+    q = hit_queries(c1t, 4000, 2)
+    ao = torch.empty(len(q[0]), dtype=torch.float32, device=dev)
+    lvr.lvr_ao_infer(ctx, m, c1t.glod, *_dev(torch, dev, *q), ao)
     ctx.sync()
     got = ao.cpu().numpy().astype(np.float64)
-    ref = np.array([O.ao_mlp(p, O.ao_features(c1t.olod, int(v), O.ao_tangent([0, 0, 0], dd)))
-                    for v, dd in zip(vox, d)])
+    ref = np.array([O.ao_mlp(p, x) for x in oracle_inputs(O, c1t, *q)])
     assert ref.std() > 0.05, "the random model should spread its outputs"
     err = np.abs(got - ref)
     assert err.max() <= S.TOL, f"max {err.max():.3e}"
     # host buffers give the same values
-    got_h = np.empty(len(vox), np.float32)
-    lvr.lvr_ao_infer(ctx, m, c1t.glod, vox, d, got_h)
+    got_h = np.empty(len(q[0]), np.float32)
+    lvr.lvr_ao_infer(ctx, m, c1t.glod, *q, got_h)
     assert np.array_equal(got_h, got.astype(np.float32))
 
 
@@ -138,10 +157,12 @@ def test_infer_out_of_range_voxels(env, c1t):
     nvox = 32 ** 3
     vox = np.array([-1, nvox, 5], np.int32)
     d = np.ones((3, 3), np.float32)
+    pos = np.full((3, 3), 5.5, np.float32)
+    nrm = np.tile(np.array([0, 0, 1.0], np.float32), (3, 1))
     with pytest.raises(lvr.LVRError):
-        lvr.lvr_ao_infer(ctx, m, c1t.glod, vox, d, np.empty(3, np.float32))
+        lvr.lvr_ao_infer(ctx, m, c1t.glod, vox, d, pos, nrm, np.empty(3, np.float32))
     ao = torch.empty(3, dtype=torch.float32, device=dev)
-    lvr.lvr_ao_infer(ctx, m, c1t.glod, torch.from_numpy(vox).to(dev), torch.from_numpy(d).to(dev), ao)
+    lvr.lvr_ao_infer(ctx, m, c1t.glod, *_dev(torch, dev, vox, d, pos, nrm), ao)
     ctx.sync()
     a = ao.cpu().numpy()
     assert np.isnan(a[0]) and np.isnan(a[1]) and np.isfinite(a[2])
@@ -187,8 +208,7 @@ def test_learned_model_rebinds_to_a_new_lod(env, c1t):
 def _oracle_rows(st, n, seed):
     from oracle import aotrain as T
     from oracle import oracle as O
-    vox, d = hit_queries(st, n, seed)
-    X = np.stack([O.ao_features(st.olod, int(v), O.ao_tangent([0, 0, 0], dd)) for v, dd in zip(vox, d)])
+    X = oracle_inputs(O, st, *hit_queries(st, n, seed))
     Xb = T.bf16(X)
     bits = (Xb.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
     t = np.random.default_rng(seed + 100).uniform(0.2, 1.0, n)
@@ -201,6 +221,7 @@ def test_train_step_matches_oracle(env, c1t):
     lvr, O, ctx, dev = env
     p = random_params(12, scale=1.0)
     Xb, bits, t = _oracle_rows(c1t, 1500, 3)
+    assert bits.shape == (1500, 400)
     m = lvr.lvr_ao_model_create(ctx, p)
     Xd = torch.from_numpy(bits.view(np.int16)).to(dev)
     yd = torch.from_numpy(t.astype(np.float32)).to(dev)
@@ -233,7 +254,7 @@ def test_train_step_argument_checks(env, c1t):
     lvr, O, ctx, dev = env
     m = lvr.lvr_ao_model_create(ctx, random_params(13))
     with pytest.raises(lvr.LVRError):
-        lvr.lvr_ao_train_step(ctx, m, np.zeros((4, 256), np.int16), np.zeros(4, np.float32))
+        lvr.lvr_ao_train_step(ctx, m, np.zeros((4, 400), np.int16), np.zeros(4, np.float32))
     with pytest.raises(ValueError):
         lvr.lvr_ao_model_create(ctx, np.zeros(10, np.float32))
     bad = random_params(13)
@@ -241,7 +262,7 @@ def test_train_step_argument_checks(env, c1t):
     with pytest.raises(lvr.LVRError):
         lvr.lvr_ao_model_create(ctx, bad)
     # a batch of one row works (bias and output-layer reductions of length 1)
-    X = torch.zeros((1, 256), dtype=torch.int16, device=dev)
+    X = torch.zeros((1, 400), dtype=torch.int16, device=dev)
     y = torch.full((1,), 0.5, dtype=torch.float32, device=dev)
     assert np.isfinite(lvr.lvr_ao_train_step(ctx, m, X, y))
 
@@ -258,9 +279,20 @@ def test_samples_record_the_target_hit(env, c1t):
     d = torch.empty((n, 3), dtype=torch.float32, device=dev)
     ao = torch.empty(n, dtype=torch.float32, device=dev)
     desc = lvr.make_desc(0.2, c1t.tf, opaque=True, ao_mode=1, ka=1.0, kd=0.0, bg=(0, 0, 0))
-    lvr.lvr_ao_samples(ctx, c1t.gls, c1t.glod, lv, desc, 1, 5, vox, d, ao)
+    pos = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    nrm = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    lvr.lvr_ao_samples(ctx, c1t.gls, c1t.glod, lv, desc, 1, 5, vox, d, ao, pos, nrm)
     ctx.sync()
     v, a = vox.cpu().numpy(), ao.cpu().numpy()
+    # the point lies in its voxel (to float32 rounding), the normal is unit and
+    # perpendicular to the segment unless the hit is on an end cap
+    hv = v >= 0
+    R = c1t.R
+    vc = np.stack([v % R, (v // R) % R, v // (R * R)], 1)[hv]
+    pp, nn, uu = pos.cpu().numpy()[hv], nrm.cpu().numpy()[hv], d.cpu().numpy()[hv]
+    assert np.all(pp >= vc - 1e-4) and np.all(pp <= vc + 1 + 1e-4)
+    assert np.allclose(np.linalg.norm(nn, axis=1), 1.0, atol=1e-5)
+    assert np.median(np.abs((nn * uu).sum(1))) < 1e-4
     # opaque, ka = 1, kd = 0, white TF, black background: pixel = AO at the first hit
     tf = np.ones((256, 4), np.float32)
     ref, tie, _ = O.render(c1t.ovs, c1t.olod, ov, O.make_rdesc(0.2, tf, opaque=True, ao=True, ka=1.0, kd=0.0,

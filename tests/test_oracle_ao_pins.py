@@ -39,35 +39,56 @@ def test_tangent_sign_and_zero(orc):
     assert np.array_equal(orc.ao_tangent([1, 2, 3], [1, 2, 3]), [0.0, 0.0, 0.0])
 
 
-def test_features_single_voxel_closed_form(orc):
-    """Grid 7 x 6 x 5 (x, y, z) with one non-empty voxel at (3, 2, 2): seen from
-    the hit voxel (2, 1, 3) it is the neighbour (dx, dy, dz) = (1, 1, -1), whose
-    slot is (dz+2)*25 + (dy+2)*5 + (dx+2) = 43."""
-    cnt = np.zeros((5, 6, 7), np.uint32)
-    ln = np.zeros((5, 6, 7))
-    cnt[2, 2, 3], ln[2, 2, 3] = 3, 2.5
-    lod = orc.HandLod(cnt, ln)
-    vox = 2 + 7 * (1 + 6 * 3)
-    t = [0.6, 0.0, -0.8]
-    x = orc.ao_features(lod, vox, t)
-    want = np.zeros(256)
-    want[:3] = t
-    want[3 + 2 * 43] = math.log1p(3.0)
-    want[4 + 2 * 43] = math.log1p(2.5)
-    assert np.array_equal(x, want)
+def _dens_levels(dims0, fill=0.0):
+    d0 = np.full(dims0[::-1], fill)
+    d1 = np.full([(n + 1) // 2 for n in dims0][::-1], fill)
+    d2 = np.full([(n + 3) // 4 for n in dims0][::-1], fill)
+    return [d0, d1, d2]
+
+
+def test_features_single_cell_per_level_closed_form(orc):
+    """Grid 12 x 10 x 9 (x, y, z), hit voxel (5, 3, 6) at p = (5.25, 3.5, 6.75).
+    One non-empty cell per level: level 0 (6, 4, 5) is the neighbour
+    (1, 1, -1) -> slot (dz+2)*25 + (dy+2)*5 + (dx+2) = 43; level 1: the voxel
+    lies in cell (2, 1, 3) and (0, 2, 4) is (-2, 1, 1) -> 75 + 15 + 0 = 90;
+    level 2: cell (1, 0, 1) and (1, 0, 1) itself -> slot 62. Input value
+    log1p(8 dens / 8^l). Offsets: p / 2^l - floor(v / 2^l) - 1/2."""
+    d = _dens_levels((12, 10, 9))
+    d[0][5, 4, 6] = 0.5
+    d[1][4, 2, 0] = 3.0
+    d[2][1, 0, 1] = 20.0
+    lod = orc.HandLod(d)
+    v = (5, 3, 6)
+    vox = v[0] + 12 * (v[1] + 10 * v[2])
+    t, n, p = [0.6, 0.0, -0.8], [0.0, 1.0, 0.0], [5.25, 3.5, 6.75]
+    x = orc.ao_features(lod, vox, t, n, p)
+    want = np.zeros(400)
+    want[0:3], want[3:6] = t, n
+    want[6:9] = [0.25 - 0.5, 0.5 - 0.5, 0.75 - 0.5]
+    want[9:12] = [5.25 / 2 - 2 - 0.5, 3.5 / 2 - 1 - 0.5, 6.75 / 2 - 3 - 0.5]
+    want[12:15] = [5.25 / 4 - 1 - 0.5, 3.5 / 4 - 0 - 0.5, 6.75 / 4 - 1 - 0.5]
+    want[16 + 43] = math.log1p(8 * 0.5)
+    want[16 + 125 + 90] = math.log1p(8 * 3.0 / 8)
+    want[16 + 250 + 62] = math.log1p(8 * 20.0 / 64)
+    assert np.allclose(x, want, rtol=0, atol=1e-15)
+    assert np.count_nonzero(x[16:]) == 3
 
 
 def test_features_grid_corner_zero_outside(orc):
-    """Every voxel holds (1, 1); at the corner voxel only offsets 0..2 on each
-    axis are inside: 27 neighbours, in the slots with dx, dy, dz >= 0."""
-    cnt = np.ones((4, 4, 4), np.uint32)
-    lod = orc.HandLod(cnt, np.ones((4, 4, 4)))
-    x = orc.ao_features(lod, 0, [0, 0, 1.0])
-    nb = x[3:253].reshape(5, 5, 5, 2)        # [dz][dy][dx][count, length]
-    assert np.all(nb[2:, 2:, 2:] == math.log1p(1.0))
-    nb[2:, 2:, 2:] = 0.0
-    assert not nb.any()
-    assert np.all(x[253:] == 0.0)
+    """Uniform density; at the corner voxel only offsets 0..2 on each axis are
+    inside at every level: 27 non-zero slots per level, dx, dy, dz >= 0."""
+    d = _dens_levels((20, 20, 20), 1.0)
+    lod = orc.HandLod(d)
+    x = orc.ao_features(lod, 0, [0, 0, 1.0], [1.0, 0, 0], [0.5, 0.5, 0.5])
+    for l in range(3):
+        nb = x[16 + 125 * l:16 + 125 * (l + 1)].reshape(5, 5, 5)     # [dz][dy][dx]
+        assert np.all(nb[2:, 2:, 2:] == math.log1p(8.0 / 8 ** l))
+        nb = nb.copy()
+        nb[2:, 2:, 2:] = 0.0
+        assert not nb.any()
+    assert np.all(x[391:] == 0.0) and x[15] == 0.0
+    with pytest.raises(ValueError):
+        orc.ao_features(orc.HandLod(d[:2]), 0, [0, 0, 1.0], [1.0, 0, 0], [0.5, 0.5, 0.5])
 
 
 def _params():
@@ -77,7 +98,7 @@ def _params():
 def test_mlp_zero_weights_is_sigmoid_of_output_bias(orc):
     p = _params()
     p[T.OB4] = 0.75
-    x = np.random.default_rng(2).standard_normal(256)
+    x = np.random.default_rng(2).standard_normal(400)
     assert orc.ao_mlp(p, x) == 1.0 / (1.0 + math.exp(-0.75))
 
 
@@ -95,6 +116,8 @@ def test_mlp_exact_network_matches_torch(orc):
     rng = np.random.default_rng(3)
     p = _params()
     p[T.OW1:T.OB1] = _sparse(rng, T.NH, T.NIN, 8, 1.0).reshape(-1)
+    p[T.OW1:T.OB1].reshape(T.NH, T.NIN)[:, 15] = 0.0
+    p[T.OW1:T.OB1].reshape(T.NH, T.NIN)[:, 391:] = 0.0
     p[T.OB1:T.OW2] = rng.integers(-2, 3, T.NH) / 2.0
     p[T.OW2:T.OB2] = _sparse(rng, T.NH, T.NH, 4, 1 / 8).reshape(-1)
     p[T.OB2:T.OW3] = rng.integers(-2, 3, T.NH) / 16.0
@@ -102,10 +125,9 @@ def test_mlp_exact_network_matches_torch(orc):
     p[T.OB3:T.OW4] = rng.integers(-2, 3, T.NH) / 64.0
     p[T.OW4:T.OB4] = _sparse(rng, 1, T.NH, 8, 1 / 2).reshape(-1)
     p[T.OB4] = 0.25
-    x = np.zeros(256)
-    x[:3] = [0.5, 1.0, -0.5]
-    x[3:253] = rng.integers(0, 3, 250) / 2.0
-    p[T.OW1:T.OB1].reshape(T.NH, T.NIN)[:, 253:] = 0.0
+    x = np.zeros(400)
+    x[:15] = rng.integers(-2, 3, 15) / 2.0
+    x[16:391] = rng.integers(0, 3, 375) / 2.0
     W1, b1, W2, b2, W3, b3, W4, b4 = [torch.tensor(np.asarray(a, np.float64)) for a in T.unpack(p)]
     h = torch.tensor(x)
     h = torch.relu(torch.nn.functional.linear(h, W1, b1))
@@ -122,21 +144,21 @@ def test_mlp_exact_network_matches_torch(orc):
 
 
 def test_mlp_rounds_the_neighbourhood_sum_before_the_direction(orc):
-    """Neighbourhood inputs 256 and 1 with unit weights sum to 257, which is
-    stored as bfloat16 256; adding the direction part 0.5 gives 256.5 -> 256.
+    """Per-voxel inputs 256 and 1 with unit weights sum to 257, which is
+    stored as bfloat16 256; adding the per-hit part 0.5 gives 256.5 -> 256.
     Without that rounding the unit would be bfloat16(257.5) = 258. Then
     h2 = h1 / 256, h3 = h2, output = sigmoid(h3 - 1): 1/2 exactly (the other
     order would give sigmoid(2/256))."""
     p = _params()
-    p[T.OW1 + 0] = 1.0          # W1[0][0] (direction)
-    p[T.OW1 + 3] = 1.0          # W1[0][3]
-    p[T.OW1 + 4] = 1.0          # W1[0][4]
+    p[T.OW1 + 0] = 1.0          # W1[0][0] (per hit)
+    p[T.OW1 + 16] = 1.0         # W1[0][16] (per voxel)
+    p[T.OW1 + 17] = 1.0         # W1[0][17]
     p[T.OW2] = 1.0 / 256.0      # W2[0][0]
     p[T.OW3] = 1.0              # W3[0][0]
     p[T.OW4] = 1.0              # W4[0]
     p[T.OB4] = -1.0
-    x = np.zeros(256)
-    x[0], x[3], x[4] = 0.5, 256.0, 1.0
+    x = np.zeros(400)
+    x[0], x[16], x[17] = 0.5, 256.0, 1.0
     assert orc.ao_mlp(p, x) == 0.5
 
 
@@ -146,15 +168,15 @@ def test_mlp_rounds_each_hidden_activation(orc):
     sigmoid(h3 - 1) = sigmoid(2^-7). Keeping z2 unrounded would give
     h3 = 1 + 2^-6; keeping z3 unrounded, sigmoid(0.0108...)."""
     p = _params()
-    p[T.OW1 + 3] = 1.0
+    p[T.OW1 + 20] = 1.0
     p[T.OW2] = 1.0
     p[T.OB2] = 2.0 ** -9
     p[T.OW3] = 1.0 + 2.0 ** -7
     p[T.OB3] = 0.003
     p[T.OW4] = 1.0
     p[T.OB4] = -1.0
-    x = np.zeros(256)
-    x[3] = 1.0
+    x = np.zeros(400)
+    x[20] = 1.0
     want = 1.0 / (1.0 + math.exp(-(2.0 ** -7)))
     assert orc.ao_mlp(p, x) == want
     assert T.forward(p, x[None, :])["y"][0] == pytest.approx(want, rel=1e-15)
@@ -165,7 +187,7 @@ def test_training_gradient_is_the_derivative(orc):
     differences of the float64 loss, in every parameter block."""
     rng = np.random.default_rng(4)
     p = (rng.standard_normal(T.NPARAM) * 0.2).astype(np.float64)
-    X = rng.standard_normal((12, 256))
+    X = rng.standard_normal((12, 400))
     t = rng.uniform(0.0, 1.0, 12)
     _, g = T.loss_and_grad(p, X, t, rnd=False)
     blocks = [(T.OW1, T.OB1), (T.OB1, T.OW2), (T.OW2, T.OB2), (T.OB2, T.OW3), (T.OW3, T.OB3),
@@ -211,10 +233,10 @@ def test_rounded_gradient_matches_torch_autograd():
     the gradient the oracle computes by hand."""
     rng = np.random.default_rng(5)
     p = rng.standard_normal(T.NPARAM) * 0.1
-    X = np.abs(rng.standard_normal((32, 256)))
+    X = np.abs(rng.standard_normal((32, 400)))
     t = rng.uniform(0.0, 1.0, 32)
     tp = torch.tensor(p, requires_grad=True)
-    W1, b1 = tp[T.OW1:T.OB1].reshape(64, 256), tp[T.OB1:T.OW2]
+    W1, b1 = tp[T.OW1:T.OB1].reshape(64, 400), tp[T.OB1:T.OW2]
     W2, b2 = tp[T.OW2:T.OB2].reshape(64, 64), tp[T.OB2:T.OW3]
     W3, b3 = tp[T.OW3:T.OB3].reshape(64, 64), tp[T.OB3:T.OW4]
     W4, b4 = tp[T.OW4:T.OB4], tp[T.OB4]
