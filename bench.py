@@ -240,12 +240,97 @@ def run_gpu(args):
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clk,
         }
+        if not args.no_learned and world == 1:
+            line["learned_ao"] = learned_ao(args, lvr, synth, ctx, dev, stream,
+                                            main=(xyz, attr, offs, gdesc, sig, view, out))
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(ls, tf, cam, budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     ctx.close()
+
+
+# ---------------------------------------------------------------- learned AO (config 4)
+C4_SEEDS = list(range(100, 108))
+
+
+def _frame_ms(lvr, ctx, stream, ls, lod, view, desc, out, model=None, n=20, warm=3):
+    import torch
+    for _ in range(warm):
+        lvr.lvr_render(ctx, ls, lod, view, desc, out, ao_model=model)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        lvr.lvr_render(ctx, ls, lod, view, desc, out, ao_model=model)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def learned_ao(args, lvr, synth, ctx, dev, stream, main):
+    """Config 4: train the learned AO on traced AO of eight seeded small
+    streamline sets (500 x 64, 32^3, r = 0.2), judge it against the traced AO
+    at every composited hit of a 1080p transparent frame of an unseen set
+    (seed 0), and time traced against learned AO frames."""
+    import torch
+    tf = synth.tf_ramp(*ALPHA)
+    sig = synth.sigma_lut(tf)
+
+    def small(seed):
+        s = synth.make_streamlines(500, 64, seed)
+        g = lvr.grid_desc(32, 32, scale=32.0, attr_min=float(s.attr.min()), attr_max=float(s.attr.max()))
+        gls = lvr.lvr_voxelize(ctx, torch.from_numpy(s.xyz).to(dev), torch.from_numpy(s.attr).to(dev),
+                               torch.from_numpy(s.offsets).to(dev), g)
+        return gls, lvr.lvr_build_lod(ctx, gls, 3, sig)
+
+    train = [small(s) for s in C4_SEEDS]
+    test_ls, test_lod = small(0)
+    d_tr = lvr.make_desc(0.2, tf, ert_alpha=ERT, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0)
+    d_le = lvr.make_desc(0.2, tf, ert_alpha=ERT, shadows=True, ao_mode=2, ao_rays=16, ao_radius=15.0)
+    td = lvr.ao_train_desc(args.learned_samples, args.learned_epochs, 8192, 3e-3, 1234, d_tr, view_size=256,
+                           depth=32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    model, mse = lvr.lvr_train_ao(ctx, [t[0] for t in train], [t[1] for t in train], td)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    cam = synth.orbit_view((32, 32, 32), W, H)
+    view = lvr.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"])
+    err = lvr.lvr_ao_judge(ctx, test_ls, test_lod, view, d_tr, model)
+    out = main[-1]
+    tr = _frame_ms(lvr, ctx, stream, test_ls, test_lod, view, d_tr, out)
+    le = _frame_ms(lvr, ctx, stream, test_ls, test_lod, view, d_le, out, model)
+    res = {
+        "config": "config 4: 3x64 MLP, 400 bf16 inputs (direction, normal, LoD-cell offsets; 5^3 log-density "
+                  "cells at LoD levels 0-2), trained on traced AO of 8 seeded 500x64 sets (32^3, r=0.2); judged "
+                  "at every composited hit of a 1920x1080 transparent frame of an unseen set (seed 0)",
+        "samples": args.learned_samples, "epochs": args.learned_epochs, "train_s": round(train_s, 3),
+        "final_mse": round(mse, 6),
+        "error": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in err.items()},
+        "frame_1080p_c1": {"traced_ms": round(tr, 4), "learned_ms": round(le, 4),
+                           "fps_traced": round(1e3 / tr, 1), "fps_learned": round(1e3 / le, 1),
+                           "speedup": round(tr / le, 3)},
+    }
+    # the same model on the large workload's frame (outside its training distribution)
+    xyz, attr, offs, gdesc, sig2, view2, _ = main
+    big = lvr.lvr_voxelize(ctx, xyz, attr, offs, gdesc())
+    big_lod = lvr.lvr_build_lod(ctx, big, LEVELS, sig2)
+    d2_tr = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0)
+    d2_le = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, shadows=True, ao_mode=2, ao_rays=16, ao_radius=15.0)
+    torch.cuda.synchronize()
+    b0 = time.perf_counter()
+    lvr.lvr_render(ctx, big, big_lod, view2, d2_le, out, ao_model=model)   # binds the voxel term
+    torch.cuda.synchronize()
+    first_ms = (time.perf_counter() - b0) * 1e3
+    tr2 = _frame_ms(lvr, ctx, stream, big, big_lod, view2, d2_tr, out, n=5)
+    le2 = _frame_ms(lvr, ctx, stream, big, big_lod, view2, d2_le, out, model, n=5)
+    err2 = lvr.lvr_ao_judge(ctx, big, big_lod, view2, d2_tr, model)
+    res["frame_1080p_c2"] = {"traced_ms": round(tr2, 3), "learned_ms": round(le2, 3),
+                             "speedup": round(tr2 / le2, 3), "first_learned_frame_ms": round(first_ms, 2),
+                             "mean_abs_error": round(err2["mean_abs"], 5), "p99_abs_error": round(err2["p99_abs"], 5),
+                             "note": "model trained on the small sets only"}
+    return res
 
 
 # voxelise: count, 3 scan kernels, scatter, 2 sort kernels; LoD: 1 + 2 pooling; render: 1
@@ -326,6 +411,9 @@ def main():
     ap.add_argument("--impl", default="lvr", choices=["lvr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-AO (config 4) block")
+    ap.add_argument("--learned-samples", type=int, default=4_000_000)
+    ap.add_argument("--learned-epochs", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -151,9 +151,9 @@ __global__ void __launch_bounds__(128)
 infer_kernel(Net net, const bf16 *__restrict__ vterm, int dx, int dy, int64_t nvox, int64_t n,
              const int32_t *__restrict__ vox, const float *__restrict__ dir, const float *__restrict__ pos,
              const float *__restrict__ nrm, float *ao) {
-    __shared__ __align__(16) bf16 tile[4][16][NH];
+    __shared__ __align__(16) bf16 tile[4][16 * HIN_STRIDE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
-    bf16(*h)[NH] = tile[warp];
+    bf16 *hin = tile[warp];
     auto ok = [&](int64_t i) { return i < n && vox[i] >= 0 && vox[i] < nvox; };
     for (int64_t base = ((int64_t)blockIdx.x * 4 + warp) * 16; base < n; base += (int64_t)gridDim.x * 64) {
         if (lane < 16) {
@@ -161,13 +161,12 @@ infer_kernel(Net net, const bf16 *__restrict__ vterm, int dx, int dy, int64_t nv
             float hx[NHIT];
             if (ok(i)) sample_hit_inputs(dx, dy, vox[i], dir + 3 * i, pos + 3 * i, nrm + 3 * i, hx);
             else for (int k = 0; k < NHIT; k++) hx[k] = 0.0f;
-            store_hit_inputs(hx, h[lane]);
+            store_hit_inputs(hx, hin + lane * HIN_STRIDE);
         }
         __syncwarp();
-        layer1_tile(net, ok(base + g) ? vterm + (int64_t)vox[base + g] * NH : nullptr,
-                    ok(base + g + 8) ? vterm + (int64_t)vox[base + g + 8] * NH : nullptr, &h[0][0]);
         float lo, hi;
-        layers234(net, &h[0][0], lo, hi);
+        mlp_tile(net, ok(base + g) ? vterm + (int64_t)vox[base + g] * NH : nullptr,
+                 ok(base + g + 8) ? vterm + (int64_t)vox[base + g + 8] * NH : nullptr, hin, lo, hi);
         if ((lane & 3) == 0) {
             const int g = lane >> 2;
             if (base + g < n) ao[base + g] = vox[base + g] >= 0 && vox[base + g] < nvox ? lo : __int_as_float(0x7fc00000);

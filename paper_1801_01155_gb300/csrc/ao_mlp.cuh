@@ -91,50 +91,102 @@ __device__ __forceinline__ void hit_inputs(float ux, float uy, float uz, float n
     }
 }
 
-// Layers 2..4 for 16 hits of one warp. `h` is the warp's 16 x 64 bf16 layer-1
-// activation tile in shared memory (row stride 64 elements); it is reused for
-// the layer-2 activations. Returns, in lanes with t == 0 (lane % 4 == 0), the
-// AO of rows g (lo) and g + 8 (hi).
-__device__ __forceinline__ void layers234(const Net &net, __nv_bfloat16 *h, float &ao_lo, float &ao_hi) {
+// Row stride of a warp's per-hit input tile (16 hits x 16 inputs): 24
+// elements keep the rows 16-byte aligned and the fragment loads free of bank
+// conflicts.
+constexpr int HIN_STRIDE = 24;
+
+// Per-hit inputs of one hit as 16 bf16 (input 15 zero) into `row` (16-byte aligned).
+__device__ __forceinline__ void store_hit_inputs(const float h[NHIT], __nv_bfloat16 *row) {
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 7; i++) w[i] = pack_bf16x2(h[2 * i], h[2 * i + 1]);
+    w[7] = pack_bf16x2(h[14], 0.0f);
+    uint4 *d = reinterpret_cast<uint4 *>(row);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// The output fragments of one m16n8 layer (8 n-tiles, 64 features) are, lane
+// for lane, the A fragments of the next layer's 4 k-steps: k-step k takes
+// n-tiles 2k (columns 0..7) and 2k+1 (columns 8..15). ReLU and bf16 here.
+__device__ __forceinline__ void relu_to_a(const float acc[8][4], uint32_t a[4][4]) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        a[k][0] = pack_bf16x2(fmaxf(acc[2 * k][0], 0.0f), fmaxf(acc[2 * k][1], 0.0f));
+        a[k][1] = pack_bf16x2(fmaxf(acc[2 * k][2], 0.0f), fmaxf(acc[2 * k][3], 0.0f));
+        a[k][2] = pack_bf16x2(fmaxf(acc[2 * k + 1][0], 0.0f), fmaxf(acc[2 * k + 1][1], 0.0f));
+        a[k][3] = pack_bf16x2(fmaxf(acc[2 * k + 1][2], 0.0f), fmaxf(acc[2 * k + 1][3], 0.0f));
+    }
+}
+
+// acc = bias + A (16 x 64) x W^T for a 64 x 64 layer W (bf16 [out][in]).
+__device__ __forceinline__ void dense64(const __nv_bfloat16 *W, const float *bias, const uint32_t a[4][4],
+                                        float acc[8][4]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float acc[8][4];
-    // layer 2 then layer 3: acc = h * W^T (+ b), ReLU, bf16 back into h
-#pragma unroll 1
-    for (int layer = 0; layer < 2; layer++) {
-        const __nv_bfloat16 *W = layer == 0 ? net.w2 : net.w3;
-        const float *bias = layer == 0 ? net.b2 : net.b3;
+#pragma unroll
+    for (int n = 0; n < 8; n++) {
+        acc[n][0] = acc[n][2] = __ldg(bias + n * 8 + 2 * t);
+        acc[n][1] = acc[n][3] = __ldg(bias + n * 8 + 2 * t + 1);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
 #pragma unroll
         for (int n = 0; n < 8; n++) {
-            acc[n][0] = acc[n][2] = __ldg(bias + n * 8 + 2 * t);
-            acc[n][1] = acc[n][3] = __ldg(bias + n * 8 + 2 * t + 1);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            uint32_t a[4];
-            const uint32_t *hr0 = reinterpret_cast<const uint32_t *>(h + g * NH + k * 16);
-            const uint32_t *hr1 = reinterpret_cast<const uint32_t *>(h + (g + 8) * NH + k * 16);
-            a[0] = hr0[t];
-            a[1] = hr1[t];
-            a[2] = hr0[t + 4];
-            a[3] = hr1[t + 4];
-#pragma unroll
-            for (int n = 0; n < 8; n++) {
-                const uint32_t *wr = reinterpret_cast<const uint32_t *>(W + (n * 8 + g) * NH + k * 16);
-                mma16816(acc[n], a, __ldg(wr + t), __ldg(wr + t + 4));
-            }
-        }
-        __syncwarp();
-        if (layer == 0) {
-#pragma unroll
-            for (int n = 0; n < 8; n++) {
-                uint32_t *o0 = reinterpret_cast<uint32_t *>(h + g * NH + n * 8);
-                uint32_t *o1 = reinterpret_cast<uint32_t *>(h + (g + 8) * NH + n * 8);
-                o0[t] = pack_bf16x2(fmaxf(acc[n][0], 0.0f), fmaxf(acc[n][1], 0.0f));
-                o1[t] = pack_bf16x2(fmaxf(acc[n][2], 0.0f), fmaxf(acc[n][3], 0.0f));
-            }
-            __syncwarp();
+            const uint32_t *wr = reinterpret_cast<const uint32_t *>(W + (n * 8 + g) * NH + k * 16);
+            mma16816(acc[n], a[k], __ldg(wr + t), __ldg(wr + t + 4));
         }
     }
+}
+
+// The whole model for the 16 hits of one warp, on tensor cores, with the
+// activations kept in registers. `hin` is the warp's per-hit input tile
+// (row r = hit r, stride HIN_STRIDE); vt_lo / vt_hi point to the voxel
+// terms of rows g = lane / 4 and g + 8 (null: zero). Layer 1 starts its
+// accumulators at b1 + voxel term and adds the per-hit part in one k-step.
+// Returns, in lanes with lane % 4 == 0, the AO of rows g (lo) and g + 8 (hi).
+__device__ __forceinline__ void mlp_tile(const Net &net, const __nv_bfloat16 *vt_lo, const __nv_bfloat16 *vt_hi,
+                                         const __nv_bfloat16 *hin, float &ao_lo, float &ao_hi) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float acc[8][4];
+    uint32_t a[4][4];
+    {
+        uint32_t x[4];
+        const uint32_t *r0 = reinterpret_cast<const uint32_t *>(hin + g * HIN_STRIDE);
+        const uint32_t *r1 = reinterpret_cast<const uint32_t *>(hin + (g + 8) * HIN_STRIDE);
+        x[0] = r0[t];
+        x[1] = r1[t];
+        x[2] = r0[t + 4];
+        x[3] = r1[t + 4];
+#pragma unroll
+        for (int n = 0; n < 8; n++) {
+            const int f = n * 8 + 2 * t;
+            const float b0 = __ldg(net.b1 + f), b1 = __ldg(net.b1 + f + 1);
+            float lo0 = 0.0f, lo1 = 0.0f, hi0 = 0.0f, hi1 = 0.0f;
+            if (vt_lo) {
+                const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_lo + f));
+                const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&u);
+                lo0 = __bfloat162float(pr.x);
+                lo1 = __bfloat162float(pr.y);
+            }
+            if (vt_hi) {
+                const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_hi + f));
+                const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&u);
+                hi0 = __bfloat162float(pr.x);
+                hi1 = __bfloat162float(pr.y);
+            }
+            acc[n][0] = b0 + lo0;
+            acc[n][1] = b1 + lo1;
+            acc[n][2] = b0 + hi0;
+            acc[n][3] = b1 + hi1;
+            const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w1 + (n * 8 + g) * NIN);
+            mma16816(acc[n], x, __ldg(wr + t), __ldg(wr + t + 4));
+        }
+    }
+    relu_to_a(acc, a);
+    dense64(net.w2, net.b2, a, acc);
+    relu_to_a(acc, a);
+    dense64(net.w3, net.b3, a, acc);
     // layer 4 from the layer-3 fragments: bf16(ReLU(z3)) . w4, summed over the quad
     float lo = 0.0f, hi = 0.0f;
 #pragma unroll
@@ -152,68 +204,6 @@ __device__ __forceinline__ void layers234(const Net &net, __nv_bfloat16 *h, floa
     const float b4 = __ldg(net.b4);
     ao_lo = 1.0f / (1.0f + __expf(-(lo + b4)));
     ao_hi = 1.0f / (1.0f + __expf(-(hi + b4)));
-}
-
-// Per-hit inputs of one hit as 16 bf16 (input 15 zero) into `row` (16-byte aligned).
-__device__ __forceinline__ void store_hit_inputs(const float h[NHIT], __nv_bfloat16 *row) {
-    uint32_t w[8];
-#pragma unroll
-    for (int i = 0; i < 7; i++) w[i] = pack_bf16x2(h[2 * i], h[2 * i + 1]);
-    w[7] = pack_bf16x2(h[14], 0.0f);
-    uint4 *d = reinterpret_cast<uint4 *>(row);
-    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
-}
-
-// Layer 1 for the 16 hits of one warp on tensor cores. On entry h[r][0..15]
-// (row stride 64) holds hit r's per-hit inputs; vt_lo / vt_hi point to the
-// voxel terms of rows g = lane / 4 and g + 8 (null: zero). The accumulators
-// start at b1 + voxel term and receive the per-hit part in one k-step; on
-// exit h[r][0..63] = bf16(ReLU(z1)).
-__device__ __forceinline__ void layer1_tile(const Net &net, const __nv_bfloat16 *vt_lo, const __nv_bfloat16 *vt_hi,
-                                            __nv_bfloat16 *h) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    uint32_t a[4];
-    const uint32_t *r0 = reinterpret_cast<const uint32_t *>(h + g * NH);
-    const uint32_t *r1 = reinterpret_cast<const uint32_t *>(h + (g + 8) * NH);
-    a[0] = r0[t];
-    a[1] = r1[t];
-    a[2] = r0[t + 4];
-    a[3] = r1[t + 4];
-    float acc[8][4];
-#pragma unroll
-    for (int n = 0; n < 8; n++) {
-        const int f = n * 8 + 2 * t;
-        const float b0 = __ldg(net.b1 + f), b1 = __ldg(net.b1 + f + 1);
-        float lo0 = 0.0f, lo1 = 0.0f, hi0 = 0.0f, hi1 = 0.0f;
-        if (vt_lo) {
-            const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_lo + f));
-            const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&u);
-            lo0 = __bfloat162float(pr.x);
-            lo1 = __bfloat162float(pr.y);
-        }
-        if (vt_hi) {
-            const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_hi + f));
-            const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&u);
-            hi0 = __bfloat162float(pr.x);
-            hi1 = __bfloat162float(pr.y);
-        }
-        acc[n][0] = b0 + lo0;
-        acc[n][1] = b1 + lo1;
-        acc[n][2] = b0 + hi0;
-        acc[n][3] = b1 + hi1;
-        const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w1 + (n * 8 + g) * NIN);
-        mma16816(acc[n], a, __ldg(wr + t), __ldg(wr + t + 4));
-    }
-    __syncwarp();
-#pragma unroll
-    for (int n = 0; n < 8; n++) {
-        uint32_t *o0 = reinterpret_cast<uint32_t *>(h + g * NH + n * 8);
-        uint32_t *o1 = reinterpret_cast<uint32_t *>(h + (g + 8) * NH + n * 8);
-        o0[t] = pack_bf16x2(fmaxf(acc[n][0], 0.0f), fmaxf(acc[n][1], 0.0f));
-        o1[t] = pack_bf16x2(fmaxf(acc[n][2], 0.0f), fmaxf(acc[n][3], 0.0f));
-    }
-    __syncwarp();
 }
 
 }  // namespace aomlp

@@ -226,7 +226,7 @@ struct Smem {
     uint32_t sk[KS][RT];
     float slot[kVid ? NF : NF - 1][KS][RT];
     uint8_t item[4][32 * KS];     // per warp: (owner lane, slot) of each collected hit
-    __align__(16) __nv_bfloat16 htile[MODE == MODE_LEARNED || MODE == MODE_JUDGE ? 4 * 16 * 64 : 8];   // per warp: 16 x 64
+    __align__(16) __nv_bfloat16 hin[MODE == MODE_LEARNED || MODE == MODE_JUDGE ? 4 * 16 * aomlp::HIN_STRIDE : 8];   // per warp: per-hit inputs of 16 hits
 };
 
 struct Ray {
@@ -469,11 +469,11 @@ __device__ void light_hits(const RenderParams &P, Smem<MODE> &sm, int warp, int 
     }
     if constexpr (MODE == MODE_LEARNED || MODE == MODE_JUDGE) {
         // learned AO (Sec. 5.3 surrogate), 16 hits per step: per-hit inputs
-        // into a shared tile, layer 1 as voxel term + per-hit part, then
-        // layers 2..4, all on tensor cores. The judge keeps it in F_V (no
-        // shadows there) beside the traced AO.
+        // into a shared tile, then the model on tensor cores with the
+        // activations in registers. The judge keeps it in F_V (no shadows
+        // there) beside the traced AO.
         constexpr int FL = MODE == MODE_JUDGE ? F_V : F_AO;
-        __nv_bfloat16 *h = sm.htile + warp * 16 * 64;
+        __nv_bfloat16 *h = sm.hin + warp * 16 * aomlp::HIN_STRIDE;
         const uint32_t rx = (uint32_t)P.res[0], ry = (uint32_t)P.res[1];
         for (int g0 = 0; g0 < total; g0 += 16) {
             if (lane < 16) {   // per-hit inputs of hit g0 + lane into row lane
@@ -490,7 +490,7 @@ __device__ void light_hits(const RenderParams &P, Smem<MODE> &sm, int warp, int 
 #pragma unroll
                     for (int k = 0; k < aomlp::NHIT; k++) hx[k] = 0.0f;
                 }
-                aomlp::store_hit_inputs(hx, h + lane * 64);
+                aomlp::store_hit_inputs(hx, h + lane * aomlp::HIN_STRIDE);
             }
             __syncwarp();
             const int gl = g0 + (lane >> 2), gh = gl + 8;
@@ -499,9 +499,8 @@ __device__ void light_hits(const RenderParams &P, Smem<MODE> &sm, int warp, int 
                 vlo = P.vterm + (size_t)__float_as_uint(sm.slot[F_VID][slot_index(sm, warp, gl)][slot_owner(sm, warp, gl)]) * 64;
             if (gh < total)
                 vhi = P.vterm + (size_t)__float_as_uint(sm.slot[F_VID][slot_index(sm, warp, gh)][slot_owner(sm, warp, gh)]) * 64;
-            aomlp::layer1_tile(P.net, vlo, vhi, h);
             float lo, hi;
-            aomlp::layers234(P.net, h, lo, hi);
+            aomlp::mlp_tile(P.net, vlo, vhi, h, lo, hi);
             if ((lane & 3) == 0) {
                 const int g = lane >> 2;
                 if (g0 + g < total) sm.slot[FL][slot_index(sm, warp, g0 + g)][slot_owner(sm, warp, g0 + g)] = lo;
