@@ -174,6 +174,19 @@ lvr_status lvr_export_lod(lvr_ctx *ctx, const lvr_lod *lod, int level, uint32_t 
                           float *len, float *dens);
 void lvr_free_lod(lvr_lod *lod);
 
+/* ------------------------------------------------------------------ record layouts
+ * The ray caster reads each segment as the packed 8-byte record of the
+ * voxelisation (LVR_LAYOUT_AOS8) or, after lvr_lineset_layout, as a 16-byte
+ * record holding the entry and exit face points as six IEEE half floats and
+ * the attribute byte (LVR_LAYOUT_AOS16): more bytes per record, no bit
+ * decoding. Face points are (2 bin + 1) / (2 N), exact in half precision
+ * for the power-of-two bin counts N <= 128 the voxeliser accepts, so both
+ * layouts give bit-identical images. The paper stores only the packed form
+ * (Sec. 6.2). */
+#define LVR_LAYOUT_AOS8 0
+#define LVR_LAYOUT_AOS16 1
+lvr_status lvr_lineset_layout(lvr_ctx *ctx, lvr_lineset *ls, int layout);
+
 /* ------------------------------------------------------------------ rendering
  * Secs. 4-5. One ray per pixel (pinhole camera, pixel centres, row 0 at the
  * top) is traversed through the grid by 3D-DDA; the segments stored in each
@@ -216,6 +229,8 @@ typedef struct lvr_render_desc {
     float   ka, kd;        /* ambient / diffuse weights (0.3 / 0.7 typical) */
     float   bg[3];         /* background colour */
     int32_t tile_w, tile_h;/* ray tile of one warp: 8x4 (0,0 = default), 4x8, 16x2, 32x1 */
+    int32_t layout;        /* segment records read by the ray caster: LVR_LAYOUT_AOS8 (packed,
+                              default) or LVR_LAYOUT_AOS16 (needs lvr_lineset_layout) */
 } lvr_render_desc;
 
 /* rgba: host or device float32 [h * w * 4] for the crop rectangle (row-major,
@@ -229,6 +244,46 @@ typedef struct lvr_render_desc {
 lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
                       const lvr_view *view, const lvr_render_desc *desc,
                       lvr_ao_model *ao, float *rgba, uint64_t *counters);
+
+/* ------------------------------------------------------------------ batched rendering
+ * Many views, possibly of different line sets, sizes and tile shapes, in one
+ * persistent launch (the paper renders one view at a time): the work queue
+ * is the concatenation of every view's 32-ray tiles, largest views first;
+ * each warp takes the next tile from one device counter. The launch (counter
+ * reset + kernel) is captured once into a CUDA graph and replayed by
+ * lvr_batch_render. Each view renders exactly as lvr_render would render it
+ * alone (bit-identical output). All items share one kind of AO: either all
+ * ao_mode 2 (learned) or all ao_mode 0/1, and one record layout; rgba must
+ * be device memory [h][w][4] for the view's crop and stay valid while the
+ * batch exists. Items' line sets, LoDs and models must outlive the batch;
+ * learned models are bound to their LoDs at creation. */
+typedef struct lvr_batch lvr_batch;
+typedef struct lvr_batch_item {
+    const lvr_lineset     *ls;
+    const lvr_lod         *lod;     /* may be NULL unless shadows or AO are on */
+    lvr_view               view;
+    const lvr_render_desc *desc;
+    lvr_ao_model          *ao;      /* ao_mode 2 only */
+    float                 *rgba;    /* device float32 [h][w][4] */
+} lvr_batch_item;
+lvr_status lvr_batch_create(lvr_ctx *ctx, const lvr_batch_item *items, int n, lvr_batch **out);
+/* Launches the captured graph on the context's stream (asynchronous). */
+lvr_status lvr_batch_render(lvr_ctx *ctx, lvr_batch *b);
+/* Total 32-ray tiles and rays of the batch. */
+lvr_status lvr_batch_size(const lvr_batch *b, int64_t *tiles, int64_t *rays);
+void lvr_free_batch(lvr_batch *b);
+
+/* Autotuner: renders the items as a batch with every candidate ray tile
+ * (8x4, 4x8, 16x2, 32x1) and record layout (AOS8, and AOS16 when every
+ * line set has its 16-byte records), `reps` timed replays each after one
+ * warm-up, and reports the fastest. Items' own tile and layout are ignored
+ * during the search; outputs are overwritten. ms[c] is the mean time of
+ * candidate c = layout * 4 + tile index, or -1 when not run. */
+typedef struct lvr_tune {
+    int32_t tile_w, tile_h, layout;
+    float   ms[8];
+} lvr_tune;
+lvr_status lvr_autotune(lvr_ctx *ctx, const lvr_batch_item *items, int n, int reps, lvr_tune *out);
 
 /* ------------------------------------------------------------------ learned ambient occlusion
  * The paper has no counterpart: a small network that predicts the traced

@@ -401,7 +401,7 @@ namespace {
 
 lvr_status refresh(lvr_ctx *ctx, lvr_ao_model *m) {
     refresh_kernel<<<64, 256, 0, ctx->stream>>>(m->params, (bf16 *)m->w1b, (bf16 *)m->w2b, (bf16 *)m->w3b, m->w4b);
-    m->bound_gen = 0;   // voxel terms depend on W1
+    for (auto &b : m->bound) b.gen = 0;   // voxel terms depend on W1
     LVR_CUDA(ctx, cudaGetLastError());
     return LVR_OK;
 }
@@ -563,25 +563,43 @@ static lvr_status make_logd(lvr_ctx *ctx, const lvr_lod *lod, void **buf, size_t
     return LVR_OK;
 }
 
-lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod) {
-    if (m->bound_gen == lod->gen && m->vterm) return LVR_OK;
+lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, const void **vterm) {
+    m->clock++;
+    for (auto &b : m->bound)
+        if (b.gen == lod->gen && b.vterm) {
+            b.used = m->clock;
+            *vterm = b.vterm;
+            return LVR_OK;
+        }
+    // an empty entry (the one with the largest buffer), else the least recently used
+    lvr_ao_model::Bound *slot = nullptr;
+    for (auto &b : m->bound)
+        if (b.gen == 0 && (!slot || b.bytes > slot->bytes)) slot = &b;
+    if (!slot) {
+        slot = &m->bound[0];
+        for (auto &b : m->bound)
+            if (b.used < slot->used) slot = &b;
+    }
     Logd L;
     lvr_status st = make_logd(ctx, lod, &m->logd, &m->logd_bytes, L);
     if (st != LVR_OK) return st;
     const int64_t nvox = (int64_t)lod->dims[0][0] * lod->dims[0][1] * lod->dims[0][2];
     const size_t vb = (size_t)nvox * NH * 2;
-    if (m->vterm_bytes < vb) {
-        dev_free(ctx, m->vterm);
-        m->vterm = nullptr;
-        m->vterm_bytes = 0;
-        if ((st = dev_alloc(ctx, &m->vterm, vb)) != LVR_OK) return st;
-        m->vterm_bytes = vb;
+    if (slot->bytes < vb) {
+        dev_free(ctx, slot->vterm);
+        slot->vterm = nullptr;
+        slot->bytes = 0;
+        slot->gen = 0;
+        if ((st = dev_alloc(ctx, &slot->vterm, vb)) != LVR_OK) return st;
+        slot->bytes = vb;
     }
     const int64_t tiles = (nvox + 31) / 32;
-    vterm_kernel<<<(unsigned)(tiles > 65535 * 8 ? 65535 * 8 : tiles), 64, 0, ctx->stream>>>(L, (const bf16 *)m->w1b,
-                                                                                              (bf16 *)m->vterm);
+    vterm_kernel<<<(unsigned)(tiles > 65535 * 8 ? 65535 * 8 : tiles), 64, 0, ctx->stream>>>(
+        L, (const bf16 *)m->w1b, (bf16 *)slot->vterm);
     LVR_CUDA(ctx, cudaGetLastError());
-    m->bound_gen = lod->gen;
+    slot->gen = lod->gen;
+    slot->used = m->clock;
+    *vterm = slot->vterm;
     return LVR_OK;
 }
 
@@ -622,8 +640,9 @@ extern "C" void lvr_free_ao_model(lvr_ao_model *m) {
     if (!m) return;
     lvr_ctx *ctx = m->ctx;
     cudaSetDevice(ctx->device);
-    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w4b, m->logd, m->vterm};
+    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w4b, m->logd};
     for (void *p : ps) dev_free(ctx, p);
+    for (auto &b : m->bound) dev_free(ctx, b.vterm);
     delete m;
 }
 
@@ -650,7 +669,8 @@ extern "C" lvr_status lvr_ao_infer(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod 
     if (!is_device_ptr(voxel))
         for (int64_t i = 0; i < n; i++)
             if (voxel[i] < 0 || voxel[i] >= nvox) return set_err(ctx, LVR_EINVAL, "voxel id out of range");
-    if ((st = ao_bind(ctx, m, lod)) != LVR_OK) return st;
+    const void *vt = nullptr;
+    if ((st = ao_bind(ctx, m, lod, &vt)) != LVR_OK) return st;
     const bool host_out = !is_device_ptr(ao);
     float *dout = ao;
     if (host_out) {
@@ -659,7 +679,7 @@ extern "C" lvr_status lvr_ao_infer(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod 
     }
     const int64_t tiles = (n + 63) / 64;
     infer_kernel<<<(unsigned)(tiles > 65535 ? 65535 : tiles), 128, 0, ctx->stream>>>(
-        ao_net(m), (const bf16 *)m->vterm, dx, dy, nvox, n, (const int32_t *)dv, (const float *)dd,
+        ao_net(m), (const bf16 *)vt, dx, dy, nvox, n, (const int32_t *)dv, (const float *)dd,
         (const float *)dp, (const float *)dn, dout);
     LVR_CUDA(ctx, cudaGetLastError());
     if (host_out) return copy_out(ctx, ao, dout, (size_t)n * 4);

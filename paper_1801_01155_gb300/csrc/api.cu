@@ -235,5 +235,6 @@ extern "C" void lvr_free_lineset(lvr_lineset *ls) {
     dev_free(ctx, ls->offset);
     dev_free(ctx, ls->rec);
     dev_free(ctx, ls->key);
+    dev_free(ctx, ls->rec16);
     delete ls;
 }

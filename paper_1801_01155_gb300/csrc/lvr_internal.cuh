@@ -35,7 +35,7 @@ struct lvr_ctx {
     size_t stage_in_bytes = 0;
     void *stage_out = nullptr;
     size_t stage_out_bytes = 0;
-    int render_blocks[4] = {0, 0, 0, 0};   // persistent render grid per kernel variant (SMs x resident blocks)
+    int render_blocks[16] = {};            // persistent render grid per kernel variant (SMs x resident blocks)
 };
 
 struct lvr_lineset {
@@ -49,6 +49,7 @@ struct lvr_lineset {
     uint32_t *offset = nullptr;   // [nvox + 1]
     uint64_t *rec = nullptr;      // [nseg] packed segment records
     uint64_t *key = nullptr;      // [nseg] (curve << 32) | ordinal
+    void *rec16 = nullptr;        // [nseg] 16-byte records (lvr_lineset_layout), or null
 };
 
 struct lvr_lod {
@@ -69,17 +70,30 @@ struct lvr_ao_model {
     int64_t adam_t = 0;
     void *w1b = nullptr, *w2b = nullptr, *w3b = nullptr;   // bf16 copies
     float *w4b = nullptr;
-    // voxel term of the LoD the model was last bound to
-    uint64_t bound_gen = 0;
-    void *logd = nullptr;         // bf16 per cell of levels 0..2: log1p(8 dens_l / 8^l)
+    void *logd = nullptr;         // scratch: bf16 per cell of levels 0..2, log1p(8 dens_l / 8^l)
     size_t logd_bytes = 0;
-    void *vterm = nullptr;        // bf16 [voxels][64]
-    size_t vterm_bytes = 0;
+    // voxel terms of the last LoDs the model was bound to (least recently used replaced)
+    static constexpr int kBound = 8;
+    struct Bound {
+        uint64_t gen = 0;         // LoD generation, 0: empty
+        void *vterm = nullptr;    // bf16 [voxels][64]
+        size_t bytes = 0;
+        uint64_t used = 0;
+    } bound[kBound];
+    uint64_t clock = 0;
 };
 
-// Bind `m` to `lod`: (re)compute the per-voxel log features and layer-1
-// voxel term if the model was bound to another LoD (ao_mlp.cu).
-lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod);
+// Bind `m` to `lod`: the layer-1 voxel term of every voxel of `lod`, from
+// the cache or computed (ao_mlp.cu). *vterm stays valid until kBound other
+// LoDs have been bound or the weights change.
+lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, const void **vterm);
+
+// The cached voxel term of `lod` in `m`, or null (no side effects).
+inline const void *ao_cached(const lvr_ao_model *m, const lvr_lod *lod) {
+    for (const auto &b : m->bound)
+        if (b.gen == lod->gen && b.vterm) return b.vterm;
+    return nullptr;
+}
 
 // ------------------------------------------------------------------ packed record
 // 64-bit segment record (Sec. 3.2 / Sec. 6.2 encoding, widened to one word):

@@ -34,8 +34,12 @@
 // Ownership. A voxel keeps a hit iff its entry point lies inside the voxel
 // (in local coordinates, in [0,1)^3). DDA ties step in axis order x, y, z.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
+#include <cuda_fp16.h>
+
+#include <algorithm>
 #include <vector>
 
 #include "ao_mlp.cuh"
@@ -52,6 +56,7 @@ constexpr unsigned FULL = 0xffffffffu;
 struct RenderParams {
     const uint32_t *offset;
     const uint64_t *rec;
+    const uint4 *rec16;           // expanded 16-byte records (layout LAYOUT_AOS16), or null
     int32_t res[3];
     float invN;
     float r2;
@@ -68,7 +73,7 @@ struct RenderParams {
     int32_t shadows, ao, ao_rays, nrays;
     float ao_radius, ka, kd, bg[3];
     float aod[MAX_AO][3];         // hemisphere directions in the (T, B, n) frame
-    float tf[1024];
+    const float4 *gtf;            // batched views: this view's transfer function in global memory
     float4 *out;                  // may be null (sample mode)
     unsigned long long *counters;
     unsigned *tile_counter;
@@ -88,7 +93,11 @@ struct RenderParams {
     unsigned long long *judge;    // [4]: hits, sum |e|, sum traced, sum learned (x 2^32)
     unsigned *judge_max;          // max |e| as float bits
     unsigned *judge_hist;         // [JH] histogram of |e|
+    // transfer function: RGBA per attribute byte (last: batched views copy
+    // only the fields before it into shared memory)
+    alignas(16) float tf[1024];
 };
+constexpr int HOT_BYTES = (int)((offsetof(RenderParams, tf) + 15) & ~(size_t)15);   // fields before tf
 
 struct Vec { float x, y, z; };
 __device__ __forceinline__ Vec mk(float x, float y, float z) { return {x, y, z}; }
@@ -217,11 +226,36 @@ constexpr int JH = 4096;          // judge histogram bins over |e| in [0, 1]
 // voxel id (last field) is kept only by the variants that need it, so the
 // image variant stays within six resident blocks per SM.
 enum { F_PX, F_PY, F_PZ, F_NX, F_NY, F_NZ, F_UX, F_UY, F_UZ, F_CR, F_CG, F_CB, F_AO, F_V, F_VID, NF };
-template <int MODE>
+// End points and attribute of record k in the given layout.
+template <int LAYOUT>
+__device__ __forceinline__ void fetch_record(const RenderParams &P, uint32_t k, Vec &a, Vec &b, uint32_t &attr) {
+    if constexpr (LAYOUT == 1) {
+        const uint4 q = __ldg(P.rec16 + k);
+        const __half2 h0 = *reinterpret_cast<const __half2 *>(&q.x), h1 = *reinterpret_cast<const __half2 *>(&q.y),
+                      h2 = *reinterpret_cast<const __half2 *>(&q.z);
+        a = mk(__low2float(h0), __high2float(h0), __low2float(h1));
+        b = mk(__high2float(h1), __low2float(h2), __high2float(h2));
+        attr = q.w & 0xffu;
+    } else {
+        const uint64_t r = __ldg(P.rec + k);
+        a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
+        b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
+        attr = rec_attr(r);
+    }
+}
+
+// Record layouts: the packed 8-byte record, or 16 bytes with the end points
+// as six half floats (exact for power-of-two bin counts) and the attribute.
+enum { LAYOUT_AOS8 = 0, LAYOUT_AOS16 = 1 };
+
+template <int MODE, int LAYOUT, bool BATCH>
 struct Smem {
     static constexpr int kMode = MODE;
+    static constexpr int kLayout = LAYOUT;
+    static constexpr bool kBatch = BATCH;   // the transfer function is read from global memory
     static constexpr bool kVid = MODE != MODE_IMAGE;
-    float4 tf[256];
+    float4 tf[BATCH ? 1 : 256];
+    float4 hot[BATCH ? 4 : 1][BATCH ? HOT_BYTES / 16 : 1];   // batched: each warp's current view parameters
     float st[KS][RT];             // staged (t, k) of the current voxel, ascending
     uint32_t sk[KS][RT];
     float slot[kVid ? NF : NF - 1][KS][RT];
@@ -279,9 +313,9 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
             const int room = KS - used;
             int nh = 0;
             for (uint32_t k = beg; k < end; k++) {
-                const uint64_t r = __ldg(P.rec + k);
-                const Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
-                const Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
+                Vec a, b;
+                uint32_t attr;
+                fetch_record<SM::kLayout>(P, k, a, b, attr);
                 const float t = capsule_entry(p, ray.D, a, b, P.r2);
                 if (!owned(p, ray.D, t, -ray.T)) continue;
                 if (ray.resume && !key_after(t, k, ray.rt, ray.rk)) continue;
@@ -302,9 +336,9 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
             for (int q = 0; q < take; q++) {
                 const float t = sm.st[q][tid];
                 const uint32_t k = sm.sk[q][tid];
-                const uint64_t r = __ldg(P.rec + k);
-                const Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
-                const Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
+                Vec a, b;
+                uint32_t attr;
+                fetch_record<SM::kLayout>(P, k, a, b, attr);
                 const Vec Pl = axpy(t, ray.D, p);
                 const Vec ba = sub(b, a);
                 const float L2 = dot(ba, ba);
@@ -316,7 +350,7 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                 }
                 Vec n = sub(Pl, axpy(h, ba, a));
                 n = scale(n, rsqrtf(dot(n, n)));
-                const float4 c = sm.tf[rec_attr(r)];
+                const float4 c = SM::kBatch ? __ldg(P.gtf + attr) : sm.tf[attr];
                 // front-to-back weight (Sec. 5.1); the opacity update is rounded
                 // step by step so the termination test is reproducible:
                 // A <- A + (1 - A) * alpha
@@ -456,9 +490,10 @@ __device__ __forceinline__ int slot_index(const SM &sm, int warp, int g) { retur
 //    neighbourhood at the same distances; occlusion is summed over the group
 //    with a fixed butterfly, so the result does not depend on the schedule.
 //  - Each hit's weighted colour is then scaled by ka * AO + kd * V * |n.L|.
-template <int MODE>
-__device__ void light_hits(const RenderParams &P, Smem<MODE> &sm, int warp, int lane, int total, unsigned &nsamp,
+template <class SM>
+__device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, int total, unsigned &nsamp,
                            unsigned long long js[4], float &jmax) {
+    constexpr int MODE = SM::kMode;
     const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
     if (P.shadows) {
         for (int g = lane; g < total; g += 32) {
@@ -560,147 +595,145 @@ __device__ void light_hits(const RenderParams &P, Smem<MODE> &sm, int warp, int 
     }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(RT, MODE == MODE_LEARNED || MODE == MODE_JUDGE ? 4 : 6)
-render_kernel(const __grid_constant__ RenderParams P) {
-    __shared__ Smem<MODE> sm;
-    for (int i = threadIdx.x; i < 256; i += RT)
-        sm.tf[i] = make_float4(P.tf[4 * i], P.tf[4 * i + 1], P.tf[4 * i + 2], P.tf[4 * i + 3]);
-    __syncthreads();
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// Per-block counters of the traversal and the judge.
+struct Stats {
     unsigned nvox = 0, nrec = 0, nsamp = 0, nhit = 0;
     unsigned long long js[4] = {0ull, 0ull, 0ull, 0ull};
     float jmax = 0.0f;
+};
 
-    for (;;) {
-        unsigned tile = 0;
-        if (lane == 0) tile = atomicAdd(P.tile_counter, 1u);
-        tile = __shfl_sync(FULL, tile, 0);
-        if (tile >= (unsigned)P.ntiles) break;
-        const int px = (int)(tile % (unsigned)P.tiles_x) * P.tile_w + lane % P.tile_w;
-        const int py = (int)(tile / (unsigned)P.tiles_x) * P.tile_h + lane / P.tile_w;
-        const bool valid = px < P.cw && py < P.ch;
-        Ray ray;
-        ray.hidx = ray.target = 0;
-        if (MODE == MODE_SAMPLES && valid) {
-            const int64_t pix = (int64_t)py * P.cw + px;
-            P.samp_vox[pix] = -1;
-            uint32_t hsh = P.samp_seed ^ (uint32_t)pix * 0x9e3779b9u;   // integer hash (lowbias32)
-            hsh ^= hsh >> 16; hsh *= 0x7feb352du; hsh ^= hsh >> 15; hsh *= 0x846ca68bu; hsh ^= hsh >> 16;
-            ray.target = (int)(hsh % (uint32_t)P.samp_depth);
-        }
-        ray.A = ray.Cr = ray.Cg = ray.Cb = 0.0f;
-        ray.done = !valid;
-        ray.resume = false;
-        ray.rt = 0.0f;
-        ray.rk = 0;
-        ray.T = 0.0f;
-        if (valid) {
-            const int i = P.x0 + px, j = P.y0 + py;
-            // primary ray: float32 contract, each step correctly rounded
-            const float sx = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * i + 1), (float)P.W), 1.0f), P.tw);
-            const float sy = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * j + 1), (float)P.H), 1.0f), P.th);
-            float d[3];
+// One 32-ray tile (one warp) of one view, from primary rays to output pixels.
+template <class SM>
+__device__ __forceinline__ void render_tile(const RenderParams &P, SM &sm, unsigned tile, int tid, int warp,
+                                            int lane, Stats &S) {
+    constexpr int MODE = SM::kMode;
+    const int px = (int)(tile % (unsigned)P.tiles_x) * P.tile_w + lane % P.tile_w;
+    const int py = (int)(tile / (unsigned)P.tiles_x) * P.tile_h + lane / P.tile_w;
+    const bool valid = px < P.cw && py < P.ch;
+    Ray ray;
+    ray.hidx = ray.target = 0;
+    if (MODE == MODE_SAMPLES && valid) {
+        const int64_t pix = (int64_t)py * P.cw + px;
+        P.samp_vox[pix] = -1;
+        uint32_t hsh = P.samp_seed ^ (uint32_t)pix * 0x9e3779b9u;   // integer hash (lowbias32)
+        hsh ^= hsh >> 16; hsh *= 0x7feb352du; hsh ^= hsh >> 15; hsh *= 0x846ca68bu; hsh ^= hsh >> 16;
+        ray.target = (int)(hsh % (uint32_t)P.samp_depth);
+    }
+    ray.A = ray.Cr = ray.Cg = ray.Cb = 0.0f;
+    ray.done = !valid;
+    ray.resume = false;
+    ray.rt = 0.0f;
+    ray.rk = 0;
+    ray.T = 0.0f;
+    if (valid) {
+        const int i = P.x0 + px, j = P.y0 + py;
+        // primary ray: float32 contract, each step correctly rounded
+        const float sx = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * i + 1), (float)P.W), 1.0f), P.tw);
+        const float sy = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * j + 1), (float)P.H), 1.0f), P.th);
+        float d[3];
 #pragma unroll
-            for (int a = 0; a < 3; a++)
-                d[a] = __fsub_rn(__fadd_rn(P.F[a], __fmul_rn(sx, P.R[a])), __fmul_rn(sy, P.U[a]));
-            const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
-            const float inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
-            ray.D = mk(__fmul_rn(d[0], inv), __fmul_rn(d[1], inv), __fmul_rn(d[2], inv));
-            const float Da[3] = {ray.D.x, ray.D.y, ray.D.z};
-            // slab test: only the entry parameter is needed, approximately
-            float tnear = 0.0f, tfar = INFINITY;
+        for (int a = 0; a < 3; a++)
+            d[a] = __fsub_rn(__fadd_rn(P.F[a], __fmul_rn(sx, P.R[a])), __fmul_rn(sy, P.U[a]));
+        const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
+        const float inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
+        ray.D = mk(__fmul_rn(d[0], inv), __fmul_rn(d[1], inv), __fmul_rn(d[2], inv));
+        const float Da[3] = {ray.D.x, ray.D.y, ray.D.z};
+        // slab test: only the entry parameter is needed, approximately
+        float tnear = 0.0f, tfar = INFINITY;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (Da[a] != 0.0f) {
+                const float ia = 1.0f / Da[a];
+                const float t1 = (0.0f - P.eye[a]) * ia, t2 = ((float)P.res[a] - P.eye[a]) * ia;
+                tnear = fmaxf(tnear, fminf(t1, t2));
+                tfar = fminf(tfar, fmaxf(t1, t2));
+            } else if (P.eye[a] < 0.0f || P.eye[a] > (float)P.res[a]) {
+                tnear = INFINITY;
+            }
+        }
+        if (!(tnear < tfar)) {
+            ray.done = true;
+        } else {
+            // entry point in float-float, split into voxel index + local position
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                if (Da[a] != 0.0f) {
-                    const float ia = 1.0f / Da[a];
-                    const float t1 = (0.0f - P.eye[a]) * ia, t2 = ((float)P.res[a] - P.eye[a]) * ia;
-                    tnear = fmaxf(tnear, fminf(t1, t2));
-                    tfar = fminf(tfar, fmaxf(t1, t2));
-                } else if (P.eye[a] < 0.0f || P.eye[a] > (float)P.res[a]) {
-                    tnear = INFINITY;
-                }
+                const float ph = __fmul_rn(tnear, Da[a]);
+                const float pe = __fmaf_rn(tnear, Da[a], -ph);
+                float sh, s2;
+                two_sum(P.eye[a], ph, sh, s2);
+                const float lo = __fadd_rn(s2, pe);
+                float fl = floorf(sh);
+                float f = __fadd_rn(__fsub_rn(sh, fl), lo);
+                if (f < 0.0f) { fl -= 1.0f; f += 1.0f; }
+                else if (f >= 1.0f) { fl += 1.0f; f -= 1.0f; }
+                int vi = (int)fl;
+                if (vi < 0) { f += (float)vi; vi = 0; }
+                if (vi > P.res[a] - 1) { f += (float)(vi - (P.res[a] - 1)); vi = P.res[a] - 1; }
+                ray.v[a] = vi;
+                ray.pl[a] = f;
+                ray.invD[a] = Da[a] != 0.0f ? 1.0f / Da[a] : INFINITY;
             }
-            if (!(tnear < tfar)) {
-                ray.done = true;
-            } else {
-                // entry point in float-float, split into voxel index + local position
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    const float ph = __fmul_rn(tnear, Da[a]);
-                    const float pe = __fmaf_rn(tnear, Da[a], -ph);
-                    float sh, s2;
-                    two_sum(P.eye[a], ph, sh, s2);
-                    const float lo = __fadd_rn(s2, pe);
-                    float fl = floorf(sh);
-                    float f = __fadd_rn(__fsub_rn(sh, fl), lo);
-                    if (f < 0.0f) { fl -= 1.0f; f += 1.0f; }
-                    else if (f >= 1.0f) { fl += 1.0f; f -= 1.0f; }
-                    int vi = (int)fl;
-                    if (vi < 0) { f += (float)vi; vi = 0; }
-                    if (vi > P.res[a] - 1) { f += (float)(vi - (P.res[a] - 1)); vi = P.res[a] - 1; }
-                    ray.v[a] = vi;
-                    ray.pl[a] = f;
-                    ray.invD[a] = Da[a] != 0.0f ? 1.0f / Da[a] : INFINITY;
-                }
-                ray.T = tnear;
-            }
-        }
-        // alternate traversal and lighting until every ray of the tile is finished
-        for (;;) {
-            const int used = traverse(P, sm, ray, tid, nvox, nrec, nhit);
-            if (P.nrays > 0) {
-                // list the warp's hits: (owner lane, slot), lane-major
-                int pre = used;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(FULL, pre, o);
-                    if (lane >= o) pre += y;
-                }
-                const int total = __shfl_sync(FULL, pre, 31);
-                pre -= used;
-                for (int q = 0; q < used; q++) sm.item[warp][pre + q] = (uint8_t)((lane << 3) | q);
-                __syncwarp();
-                if (total > 0) {
-                    light_hits(P, sm, warp, lane, total, nsamp, js, jmax);
-                    __syncwarp();
-                    for (int q = 0; q < used; q++) {
-                        ray.Cr += sm.slot[F_CR][q][tid];
-                        ray.Cg += sm.slot[F_CG][q][tid];
-                        ray.Cb += sm.slot[F_CB][q][tid];
-                    }
-                    if constexpr (MODE == MODE_SAMPLES) {   // the one stored hit
-                      if (used > 0) {
-                        const int64_t pix = (int64_t)py * P.cw + px;
-                        P.samp_vox[pix] = (int32_t)__float_as_uint(sm.slot[F_VID][0][tid]);
-                        P.samp_dir[3 * pix] = sm.slot[F_UX][0][tid];
-                        P.samp_dir[3 * pix + 1] = sm.slot[F_UY][0][tid];
-                        P.samp_dir[3 * pix + 2] = sm.slot[F_UZ][0][tid];
-                        P.samp_ao[pix] = sm.slot[F_AO][0][tid];
-                        if (P.samp_pos) {
-                            P.samp_pos[3 * pix] = sm.slot[F_PX][0][tid];
-                            P.samp_pos[3 * pix + 1] = sm.slot[F_PY][0][tid];
-                            P.samp_pos[3 * pix + 2] = sm.slot[F_PZ][0][tid];
-                            P.samp_nrm[3 * pix] = sm.slot[F_NX][0][tid];
-                            P.samp_nrm[3 * pix + 1] = sm.slot[F_NY][0][tid];
-                            P.samp_nrm[3 * pix + 2] = sm.slot[F_NZ][0][tid];
-                        }
-                      }
-                    }
-                }
-                __syncwarp();
-            }
-            if (__all_sync(FULL, ray.done)) break;
-        }
-        if (valid && P.out) {
-            const float4 o = make_float4(fmaf(1.0f - ray.A, P.bg[0], ray.Cr), fmaf(1.0f - ray.A, P.bg[1], ray.Cg),
-                                         fmaf(1.0f - ray.A, P.bg[2], ray.Cb), ray.A);
-            P.out[(int64_t)py * P.cw + px] = o;
+            ray.T = tnear;
         }
     }
+    // alternate traversal and lighting until every ray of the tile is finished
+    for (;;) {
+        const int used = traverse(P, sm, ray, tid, S.nvox, S.nrec, S.nhit);
+        if (P.nrays > 0) {
+            // list the warp's hits: (owner lane, slot), lane-major
+            int pre = used;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, pre, o);
+                if (lane >= o) pre += y;
+            }
+            const int total = __shfl_sync(FULL, pre, 31);
+            pre -= used;
+            for (int q = 0; q < used; q++) sm.item[warp][pre + q] = (uint8_t)((lane << 3) | q);
+            __syncwarp();
+            if (total > 0) {
+                light_hits(P, sm, warp, lane, total, S.nsamp, S.js, S.jmax);
+                __syncwarp();
+                for (int q = 0; q < used; q++) {
+                    ray.Cr += sm.slot[F_CR][q][tid];
+                    ray.Cg += sm.slot[F_CG][q][tid];
+                    ray.Cb += sm.slot[F_CB][q][tid];
+                }
+                if constexpr (MODE == MODE_SAMPLES) {   // the one stored hit
+                  if (used > 0) {
+                    const int64_t pix = (int64_t)py * P.cw + px;
+                    P.samp_vox[pix] = (int32_t)__float_as_uint(sm.slot[F_VID][0][tid]);
+                    P.samp_dir[3 * pix] = sm.slot[F_UX][0][tid];
+                    P.samp_dir[3 * pix + 1] = sm.slot[F_UY][0][tid];
+                    P.samp_dir[3 * pix + 2] = sm.slot[F_UZ][0][tid];
+                    P.samp_ao[pix] = sm.slot[F_AO][0][tid];
+                    if (P.samp_pos) {
+                        P.samp_pos[3 * pix] = sm.slot[F_PX][0][tid];
+                        P.samp_pos[3 * pix + 1] = sm.slot[F_PY][0][tid];
+                        P.samp_pos[3 * pix + 2] = sm.slot[F_PZ][0][tid];
+                        P.samp_nrm[3 * pix] = sm.slot[F_NX][0][tid];
+                        P.samp_nrm[3 * pix + 1] = sm.slot[F_NY][0][tid];
+                        P.samp_nrm[3 * pix + 2] = sm.slot[F_NZ][0][tid];
+                    }
+                  }
+                }
+            }
+            __syncwarp();
+        }
+        if (__all_sync(FULL, ray.done)) break;
+    }
+    if (valid && P.out) {
+        const float4 o = make_float4(fmaf(1.0f - ray.A, P.bg[0], ray.Cr), fmaf(1.0f - ray.A, P.bg[1], ray.Cg),
+                                     fmaf(1.0f - ray.A, P.bg[2], ray.Cb), ray.A);
+        P.out[(int64_t)py * P.cw + px] = o;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void flush_stats(const RenderParams &P, int lane, Stats &S) {
     if (P.counters) {
-        const unsigned c0 = __reduce_add_sync(FULL, nvox), c1 = __reduce_add_sync(FULL, nrec),
-                       c2 = __reduce_add_sync(FULL, nsamp), c3 = __reduce_add_sync(FULL, nhit);
+        const unsigned c0 = __reduce_add_sync(FULL, S.nvox), c1 = __reduce_add_sync(FULL, S.nrec),
+                       c2 = __reduce_add_sync(FULL, S.nsamp), c3 = __reduce_add_sync(FULL, S.nhit);
         if (lane == 0) {
             atomicAdd(P.counters + 0, (unsigned long long)c0);
             atomicAdd(P.counters + 1, (unsigned long long)c1);
@@ -711,13 +744,77 @@ render_kernel(const __grid_constant__ RenderParams P) {
     if constexpr (MODE == MODE_JUDGE) {
 #pragma unroll
         for (int c = 0; c < 4; c++)
-            for (int o = 16; o > 0; o >>= 1) js[c] += __shfl_xor_sync(FULL, js[c], o);
-        for (int o = 16; o > 0; o >>= 1) jmax = fmaxf(jmax, __shfl_xor_sync(FULL, jmax, o));
+            for (int o = 16; o > 0; o >>= 1) S.js[c] += __shfl_xor_sync(FULL, S.js[c], o);
+        for (int o = 16; o > 0; o >>= 1) S.jmax = fmaxf(S.jmax, __shfl_xor_sync(FULL, S.jmax, o));
         if (lane == 0) {
 #pragma unroll
-            for (int c = 0; c < 4; c++) atomicAdd(P.judge + c, js[c]);
-            atomicMax(P.judge_max, __float_as_uint(jmax));
+            for (int c = 0; c < 4; c++) atomicAdd(P.judge + c, S.js[c]);
+            atomicMax(P.judge_max, __float_as_uint(S.jmax));
         }
+    }
+}
+
+constexpr int min_blocks(int mode) { return mode == MODE_LEARNED || mode == MODE_JUDGE ? 4 : 6; }
+
+// One view: a persistent grid takes 32-ray tiles from a global counter.
+template <int MODE, int LAYOUT>
+__global__ void __launch_bounds__(RT, min_blocks(MODE))
+render_kernel(const __grid_constant__ RenderParams P) {
+    __shared__ Smem<MODE, LAYOUT, false> sm;
+    for (int i = threadIdx.x; i < 256; i += RT)
+        sm.tf[i] = make_float4(P.tf[4 * i], P.tf[4 * i + 1], P.tf[4 * i + 2], P.tf[4 * i + 3]);
+    __syncthreads();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    Stats S;
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(P.tile_counter, 1u);
+        tile = __shfl_sync(FULL, tile, 0);
+        if (tile >= (unsigned)P.ntiles) break;
+        render_tile(P, sm, tile, tid, warp, lane, S);
+    }
+    flush_stats<MODE>(P, lane, S);
+}
+
+// Many views in one persistent launch: the work queue is the concatenation
+// of the views' tile lists (largest views first); a warp takes the next tile
+// from one global counter and finds its view by binary search over the
+// views' first-tile offsets. Each view's parameters live in global memory.
+struct BatchParams {
+    const RenderParams *items;
+    const unsigned *tile0;        // [n + 1]: first tile of each view, total last
+    int32_t n;
+    unsigned *counter;
+};
+
+template <int MODE, int LAYOUT>
+__global__ void __launch_bounds__(RT, min_blocks(MODE))
+render_batch_kernel(const __grid_constant__ BatchParams B) {
+    __shared__ Smem<MODE, LAYOUT, true> sm;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned total = __ldg(B.tile0 + B.n);
+    int cur = -1;
+    Stats S;
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(B.counter, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= total) break;
+        int lo = 0, hi = B.n - 1;   // last view with tile0 <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(B.tile0 + mid) <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != cur) {   // this warp's view changed: copy its parameters (all but the TF)
+            __syncwarp();
+            const float4 *src = reinterpret_cast<const float4 *>(B.items + lo);
+            for (int i = lane; i < HOT_BYTES / 16; i += 32) sm.hot[warp][i] = __ldg(src + i);
+            __syncwarp();
+            cur = lo;
+        }
+        render_tile(*reinterpret_cast<const RenderParams *>(sm.hot[warp]), sm, t - __ldg(B.tile0 + lo), tid, warp,
+                    lane, S);
     }
 }
 
@@ -753,6 +850,9 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
         return set_err(ctx, LVR_EINVAL, "ao_rays must be in [1,32]");
     if (lod && (lod->dims[0][0] != ls->res[0] || lod->dims[0][1] != ls->res[1] || lod->dims[0][2] != ls->res[2]))
         return set_err(ctx, LVR_EINVAL, "LoD does not belong to this line set");
+    if (desc->layout != LAYOUT_AOS8 && desc->layout != LAYOUT_AOS16) return set_err(ctx, LVR_EINVAL, "bad layout");
+    if (desc->layout == LAYOUT_AOS16 && !ls->rec16 && ls->nseg > 0)
+        return set_err(ctx, LVR_EINVAL, "16-byte records not built (lvr_lineset_layout)");
     int tw = desc->tile_w, th = desc->tile_h;
     if (tw == 0 && th == 0) { tw = 8; th = 4; }
     if (tw * th != 32 || tw < 1 || th < 1) return set_err(ctx, LVR_EINVAL, "tile must have 32 pixels");
@@ -760,6 +860,7 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     memset(&P, 0, sizeof P);
     P.offset = ls->offset;
     P.rec = ls->rec;
+    P.rec16 = (const uint4 *)ls->rec16;
     for (int a = 0; a < 3; a++) P.res[a] = ls->res[a];
     P.invN = 1.0f / (float)ls->bins;
     P.r2 = desc->radius * desc->radius;
@@ -827,31 +928,59 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     }
     memcpy(P.tf, desc->tf_rgba, sizeof P.tf);
     if (P.learned) {
-        lvr_status st = ao_bind(ctx, ao, lod);
+        const void *vt = nullptr;
+        lvr_status st = ao_bind(ctx, ao, lod, &vt);
         if (st != LVR_OK) return st;
         P.net = ao_net(ao);
-        P.vterm = (const __nv_bfloat16 *)ao->vterm;
+        P.vterm = (const __nv_bfloat16 *)vt;
     }
     return LVR_OK;
 }
 
-static lvr_status launch(lvr_ctx *ctx, RenderParams &P) {
+typedef void (*RenderKernel)(RenderParams);
+
+static RenderKernel pick_kernel(int mode, int layout) {
+    switch (mode * 2 + layout) {
+    case MODE_IMAGE * 2: return render_kernel<MODE_IMAGE, LAYOUT_AOS8>;
+    case MODE_IMAGE * 2 + 1: return render_kernel<MODE_IMAGE, LAYOUT_AOS16>;
+    case MODE_LEARNED * 2: return render_kernel<MODE_LEARNED, LAYOUT_AOS8>;
+    case MODE_LEARNED * 2 + 1: return render_kernel<MODE_LEARNED, LAYOUT_AOS16>;
+    case MODE_SAMPLES * 2: return render_kernel<MODE_SAMPLES, LAYOUT_AOS8>;
+    case MODE_JUDGE * 2: return render_kernel<MODE_JUDGE, LAYOUT_AOS8>;
+    default: return nullptr;
+    }
+}
+
+static int kernel_mode(const RenderParams &P) {
+    return P.judge ? MODE_JUDGE : (P.learned ? MODE_LEARNED : (P.samp_vox ? MODE_SAMPLES : MODE_IMAGE));
+}
+
+// Persistent grid size of a kernel: SMs x resident blocks (cached per variant).
+static lvr_status grid_blocks(lvr_ctx *ctx, int slot, const void *kern, int *blocks) {
+    int &b = ctx->render_blocks[slot];
+    if (!b) {
+        int sms = 0, per_sm = 0;
+        LVR_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        LVR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RT, 0));
+        b = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    *blocks = b;
+    return LVR_OK;
+}
+
+static lvr_status launch(lvr_ctx *ctx, RenderParams &P, int layout) {
     cudaStream_t s = ctx->stream;
     P.tile_counter = ctx->d_status + 1;
     LVR_CUDA(ctx, cudaMemsetAsync(P.tile_counter, 0, 4, s));
-    const int mode = P.judge ? MODE_JUDGE : (P.learned ? MODE_LEARNED : (P.samp_vox ? MODE_SAMPLES : MODE_IMAGE));
-    void (*const kern[4])(RenderParams) = {render_kernel<MODE_IMAGE>, render_kernel<MODE_LEARNED>,
-                                           render_kernel<MODE_SAMPLES>, render_kernel<MODE_JUDGE>};
-    int &blocks = ctx->render_blocks[mode];
-    if (!blocks) {
-        int sms = 0, per_sm = 0;
-        LVR_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-        LVR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[mode], RT, 0));
-        blocks = sms * (per_sm > 0 ? per_sm : 1);
-    }
+    const int mode = kernel_mode(P);
+    const RenderKernel kern = pick_kernel(mode, layout);
+    if (!kern) return set_err(ctx, LVR_EINVAL, "this render mode has no 16-byte record variant");
+    int blocks;
+    lvr_status st = grid_blocks(ctx, mode * 2 + layout, (const void *)kern, &blocks);
+    if (st != LVR_OK) return st;
     const int need = (P.ntiles + RT / 32 - 1) / (RT / 32);
     const int grid = need < blocks ? need : blocks;
-    kern[mode]<<<grid, RT, 0, s>>>(P);
+    kern<<<grid, RT, 0, s>>>(P);
     LVR_CUDA(ctx, cudaGetLastError());
     return LVR_OK;
 }
@@ -875,7 +1004,7 @@ extern "C" lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_
         P.counters = host_cnt ? (unsigned long long *)ctx->d_u64 : (unsigned long long *)counters;
         LVR_CUDA(ctx, cudaMemsetAsync(P.counters, 0, 32, s));
     }
-    if ((st = launch(ctx, P)) != LVR_OK) return st;
+    if ((st = launch(ctx, P, desc->layout)) != LVR_OK) return st;
     if (host_out) LVR_CUDA(ctx, cudaMemcpyAsync(rgba, P.out, out_bytes, cudaMemcpyDeviceToHost, s));
     if (host_cnt) LVR_CUDA(ctx, cudaMemcpyAsync(counters, P.counters, 32, cudaMemcpyDeviceToHost, s));
     if (host_out || host_cnt) LVR_CUDA(ctx, cudaStreamSynchronize(s));
@@ -903,7 +1032,7 @@ lvr_status render_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lo
     P.samp_depth = depth;
     P.samp_pos = pos && nrm ? pos : nullptr;
     P.samp_nrm = pos && nrm ? nrm : nullptr;
-    return launch(ctx, P);
+    return launch(ctx, P, LAYOUT_AOS8);
 }
 
 extern "C" lvr_status lvr_ao_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
@@ -941,7 +1070,7 @@ extern "C" lvr_status lvr_ao_judge(lvr_ctx *ctx, const lvr_lineset *ls, const lv
     P.judge_max = hist + JH + 8;
     cudaError_t e = cudaMemsetAsync(hist, 0, JH * 4 + 64, s);
     if (e == cudaSuccess) {
-        st = launch(ctx, P);
+        st = launch(ctx, P, LAYOUT_AOS8);
         e = cudaGetLastError();
     }
     std::vector<unsigned> h(JH + 16);
@@ -973,4 +1102,240 @@ extern "C" lvr_status lvr_ao_judge(lvr_ctx *ctx, const lvr_lineset *ls, const lv
         if (err->p99_abs > err->max_abs) err->p99_abs = err->max_abs;
     }
     return LVR_OK;
+}
+
+// ------------------------------------------------------------------ record layouts
+namespace {
+
+// 16-byte records: end points as six halves (exact: (2 bin + 1) / (2N) with
+// N a power of two <= 1024 has at most 11 significant bits) and the attribute.
+__global__ void expand_records_kernel(const uint64_t *__restrict__ rec, int64_t n, float invN, uint4 *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = rec[i];
+        const Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), invN);
+        const Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), invN);
+        const __half2 h0 = __floats2half2_rn(a.x, a.y), h1 = __floats2half2_rn(a.z, b.x),
+                      h2 = __floats2half2_rn(b.y, b.z);
+        uint4 q;
+        q.x = *reinterpret_cast<const uint32_t *>(&h0);
+        q.y = *reinterpret_cast<const uint32_t *>(&h1);
+        q.z = *reinterpret_cast<const uint32_t *>(&h2);
+        q.w = rec_attr(r);
+        out[i] = q;
+    }
+}
+
+}  // namespace
+
+extern "C" lvr_status lvr_lineset_layout(lvr_ctx *ctx, lvr_lineset *ls, int layout) {
+    if (!ctx) return LVR_EINVAL;
+    if (!ls) return set_err(ctx, LVR_EINVAL, "lvr_lineset_layout: null line set");
+    if (layout == LAYOUT_AOS8) return LVR_OK;
+    if (layout != LAYOUT_AOS16) return set_err(ctx, LVR_EINVAL, "bad layout");
+    if (ls->bins < 1 || ls->bins > 1024 || (ls->bins & (ls->bins - 1)))
+        return set_err(ctx, LVR_EINVAL, "16-byte records need a power-of-two bin count <= 1024");
+    if (ls->rec16 || ls->nseg == 0) return LVR_OK;
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    lvr_status st = dev_alloc(ctx, &ls->rec16, (size_t)ls->nseg * 16);
+    if (st != LVR_OK) return st;
+    const unsigned g = grid1d(ls->nseg, 256) > 65535 ? 65535 : grid1d(ls->nseg, 256);
+    expand_records_kernel<<<g, 256, 0, ctx->stream>>>(ls->rec, ls->nseg, 1.0f / (float)ls->bins, (uint4 *)ls->rec16);
+    LVR_CUDA(ctx, cudaGetLastError());
+    return LVR_OK;
+}
+
+// ------------------------------------------------------------------ batched rendering
+struct lvr_batch {
+    lvr_ctx *ctx = nullptr;
+    int n = 0;
+    int mode = 0, layout = 0;
+    int64_t tiles = 0, rays = 0;
+    RenderParams *d_items = nullptr;
+    unsigned *d_tile0 = nullptr;
+    unsigned *d_counter = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+typedef void (*BatchKernel)(BatchParams);
+
+BatchKernel pick_batch_kernel(int mode, int layout) {
+    switch (mode * 2 + layout) {
+    case MODE_IMAGE * 2: return render_batch_kernel<MODE_IMAGE, LAYOUT_AOS8>;
+    case MODE_IMAGE * 2 + 1: return render_batch_kernel<MODE_IMAGE, LAYOUT_AOS16>;
+    case MODE_LEARNED * 2: return render_batch_kernel<MODE_LEARNED, LAYOUT_AOS8>;
+    case MODE_LEARNED * 2 + 1: return render_batch_kernel<MODE_LEARNED, LAYOUT_AOS16>;
+    default: return nullptr;
+    }
+}
+
+// Builds a batch; `tile` / `layout` >= 0 override every item's own choice.
+lvr_status batch_build(lvr_ctx *ctx, const lvr_batch_item *items, int n, int tile_w, int tile_h, int layout,
+                       lvr_batch **out) {
+    *out = nullptr;
+    if (n < 1 || !items) return set_err(ctx, LVR_EINVAL, "batch needs at least one item");
+    std::vector<RenderParams> P(n);
+    std::vector<int> order(n);
+    int mode = -1, lay = -1;
+    for (int i = 0; i < n; i++) {
+        const lvr_batch_item &it = items[i];
+        if (!it.desc || !it.rgba) return set_err(ctx, LVR_EINVAL, "batch item %d: null desc or output", i);
+        if (!is_device_ptr(it.rgba)) return set_err(ctx, LVR_EINVAL, "batch item %d: rgba must be device memory", i);
+        lvr_render_desc d = *it.desc;
+        if (tile_w > 0) { d.tile_w = tile_w; d.tile_h = tile_h; }
+        if (layout >= 0) d.layout = layout;
+        lvr_status st = setup(ctx, it.ls, it.lod, &it.view, &d, it.ao, P[i]);
+        if (st != LVR_OK) return st;
+        const int m = P[i].learned ? MODE_LEARNED : MODE_IMAGE;
+        if (mode >= 0 && (m != mode || d.layout != lay))
+            return set_err(ctx, LVR_EINVAL, "batch items must share the AO kind and the record layout");
+        mode = m;
+        lay = d.layout;
+        P[i].out = (float4 *)it.rgba;
+        order[i] = i;
+    }
+    // every item's voxel term must still be bound (a model caches a limited number of LoDs)
+    for (int i = 0; i < n; i++) {
+        if (!P[i].learned) continue;
+        if (ao_cached(items[i].ao, items[i].lod) != (const void *)P[i].vterm)
+            return set_err(ctx, LVR_EINVAL, "a model is used with more than %d LoDs in one batch",
+                           lvr_ao_model::kBound);
+    }
+    // largest views first, so the queue ends with small tiles lists
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P[a].ntiles > P[b].ntiles; });
+    lvr_batch *B = new lvr_batch();
+    B->ctx = ctx;
+    B->n = n;
+    B->mode = mode;
+    B->layout = lay;
+    std::vector<RenderParams> sorted(n);
+    std::vector<unsigned> tile0(n + 1);
+    int64_t tot = 0;
+    for (int i = 0; i < n; i++) {
+        sorted[i] = P[order[i]];
+        tile0[i] = (unsigned)tot;
+        tot += sorted[i].ntiles;
+        B->rays += (int64_t)sorted[i].cw * sorted[i].ch;
+    }
+    if (tot >= (int64_t)0xffffffffu) {
+        delete B;
+        return set_err(ctx, LVR_EINVAL, "batch too large");
+    }
+    tile0[n] = (unsigned)tot;
+    B->tiles = tot;
+    cudaStream_t s = ctx->stream;
+    lvr_status st = LVR_OK;
+    auto fail = [&](lvr_status e) { lvr_free_batch(B); return e; };
+    if ((st = dev_alloc(ctx, (void **)&B->d_items, sizeof(RenderParams) * n)) != LVR_OK) return fail(st);
+    for (int i = 0; i < n; i++) sorted[i].gtf = reinterpret_cast<const float4 *>(B->d_items[i].tf);
+    if ((st = dev_alloc(ctx, (void **)&B->d_tile0, sizeof(unsigned) * (n + 1) + 256)) != LVR_OK) return fail(st);
+    B->d_counter = B->d_tile0 + ((n + 1 + 63) & ~63);
+    cudaError_t e = cudaMemcpyAsync(B->d_items, sorted.data(), sizeof(RenderParams) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_tile0, tile0.data(), sizeof(unsigned) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors go out of scope
+    if (e != cudaSuccess) return fail(cuda_err(ctx, e, "lvr_batch_create"));
+    const BatchKernel kern = pick_batch_kernel(mode, lay);
+    int blocks;
+    if ((st = grid_blocks(ctx, 8 + mode * 2 + lay, (const void *)kern, &blocks)) != LVR_OK) return fail(st);
+    const int64_t need = (tot + RT / 32 - 1) / (RT / 32);
+    const int grid = need < blocks ? (int)need : blocks;
+    BatchParams bp;
+    bp.items = B->d_items;
+    bp.tile0 = B->d_tile0;
+    bp.n = n;
+    bp.counter = B->d_counter;
+    // capture: counter reset + the persistent launch
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(B->d_counter, 0, 4, s);
+        kern<<<grid, RT, 0, s>>>(bp);
+        e = cudaStreamEndCapture(s, &B->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+    if (e != cudaSuccess) return fail(cuda_err(ctx, e, "lvr_batch_create (graph)"));
+    *out = B;
+    return LVR_OK;
+}
+
+}  // namespace
+
+extern "C" lvr_status lvr_batch_create(lvr_ctx *ctx, const lvr_batch_item *items, int n, lvr_batch **out) {
+    if (!ctx) return LVR_EINVAL;
+    if (!out) return set_err(ctx, LVR_EINVAL, "lvr_batch_create: null output");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    return batch_build(ctx, items, n, -1, -1, -1, out);
+}
+
+extern "C" lvr_status lvr_batch_render(lvr_ctx *ctx, lvr_batch *b) {
+    if (!ctx) return LVR_EINVAL;
+    if (!b || b->ctx != ctx) return set_err(ctx, LVR_EINVAL, "lvr_batch_render: bad batch");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    LVR_CUDA(ctx, cudaGraphLaunch(b->exec, ctx->stream));
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_batch_size(const lvr_batch *b, int64_t *tiles, int64_t *rays) {
+    if (!b) return LVR_EINVAL;
+    if (tiles) *tiles = b->tiles;
+    if (rays) *rays = b->rays;
+    return LVR_OK;
+}
+
+extern "C" void lvr_free_batch(lvr_batch *b) {
+    if (!b) return;
+    lvr_ctx *ctx = b->ctx;
+    cudaSetDevice(ctx->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    dev_free(ctx, b->d_items);
+    dev_free(ctx, b->d_tile0);
+    delete b;
+}
+
+extern "C" lvr_status lvr_autotune(lvr_ctx *ctx, const lvr_batch_item *items, int n, int reps, lvr_tune *out) {
+    if (!ctx) return LVR_EINVAL;
+    if (!out || reps < 1) return set_err(ctx, LVR_EINVAL, "lvr_autotune: bad argument");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    static const int tiles[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
+    bool aos16 = n > 0 && items;
+    for (int i = 0; aos16 && i < n; i++) aos16 = items[i].ls && (items[i].ls->rec16 || items[i].ls->nseg == 0);
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t e0, e1;
+    LVR_CUDA(ctx, cudaEventCreate(&e0));
+    LVR_CUDA(ctx, cudaEventCreate(&e1));
+    memset(out, 0, sizeof *out);
+    float best = INFINITY;
+    lvr_status st = LVR_OK;
+    for (int c = 0; c < 8 && st == LVR_OK; c++) {
+        out->ms[c] = -1.0f;
+        const int layout = c / 4, ti = c % 4;
+        if (layout == LAYOUT_AOS16 && !aos16) continue;
+        lvr_batch *B = nullptr;
+        if ((st = batch_build(ctx, items, n, tiles[ti][0], tiles[ti][1], layout, &B)) != LVR_OK) break;
+        cudaError_t e = cudaGraphLaunch(B->exec, s);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; r++) e = cudaGraphLaunch(B->exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        lvr_free_batch(B);
+        if (e != cudaSuccess) {
+            st = cuda_err(ctx, e, "lvr_autotune");
+            break;
+        }
+        out->ms[c] = ms / reps;
+        if (out->ms[c] < best) {
+            best = out->ms[c];
+            out->tile_w = tiles[ti][0];
+            out->tile_h = tiles[ti][1];
+            out->layout = layout;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }

@@ -61,7 +61,19 @@ class RenderDesc(C.Structure):
                 ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao_mode", C.c_int32),
                 ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
                 ("kd", C.c_float), ("bg", C.c_float * 3), ("tile_w", C.c_int32),
-                ("tile_h", C.c_int32)]
+                ("tile_h", C.c_int32), ("layout", C.c_int32)]
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("ls", C.c_void_p), ("lod", C.c_void_p), ("view", View), ("desc", C.POINTER(RenderDesc)),
+                ("ao", C.c_void_p), ("rgba", C.c_void_p)]
+
+
+class Tune(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("layout", C.c_int32), ("ms", C.c_float * 8)]
+
+
+LAYOUT_AOS8, LAYOUT_AOS16 = 0, 1
 
 
 class AoTrainDesc(C.Structure):
@@ -96,6 +108,12 @@ _SIGS = {
     "lvr_render": ([_vp, _vp, _vp, C.POINTER(View), C.POINTER(RenderDesc), _vp, _vp, _vp], C.c_int),
     "lvr_voxelize_static": ([_vp, _vp, _vp, _i64, _i64, C.POINTER(GridDesc), _vp, _vp, _vp, _i64,
                              C.POINTER(_i64), _vp], C.c_int),
+    "lvr_lineset_layout": ([_vp, _vp, C.c_int], C.c_int),
+    "lvr_batch_create": ([_vp, C.POINTER(BatchItem), C.c_int, C.POINTER(_vp)], C.c_int),
+    "lvr_batch_render": ([_vp, _vp], C.c_int),
+    "lvr_batch_size": ([_vp, C.POINTER(_i64), C.POINTER(_i64)], C.c_int),
+    "lvr_free_batch": ([_vp], None),
+    "lvr_autotune": ([_vp, C.POINTER(BatchItem), C.c_int, C.c_int, C.POINTER(Tune)], C.c_int),
     "lvr_ao_nparams": ([], C.c_int),
     "lvr_ao_model_create": ([_vp, _vp, C.POINTER(_vp)], C.c_int),
     "lvr_ao_model_params": ([_vp, _vp, _vp], C.c_int),
@@ -323,7 +341,7 @@ def make_view(eye, at, up, fovy_deg, width, height, light_dir, crop=None) -> Vie
 
 
 def make_desc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao_mode=0, ao_rays=16,
-              ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), tile=(0, 0)) -> RenderDesc:
+              ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), tile=(0, 0), layout=0) -> RenderDesc:
     d = RenderDesc()
     d.radius = float(radius)
     tf = np.ascontiguousarray(np.asarray(tf, np.float32)).reshape(-1)
@@ -339,6 +357,7 @@ def make_desc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao_mode=0
     d.kd = float(kd)
     d.bg[:] = [float(x) for x in bg]
     d.tile_w, d.tile_h = int(tile[0]), int(tile[1])
+    d.layout = int(layout)
     return d
 
 
@@ -460,3 +479,69 @@ def ao_train_desc(n_samples, epochs, batch, lr, seed, render: RenderDesc, view_s
     d._render = render                       # keep the referenced struct alive
     d.render = C.pointer(render)
     return d
+
+
+# ---------------------------------------------------------------- record layouts, batches, autotuner
+def lvr_lineset_layout(ctx: Context, ls: LineSet, layout: int):
+    _check(ctx.handle, _L.lvr_lineset_layout(ctx.handle, ls.handle, int(layout)))
+
+
+class Batch:
+    """lvr_batch: many views in one persistent launch, replayed from a CUDA graph."""
+
+    def __init__(self, ctx: Context, h, keep):
+        self.ctx, self.handle, self._keep = ctx, h, keep
+
+    def render(self):
+        _check(self.ctx.handle, _L.lvr_batch_render(self.ctx.handle, self.handle))
+
+    def size(self):
+        t, r = _i64(0), _i64(0)
+        _check(self.ctx.handle, _L.lvr_batch_size(self.handle, C.byref(t), C.byref(r)))
+        return t.value, r.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            _L.lvr_free_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.handle:
+            self.free()
+
+
+def _items(entries):
+    """entries: (LineSet, Lod | None, View, RenderDesc, AoModel | None, rgba device tensor)."""
+    arr = (BatchItem * len(entries))()
+    keep = []
+    for i, (ls, lod, view, desc, model, rgba) in enumerate(entries):
+        arr[i].ls = ls.handle
+        arr[i].lod = lod.handle if lod is not None else None
+        arr[i].view = view
+        arr[i].desc = C.pointer(desc)
+        arr[i].ao = model.handle if model is not None else None
+        arr[i].rgba = _ptr(rgba)
+        keep += [ls, lod, desc, model, rgba]
+    return arr, keep
+
+
+def lvr_batch_create(ctx: Context, entries) -> Batch:
+    arr, keep = _items(entries)
+    h = _vp()
+    _check(ctx.handle, _L.lvr_batch_create(ctx.handle, arr, len(entries), C.byref(h)))
+    return Batch(ctx, h, keep)
+
+
+def lvr_batch_render(ctx: Context, b: Batch):
+    b.render()
+
+
+def lvr_free_batch(b: Batch):
+    b.free()
+
+
+def lvr_autotune(ctx: Context, entries, reps: int = 3) -> dict:
+    arr, keep = _items(entries)
+    t = Tune()
+    _check(ctx.handle, _L.lvr_autotune(ctx.handle, arr, len(entries), int(reps), C.byref(t)))
+    return {"tile": (t.tile_w, t.tile_h), "layout": t.layout, "ms": list(t.ms)}
