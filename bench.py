@@ -35,7 +35,8 @@ ERT = 0.99
 METRIC = "Mrays/s, 1080p transparent + soft shadow + 16 traced AO rays/hit (voxelise + LoD + render per step)"
 WORKLOAD = ("config-2 streamline set (100k lines x 200 vertices, seed 1) in a 256^3 grid with 32^2 face bins, "
             "3-level density LoD, 1920x1080 transparent tubes r=0.15 (alpha 0.05-0.3, ERT 0.99) "
-            "with soft shadows and 16 traced AO rays per hit (config-3 illumination)")
+            "with soft shadows and 16 traced AO rays per hit (config-3 illumination); ray tile and record "
+            "layout chosen by the autotuner before timing")
 
 
 def peaks():
@@ -130,8 +131,21 @@ def run_gpu(args):
         cnt = torch.zeros(4, dtype=torch.int64, device=dev)
     torch.cuda.synchronize()
 
+    # ray tile and record layout: the autotuner's choice on this frame (untimed setup)
+    s0 = lvr.lvr_voxelize(ctx, xyz, attr, offs, gdesc())
+    lvr.lvr_lineset_layout(ctx, s0, lvr.LAYOUT_AOS16)
+    lod0 = lvr.lvr_build_lod(ctx, s0, LEVELS, sig)
+    tune = lvr.lvr_autotune(ctx, [(s0, lod0, view, desc, None, out)], reps=2)
+    lod0.free()
+    s0.free()
+    layout = tune["layout"]
+    desc = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0,
+                         tile=tune["tile"], layout=layout)
+
     def step(counters=None, ev=None):
         s = lvr.lvr_voxelize(ctx, xyz, attr, offs, gdesc())
+        if layout:
+            lvr.lvr_lineset_layout(ctx, s, layout)
         lod = lvr.lvr_build_lod(ctx, s, LEVELS, sig)
         if ev is not None:
             ev[0].record(stream)
@@ -145,7 +159,8 @@ def run_gpu(args):
     step(counters=cnt)
     torch.cuda.synchronize()
     nvox, nrec, nsamp, nhit = (int(x) for x in cnt.cpu().numpy())
-    alg_bytes = 8 * nvox + 8 * nrec + 32 * nsamp
+    rec_bytes = 16 if layout else 8
+    alg_bytes = 8 * nvox + rec_bytes * nrec + 32 * nsamp
 
     for _ in range(args.warmup):
         step()
@@ -183,6 +198,8 @@ def run_gpu(args):
 
     def step_e2e():
         s = lvr.lvr_voxelize(ctx, pin_xyz, pin_attr, pin_offs, gdesc())
+        if layout:
+            lvr.lvr_lineset_layout(ctx, s, layout)
         lod = lvr.lvr_build_lod(ctx, s, LEVELS, sig)
         lvr.lvr_render(ctx, s, lod, view, desc, pin_out)
         lod.free()
@@ -234,15 +251,22 @@ def run_gpu(args):
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "render_kernel", "bytes_per_launch": alg_bytes,
                          "peak_source": f"{which} hbm_gbs (STREAM copy)",
-                         "bytes_model": "8*voxels visited + 8*records tested + 32*LoD trilinear samples"},
+                         "bytes_model": f"8*voxels visited + {rec_bytes}*records tested ({['aos8', 'aos16'][layout]} "
+                                        "records) + 32*LoD trilinear samples",
+                         "frac_if_aos8_bytes": round((8 * nvox + 8 * nrec + 32 * nsamp) / (render_ms / 1e3) / 1e9
+                                                     / peak, 4)},
             "e2e": {"value": round(e2e_value, 3), "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms / args.steps, 3)},
-            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "gpu_launches": (LAUNCHES_PER_STEP + (1 if layout else 0)) * args.steps,
+            "autotune": {"tile": list(tune["tile"]), "layout": ["aos8", "aos16"][layout],
+                         "ms_per_candidate": [round(m, 3) for m in tune["ms"]]},
             "clocks": clk,
         }
         if not args.no_learned and world == 1:
-            line["learned_ao"] = learned_ao(args, lvr, synth, ctx, dev, stream,
-                                            main=(xyz, attr, offs, gdesc, sig, view, out))
+            line["learned_ao"], model = learned_ao(args, lvr, synth, ctx, dev, stream,
+                                                   main=(xyz, attr, offs, gdesc, sig, view, out))
+            if not args.no_batch:
+                line["batched"] = batched(args, lvr, synth, ctx, dev, stream, model)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(ls, tf, cam, budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
@@ -330,7 +354,86 @@ def learned_ao(args, lvr, synth, ctx, dev, stream, main):
                              "speedup": round(tr2 / le2, 3), "first_learned_frame_ms": round(first_ms, 2),
                              "mean_abs_error": round(err2["mean_abs"], 5), "p99_abs_error": round(err2["p99_abs"], 5),
                              "note": "model trained on the small sets only"}
-    return res
+    return res, model
+
+
+# ---------------------------------------------------------------- batched views (config 5)
+C5_SETS = [(20_000, 150, 21, 64, 0.2), (100_000, 150, 22, 256, 0.15), (2_000_000, 150, 23, 512, 0.1)]
+C5_SIZES = [(256, 256), (512, 512), (1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
+C5_VIEWS = 64
+
+
+def batched(args, lvr, synth, ctx, dev, stream, model):
+    """Config 5: 64 views of uneven size over three line sets, transparent
+    with learned AO, in one persistent launch replayed from a CUDA graph;
+    ray tile and record layout from the autotuner (searched on every 4th
+    view); compared with one lvr_render call per view."""
+    import torch
+    tf = synth.tf_ramp(*ALPHA)
+    sig = synth.sigma_lut(tf)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sets = []
+    for n, nv, seed, res, rad in C5_SETS:
+        xyz, attr, offs = synth.make_streamlines_device(n, nv, seed, dev)
+        g = lvr.grid_desc(res, NBINS, scale=float(res), attr_min=float(attr.min()), attr_max=float(attr.max()))
+        ls = lvr.lvr_voxelize(ctx, xyz, attr, offs, g)
+        del xyz, attr, offs
+        lvr.lvr_lineset_layout(ctx, ls, lvr.LAYOUT_AOS16)
+        sets.append((ls, lvr.lvr_build_lod(ctx, ls, LEVELS, sig), res, rad, ls.info().n_segments))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    views = []
+    for i in range(C5_VIEWS):
+        ls, lod, res, rad, _ = sets[i % 3]
+        w, h = C5_SIZES[(i // 3) % len(C5_SIZES)]
+        cam = synth.orbit_views(1, (res,) * 3, [(w, h)], seed=500 + i)[0]
+        view = lvr.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], w, h, cam["light_dir"])
+        out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+        views.append([ls, lod, view, (rad, w, h), model, out])
+
+    def entries(tile, layout, sub=None):
+        sel = views if sub is None else views[::sub]
+        return [(v[0], v[1], v[2], lvr.make_desc(v[3][0], tf, ert_alpha=ERT, ao_mode=2, tile=tile, layout=layout),
+                 v[4], v[5]) for v in sel]
+
+    tune = lvr.lvr_autotune(ctx, entries((0, 0), 0, sub=4), reps=1)
+    ents = entries(tune["tile"], tune["layout"])
+    b = lvr.lvr_batch_create(ctx, ents)
+    tiles, rays = b.size()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.render()
+    e0.record(stream)
+    reps = 3
+    for _ in range(reps):
+        b.render()
+    e1.record(stream)
+    e1.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+
+    def sequential():
+        for (ls, lod, view, desc, m, out) in ents:
+            lvr.lvr_render(ctx, ls, lod, view, desc, out, ao_model=m)
+    sequential()
+    e0.record(stream)
+    for _ in range(reps):
+        sequential()
+    e1.record(stream)
+    e1.synchronize()
+    seq_ms = e0.elapsed_time(e1) / reps
+    return {
+        "config": "config 5: 64 views (256^2 to 3840x2160) over three line sets (64^3/20k, 256^3/100k, 512^3/2M "
+                  "lines x 150 vertices, r = 0.2/0.15/0.1), transparent (ERT 0.99) with learned AO, one persistent "
+                  "launch from a CUDA graph",
+        "sets": [{"res": s[2], "lines": C5_SETS[k][0], "segments": s[4]} for k, s in enumerate(sets)],
+        "build_s": round(build_s, 3), "views": len(ents), "rays": rays, "tiles": tiles,
+        "batch_ms": round(batch_ms, 3), "mrays_s": round(rays / batch_ms / 1e3, 2),
+        "views_per_s": round(len(ents) / batch_ms * 1e3, 2),
+        "sequential_ms": round(seq_ms, 3), "speedup_vs_sequential": round(seq_ms / batch_ms, 3),
+        "autotune": {"tile": list(tune["tile"]), "layout": ["aos8", "aos16"][tune["layout"]],
+                     "ms_per_candidate": [round(m, 3) for m in tune["ms"]],
+                     "candidates": "layout x tile: (aos8, aos16) x (8x4, 4x8, 16x2, 32x1), on every 4th view"},
+    }
 
 
 # voxelise: count, 3 scan kernels, scatter, 2 sort kernels; LoD: 1 + 2 pooling; render: 1
@@ -414,6 +517,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-AO (config 4) block")
     ap.add_argument("--learned-samples", type=int, default=4_000_000)
     ap.add_argument("--learned-epochs", type=int, default=8)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-views (config 5) block")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

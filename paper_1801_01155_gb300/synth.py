@@ -175,6 +175,43 @@ def make_streamlines(n_lines: int, n_vertices: int, seed: int,
     return ls
 
 
+def make_streamlines_device(n_lines: int, n_vertices: int, seed: int, device,
+                            dt: float = 1e-3, modes: int = 16, chunk: int = 262144):
+    """The same RK4 streamlines as make_streamlines, integrated in float64 on
+    a torch device (for line sets too large to trace on the host). Returns
+    device tensors (xyz float32 [n*v][3], attr float32 [n*v], offsets int64
+    [n+1]). Device cos may differ from the host's in the last bits, so the
+    vertices can differ from make_streamlines' by rounding."""
+    import torch
+    field = fourier_field(seed, modes)
+    seeds = torch.from_numpy(field.rng.random((n_lines, 3))).to(device)
+    K = torch.from_numpy(field.k.T.astype(np.float64)).to(device)
+    AMP = torch.from_numpy(field.amp).to(device)
+    PHI = torch.from_numpy(field.phi).to(device)
+    two_pi = 2.0 * math.pi
+
+    def vel(x):
+        return torch.cos(torch.addmm(PHI, x, K, alpha=two_pi)) @ AMP
+
+    xyz = torch.empty((n_lines, n_vertices, 3), dtype=torch.float32, device=device)
+    attr = torch.empty((n_lines, n_vertices), dtype=torch.float32, device=device)
+    for c0 in range(0, n_lines, chunk):
+        x = seeds[c0:c0 + chunk].clone()
+        for i in range(n_vertices):
+            u = vel(x)
+            xyz[c0:c0 + chunk, i] = x.to(torch.float32)
+            attr[c0:c0 + chunk, i] = torch.sqrt((u * u).sum(1)).to(torch.float32)
+            if i + 1 == n_vertices:
+                break
+            k1 = u
+            k2 = vel(x + (0.5 * dt) * k1)
+            k3 = vel(x + (0.5 * dt) * k2)
+            k4 = vel(x + dt * k3)
+            x = x + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    offsets = torch.arange(0, (n_lines + 1) * n_vertices, n_vertices, dtype=torch.int64, device=device)
+    return xyz.reshape(-1, 3), attr.reshape(-1), offsets
+
+
 # ---------------------------------------------------------------- transfer functions
 def tf_ramp(alpha_min: float = 1.0, alpha_max: float = 1.0) -> np.ndarray:
     """256-entry RGBA transfer function, float32 (256, 4).
