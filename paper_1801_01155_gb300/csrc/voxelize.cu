@@ -68,9 +68,19 @@ __device__ __forceinline__ bool load_vertex(const VoxParams &P, int64_t i, int64
     return ok;
 }
 
-__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {   // b > 0
-    int64_t q = a / b;
-    return (a % b != 0 && a < 0) ? q - 1 : q;
+// floor(num / den) for 0 <= num < 2^62, 0 < den, quotient below 2^24: a
+// float32 estimate (relative error < 2^-22, so off by at most one) corrected
+// with exact 64-bit products. Replaces a 64-bit division routine.
+__device__ __forceinline__ int64_t udiv_small(int64_t num, int64_t den) {
+    int64_t q = (int64_t)floorf(__fdividef((float)num, (float)den));
+    if (q < 0) q = 0;
+    while (q > 0 && q * den > num) q--;
+    while ((q + 1) * den <= num) q++;
+    return q;
+}
+
+__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {   // b > 0, |a / b| < 2^24
+    return a >= 0 ? udiv_small(a, b) : -udiv_small(b - 1 - a, b);
 }
 
 // Bin of the face point on an axis b whose coordinate is X0b + Db * n / d,
@@ -83,7 +93,7 @@ __device__ __forceinline__ uint32_t face_bin(int64_t X0b, int64_t Db, int64_t vb
         atomicOr(status, ST_INTERNAL);
         rem_d = rem_d < 0 ? 0 : lim;
     }
-    int64_t b = ((int64_t)N * rem_d) / lim;
+    int64_t b = udiv_small((int64_t)N * rem_d, lim);
     return (uint32_t)(b > N - 1 ? N - 1 : b);
 }
 
@@ -151,9 +161,13 @@ vox_curves_kernel(VoxParams P, uint32_t *cnt, const uint32_t *__restrict__ offse
             const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
             const bool pos = D[ax] > 0;
             const uint32_t hf = 2u * ax + (pos ? 1u : 0u);
-            const uint32_t hu = face_bin(X0[b0], D[b0], cur[b0], bn, bd, N, P.status);
-            const uint32_t hv = face_bin(X0[b1], D[b1], cur[b1], bn, bd, N, P.status);
-            const int64_t hA = A0 + floor_div((A1 - A0) * bn, bd);
+            uint32_t hu = 0, hv = 0;
+            int64_t hA = 0;
+            if (SCATTER) {   // the count pass needs only the voxel sequence
+                hu = face_bin(X0[b0], D[b0], cur[b0], bn, bd, N, P.status);
+                hv = face_bin(X0[b1], D[b1], cur[b1], bn, bd, N, P.status);
+                hA = A0 + floor_div((A1 - A0) * bn, bd);
+            }
             if (have_prev) {
                 const bool st = cur[0] >= 0 && cur[0] < P.res[0] && cur[1] >= 0 &&
                                 cur[1] < P.res[1] && cur[2] >= 0 && cur[2] < P.res[2];
