@@ -118,8 +118,8 @@ def run_gpu(args):
     ctx = lvr.Context(local, stream)
     ls, tf, cam = make_inputs()
     sig = synth.sigma_lut(tf)
-    gdesc = lambda: lvr.grid_desc(R, NBINS, scale=float(R), attr_min=float(ls.attr.min()),  # noqa: E731
-                                  attr_max=float(ls.attr.max()))
+    amin, amax = float(ls.attr.min()), float(ls.attr.max())
+    gdesc = lambda: lvr.grid_desc(R, NBINS, scale=float(R), attr_min=amin, attr_max=amax)  # noqa: E731
     view = lvr.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"])
     desc = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0)
 
@@ -205,7 +205,7 @@ def run_gpu(args):
         lod.free()
         s.free()
 
-    for _ in range(max(1, args.warmup // 2)):
+    for _ in range(args.warmup):
         step_e2e()
     torch.cuda.synchronize()
     if world > 1:
@@ -226,12 +226,7 @@ def run_gpu(args):
     if rank == 0:
         peak, which = peaks()
         achieved = alg_bytes / (render_ms / 1e3) / 1e9
-        traffic = None
-        tf_path = os.path.join(ROOT, "profiles", "render_traffic.json")
-        if os.path.exists(tf_path):
-            t = json.load(open(tf_path))
-            if t.get("kernel_version") == KERNEL_VERSION and t.get("workload") == "bench":
-                traffic = t.get("dram_bytes_per_launch")
+        traffic = measured_traffic(layout, tune["tile"])
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -438,7 +433,27 @@ def batched(args, lvr, synth, ctx, dev, stream, model):
 
 # voxelise: count, 3 scan kernels, scatter, 2 sort kernels; LoD: 1 + 2 pooling; render: 1
 LAUNCHES_PER_STEP = 7 + 3 + 1
-KERNEL_VERSION = "render-v1"
+KERNEL_VERSION = "render-v3"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_kernel_traffic_c2_1080p.md")
+
+
+def measured_traffic(layout, tile):
+    """DRAM bytes per render launch from the committed ncu summary, if it was
+    taken for this kernel version, record layout and ray tile; else None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            kv[k.strip()] = v.strip()
+    if (kv.get("kernel_version") != KERNEL_VERSION or kv.get("layout") != ["aos8", "aos16"][layout]
+            or kv.get("tile") != f"{tile[0]}x{tile[1]}"):
+        return None
+    try:
+        return int(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 # ---------------------------------------------------------------- oracle (CPU) arm
