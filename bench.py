@@ -54,6 +54,23 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x, device):
+    """The largest x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, rays_per_step, steps, ms):
+    """Whole-job Mrays/s: each of `world` replicas renders `steps` frames of
+    `rays_per_step` rays; the job takes as long as its slowest rank (ms)."""
+    return world * rays_per_step * steps / (ms / 1e3) / 1e6
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -181,13 +198,10 @@ def run_gpu(args):
     clk = clocks.stop() if clocks else None
     ms = t0.elapsed_time(t1)
     render_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max(ms, dev)
     ms_step = ms / args.steps
     rays = W * H
-    value = world * rays * args.steps / (ms / 1e3) / 1e6
+    value = job_throughput(world, rays, args.steps, ms)
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs
     # and D2H of the image inside the timed region
@@ -215,11 +229,8 @@ def run_gpu(args):
         step_e2e()
     torch.cuda.synchronize()
     e_ms = (time.perf_counter() - e0) * 1e3
-    if world > 1:
-        tt = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_ms = float(tt.item())
-    e2e_value = world * rays * args.steps / (e_ms / 1e3) / 1e6
+    e_ms = reduce_max(e_ms, dev)
+    e2e_value = job_throughput(world, rays, args.steps, e_ms)
     h2d = ls.xyz.nbytes + ls.attr.nbytes + ls.offsets.nbytes
     d2h = pin_out.numel() * 4
 
