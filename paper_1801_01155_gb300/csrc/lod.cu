@@ -73,6 +73,23 @@ lod_pool_kernel(int cx, int cy, int cz, const uint32_t *__restrict__ ccnt, const
     pdens[p] = R;
 }
 
+// Corner-packed copy of one level for trilinear sampling: padded cell
+// (i, j, k) -> X = i - 1, Y = j - 1, Z = k - 1; .x = v(X, Y), .y = v(X+1, Y),
+// .z = v(X, Y+1), .w = v(X+1, Y+1) in slice Z, zero outside the grid.
+__global__ void __launch_bounds__(256)
+lod_pack_kernel(const float *__restrict__ d, int dx, int dy, int dz, float4 *pk) {
+    const int px = dx + 2, py = dy + 2;
+    const int64_t np = (int64_t)px * py * (dz + 2);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < np; c += (int64_t)gridDim.x * blockDim.x) {
+        const int X = (int)(c % px) - 1, Y = (int)((c / px) % py) - 1, Z = (int)(c / ((int64_t)px * py)) - 1;
+        auto v = [&](int x, int y) {
+            return (x >= 0 && y >= 0 && Z >= 0 && x < dx && y < dy && Z < dz)
+                       ? d[x + (int64_t)dx * (y + (int64_t)dy * Z)] : 0.0f;
+        };
+        pk[c] = make_float4(v(X, Y), v(X + 1, Y), v(X, Y + 1), v(X + 1, Y + 1));
+    }
+}
+
 }  // namespace
 
 extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int levels,
@@ -97,7 +114,9 @@ extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int lev
         const size_t n = (size_t)L->dims[l][0] * L->dims[l][1] * L->dims[l][2];
         if ((st = dev_alloc(ctx, (void **)&L->cnt[l], n * 4)) != LVR_OK) break;
         if ((st = dev_alloc(ctx, (void **)&L->len[l], n * 4)) != LVR_OK) break;
-        st = dev_alloc(ctx, (void **)&L->dens[l], n * 4);
+        if ((st = dev_alloc(ctx, (void **)&L->dens[l], n * 4)) != LVR_OK) break;
+        const size_t np = (size_t)(L->dims[l][0] + 2) * (L->dims[l][1] + 2) * (L->dims[l][2] + 2);
+        st = dev_alloc(ctx, (void **)&L->pk[l], np * 16);
     }
     if (st == LVR_OK) st = ensure_stage_in(ctx, 1024);
     if (st != LVR_OK) {
@@ -115,6 +134,12 @@ extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int lev
             lod_pool_kernel<<<grid1d(np, 256), 256, 0, s>>>(c[0], c[1], c[2], L->cnt[l - 1], L->len[l - 1],
                                                              L->dens[l - 1], p[0], p[1], p[2], L->cnt[l],
                                                              L->len[l], L->dens[l]);
+        }
+        for (int l = 0; l < levels; l++) {
+            const int32_t *dm = L->dims[l];
+            const int64_t np = (int64_t)(dm[0] + 2) * (dm[1] + 2) * (dm[2] + 2);
+            const unsigned g = grid1d(np, 256) > 65535 ? 65535 : grid1d(np, 256);
+            lod_pack_kernel<<<g, 256, 0, s>>>(L->dens[l], dm[0], dm[1], dm[2], L->pk[l]);
         }
         e = cudaGetLastError();
     }
@@ -153,6 +178,7 @@ extern "C" void lvr_free_lod(lvr_lod *lod) {
         dev_free(lod->ctx, lod->cnt[l]);
         dev_free(lod->ctx, lod->len[l]);
         dev_free(lod->ctx, lod->dens[l]);
+        dev_free(lod->ctx, lod->pk[l]);
     }
     delete lod;
 }

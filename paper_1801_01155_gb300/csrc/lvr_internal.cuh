@@ -60,6 +60,10 @@ struct lvr_lod {
     uint32_t *cnt[4] = {};
     float *len[4] = {};
     float *dens[4] = {};
+    // sampling copy of dens: per cell (i, j, k) of the grid padded by one cell
+    // on every side, the four x/y corners (i, j), (i+1, j), (i, j+1), (i+1, j+1)
+    // of z-slice k as one float4 (zero outside the grid)
+    float4 *pk[4] = {};
 };
 
 struct lvr_ao_model {

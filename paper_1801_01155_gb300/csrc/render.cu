@@ -62,7 +62,7 @@ struct RenderParams {
     float r2;
     int32_t levels;
     int32_t ldims[4][3];
-    const float *dens[4];
+    const float4 *pk[4];          // corner-packed levels, padded by one cell per side
     float lod_lo, lod_hi[3];      // support of the density field (level-0 voxels)
     float F[3], R[3], U[3], th, tw, eye[3];
     int32_t W, H, x0, y0, cw, ch;
@@ -163,38 +163,26 @@ __device__ __forceinline__ float capsule_entry(Vec p, Vec D, Vec a, Vec b, float
     return sphere_entry(p, D, a, r2);
 }
 
-// Cell-centred trilinear density at level l, zero outside the grid.
+// Cell-centred trilinear density at level l, zero outside the grid: two
+// 16-byte loads of the corner-packed level (slices iz and iz + 1), the same
+// lerps in the same order as eight scalar corner loads would feed.
 __device__ __forceinline__ float sample_level(const RenderParams &P, int l, Vec x) {
     const float inv = __int_as_float((127 - l) << 23);         // 2^-l
     const float qx = fmaf(x.x, inv, -0.5f), qy = fmaf(x.y, inv, -0.5f), qz = fmaf(x.z, inv, -0.5f);
     const float fx0 = floorf(qx), fy0 = floorf(qy), fz0 = floorf(qz);
     const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
-    const float fx = qx - fx0, fy = qy - fy0, fz = qz - fz0;
     const int dx = P.ldims[l][0], dy = P.ldims[l][1], dz = P.ldims[l][2];
-    const float *__restrict__ d = P.dens[l];
-    if ((unsigned)ix < (unsigned)(dx - 1) && (unsigned)iy < (unsigned)(dy - 1) && (unsigned)iz < (unsigned)(dz - 1)) {
-        // all eight corners inside: one base index, three strides
-        const unsigned sy = (unsigned)dx, sz = (unsigned)dx * (unsigned)dy;
-        const float *c = d + ((unsigned)ix + sy * ((unsigned)iy + (unsigned)dy * (unsigned)iz));
-        const float v000 = __ldg(c), v100 = __ldg(c + 1), v010 = __ldg(c + sy), v110 = __ldg(c + sy + 1);
-        const float v001 = __ldg(c + sz), v101 = __ldg(c + sz + 1), v011 = __ldg(c + sz + sy),
-                    v111 = __ldg(c + sz + sy + 1);
-        const float x00 = fmaf(fx, v100 - v000, v000), x10 = fmaf(fx, v110 - v010, v010);
-        const float x01 = fmaf(fx, v101 - v001, v001), x11 = fmaf(fx, v111 - v011, v011);
-        const float y0 = fmaf(fy, x10 - x00, x00), y1 = fmaf(fy, x11 - x01, x01);
-        return fmaf(fz, y1 - y0, y0);
-    }
-    float acc = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const int X = ix + (c & 1), Y = iy + ((c >> 1) & 1), Z = iz + ((c >> 2) & 1);
-        if ((unsigned)X < (unsigned)dx && (unsigned)Y < (unsigned)dy && (unsigned)Z < (unsigned)dz) {
-            const float w = ((c & 1) ? fx : 1.0f - fx) * (((c >> 1) & 1) ? fy : 1.0f - fy) *
-                            (((c >> 2) & 1) ? fz : 1.0f - fz);
-            acc = fmaf(w, __ldg(d + (X + (int64_t)dx * (Y + (int64_t)dy * Z))), acc);
-        }
-    }
-    return acc;
+    // cells with both corners outside on some axis sample zero
+    if ((unsigned)(ix + 1) > (unsigned)dx || (unsigned)(iy + 1) > (unsigned)dy || (unsigned)(iz + 1) > (unsigned)dz)
+        return 0.0f;
+    const float fx = qx - fx0, fy = qy - fy0, fz = qz - fz0;
+    const unsigned px = (unsigned)dx + 2u, sz = px * ((unsigned)dy + 2u);
+    const float4 *c = P.pk[l] + ((unsigned)(ix + 1) + px * (unsigned)(iy + 1) + sz * (unsigned)(iz + 1));
+    const float4 a = __ldg(c), b = __ldg(c + sz);
+    const float x00 = fmaf(fx, a.y - a.x, a.x), x10 = fmaf(fx, a.w - a.z, a.z);
+    const float x01 = fmaf(fx, b.y - b.x, b.x), x11 = fmaf(fx, b.w - b.z, b.z);
+    const float y0 = fmaf(fy, x10 - x00, x00), y1 = fmaf(fy, x11 - x01, x01);
+    return fmaf(fz, y1 - y0, y0);
 }
 
 // A voxel owns a hit iff the entry point p + t D lies in its [0,1)^3 and in
@@ -868,7 +856,7 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
         P.levels = lod->levels;
         for (int l = 0; l < lod->levels; l++) {
             for (int a = 0; a < 3; a++) P.ldims[l][a] = lod->dims[l][a];
-            P.dens[l] = lod->dens[l];
+            P.pk[l] = lod->pk[l];
         }
         const float cell = (float)(1 << (lod->levels - 1));
         P.lod_lo = -0.5f * cell;
