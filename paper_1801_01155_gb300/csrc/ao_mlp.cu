@@ -429,7 +429,7 @@ struct Work {
 
 lvr_status work_alloc(lvr_ctx *ctx, int R, Work &w, std::vector<void *> &keep) {
     w.splits = R >= 4096 ? 32 : (R >= 1024 ? 8 : 1);
-    const size_t rb = (size_t)(R < 64 ? 64 : R);   // dH doubles as the 65-float output-layer scratch
+    const size_t rb = (size_t)R;
     const size_t nblk = (rb + EB - 1) / EB + (rb + 63) / 64 + 8;
     struct { void **p; size_t b; } req[] = {
         {(void **)&w.X, rb * NIN * 2}, {(void **)&w.H1, rb * NH * 2}, {(void **)&w.H2, rb * NH * 2},
@@ -476,9 +476,8 @@ void pass(cudaStream_t s, const lvr_ao_model *m, int R, Work &w, float *grads) {
     out_kernel<<<nb, EB, 0, s>>>(w.H3, m->w4b, p + OB4, w.y, R, w.dz4, w.part, w.pred);
     if (!grads) return;
     // output layer gradients: db4, dW4
-    colsum_kernel<<<1, 128, 0, s>>>(w.part + 1, nb, 1 + NH, 2 + NH, w.dH);   // scratch: [db4, dW4...]
-    cudaMemcpyAsync(grads + OB4, w.dH, 4, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(grads + OW4, w.dH + 1, NH * 4, cudaMemcpyDeviceToDevice, s);
+    colsum_kernel<<<1, 32, 0, s>>>(w.part + 1, nb, 1, 2 + NH, grads + OB4);    // db4 = sum dz4
+    colsum_kernel<<<1, 64, 0, s>>>(w.part + 2, nb, NH, 2 + NH, grads + OW4);   // dW4 = H3^T dz4
     const int nb64 = (R + 63) / 64;
     float *bpart = w.part + (size_t)nb * (2 + NH);
     // layer 3: dZ3 = (dz4 w4) * [Z3 > 0]; dW3 = dZ3^T H2; db3
@@ -498,12 +497,22 @@ void pass(cudaStream_t s, const lvr_ao_model *m, int R, Work &w, float *grads) {
 }
 
 lvr_status adam_step(lvr_ctx *ctx, lvr_ao_model *m, float lr) {
-    if (!m->adam_m) {
-        lvr_status st;
-        if ((st = dev_alloc(ctx, (void **)&m->adam_m, NPARAM * 4)) != LVR_OK) return st;
-        if ((st = dev_alloc(ctx, (void **)&m->adam_v, NPARAM * 4)) != LVR_OK) return st;
-        LVR_CUDA(ctx, cudaMemsetAsync(m->adam_m, 0, NPARAM * 4, ctx->stream));
-        LVR_CUDA(ctx, cudaMemsetAsync(m->adam_v, 0, NPARAM * 4, ctx->stream));
+    if (!m->adam_m || !m->adam_v) {   // both moments, zeroed, or neither
+        float *mm = nullptr, *vv = nullptr;
+        lvr_status st = dev_alloc(ctx, (void **)&mm, NPARAM * 4);
+        if (st == LVR_OK) st = dev_alloc(ctx, (void **)&vv, NPARAM * 4);
+        cudaError_t e = cudaSuccess;
+        if (st == LVR_OK) e = cudaMemsetAsync(mm, 0, NPARAM * 4, ctx->stream);
+        if (st == LVR_OK && e == cudaSuccess) e = cudaMemsetAsync(vv, 0, NPARAM * 4, ctx->stream);
+        if (st != LVR_OK || e != cudaSuccess) {
+            dev_free(ctx, mm);
+            dev_free(ctx, vv);
+            return st != LVR_OK ? st : cuda_err(ctx, e, "adam moments");
+        }
+        dev_free(ctx, m->adam_m);
+        dev_free(ctx, m->adam_v);
+        m->adam_m = mm;
+        m->adam_v = vv;
         m->adam_t = 0;
     }
     m->adam_t++;
@@ -512,14 +521,17 @@ lvr_status adam_step(lvr_ctx *ctx, lvr_ao_model *m, float lr) {
     return refresh(ctx, m);
 }
 
-float host_loss(lvr_ctx *ctx, const Work &w, int R) {
+// Mean squared error of the last forward pass over R rows (sum of the
+// per-block partial sums in fixed order).
+lvr_status host_loss(lvr_ctx *ctx, const Work &w, int R, double *mse) {
     const int nb = (R + EB - 1) / EB;
     std::vector<float> part((size_t)nb * (2 + NH));
-    cudaMemcpyAsync(part.data(), w.part, part.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
-    cudaStreamSynchronize(ctx->stream);
+    LVR_CUDA(ctx, cudaMemcpyAsync(part.data(), w.part, part.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    LVR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     double s = 0.0;
     for (int b = 0; b < nb; b++) s += part[(size_t)b * (2 + NH)];
-    return (float)(s / R);
+    *mse = s / R;
+    return LVR_OK;
 }
 
 // splitmix64: counter-based generator for initial weights and sampling views
@@ -725,14 +737,18 @@ extern "C" lvr_status lvr_ao_train_step(lvr_ctx *ctx, lvr_ao_model *m, int64_t n
         for (void *p : keep) dev_free(ctx, p);
         return st;
     }
-    cudaMemcpyAsync(w.X, X, (size_t)n * NIN * 2, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(w.y, y, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
-    pass(s, m, (int)n, w, m->grads);
-    if (loss) *loss = host_loss(ctx, w, (int)n);
-    if (grads) st = copy_out(ctx, grads, m->grads, NPARAM * 4);
+    cudaError_t e = cudaMemcpyAsync(w.X, X, (size_t)n * NIN * 2, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.y, y, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+        pass(s, m, (int)n, w, m->grads);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = cuda_err(ctx, e, "lvr_ao_train_step");
+    double mse = 0.0;
+    if (st == LVR_OK && loss && (st = host_loss(ctx, w, (int)n, &mse)) == LVR_OK) *loss = (float)mse;
+    if (st == LVR_OK && grads) st = copy_out(ctx, grads, m->grads, NPARAM * 4);
     if (st == LVR_OK && lr > 0.0f) st = adam_step(ctx, m, lr);
     for (void *p : keep) dev_free(ctx, p);
-    LVR_CUDA(ctx, cudaGetLastError());
     return st;
 }
 
@@ -866,7 +882,9 @@ extern "C" lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets,
         const int rows = (int)(N - b < R ? N - b : R);
         gather_rows_kernel<<<rows, 32, 0, s>>>(Xall, sao, N, b, 1, rows, w.X, w.y);
         pass(s, m, rows, w, nullptr);
-        se += (double)host_loss(ctx, w, rows) * rows;
+        double mse = 0.0;
+        if ((st = host_loss(ctx, w, rows, &mse)) != LVR_OK) { lvr_free_ao_model(m); cleanup(); return st; }
+        se += mse * rows;
     }
     if (final_mse) *final_mse = (float)(se / N);
     cleanup();
