@@ -126,6 +126,9 @@ typedef struct orc_rdesc {
     float   ka, kd;             /* ambient and diffuse weights */
     float   bg[3];              /* background colour */
     const float *ao_params;     /* learned AO parameters (ao == 2), see orc_ao_mlp */
+    int32_t still;              /* 1: camera at rest (reading R2): also test the 26
+                                   neighbouring voxels' segments; one hit per line id
+                                   per voxel */
 } orc_rdesc;
 
 /* counters[0..3]: voxels visited, records tested, LoD trilinear samples,

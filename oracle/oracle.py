@@ -30,7 +30,7 @@ class RDesc(C.Structure):
     _fields_ = [("radius", C.c_float), ("tf", C.c_float * 1024), ("opaque", C.c_int32),
                 ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao", C.c_int32),
                 ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
-                ("kd", C.c_float), ("bg", C.c_float * 3), ("ao_params", C.c_void_p)]
+                ("kd", C.c_float), ("bg", C.c_float * 3), ("ao_params", C.c_void_p), ("still", C.c_int32)]
 
 
 def _p(a):
@@ -229,7 +229,8 @@ def make_view(eye, at, up, fovy_deg, width, height, light_dir) -> View:
 
 
 def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False,
-               ao_rays=16, ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), ao_params=None) -> RDesc:
+               ao_rays=16, ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), ao_params=None,
+               still=False) -> RDesc:
     """ao: False/0 off, True/1 traced, 2 learned (ao_params: float32 [ao_nparams()])."""
     d = RDesc()
     d.radius = float(radius)
@@ -245,6 +246,7 @@ def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False
     d.ka = float(ka)
     d.kd = float(kd)
     d.bg[:] = [float(x) for x in bg]
+    d.still = int(bool(still))
     if ao_params is not None:
         ao_params = np.ascontiguousarray(ao_params, np.float32)
         assert ao_params.size == ao_nparams()

@@ -477,6 +477,21 @@ static void flag_sorted_ties(const orc_voxset *vs, const hit *hs, int nh, pixsta
     }
 }
 
+/* Sec. 4.1's line-id rule (reading R2): among one voxel's hits, sorted by
+ * (depth, index), keep only the first of each local line id (curve index
+ * mod 32, the record's 5-bit id). Returns the new count. */
+static int dedup_line_ids(const orc_voxset *vs, hit *hs, int nh) {
+    uint32_t seen = 0;
+    int m = 0;
+    for (int i = 0; i < nh; i++) {
+        const uint32_t id = 1u << (vs->seg[hs[i].k].curve & 31u);
+        if (seen & id) continue;
+        seen |= id;
+        hs[m++] = hs[i];
+    }
+    return m;
+}
+
 /* One ray by DDA traversal (Sec. 4). */
 static void trace_dda(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *rd,
                       const double *O, const double *D, const double *Lt, pixstate *ps,
@@ -514,32 +529,43 @@ static void trace_dda(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *r
         int ax = 0;
         for (int a = 1; a < 3; a++) if (tmax[a] < tmax[ax]) ax = a;
         double t1 = tmax[ax];
-        int64_t vid = v[0] + (int64_t)R[0] * (v[1] + (int64_t)R[1] * v[2]);
-        uint32_t beg = vs->offset[vid], end = vs->offset[vid + 1];
         ps->nvox++;
-        if (end > beg) {
-            ps->nrec += end - beg;
-            if ((int)(end - beg) > *bufcap) {
-                *bufcap = (int)(end - beg);
-                *buf = (hit *)realloc(*buf, sizeof(hit) * (size_t)*bufcap);
-            }
-            int nh = 0;
-            for (uint32_t k = beg; k < end; k++) {
-                double a[3], b[3], tc;
-                entry E;
-                seg_world(vs, &vs->seg[k], a, b);
-                double dist = line_segment_distance(O, D, a, b, &tc);
-                if (tc > t0 - 0.01 && tc < t1 + 0.01) note(ps, fabs(dist - r) / EPS_G, TIE_GRAZE);
-                if (!capsule_entry_s(O, D, a, b, r, &E)) continue;
-                double t = E.t, eps = EPS_T + ERR_Q * E.sens;
-                note(ps, fmin(fabs(t - t0), fabs(t - t1)) / eps, TIE_OWNER);
-                if (t >= t0 && t < t1) {
-                    (*buf)[nh].t = t; (*buf)[nh].eps = eps; (*buf)[nh].k = k; (*buf)[nh].e = E;
-                    nh++;
+        /* candidate segments: those stored in this voxel, or (camera at rest,
+         * reading R2) in this voxel and its 26 neighbours */
+        const int reach = rd->still ? 1 : 0;
+        int nh = 0;
+        for (int dz = -reach; dz <= reach; dz++)
+            for (int dy = -reach; dy <= reach; dy++)
+                for (int dx = -reach; dx <= reach; dx++) {
+                    const int64_t X = v[0] + dx, Y = v[1] + dy, Z = v[2] + dz;
+                    if (X < 0 || Y < 0 || Z < 0 || X >= R[0] || Y >= R[1] || Z >= R[2]) continue;
+                    const int64_t vid = X + (int64_t)R[0] * (Y + (int64_t)R[1] * Z);
+                    const uint32_t beg = vs->offset[vid], end = vs->offset[vid + 1];
+                    if (end == beg) continue;
+                    ps->nrec += end - beg;
+                    if (nh + (int)(end - beg) > *bufcap) {
+                        *bufcap = nh + (int)(end - beg) + 64;
+                        *buf = (hit *)realloc(*buf, sizeof(hit) * (size_t)*bufcap);
+                    }
+                    for (uint32_t k = beg; k < end; k++) {
+                        double a[3], b[3], tc;
+                        entry E;
+                        seg_world(vs, &vs->seg[k], a, b);
+                        double dist = line_segment_distance(O, D, a, b, &tc);
+                        if (tc > t0 - 0.01 && tc < t1 + 0.01) note(ps, fabs(dist - r) / EPS_G, TIE_GRAZE);
+                        if (!capsule_entry_s(O, D, a, b, r, &E)) continue;
+                        double t = E.t, eps = EPS_T + ERR_Q * E.sens;
+                        note(ps, fmin(fabs(t - t0), fabs(t - t1)) / eps, TIE_OWNER);
+                        if (t >= t0 && t < t1) {
+                            (*buf)[nh].t = t; (*buf)[nh].eps = eps; (*buf)[nh].k = k; (*buf)[nh].e = E;
+                            nh++;
+                        }
+                    }
                 }
-            }
+        if (nh > 0) {
             qsort(*buf, (size_t)nh, sizeof(hit), hit_cmp);
             flag_sorted_ties(vs, *buf, nh, ps);
+            if (rd->still) nh = dedup_line_ids(vs, *buf, nh);
             for (int i = 0; i < nh && !ps->done; i++) shade_composite(vs, L, rd, O, D, Lt, &(*buf)[i], ps);
         }
         if (ps->done) break;
@@ -548,6 +574,68 @@ static void trace_dda(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *r
         if (v[ax] < 0 || v[ax] >= R[ax]) break;
         tmax[ax] = ((double)(step[ax] > 0 ? v[ax] + 1 : v[ax]) - O[ax]) / D[ax];
     }
+}
+
+/* One ray by brute force with the camera at rest (reading R2): every capsule
+ * of every voxel; a hit belongs to the grid cell that holds its entry point
+ * (dropped outside the grid); per cell the first hit of each line id is
+ * kept; globally sorted by depth. */
+static void trace_brute_still(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *rd,
+                              const double *O, const double *D, const double *Lt, pixstate *ps) {
+    const int32_t *R = vs->grid.res;
+    const double r = rd->radius;
+    int64_t cap = 64, nh = 0;
+    hit *hs = (hit *)malloc(sizeof(hit) * (size_t)cap);
+    int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    for (int64_t k = 0; k < vs->nseg; k++) {
+        double a[3], b[3], tc;
+        entry E;
+        seg_world(vs, &vs->seg[k], a, b);
+        double dist = line_segment_distance(O, D, a, b, &tc);
+        note(ps, fabs(dist - r) / EPS_G, TIE_GRAZE);
+        if (!capsule_entry_s(O, D, a, b, r, &E)) continue;
+        double t = E.t, eps = EPS_T + ERR_Q * E.sens;
+        double P[3] = {O[0] + t * D[0], O[1] + t * D[1], O[2] + t * D[2]};
+        int64_t c[3];
+        int inside = 1;
+        double margin = 1e300;
+        for (int a3 = 0; a3 < 3; a3++) {
+            c[a3] = (int64_t)floor(P[a3]);
+            if (c[a3] < 0 || c[a3] >= R[a3]) inside = 0;
+            if (D[a3] != 0.0) {
+                margin = fmin(margin, fabs(P[a3] - c[a3]) / fabs(D[a3]));
+                margin = fmin(margin, fabs(P[a3] - (c[a3] + 1)) / fabs(D[a3]));
+            }
+        }
+        note(ps, margin / eps, TIE_OWNER);
+        if (!inside) continue;
+        if (nh == cap) {
+            cap *= 2;
+            hs = (hit *)realloc(hs, sizeof(hit) * (size_t)cap);
+            cell = (int64_t *)realloc(cell, sizeof(int64_t) * (size_t)cap);
+        }
+        hs[nh].t = t; hs[nh].eps = eps; hs[nh].k = k; hs[nh].e = E;
+        nh++;
+    }
+    qsort(hs, (size_t)nh, sizeof(hit), hit_cmp);
+    flag_sorted_ties(vs, hs, (int)nh, ps);
+    /* first hit of each (cell, line id) */
+    int64_t m = 0;
+    for (int64_t i = 0; i < nh; i++) {
+        const double *t_ = &hs[i].t;
+        double P[3] = {O[0] + *t_ * D[0], O[1] + *t_ * D[1], O[2] + *t_ * D[2]};
+        const int64_t ci = (int64_t)floor(P[0]) + (int64_t)R[0] * ((int64_t)floor(P[1]) + (int64_t)R[1] * (int64_t)floor(P[2]));
+        const uint32_t id = vs->seg[hs[i].k].curve & 31u;
+        int dup = 0;
+        for (int64_t j = 0; j < m; j++)
+            if (cell[j] == ci && (vs->seg[hs[j].k].curve & 31u) == id) { dup = 1; break; }
+        if (dup) continue;
+        cell[m] = ci;
+        hs[m++] = hs[i];
+    }
+    for (int64_t i = 0; i < m && !ps->done; i++) shade_composite(vs, L, rd, O, D, Lt, &hs[i], ps);
+    free(hs);
+    free(cell);
 }
 
 /* One ray by brute force: every capsule of every voxel, kept iff its entry
@@ -633,7 +721,8 @@ int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
             pixstate ps;
             memset(&ps, 0, sizeof ps);
             ps.margin = 1e300;
-            if (mode == ORC_RENDER_BRUTE) trace_brute(vs, L, rd, O, D, Lt, &ps);
+            if (mode == ORC_RENDER_BRUTE && rd->still) trace_brute_still(vs, L, rd, O, D, Lt, &ps);
+            else if (mode == ORC_RENDER_BRUTE) trace_brute(vs, L, rd, O, D, Lt, &ps);
             else trace_dda(vs, L, rd, O, D, Lt, &ps, &buf, &bufcap);
             for (int c = 0; c < 3; c++) rgba[4 * p + c] = ps.C[c] + (1.0 - ps.A) * rd->bg[c];
             rgba[4 * p + 3] = ps.A;
