@@ -231,6 +231,11 @@ typedef struct lvr_render_desc {
     int32_t tile_w, tile_h;/* ray tile of one warp: 8x4 (0,0 = default), 4x8, 16x2, 32x1 */
     int32_t layout;        /* segment records read by the ray caster: LVR_LAYOUT_AOS8 (packed,
                               default) or LVR_LAYOUT_AOS16 (needs lvr_lineset_layout) */
+    int32_t still;         /* 1: camera at rest (Sec. 4.1): each visited voxel also tests the
+                              segments of its 26 neighbours (a hit still belongs to the voxel
+                              holding its entry point; no tube piece is missed for radii up to
+                              half a voxel) and blends only the first hit of each 5-bit line id
+                              (curve index mod 32) per voxel. Not with ao_mode 2 or batches. */
 } lvr_render_desc;
 
 /* rgba: host or device float32 [h * w * 4] for the crop rectangle (row-major,

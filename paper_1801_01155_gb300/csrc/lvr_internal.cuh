@@ -120,6 +120,7 @@ __host__ __device__ inline uint32_t rec_u_out(uint64_t r) { return (uint32_t)((r
 __host__ __device__ inline uint32_t rec_v_out(uint64_t r) { return (uint32_t)((r >> 27) & 127u); }
 __host__ __device__ inline uint32_t rec_attr(uint64_t r) { return (uint32_t)((r >> 34) & 255u); }
 __host__ __device__ inline uint32_t rec_cont(uint64_t r) { return (uint32_t)((r >> 42) & 1u); }
+__host__ __device__ inline uint32_t rec_line_id(uint64_t r) { return (uint32_t)((r >> 43) & 31u); }
 
 // ------------------------------------------------------------------ host helpers
 lvr_status set_err(lvr_ctx *ctx, lvr_status st, const char *fmt, ...);

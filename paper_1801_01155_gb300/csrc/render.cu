@@ -79,6 +79,7 @@ struct RenderParams {
     unsigned *tile_counter;
     // learned AO (ao_mode 2)
     int32_t learned;
+    int32_t still;                // camera at rest: neighbouring voxels, one hit per line id
     aomlp::Net net;
     const __nv_bfloat16 *vterm;
     // sample mode: per pixel the hit of index `target` (hash of seed and
@@ -205,8 +206,9 @@ __device__ __forceinline__ bool key_after(float t, uint32_t k, float lt, uint32_
 
 // Kernel variants: image with traced or no AO; image with learned AO; hit
 // samples (voxel, direction, traced AO) for the learned-AO trainer; image with
-// learned AO that also traces AO at every hit and records the difference.
-enum { MODE_IMAGE = 0, MODE_LEARNED = 1, MODE_SAMPLES = 2, MODE_JUDGE = 3 };
+// learned AO that also traces AO at every hit and records the difference;
+// image with the camera at rest (neighbouring voxels' segments, line ids).
+enum { MODE_IMAGE = 0, MODE_LEARNED = 1, MODE_SAMPLES = 2, MODE_JUDGE = 3, MODE_STILL = 4 };
 constexpr int JH = 4096;          // judge histogram bins over |e| in [0, 1]
 
 // Shared memory of one block: transfer function, per-lane sorted hit staging
@@ -215,6 +217,7 @@ constexpr int JH = 4096;          // judge histogram bins over |e| in [0, 1]
 // image variant stays within six resident blocks per SM.
 enum { F_PX, F_PY, F_PZ, F_NX, F_NY, F_NZ, F_UX, F_UY, F_UZ, F_CR, F_CG, F_CB, F_AO, F_V, F_VID, NF };
 // End points and attribute of record k in the given layout.
+// `attr` receives the attribute byte in bits 0-7 and the 5-bit line id in bits 8-12.
 template <int LAYOUT>
 __device__ __forceinline__ void fetch_record(const RenderParams &P, uint32_t k, Vec &a, Vec &b, uint32_t &attr) {
     if constexpr (LAYOUT == 1) {
@@ -223,12 +226,12 @@ __device__ __forceinline__ void fetch_record(const RenderParams &P, uint32_t k, 
                       h2 = *reinterpret_cast<const __half2 *>(&q.z);
         a = mk(__low2float(h0), __high2float(h0), __low2float(h1));
         b = mk(__high2float(h1), __low2float(h2), __high2float(h2));
-        attr = q.w & 0xffu;
+        attr = q.w;
     } else {
         const uint64_t r = __ldg(P.rec + k);
         a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), P.invN);
         b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), P.invN);
-        attr = rec_attr(r);
+        attr = rec_attr(r) | (rec_line_id(r) << 8);
     }
 }
 
@@ -241,11 +244,13 @@ struct Smem {
     static constexpr int kMode = MODE;
     static constexpr int kLayout = LAYOUT;
     static constexpr bool kBatch = BATCH;   // the transfer function is read from global memory
-    static constexpr bool kVid = MODE != MODE_IMAGE;
+    static constexpr bool kVid = MODE != MODE_IMAGE && MODE != MODE_STILL;
+    static constexpr bool kStill = MODE == MODE_STILL;
     float4 tf[BATCH ? 1 : 256];
     float4 hot[BATCH ? 4 : 1][BATCH ? HOT_BYTES / 16 : 1];   // batched: each warp's current view parameters
     float st[KS][RT];             // staged (t, k) of the current voxel, ascending
     uint32_t sk[KS][RT];
+    uint16_t sa[MODE == MODE_STILL ? KS : 1][MODE == MODE_STILL ? RT : 2];   // at rest: (line id << 5) | neighbour
     float slot[kVid ? NF : NF - 1][KS][RT];
     uint8_t item[4][32 * KS];     // per warp: (owner lane, slot) of each collected hit
     __align__(16) __nv_bfloat16 hin[MODE == MODE_LEARNED || MODE == MODE_JUDGE ? 4 * 16 * aomlp::HIN_STRIDE : 8];   // per warp: per-hit inputs of 16 hits
@@ -263,6 +268,7 @@ struct Ray {
     bool resume;
     bool done;
     int hidx, target;             // sample mode: index of the next hit, index to record
+    uint32_t idmask;              // camera at rest: line ids blended at the current voxel
 };
 
 // Phase A for one lane: traverse until KS hits are collected or the ray ends.
@@ -284,9 +290,11 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
         const uint32_t beg = __ldg(P.offset + vid), end = __ldg(P.offset + vid + 1);
         if (!ray.resume) {
             nvox++;
-            nrec += end - beg;
+            if constexpr (!SM::kStill) nrec += end - beg;
         }
-        if (end > beg) {
+        // with the camera at rest (reading R2) every voxel is searched: its
+        // neighbours' tubes may reach into it
+        if (SM::kStill || end > beg) {
             // accurate local origin: eye + T D - v in float-float, rounded once
             float po[3];
 #pragma unroll
@@ -300,25 +308,69 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
             const Vec p = mk(po[0], po[1], po[2]);
             const int room = KS - used;
             int nh = 0;
-            for (uint32_t k = beg; k < end; k++) {
-                Vec a, b;
-                uint32_t attr;
-                fetch_record<SM::kLayout>(P, k, a, b, attr);
-                const float t = capsule_entry(p, ray.D, a, b, P.r2);
-                if (!owned(p, ray.D, t, -ray.T)) continue;
-                if (ray.resume && !key_after(t, k, ray.rt, ray.rk)) continue;
-                // bounded insertion: keep the `room` smallest (t, k), ascending
+            // stage one candidate: keep the `room` smallest (t, k), ascending;
+            // at rest also only the smallest of each line id
+            auto stage = [&](float t, uint32_t k, uint32_t aux) {
+                if (!owned(p, ray.D, t, -ray.T)) return;
+                if (ray.resume && !key_after(t, k, ray.rt, ray.rk)) return;
+                if constexpr (SM::kStill) {
+                    const uint32_t id = aux >> 5;
+                    if ((ray.idmask >> id) & 1u) return;            // blended earlier at this voxel
+                    int ns = nh < room ? nh : room;
+                    for (int j = 0; j < ns; j++) {
+                        if ((uint32_t)(sm.sa[j][tid] >> 5) != id) continue;
+                        if (!key_after(sm.st[j][tid], sm.sk[j][tid], t, k)) return;   // staged one is first
+                        for (int q = j; q + 1 < ns; q++) {                            // drop the staged one
+                            sm.st[q][tid] = sm.st[q + 1][tid];
+                            sm.sk[q][tid] = sm.sk[q + 1][tid];
+                            sm.sa[q][tid] = sm.sa[q + 1][tid];
+                        }
+                        nh--;
+                        break;
+                    }
+                }
                 if (nh < room || t < sm.st[room - 1][tid]) {
                     int q = nh < room ? nh : room - 1;
                     while (q > 0 && t < sm.st[q - 1][tid]) {
                         sm.st[q][tid] = sm.st[q - 1][tid];
                         sm.sk[q][tid] = sm.sk[q - 1][tid];
+                        if constexpr (SM::kStill) sm.sa[q][tid] = sm.sa[q - 1][tid];
                         q--;
                     }
                     sm.st[q][tid] = t;
                     sm.sk[q][tid] = k;
+                    if constexpr (SM::kStill) sm.sa[q][tid] = (uint16_t)aux;
                 }
                 nh++;
+            };
+            if constexpr (SM::kStill) {
+                for (int nc = 0; nc < 27; nc++) {
+                    const int dx = nc % 3 - 1, dy = (nc / 3) % 3 - 1, dz = nc / 9 - 1;
+                    const int X = ray.v[0] + dx, Y = ray.v[1] + dy, Z = ray.v[2] + dz;
+                    if ((unsigned)X >= (unsigned)P.res[0] || (unsigned)Y >= (unsigned)P.res[1] ||
+                        (unsigned)Z >= (unsigned)P.res[2])
+                        continue;
+                    const uint32_t nv = (uint32_t)X + (uint32_t)P.res[0] * ((uint32_t)Y + (uint32_t)P.res[1] * (uint32_t)Z);
+                    const uint32_t nb = __ldg(P.offset + nv), ne = __ldg(P.offset + nv + 1);
+                    if (!ray.resume) nrec += ne - nb;
+                    const Vec o = mk((float)dx, (float)dy, (float)dz);
+                    for (uint32_t k = nb; k < ne; k++) {
+                        Vec a, b;
+                        uint32_t attr;
+                        fetch_record<SM::kLayout>(P, k, a, b, attr);
+                        // the neighbour's face points in this voxel's frame (exact: binary fractions + integers)
+                        a = mk(a.x + o.x, a.y + o.y, a.z + o.z);
+                        b = mk(b.x + o.x, b.y + o.y, b.z + o.z);
+                        stage(capsule_entry(p, ray.D, a, b, P.r2), k, ((attr >> 8) << 5) | (uint32_t)nc);
+                    }
+                }
+            } else {
+                for (uint32_t k = beg; k < end; k++) {
+                    Vec a, b;
+                    uint32_t attr;
+                    fetch_record<SM::kLayout>(P, k, a, b, attr);
+                    stage(capsule_entry(p, ray.D, a, b, P.r2), k, 0u);
+                }
             }
             const int take = nh < room ? nh : room;
             for (int q = 0; q < take; q++) {
@@ -327,6 +379,14 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                 Vec a, b;
                 uint32_t attr;
                 fetch_record<SM::kLayout>(P, k, a, b, attr);
+                if constexpr (SM::kStill) {
+                    const int nc = sm.sa[q][tid] & 31;
+                    const Vec o = mk((float)(nc % 3 - 1), (float)((nc / 3) % 3 - 1), (float)(nc / 9 - 1));
+                    a = mk(a.x + o.x, a.y + o.y, a.z + o.z);
+                    b = mk(b.x + o.x, b.y + o.y, b.z + o.z);
+                    ray.idmask |= 1u << (attr >> 8);
+                }
+                attr &= 0xffu;
                 const Vec Pl = axpy(t, ray.D, p);
                 const Vec ba = sub(b, a);
                 const float L2 = dot(ba, ba);
@@ -392,6 +452,7 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
             }
         }
         ray.resume = false;
+        ray.idmask = 0u;
         // step into the neighbour across face `ax`
         ray.T = __fadd_rn(ray.T, se);
 #pragma unroll
@@ -600,6 +661,7 @@ __device__ __forceinline__ void render_tile(const RenderParams &P, SM &sm, unsig
     const bool valid = px < P.cw && py < P.ch;
     Ray ray;
     ray.hidx = ray.target = 0;
+    ray.idmask = 0u;
     if (MODE == MODE_SAMPLES && valid) {
         const int64_t pix = (int64_t)py * P.cw + px;
         P.samp_vox[pix] = -1;
@@ -742,7 +804,9 @@ __device__ __forceinline__ void flush_stats(const RenderParams &P, int lane, Sta
     }
 }
 
-constexpr int min_blocks(int mode) { return mode == MODE_LEARNED || mode == MODE_JUDGE ? 4 : 6; }
+constexpr int min_blocks(int mode) {
+    return mode == MODE_LEARNED || mode == MODE_JUDGE ? 4 : (mode == MODE_STILL ? 5 : 6);
+}
 
 // One view: a persistent grid takes 32-ray tiles from a global counter.
 template <int MODE, int LAYOUT>
@@ -830,6 +894,7 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     if (!(view->fovy_deg > 0.0f && view->fovy_deg < 180.0f)) return set_err(ctx, LVR_EINVAL, "fovy out of (0,180)");
     if (desc->ao_mode < 0 || desc->ao_mode > 2) return set_err(ctx, LVR_EINVAL, "bad ao_mode");
     if (desc->ao_mode == 2 && !ao) return set_err(ctx, LVR_EINVAL, "learned AO needs a model");
+    if (desc->still && desc->ao_mode == 2) return set_err(ctx, LVR_EINVAL, "the camera-at-rest mode has no learned-AO variant");
     if ((desc->ao_mode == 2 || judge) && lod && lod->levels < 3)
         return set_err(ctx, LVR_EINVAL, "learned AO needs a LoD of >= 3 levels");
     const bool need_lod = desc->shadows || desc->ao_mode != 0;
@@ -899,6 +964,7 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     P.ao = desc->ao_mode == 1 || judge ? 1 : 0;
     P.ao_rays = P.ao ? desc->ao_rays : 0;
     P.learned = desc->ao_mode == 2 ? 1 : 0;
+    P.still = desc->still ? 1 : 0;
     if (judge) P.shadows = 0;   // the judge keeps the learned AO where the visibility would go
     P.nrays = P.shadows + P.ao_rays + P.learned;
     P.ao_radius = desc->ao_radius;
@@ -935,12 +1001,15 @@ static RenderKernel pick_kernel(int mode, int layout) {
     case MODE_LEARNED * 2 + 1: return render_kernel<MODE_LEARNED, LAYOUT_AOS16>;
     case MODE_SAMPLES * 2: return render_kernel<MODE_SAMPLES, LAYOUT_AOS8>;
     case MODE_JUDGE * 2: return render_kernel<MODE_JUDGE, LAYOUT_AOS8>;
+    case MODE_STILL * 2: return render_kernel<MODE_STILL, LAYOUT_AOS8>;
+    case MODE_STILL * 2 + 1: return render_kernel<MODE_STILL, LAYOUT_AOS16>;
     default: return nullptr;
     }
 }
 
 static int kernel_mode(const RenderParams &P) {
-    return P.judge ? MODE_JUDGE : (P.learned ? MODE_LEARNED : (P.samp_vox ? MODE_SAMPLES : MODE_IMAGE));
+    return P.judge ? MODE_JUDGE
+                   : (P.learned ? MODE_LEARNED : (P.samp_vox ? MODE_SAMPLES : (P.still ? MODE_STILL : MODE_IMAGE)));
 }
 
 // Persistent grid size of a kernel: SMs x resident blocks (cached per variant).
@@ -1011,6 +1080,7 @@ lvr_status render_samples(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lo
     lvr_render_desc d = *desc;
     d.ao_mode = 1;
     d.shadows = 0;
+    d.still = 0;
     lvr_status st = setup(ctx, ls, lod, view, &d, nullptr, P);
     if (st != LVR_OK) return st;
     P.samp_vox = vox;
@@ -1044,6 +1114,7 @@ extern "C" lvr_status lvr_ao_judge(lvr_ctx *ctx, const lvr_lineset *ls, const lv
     RenderParams P;
     lvr_render_desc d = *desc;
     d.ao_mode = 2;
+    d.still = 0;
     lvr_status st = setup(ctx, ls, lod, view, &d, ao, P, true);
     if (st != LVR_OK) return st;
     cudaStream_t s = ctx->stream;
@@ -1108,7 +1179,7 @@ __global__ void expand_records_kernel(const uint64_t *__restrict__ rec, int64_t 
         q.x = *reinterpret_cast<const uint32_t *>(&h0);
         q.y = *reinterpret_cast<const uint32_t *>(&h1);
         q.z = *reinterpret_cast<const uint32_t *>(&h2);
-        q.w = rec_attr(r);
+        q.w = rec_attr(r) | (rec_line_id(r) << 8);
         out[i] = q;
     }
 }
@@ -1172,6 +1243,7 @@ lvr_status batch_build(lvr_ctx *ctx, const lvr_batch_item *items, int n, int til
         if (!it.desc || !it.rgba) return set_err(ctx, LVR_EINVAL, "batch item %d: null desc or output", i);
         if (!is_device_ptr(it.rgba)) return set_err(ctx, LVR_EINVAL, "batch item %d: rgba must be device memory", i);
         lvr_render_desc d = *it.desc;
+        if (d.still) return set_err(ctx, LVR_EINVAL, "batch item %d: batches render with the camera in motion", i);
         if (tile_w > 0) { d.tile_w = tile_w; d.tile_h = tile_h; }
         if (layout >= 0) d.layout = layout;
         lvr_status st = setup(ctx, it.ls, it.lod, &it.view, &d, it.ao, P[i]);

@@ -61,7 +61,7 @@ class RenderDesc(C.Structure):
                 ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao_mode", C.c_int32),
                 ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
                 ("kd", C.c_float), ("bg", C.c_float * 3), ("tile_w", C.c_int32),
-                ("tile_h", C.c_int32), ("layout", C.c_int32)]
+                ("tile_h", C.c_int32), ("layout", C.c_int32), ("still", C.c_int32)]
 
 
 class BatchItem(C.Structure):
@@ -341,7 +341,8 @@ def make_view(eye, at, up, fovy_deg, width, height, light_dir, crop=None) -> Vie
 
 
 def make_desc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao_mode=0, ao_rays=16,
-              ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), tile=(0, 0), layout=0) -> RenderDesc:
+              ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), tile=(0, 0), layout=0,
+              still=False) -> RenderDesc:
     d = RenderDesc()
     d.radius = float(radius)
     tf = np.ascontiguousarray(np.asarray(tf, np.float32)).reshape(-1)
@@ -358,6 +359,7 @@ def make_desc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao_mode=0
     d.bg[:] = [float(x) for x in bg]
     d.tile_w, d.tile_h = int(tile[0]), int(tile[1])
     d.layout = int(layout)
+    d.still = int(bool(still))
     return d
 
 

@@ -253,3 +253,32 @@ def test_invalid_render_arguments(env, c1t):
         with pytest.raises(lvr.LVRError) as ei:
             lvr.lvr_render(ctx, c1t.gls, lod, view, desc, out)
         assert ei.value.code == lvr.EINVAL
+
+
+def test_still_camera_mode_matches_oracle(env, c1t, c1):
+    """Camera at rest (Sec. 4.1): neighbouring voxels' segments and one hit per
+    line id per voxel; transparent with shadows and AO, and opaque."""
+    cam = synth.orbit_view((32, 32, 32), 192, 108)
+    got, ref, tie, gc, oc = c1t.render(env, cam, radius=0.2, ert_alpha=0.99, shadows=True, ao_mode=1,
+                                       still=True, counters=True)
+    S.check_image(got, ref, tie, what="still transparent")
+    np.testing.assert_allclose(gc, oc.astype(np.float64), rtol=2e-3)
+    got, ref, tie, _, _ = c1.render(env, synth.orbit_view((32, 32, 32), 128, 128), radius=0.2, opaque=True,
+                                    still=True)
+    S.check_image(got, ref, tie, what="still opaque")
+
+
+def test_still_camera_mode_layouts_agree(env, c1t):
+    import torch
+    lvr, O, ctx, dev = env
+    lvr.lvr_lineset_layout(ctx, c1t.gls, lvr.LAYOUT_AOS16)
+    cam = synth.orbit_view((32, 32, 32), 96, 64)
+    lv, _, _ = S.views(cam)
+    outs = []
+    for layout in (0, 1):
+        out = torch.empty((64, 96, 4), dtype=torch.float32, device=dev)
+        lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, lvr.make_desc(0.2, c1t.tf, ert_alpha=0.99, shadows=True,
+                                                                  ao_mode=1, still=True, layout=layout), out)
+        ctx.sync()
+        outs.append(out.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
