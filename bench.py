@@ -268,6 +268,9 @@ def run_gpu(args):
                          "ms_per_candidate": [round(m, 3) for m in tune["ms"]]},
             "clocks": clk,
         }
+        if world == 1:
+            line["still_camera"] = still_frame(lvr, ctx, stream, dev, xyz, attr, offs, gdesc, sig, view, tf, layout,
+                                               tune["tile"], out)
         if not args.no_learned and world == 1:
             line["learned_ao"], model = learned_ao(args, lvr, synth, ctx, dev, stream,
                                                    main=(xyz, attr, offs, gdesc, sig, view, out))
@@ -279,6 +282,38 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     ctx.close()
+
+
+# ---------------------------------------------------------------- camera at rest (Sec. 4.1)
+def still_frame(lvr, ctx, stream, dev, xyz, attr, offs, gdesc, sig, view, tf, layout, tile, out):
+    """The headline frame with the camera at rest: every visited voxel also
+    tests its 26 neighbours' segments (one hit per line id per voxel)."""
+    import torch
+    s = lvr.lvr_voxelize(ctx, xyz, attr, offs, gdesc())
+    if layout:
+        lvr.lvr_lineset_layout(ctx, s, layout)
+    lod = lvr.lvr_build_lod(ctx, s, LEVELS, sig)
+    res = {}
+    for name, still in (("moving", False), ("still", True)):
+        d = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0,
+                          tile=tile, layout=layout, still=still)
+        cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+        lvr.lvr_render(ctx, s, lod, view, d, out, counters=cnt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            lvr.lvr_render(ctx, s, lod, view, d, out)
+        e1.record(stream)
+        e1.synchronize()
+        c = cnt.cpu().numpy() / (W * H)
+        res[name] = {"ms": round(e0.elapsed_time(e1) / 3, 3),
+                     "per_ray": {"voxels": round(float(c[0]), 2), "records": round(float(c[1]), 2),
+                                 "lod_samples": round(float(c[2]), 2), "hits": round(float(c[3]), 3)}}
+    lod.free()
+    s.free()
+    res["note"] = ("same frame as the headline; at rest the hits that tubes overhanging into a voxel "
+                   "from its neighbours contribute are found, and one hit per line id per voxel is blended")
+    return res
 
 
 # ---------------------------------------------------------------- learned AO (config 4)

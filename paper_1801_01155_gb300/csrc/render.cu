@@ -344,6 +344,7 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                 nh++;
             };
             if constexpr (SM::kStill) {
+                const float rm = sqrtf(P.r2) * 1.0001f + 1e-5f;
                 for (int nc = 0; nc < 27; nc++) {
                     const int dx = nc % 3 - 1, dy = (nc / 3) % 3 - 1, dz = nc / 9 - 1;
                     const int X = ray.v[0] + dx, Y = ray.v[1] + dy, Z = ray.v[2] + dz;
@@ -361,6 +362,11 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                         // the neighbour's face points in this voxel's frame (exact: binary fractions + integers)
                         a = mk(a.x + o.x, a.y + o.y, a.z + o.z);
                         b = mk(b.x + o.x, b.y + o.y, b.z + o.z);
+                        // a tube whose box (segment box grown by the radius, with a margin for
+                        // rounding) misses this voxel cannot have its entry point in it
+                        if (fmaxf(a.x, b.x) + rm < 0.0f || fminf(a.x, b.x) - rm > 1.0f || fmaxf(a.y, b.y) + rm < 0.0f ||
+                            fminf(a.y, b.y) - rm > 1.0f || fmaxf(a.z, b.z) + rm < 0.0f || fminf(a.z, b.z) - rm > 1.0f)
+                            continue;
                         stage(capsule_entry(p, ray.D, a, b, P.r2), k, ((attr >> 8) << 5) | (uint32_t)nc);
                     }
                 }
