@@ -129,6 +129,7 @@ typedef struct orc_rdesc {
     int32_t still;              /* 1: camera at rest (reading R2): also test the 26
                                    neighbouring voxels' segments; one hit per line id
                                    per voxel */
+    const double *ao_field;     /* ao == 3: per-voxel spherical AO (orc_ao_sphere_field) */
 } orc_rdesc;
 
 /* counters[0..3]: voxels visited, records tested, LoD trilinear samples,
@@ -155,6 +156,14 @@ double orc_march(const orc_lod *lod, const double p[3], const double dir[3], dou
 double orc_sample(const orc_lod *lod, int level, const double x[3]);
 /* Hemisphere directions around normal n with tangent hint u (reading S3). */
 void orc_ao_dirs(const double n[3], const double u[3], int k, double *dirs);
+
+/* ---- spherical per-voxel AO (reading S4) ---- */
+/* field[v] = 1 - mean over `rays` sphere directions of min(1, O), O the
+ * level-0 density summed at distances 1, 2, ..., radius from voxel v's centre. */
+void   orc_ao_sphere_field(const orc_lod *lod, int rays, double radius, double *field);
+/* trilinear value of a cell-centred field at x, coordinates clamped to the
+ * voxel centres (the field holds its edge values outside). */
+double orc_ao_field_sample(const double *field, const int32_t dims[3], const double x[3]);
 
 /* ---- learned AO surrogate (reading L1; aomlp.c) ---- */
 int    orc_ao_nparams(void);

@@ -30,7 +30,8 @@ class RDesc(C.Structure):
     _fields_ = [("radius", C.c_float), ("tf", C.c_float * 1024), ("opaque", C.c_int32),
                 ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao", C.c_int32),
                 ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
-                ("kd", C.c_float), ("bg", C.c_float * 3), ("ao_params", C.c_void_p), ("still", C.c_int32)]
+                ("kd", C.c_float), ("bg", C.c_float * 3), ("ao_params", C.c_void_p), ("still", C.c_int32),
+                ("ao_field", C.c_void_p)]
 
 
 def _p(a):
@@ -68,6 +69,9 @@ def lib():
         L.orc_sample.argtypes = [vp, C.c_int, vp]
         L.orc_sample.restype = C.c_double
         L.orc_ao_dirs.argtypes = [vp, vp, C.c_int, vp]
+        L.orc_ao_sphere_field.argtypes = [vp, C.c_int, C.c_double, vp]
+        L.orc_ao_field_sample.argtypes = [vp, vp, vp]
+        L.orc_ao_field_sample.restype = C.c_double
         L.orc_ao_nparams.restype = C.c_int
         L.orc_ao_ninputs.restype = C.c_int
         L.orc_bf16.argtypes = [C.c_double]
@@ -230,7 +234,7 @@ def make_view(eye, at, up, fovy_deg, width, height, light_dir) -> View:
 
 def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False,
                ao_rays=16, ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), ao_params=None,
-               still=False) -> RDesc:
+               still=False, ao_field=None) -> RDesc:
     """ao: False/0 off, True/1 traced, 2 learned (ao_params: float32 [ao_nparams()])."""
     d = RDesc()
     d.radius = float(radius)
@@ -247,6 +251,11 @@ def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False
     d.kd = float(kd)
     d.bg[:] = [float(x) for x in bg]
     d.still = int(bool(still))
+    if ao_field is not None:
+        ao_field = np.ascontiguousarray(ao_field, np.float64)
+        d._keep_field = ao_field
+        d.ao_field = ao_field.ctypes.data
+        d.ao = 3
     if ao_params is not None:
         ao_params = np.ascontiguousarray(ao_params, np.float32)
         assert ao_params.size == ao_nparams()
@@ -369,3 +378,21 @@ class HandLod:
     @property
     def handle(self):
         return C.cast(C.pointer(self._s), C.c_void_p)
+
+    def dims(self, level):
+        return tuple(int(x) for x in self._s.dims[level])
+
+
+# ---------------------------------------------------------------- spherical per-voxel AO (reading S4)
+def ao_sphere_field(lod: "Lod", rays=100, radius=5.0):
+    d = lod.dims(0)
+    out = np.empty(int(d[0]) * int(d[1]) * int(d[2]), np.float64)
+    lib().orc_ao_sphere_field(lod.handle, int(rays), float(radius), _p(out))
+    return out
+
+
+def ao_field_sample(field, dims, x):
+    field = np.ascontiguousarray(field, np.float64)
+    dm = np.ascontiguousarray(dims, np.int32)
+    x = np.ascontiguousarray(x, np.float64)
+    return lib().orc_ao_field_sample(_p(field), _p(dm), _p(x))

@@ -297,6 +297,68 @@ double orc_sample(const orc_lod *L, int l, const double x[3]) {
     return acc / ldexp(1.0, 3 * l);              /* sum of 8^l voxels -> average */
 }
 
+/* Reading S4 (Sec. 5.3, second approach): occlusion over the whole sphere
+ * around each voxel centre, from the level-0 density, in a pre-process.
+ * Directions: spherical Fibonacci set over the sphere, z_i = 1 - (2i+1)/K,
+ * phi_i = i pi (3 - sqrt 5); samples at unit steps s = 1 .. radius. */
+void orc_ao_sphere_field(const orc_lod *L, int rays, double radius, double *field) {
+    const int32_t *dm = L->dims[0];
+    const int64_t n = (int64_t)dm[0] * dm[1] * dm[2];
+    const double golden = M_PI * (3.0 - sqrt(5.0));
+    double *dirs = (double *)malloc(sizeof(double) * 3 * (size_t)rays);
+    for (int i = 0; i < rays; i++) {
+        const double z = 1.0 - (2.0 * i + 1.0) / rays, rr = sqrt(1.0 - z * z), ph = i * golden;
+        dirs[3 * i] = rr * cos(ph);
+        dirs[3 * i + 1] = rr * sin(ph);
+        dirs[3 * i + 2] = z;
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t v = 0; v < n; v++) {
+        const double c[3] = {v % dm[0] + 0.5, (v / dm[0]) % dm[1] + 0.5, v / ((int64_t)dm[0] * dm[1]) + 0.5};
+        double occ = 0.0;
+        for (int k = 0; k < rays; k++) {
+            double O = 0.0;
+            for (int s = 1; s <= radius; s++) {
+                const double x[3] = {c[0] + s * dirs[3 * k], c[1] + s * dirs[3 * k + 1], c[2] + s * dirs[3 * k + 2]};
+                O += orc_sample(L, 0, x);
+                if (O >= 1.0) break;
+            }
+            occ += fmin(1.0, O);
+        }
+        field[v] = 1.0 - occ / rays;
+    }
+    free(dirs);
+}
+
+double orc_ao_field_sample(const double *field, const int32_t dm[3], const double x[3]) {
+    double f[3];
+    int64_t i0[3];
+    for (int a = 0; a < 3; a++) {
+        double q = x[a] - 0.5;
+        if (q < 0.0) q = 0.0;
+        if (q > dm[a] - 1) q = dm[a] - 1;
+        double fl = floor(q);
+        if (fl > dm[a] - 2) fl = dm[a] - 2 < 0 ? 0 : dm[a] - 2;
+        i0[a] = (int64_t)fl;
+        f[a] = q - fl;
+    }
+    double acc = 0.0;
+    for (int c = 0; c < 8; c++) {
+        int64_t idx[3];
+        double w = 1.0;
+        for (int a = 0; a < 3; a++) {
+            int bit = (c >> a) & 1;
+            idx[a] = i0[a] + bit;
+            if (idx[a] > dm[a] - 1) idx[a] = dm[a] - 1;
+            w *= bit ? f[a] : 1.0 - f[a];
+        }
+        acc += w * field[idx[0] + (int64_t)dm[0] * (idx[1] + (int64_t)dm[1] * idx[2])];
+    }
+    return acc;
+}
+
 static int level_of(int64_t s, int levels) {
     int l = 0;
     while (((int64_t)2 << l) <= s) l++;          /* floor(log2 s) */
@@ -426,7 +488,9 @@ static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rd
 
     double V = 1.0, AO = 1.0;
     if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
-    if (rd->ao == 2 && L && rd->ao_params) {
+    if (rd->ao == 3 && L && rd->ao_field) {
+        AO = orc_ao_field_sample(rd->ao_field, L->dims[0], P);
+    } else if (rd->ao == 2 && L && rd->ao_params) {
         double t[3], x[512];
         orc_ao_tangent(a, b, t);
         if (orc_ao_features(L, s->voxel, t, n, P, x) == 0) AO = orc_ao_mlp(rd->ao_params, x);

@@ -87,3 +87,62 @@ def test_line_id_rule_closed_forms(orc):
         assert a[0, 3] == pytest.approx(1 - (1 - alpha) ** 2, abs=1e-12)
         want = alpha if second == 32 else 1 - (1 - alpha) ** 2
         assert b[0, 3] == pytest.approx(want, abs=1e-12)
+
+
+# ---------------------------------------------------------------- spherical per-voxel AO (reading S4)
+def _level0(orc, dens):
+    """A one-level hand LoD over level-0 density sums [z][y][x]."""
+    return orc.HandLod([dens])
+
+
+def test_sphere_ao_field_linear_density_closed_form(orc):
+    """Density linear in z, rho = alpha (k + 1/2) in voxel layer k: trilinear
+    samples reproduce it, so a ray from a centre at height zc collects
+    O = sum_{s=1..5} alpha (zc + s d_z) = alpha (5 zc + 15 d_z). The
+    Fibonacci z values 1 - (2i+1)/K average to zero, so far from the grid's
+    faces (and with every O below 1) AO = 1 - 5 alpha zc."""
+    R = 24
+    alpha = 0.004
+    z = (np.arange(R) + 0.5)[:, None, None] * np.ones((1, R, R))
+    lod = _level0(orc, alpha * z)
+    f = orc.ao_sphere_field(lod, rays=100, radius=5.0).reshape(R, R, R)
+    for k in (6, 9, 12, 17):
+        zc = k + 0.5
+        assert f[k, 10, 11] == pytest.approx(1.0 - 5 * alpha * zc, abs=1e-12)
+        assert f[k, 7, 16] == pytest.approx(1.0 - 5 * alpha * zc, abs=1e-12)
+
+
+def test_sphere_ao_field_saturates_and_empty_is_one(orc):
+    """Uniform density 0.3: O = 0.3, 0.6, 0.9, 1.2 after four unit steps, so
+    every interior ray saturates and AO = 0; an empty grid gives AO = 1."""
+    R = 20
+    lod = _level0(orc, np.full((R, R, R), 0.3))
+    f = orc.ao_sphere_field(lod, rays=64, radius=5.0).reshape(R, R, R)
+    assert f[10, 10, 10] == pytest.approx(0.0, abs=1e-12)
+    lod0 = _level0(orc, np.zeros((R, R, R)))
+    assert np.all(orc.ao_sphere_field(lod0, rays=64, radius=5.0) == 1.0)
+
+
+def test_ao_field_sample_linear_and_clamped(orc):
+    """Trilinear interpolation reproduces a linear field between voxel
+    centres; beyond the outer centres the edge values hold."""
+    dims = (7, 5, 6)
+    zz, yy, xx = np.meshgrid(np.arange(6) + 0.5, np.arange(5) + 0.5, np.arange(7) + 0.5, indexing="ij")
+    field = (0.1 * xx - 0.2 * yy + 0.05 * zz + 1.0).reshape(-1)
+    lin = lambda x, y, z: 0.1 * x - 0.2 * y + 0.05 * z + 1.0
+    for p in ([1.3, 2.2, 3.9], [0.5, 0.5, 0.5], [6.4, 4.1, 5.5], [3.0, 1.75, 2.25]):
+        assert orc.ao_field_sample(field, dims, p) == pytest.approx(lin(*p), abs=1e-12)
+    assert orc.ao_field_sample(field, dims, [0.1, 2.5, 2.5]) == pytest.approx(lin(0.5, 2.5, 2.5), abs=1e-12)
+    assert orc.ao_field_sample(field, dims, [8.0, 6.0, -1.0]) == pytest.approx(lin(6.5, 4.5, 0.5), abs=1e-12)
+
+
+def test_sphere_ao_field_single_ray_steps(orc):
+    """One ray: z_0 = 0, phi_0 = 0, so it points along +x. With density
+    alpha (i + 1/2) in voxel column i it collects alpha (5 xc + 1+2+3+4+5):
+    the samples sit at unit steps 1..5 from the centre."""
+    R = 24
+    alpha = 0.003
+    x = np.ones((R, R, 1)) * (np.arange(R) + 0.5)[None, None, :]
+    f = orc.ao_sphere_field(_level0(orc, alpha * x), rays=1, radius=5.0).reshape(R, R, R)
+    for i in (3, 8, 15):
+        assert f[9, 11, i] == pytest.approx(1.0 - alpha * (5 * (i + 0.5) + 15), abs=1e-12)
