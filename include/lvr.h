@@ -168,6 +168,18 @@ typedef struct lvr_lod_info {
     int32_t dims[4][3];
 } lvr_lod_info;
 lvr_status lvr_lod_info_get(const lvr_lod *lod, lvr_lod_info *info);
+/* Sec. 5.3's second AO approach: occlusion over the whole sphere around each
+ * voxel centre, precomputed per voxel and interpolated at hits (ao_mode 3).
+ * Directions: `rays` spherical Fibonacci directions over the sphere (z_i =
+ * 1 - (2i+1)/rays, phi_i = i pi (3 - sqrt 5)); along each, the level-0
+ * density (cell-centred trilinear, zero outside the grid) summed at unit
+ * steps 1 .. floor(radius) until it reaches 1; field = 1 - mean min(1, O).
+ * rays 1..4096, radius 1..64 voxels (the paper: 100 rays, radius 5). At a
+ * hit the field is interpolated trilinearly between voxel centres,
+ * coordinates clamped to them. Stored with the LoD (float32 per voxel). */
+lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, float radius);
+/* The field, host or device float32 [voxels]. */
+lvr_status lvr_export_ao_field(lvr_ctx *ctx, const lvr_lod *lod, float *field);
 /* Copy one level out; any pointer may be NULL; host or device; each
  * dims[level] product elements. */
 lvr_status lvr_export_lod(lvr_ctx *ctx, const lvr_lod *lod, int level, uint32_t *cnt,
@@ -223,7 +235,8 @@ typedef struct lvr_render_desc {
     float   ert_alpha;     /* early ray termination threshold (> 1: off) */
     int32_t shadows;       /* 1: soft shadows (needs a LoD) */
     int32_t ao_mode;       /* 0 off, 1 traced (density-marched, needs a LoD),
-                              2 learned surrogate (needs an lvr_ao_model) */
+                              2 learned surrogate (needs an lvr_ao_model),
+                              3 spherical per-voxel field (needs lvr_lod_ao_field) */
     int32_t ao_rays;       /* hemisphere rays per hit, 1..32 (16 typical) */
     float   ao_radius;     /* radius of influence, voxels (15 typical) */
     float   ka, kd;        /* ambient / diffuse weights (0.3 / 0.7 typical) */

@@ -7,6 +7,12 @@
 // float32 sqrt of I is correctly rounded and the division by 2N is exact.
 // Sums run in the canonical segment order (level 0) and in the fixed child
 // order z, y, x (coarser levels), so results are deterministic.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
 #include "lvr_internal.cuh"
 
 namespace {
@@ -90,7 +96,182 @@ lod_pack_kernel(const float *__restrict__ d, int dx, int dy, int dz, float4 *pk)
     }
 }
 
+// One sample of the spherical AO stencil: integer part and fraction of s d.
+struct AoStep {
+    int32_t ix, iy, iz;
+    float fx, fy, fz;
+    int32_t pad[2];
+};
+
+// Spherical per-voxel AO (Sec. 5.3, second approach): per voxel centre, for
+// each direction, the level-0 density summed at unit steps (cell-centred
+// trilinear samples, zero outside the grid) until it reaches 1; AO = 1 -
+// mean min(1, O). A sample at c + s d has the same fractional position in
+// every voxel, so the stencil (integer offsets, fractions) is one table.
+__global__ void __launch_bounds__(256)
+ao_field_kernel(const float4 *__restrict__ pk, int dx, int dy, int dz, const AoStep *__restrict__ tab, int rays,
+                int steps, float *field) {
+    const int64_t n = (int64_t)dx * dy * dz;
+    const unsigned px = (unsigned)dx + 2u, sz = px * ((unsigned)dy + 2u);
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int vx = (int)(v % dx), vy = (int)((v / dx) % dy), vz = (int)(v / ((int64_t)dx * dy));
+        float occ = 0.0f;
+        for (int k = 0; k < rays; k++) {
+            float O = 0.0f;
+            for (int s = 0; s < steps; s++) {
+                const AoStep e = tab[k * steps + s];
+                const int ix = vx + e.ix, iy = vy + e.iy, iz = vz + e.iz;
+                float val = 0.0f;
+                if ((unsigned)(ix + 1) <= (unsigned)dx && (unsigned)(iy + 1) <= (unsigned)dy &&
+                    (unsigned)(iz + 1) <= (unsigned)dz) {
+                    const float4 *c = pk + ((unsigned)(ix + 1) + px * (unsigned)(iy + 1) + sz * (unsigned)(iz + 1));
+                    const float4 a = __ldg(c), b = __ldg(c + sz);
+                    const float x00 = fmaf(e.fx, a.y - a.x, a.x), x10 = fmaf(e.fx, a.w - a.z, a.z);
+                    const float x01 = fmaf(e.fx, b.y - b.x, b.x), x11 = fmaf(e.fx, b.w - b.z, b.z);
+                    const float y0 = fmaf(e.fy, x10 - x00, x00), y1 = fmaf(e.fy, x11 - x01, x01);
+                    val = fmaf(e.fz, y1 - y0, y0);
+                }
+                O += val;
+                if (O >= 1.0f) break;
+            }
+            occ += fminf(1.0f, O);
+        }
+        field[v] = 1.0f - occ / (float)rays;
+    }
+}
+
+// The same field with the density staged per block: a block takes a tile
+// of 32 x 4 x 2 voxels and copies the level-0 density of the tile grown by
+// H cells per side (zero outside the grid) into shared memory; the samples
+// then read shared memory, the stencil the constant bank (same values, same
+// lerps: identical results).
+constexpr int AOT_X = 32, AOT_Y = 4, AOT_Z = 2;   // a warp covers one row: conflict-free reads
+
+// One stencil sample for the tiled kernel: the offset of its lower corner in
+// the shared tile and the eight trilinear weights of its corners.
+struct AoTap {
+    int32_t off;
+    float w[8];          // corner (x, y, z) bits -> weight: bit 0 x, bit 1 y, bit 2 z
+    int32_t pad[3];
+};
+constexpr int AOT_MAX_TAPS = 640;                  // stencil entries passed as a kernel parameter
+struct AoTaps {
+    AoTap t[AOT_MAX_TAPS];
+};
+
+// The same field with the density staged per block: a block takes a tile of
+// 32 x 4 x 2 voxels and copies the level-0 density of the tile grown by H
+// cells per side (zero outside the grid) into shared memory; the stencil
+// (tile offsets and corner weights) comes from the constant bank. O is not
+// cut off at 1: min(1, O) is the same either way since density >= 0.
+template <int STEPS>
+__global__ void __launch_bounds__(AOT_X * AOT_Y * AOT_Z)
+ao_field_tile_kernel(const float *__restrict__ dens, int dx, int dy, int dz, const __grid_constant__ AoTaps tab,
+                     int rays, int H, float *field) {
+    extern __shared__ float tile[];
+    const int TX = AOT_X + 2 * H, TY = AOT_Y + 2 * H, TZ = AOT_Z + 2 * H;
+    const int tx0 = blockIdx.x * AOT_X, ty0 = blockIdx.y * AOT_Y, tz0 = blockIdx.z * AOT_Z;
+    for (int i = threadIdx.x; i < TX * TY * TZ; i += blockDim.x) {
+        const int X = tx0 - H + i % TX, Y = ty0 - H + (i / TX) % TY, Z = tz0 - H + i / (TX * TY);
+        tile[i] = (X >= 0 && Y >= 0 && Z >= 0 && X < dx && Y < dy && Z < dz)
+                      ? __ldg(dens + (X + (int64_t)dx * (Y + (int64_t)dy * Z))) : 0.0f;
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % AOT_X, ly = (threadIdx.x / AOT_X) % AOT_Y, lz = threadIdx.x / (AOT_X * AOT_Y);
+    const int vx = tx0 + lx, vy = ty0 + ly, vz = tz0 + lz;
+    if (vx >= dx || vy >= dy || vz >= dz) return;
+    const float *c0 = tile + (lx + H) + TX * ((ly + H) + TY * (lz + H));
+    const int sy = TX, sz = TX * TY;
+    float occ = 0.0f;
+    for (int k = 0; k < rays; k++) {
+        float O = 0.0f;
+#pragma unroll
+        for (int s = 0; s < STEPS; s++) {
+            const AoTap &e = tab.t[k * STEPS + s];
+            const float *c = c0 + e.off;
+            O = fmaf(e.w[0], c[0], O);
+            O = fmaf(e.w[1], c[1], O);
+            O = fmaf(e.w[2], c[sy], O);
+            O = fmaf(e.w[3], c[sy + 1], O);
+            O = fmaf(e.w[4], c[sz], O);
+            O = fmaf(e.w[5], c[sz + 1], O);
+            O = fmaf(e.w[6], c[sz + sy], O);
+            O = fmaf(e.w[7], c[sz + sy + 1], O);
+        }
+        occ += fminf(1.0f, O);
+    }
+    field[vx + (int64_t)dx * (vy + (int64_t)dy * vz)] = 1.0f - occ / (float)rays;
+}
+
 }  // namespace
+
+extern "C" lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, float radius) {
+    if (!ctx) return LVR_EINVAL;
+    if (!lod) return set_err(ctx, LVR_EINVAL, "lvr_lod_ao_field: null LoD");
+    if (rays < 1 || rays > 4096 || !(radius >= 1.0f) || radius > 64.0f)
+        return set_err(ctx, LVR_EINVAL, "rays must be in [1,4096] and the radius in [1,64] voxels");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int steps = (int)floorf(radius);
+    // the stencil: spherical Fibonacci directions, samples at unit steps
+    std::vector<AoStep> tab((size_t)rays * steps);
+    const double golden = M_PI * (3.0 - sqrt(5.0));
+    for (int k = 0; k < rays; k++) {
+        const double z = 1.0 - (2.0 * k + 1.0) / rays, rr = sqrt(1.0 - z * z), ph = k * golden;
+        const double d[3] = {rr * cos(ph), rr * sin(ph), z};
+        for (int s = 1; s <= steps; s++) {
+            AoStep &e = tab[(size_t)k * steps + s - 1];
+            int32_t *ip[3] = {&e.ix, &e.iy, &e.iz};
+            float *fp[3] = {&e.fx, &e.fy, &e.fz};
+            for (int a = 0; a < 3; a++) {
+                const double o = s * d[a], fl = floor(o);
+                *ip[a] = (int32_t)fl;
+                *fp[a] = (float)(o - fl);
+            }
+            e.pad[0] = e.pad[1] = 0;
+        }
+    }
+    const int32_t *dm = lod->dims[0];
+    const int64_t n = (int64_t)dm[0] * dm[1] * dm[2];
+    lvr_status st = LVR_OK;
+    if (!lod->aof && (st = dev_alloc(ctx, (void **)&lod->aof, (size_t)n * 4)) != LVR_OK) return st;
+    const size_t tb = tab.size() * sizeof(AoStep);
+    if ((st = ensure_stage_in(ctx, tb)) != LVR_OK) return st;
+    LVR_CUDA(ctx, cudaMemcpyAsync(ctx->stage_in, tab.data(), tb, cudaMemcpyHostToDevice, ctx->stream));
+    const int H = steps + 1;   // samples reach floor(s d) in [-steps, steps] plus one corner
+    const int TX = AOT_X + 2 * H, TY = AOT_Y + 2 * H, TZ = AOT_Z + 2 * H;
+    const size_t tile_bytes = (size_t)TX * TY * TZ * 4;
+    if (steps == 5 && tile_bytes <= 48 * 1024 && tab.size() <= (size_t)AOT_MAX_TAPS) {
+        static AoTaps taps;   // host staging of the kernel parameter (copied at launch)
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t i = 0; i < tab.size(); i++) {
+            const AoStep &e = tab[i];
+            AoTap &t = taps.t[i];
+            t.off = e.ix + TX * (e.iy + TY * e.iz);
+            for (int c = 0; c < 8; c++)
+                t.w[c] = (c & 1 ? e.fx : 1.0f - e.fx) * (c & 2 ? e.fy : 1.0f - e.fy) * (c & 4 ? e.fz : 1.0f - e.fz);
+            t.pad[0] = t.pad[1] = t.pad[2] = 0;
+        }
+        const dim3 grid((dm[0] + AOT_X - 1) / AOT_X, (dm[1] + AOT_Y - 1) / AOT_Y, (dm[2] + AOT_Z - 1) / AOT_Z);
+        ao_field_tile_kernel<5><<<grid, AOT_X * AOT_Y * AOT_Z, tile_bytes, ctx->stream>>>(
+            lod->dens[0], dm[0], dm[1], dm[2], taps, rays, H, lod->aof);
+    } else {
+        const unsigned g = grid1d(n, 256) > 65535 ? 65535 : grid1d(n, 256);
+        ao_field_kernel<<<g, 256, 0, ctx->stream>>>(lod->pk[0], dm[0], dm[1], dm[2], (const AoStep *)ctx->stage_in,
+                                                   rays, steps, lod->aof);
+    }
+    LVR_CUDA(ctx, cudaGetLastError());
+    LVR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the table lives in host memory until copied
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_export_ao_field(lvr_ctx *ctx, const lvr_lod *lod, float *field) {
+    if (!ctx) return LVR_EINVAL;
+    if (!lod || !lod->aof || !field) return set_err(ctx, LVR_EINVAL, "no spherical AO field");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t n = (size_t)lod->dims[0][0] * lod->dims[0][1] * lod->dims[0][2];
+    return copy_out(ctx, field, lod->aof, n * 4);
+}
 
 extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int levels,
                                     const float *sigma256, lvr_lod **out) {
@@ -180,5 +361,6 @@ extern "C" void lvr_free_lod(lvr_lod *lod) {
         dev_free(lod->ctx, lod->dens[l]);
         dev_free(lod->ctx, lod->pk[l]);
     }
+    dev_free(lod->ctx, lod->aof);
     delete lod;
 }

@@ -64,6 +64,8 @@ struct lvr_lod {
     // on every side, the four x/y corners (i, j), (i+1, j), (i, j+1), (i+1, j+1)
     // of z-slice k as one float4 (zero outside the grid)
     float4 *pk[4] = {};
+    // spherical per-voxel AO (lvr_lod_ao_field), or null
+    float *aof = nullptr;
 };
 
 struct lvr_ao_model {

@@ -79,6 +79,7 @@ struct RenderParams {
     unsigned *tile_counter;
     // learned AO (ao_mode 2)
     int32_t learned;
+    const float *aof;             // ao_mode 3: spherical per-voxel AO field (level-0 voxels), else null
     int32_t still;                // camera at rest: neighbouring voxels, one hit per line id
     aomlp::Net net;
     const __nv_bfloat16 *vterm;
@@ -184,6 +185,32 @@ __device__ __forceinline__ float sample_level(const RenderParams &P, int l, Vec 
     const float x01 = fmaf(fx, b.y - b.x, b.x), x11 = fmaf(fx, b.w - b.z, b.z);
     const float y0 = fmaf(fy, x10 - x00, x00), y1 = fmaf(fy, x11 - x01, x01);
     return fmaf(fz, y1 - y0, y0);
+}
+
+// Spherical AO field at x: cell-centred trilinear, coordinates clamped to
+// the voxel centres (edge values hold outside).
+__device__ __forceinline__ float sample_field(const RenderParams &P, Vec x) {
+    const float xs[3] = {x.x, x.y, x.z};
+    int i0[3], i1[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int d = P.ldims[0][a];
+        const float q = fminf(fmaxf(xs[a] - 0.5f, 0.0f), (float)(d - 1));
+        int fl = (int)floorf(q);
+        if (fl > d - 2) fl = d - 2 < 0 ? 0 : d - 2;
+        i0[a] = fl;
+        i1[a] = fl + 1 < d ? fl + 1 : d - 1;
+        f[a] = q - (float)fl;
+    }
+    const int dx = P.ldims[0][0], dy = P.ldims[0][1];
+    auto at = [&](int X, int Y, int Z) { return __ldg(P.aof + (X + (int64_t)dx * (Y + (int64_t)dy * Z))); };
+    const float x00 = fmaf(f[0], at(i1[0], i0[1], i0[2]) - at(i0[0], i0[1], i0[2]), at(i0[0], i0[1], i0[2]));
+    const float x10 = fmaf(f[0], at(i1[0], i1[1], i0[2]) - at(i0[0], i1[1], i0[2]), at(i0[0], i1[1], i0[2]));
+    const float x01 = fmaf(f[0], at(i1[0], i0[1], i1[2]) - at(i0[0], i0[1], i1[2]), at(i0[0], i0[1], i1[2]));
+    const float x11 = fmaf(f[0], at(i1[0], i1[1], i1[2]) - at(i0[0], i1[1], i1[2]), at(i0[0], i1[1], i1[2]));
+    const float y0 = fmaf(f[1], x10 - x00, x00), y1 = fmaf(f[1], x11 - x01, x01);
+    return fmaf(f[2], y1 - y0, y0);
 }
 
 // A voxel owns a hit iff the entry point p + t D lies in its [0,1)^3 and in
@@ -599,6 +626,12 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
             __syncwarp();
         }
     }
+    if (MODE != MODE_LEARNED && P.aof) {   // spherical AO field (Sec. 5.3, second approach)
+        for (int g = lane; g < total; g += 32) {
+            const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
+            sm.slot[F_AO][q][o] = sample_field(P, mk(sm.slot[F_PX][q][o], sm.slot[F_PY][q][o], sm.slot[F_PZ][q][o]));
+        }
+    }
     if (MODE != MODE_LEARNED && P.ao) {
         int G = 1;
         while (G < P.ao_rays) G <<= 1;
@@ -640,7 +673,7 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
             AO = le;
             V = 1.0f;
         } else {
-            AO = (P.ao || MODE == MODE_LEARNED) ? sm.slot[F_AO][q][o] : 1.0f;
+            AO = (P.ao || P.aof || MODE == MODE_LEARNED) ? sm.slot[F_AO][q][o] : 1.0f;
             V = P.shadows ? sm.slot[F_V][q][o] : 1.0f;
         }
         const float kk = fmaf(P.ka, AO, P.kd * V * fabsf(dot(n, Lt)));
@@ -898,7 +931,8 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     }
     if (!(desc->radius > 0.0f) || !(desc->radius < 1e3f)) return set_err(ctx, LVR_EINVAL, "radius must be > 0");
     if (!(view->fovy_deg > 0.0f && view->fovy_deg < 180.0f)) return set_err(ctx, LVR_EINVAL, "fovy out of (0,180)");
-    if (desc->ao_mode < 0 || desc->ao_mode > 2) return set_err(ctx, LVR_EINVAL, "bad ao_mode");
+    if (desc->ao_mode < 0 || desc->ao_mode > 3) return set_err(ctx, LVR_EINVAL, "bad ao_mode");
+    if (desc->ao_mode == 3 && !(lod && lod->aof)) return set_err(ctx, LVR_EINVAL, "ao_mode 3 needs lvr_lod_ao_field");
     if (desc->ao_mode == 2 && !ao) return set_err(ctx, LVR_EINVAL, "learned AO needs a model");
     if (desc->still && desc->ao_mode == 2) return set_err(ctx, LVR_EINVAL, "the camera-at-rest mode has no learned-AO variant");
     if ((desc->ao_mode == 2 || judge) && lod && lod->levels < 3)
@@ -970,9 +1004,10 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     P.ao = desc->ao_mode == 1 || judge ? 1 : 0;
     P.ao_rays = P.ao ? desc->ao_rays : 0;
     P.learned = desc->ao_mode == 2 ? 1 : 0;
+    P.aof = desc->ao_mode == 3 && !judge ? lod->aof : nullptr;
     P.still = desc->still ? 1 : 0;
     if (judge) P.shadows = 0;   // the judge keeps the learned AO where the visibility would go
-    P.nrays = P.shadows + P.ao_rays + P.learned;
+    P.nrays = P.shadows + P.ao_rays + P.learned + (P.aof ? 1 : 0);
     P.ao_radius = desc->ao_radius;
     P.ka = desc->ka;
     P.kd = desc->kd;

@@ -109,6 +109,8 @@ _SIGS = {
     "lvr_voxelize_static": ([_vp, _vp, _vp, _i64, _i64, C.POINTER(GridDesc), _vp, _vp, _vp, _i64,
                              C.POINTER(_i64), _vp], C.c_int),
     "lvr_lineset_layout": ([_vp, _vp, C.c_int], C.c_int),
+    "lvr_lod_ao_field": ([_vp, _vp, C.c_int, C.c_float], C.c_int),
+    "lvr_export_ao_field": ([_vp, _vp, _vp], C.c_int),
     "lvr_batch_create": ([_vp, C.POINTER(BatchItem), C.c_int, C.POINTER(_vp)], C.c_int),
     "lvr_batch_render": ([_vp, _vp], C.c_int),
     "lvr_batch_size": ([_vp, C.POINTER(_i64), C.POINTER(_i64)], C.c_int),
@@ -547,3 +549,15 @@ def lvr_autotune(ctx: Context, entries, reps: int = 3) -> dict:
     t = Tune()
     _check(ctx.handle, _L.lvr_autotune(ctx.handle, arr, len(entries), int(reps), C.byref(t)))
     return {"tile": (t.tile_w, t.tile_h), "layout": t.layout, "ms": list(t.ms)}
+
+
+# ---------------------------------------------------------------- spherical per-voxel AO
+def lvr_lod_ao_field(ctx: Context, lod: Lod, rays: int = 100, radius: float = 5.0):
+    _check(ctx.handle, _L.lvr_lod_ao_field(ctx.handle, lod.handle, int(rays), float(radius)))
+
+
+def export_ao_field_numpy(ctx: Context, lod: Lod) -> np.ndarray:
+    d = lod.info().dims[0]
+    out = np.empty(int(d[0]) * int(d[1]) * int(d[2]), np.float32)
+    _check(ctx.handle, _L.lvr_export_ao_field(ctx.handle, lod.handle, _ptr(out)))
+    return out

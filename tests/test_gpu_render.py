@@ -282,3 +282,33 @@ def test_still_camera_mode_layouts_agree(env, c1t):
         ctx.sync()
         outs.append(out.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_sphere_ao_field_matches_oracle(env, c1t):
+    """Sec. 5.3's spherical per-voxel AO (100 rays, radius 5): every voxel's
+    value against the oracle's float64 field."""
+    lvr, O, ctx, dev = env
+    lvr.lvr_lod_ao_field(ctx, c1t.glod, 100, 5.0)
+    got = lvr.export_ao_field_numpy(ctx, c1t.glod).astype(np.float64)
+    ref = O.ao_sphere_field(c1t.olod, 100, 5.0)
+    assert ref.min() < 0.9 and ref.max() > 0.99
+    assert np.abs(got - ref).max() <= 1e-5
+
+
+def test_render_with_sphere_ao_field(env, c1t):
+    import torch
+    lvr, O, ctx, dev = env
+    lvr.lvr_lod_ao_field(ctx, c1t.glod, 100, 5.0)
+    field = O.ao_sphere_field(c1t.olod, 100, 5.0)
+    cam = synth.orbit_view((32, 32, 32), 192, 108)
+    lv, ov, pix = S.views(cam)
+    out = torch.empty((108, 192, 4), dtype=torch.float32, device=dev)
+    lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, lvr.make_desc(0.2, c1t.tf, ert_alpha=0.99, shadows=True, ao_mode=3),
+                   out)
+    ctx.sync()
+    ref, tie, _ = O.render(c1t.ovs, c1t.olod, ov, O.make_rdesc(0.2, c1t.tf, ert_alpha=0.99, shadows=True,
+                                                                 ao_field=field), pix)
+    S.check_image(out.cpu().numpy().reshape(-1, 4), ref, tie, what="spherical AO field")
+    with pytest.raises(lvr.LVRError):     # the field must be built first
+        other = lvr.lvr_build_lod(ctx, c1t.gls, 3, synth.sigma_lut(c1t.tf))
+        lvr.lvr_render(ctx, c1t.gls, other, lv, lvr.make_desc(0.2, c1t.tf, ao_mode=3), out)
