@@ -12,7 +12,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["vox.c", "lod.c", "render.c", "aomlp.c"]
+SOURCES = ["vox.c", "lod.c", "render.c", "aomlp.c", "replines.c"]
 OUT = os.path.join(HERE, "_build", "liboracle.so")
 
 

@@ -114,6 +114,23 @@ typedef struct orc_view {
     float   light_dir[3];       /* direction in which light travels */
 } orc_view;
 
+/* ---- representative lines (reading R3; replines.c) ---- */
+typedef struct orc_reps {
+    int      levels;
+    int32_t  dims[ORC_MAX_LEVELS][3];
+    uint8_t *rep[ORC_MAX_LEVELS];   /* per cell: valid, face_a, u_a, v_a, face_b, u_b, v_b */
+} orc_reps;
+int    orc_reps_build(const orc_voxset *vs, int levels, orc_reps **out);
+void   orc_reps_free(orc_reps *reps);
+void   orc_reps_export(const orc_reps *reps, int level, uint8_t *out7);
+void   orc_rep_world(const orc_reps *reps, int level, int64_t cell, int N, double a[3], double b[3]);
+double orc_halfline_segment_distance(const double o[3], const double d[3], const double a[3],
+                                     const double b[3]);
+/* visibility (0 or 1) of point P toward the light direction Lt (unit, toward
+ * the light) against the representative lines of `level` (reading S5) */
+double orc_shadow_reps_visibility(const orc_voxset *vs, const orc_reps *reps, float radius, int level,
+                                  const double P[3], const double Lt[3]);
+
 typedef struct orc_rdesc {
     float   radius;             /* tube radius, voxel units */
     float   tf[1024];           /* RGBA per attribute byte */
@@ -130,6 +147,8 @@ typedef struct orc_rdesc {
                                    neighbouring voxels' segments; one hit per line id
                                    per voxel */
     const double *ao_field;     /* ao == 3: per-voxel spherical AO (orc_ao_sphere_field) */
+    const orc_reps *reps;       /* shadows == 2: representative lines (reading S5) */
+    int32_t shadow_level;       /* their level */
 } orc_rdesc;
 
 /* counters[0..3]: voxels visited, records tested, LoD trilinear samples,

@@ -31,7 +31,7 @@ class RDesc(C.Structure):
                 ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao", C.c_int32),
                 ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
                 ("kd", C.c_float), ("bg", C.c_float * 3), ("ao_params", C.c_void_p), ("still", C.c_int32),
-                ("ao_field", C.c_void_p)]
+                ("ao_field", C.c_void_p), ("reps", C.c_void_p), ("shadow_level", C.c_int32)]
 
 
 def _p(a):
@@ -69,6 +69,13 @@ def lib():
         L.orc_sample.argtypes = [vp, C.c_int, vp]
         L.orc_sample.restype = C.c_double
         L.orc_ao_dirs.argtypes = [vp, vp, C.c_int, vp]
+        L.orc_reps_build.argtypes = [vp, C.c_int, C.POINTER(vp)]
+        L.orc_reps_free.argtypes = [vp]
+        L.orc_reps_export.argtypes = [vp, C.c_int, vp]
+        L.orc_halfline_segment_distance.argtypes = [vp, vp, vp, vp]
+        L.orc_halfline_segment_distance.restype = C.c_double
+        L.orc_shadow_reps_visibility.argtypes = [vp, vp, C.c_float, C.c_int, vp, vp]
+        L.orc_shadow_reps_visibility.restype = C.c_double
         L.orc_ao_sphere_field.argtypes = [vp, C.c_int, C.c_double, vp]
         L.orc_ao_field_sample.argtypes = [vp, vp, vp]
         L.orc_ao_field_sample.restype = C.c_double
@@ -234,7 +241,8 @@ def make_view(eye, at, up, fovy_deg, width, height, light_dir) -> View:
 
 def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False,
                ao_rays=16, ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), ao_params=None,
-               still=False, ao_field=None) -> RDesc:
+               still=False, ao_field=None, reps=None, shadow_level=1) -> RDesc:
+    """shadows: False/0 off, True/1 density cone march, 2 representative lines (reps, shadow_level)."""
     """ao: False/0 off, True/1 traced, 2 learned (ao_params: float32 [ao_nparams()])."""
     d = RDesc()
     d.radius = float(radius)
@@ -251,6 +259,11 @@ def make_rdesc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao=False
     d.kd = float(kd)
     d.bg[:] = [float(x) for x in bg]
     d.still = int(bool(still))
+    if reps is not None:
+        d._keep_reps = reps
+        d.reps = reps.handle.value
+        d.shadow_level = int(shadow_level)
+        d.shadows = 2
     if ao_field is not None:
         ao_field = np.ascontiguousarray(ao_field, np.float64)
         d._keep_field = ao_field
@@ -396,3 +409,42 @@ def ao_field_sample(field, dims, x):
     dm = np.ascontiguousarray(dims, np.int32)
     x = np.ascontiguousarray(x, np.float64)
     return lib().orc_ao_field_sample(_p(field), _p(dm), _p(x))
+
+
+# ---------------------------------------------------------------- representative lines (reading R3)
+class Reps:
+    """Representative lines of every level of a voxel set."""
+
+    def __init__(self, vs: "VoxSet", levels: int):
+        h = C.c_void_p()
+        _check(lib().orc_reps_build(vs.handle, int(levels), C.byref(h)))
+        self.handle, self.vs, self.levels = h, vs, levels
+
+    def export(self, level):
+        """uint8 [cells][7]: valid, face_a, u_a, v_a, face_b, u_b, v_b."""
+        dims = [int(x) for x in vs_dims(self.vs)]
+        for _ in range(level):
+            dims = [(d + 1) // 2 for d in dims]
+        out = np.empty((dims[0] * dims[1] * dims[2], 7), np.uint8)
+        lib().orc_reps_export(self.handle, int(level), _p(out))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().orc_reps_free(self.handle)
+            self.handle = None
+
+
+def vs_dims(vs: "VoxSet"):
+    return tuple(vs.grid.res)
+
+
+def halfline_segment_distance(o, d, a, b) -> float:
+    o, d, a, b = (np.ascontiguousarray(x, np.float64) for x in (o, d, a, b))
+    return lib().orc_halfline_segment_distance(_p(o), _p(d), _p(a), _p(b))
+
+
+def shadow_reps_visibility(vs: "VoxSet", reps: Reps, radius, level, P, Lt) -> float:
+    P = np.ascontiguousarray(P, np.float64)
+    Lt = np.ascontiguousarray(Lt, np.float64)
+    return lib().orc_shadow_reps_visibility(vs.handle, reps.handle, float(radius), int(level), _p(P), _p(Lt))

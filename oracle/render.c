@@ -465,6 +465,80 @@ static int hit_cmp(const void *x, const void *y) {
     return (a->k > b->k) - (a->k < b->k);
 }
 
+/* Reading S5: hard shadow against the representative lines of one level.
+ * The half-line starts one cell size of that level toward the light and
+ * crosses that level's cells; blocked if it comes within radius x 2^level
+ * of the line of a crossed cell. Near-grazes and near-edge crossings are
+ * flagged. */
+static const double EPS_R = 1e-5;   /* relative: distance vs radius, cell-edge crossings */
+static double shadow_reps(const orc_voxset *vs, const orc_rdesc *rd, const double *P, const double *Lt,
+                          pixstate *ps) {
+    const orc_reps *R = rd->reps;
+    const int l = rd->shadow_level;
+    const double size = ldexp(1.0, l), rl = rd->radius * size;
+    const int32_t *dm = R->dims[l];
+    double S[3], q[3];
+    for (int a = 0; a < 3; a++) {
+        S[a] = P[a] + size * Lt[a];
+        q[a] = S[a] / size;                       /* level-l cell coordinates */
+    }
+    /* enter the level's grid */
+    double tnear = 0.0, tfar = 1e300;
+    for (int a = 0; a < 3; a++) {
+        if (Lt[a] != 0.0) {
+            double t1 = (0.0 - q[a]) / Lt[a], t2 = ((double)dm[a] - q[a]) / Lt[a];
+            tnear = fmax(tnear, fmin(t1, t2));
+            tfar = fmin(tfar, fmax(t1, t2));
+        } else if (q[a] < 0.0 || q[a] > dm[a]) {
+            return 1.0;
+        }
+    }
+    if (!(tnear < tfar)) return 1.0;
+    int64_t v[3], step[3];
+    double tmax[3];
+    for (int a = 0; a < 3; a++) {
+        double x = q[a] + tnear * Lt[a];
+        int64_t vi = (int64_t)floor(x);
+        if (vi < 0) vi = 0;
+        if (vi > dm[a] - 1) vi = dm[a] - 1;
+        v[a] = vi;
+        step[a] = Lt[a] > 0.0 ? 1 : (Lt[a] < 0.0 ? -1 : 0);
+        tmax[a] = step[a] == 0 ? 1e300 : ((double)(step[a] > 0 ? vi + 1 : vi) - q[a]) / Lt[a];
+    }
+    const int N = vs->grid.bins;
+    for (;;) {
+        int64_t cell = v[0] + (int64_t)dm[0] * (v[1] + (int64_t)dm[1] * v[2]);
+        if (R->rep[l][7 * cell]) {
+            double a[3], b[3];
+            orc_rep_world(R, l, cell, N, a, b);
+            double dist = orc_halfline_segment_distance(S, Lt, a, b);
+            note(ps, fabs(dist - rl) / (EPS_R * rl), TIE_GRAZE);
+            if (dist <= rl) return 0.0;
+        }
+        int ax = 0;
+        for (int a = 1; a < 3; a++) if (tmax[a] < tmax[ax]) ax = a;
+        for (int a = 0; a < 3; a++)
+            if (a != ax && tmax[a] < 1e299) note(ps, fabs(tmax[a] - tmax[ax]) / EPS_R, TIE_OWNER);
+        v[ax] += step[ax];
+        if (v[ax] < 0 || v[ax] >= dm[ax]) break;
+        tmax[ax] = ((double)(step[ax] > 0 ? v[ax] + 1 : v[ax]) - q[ax]) / Lt[ax];
+    }
+    return 1.0;
+}
+
+double orc_shadow_reps_visibility(const orc_voxset *vs, const orc_reps *reps, float radius, int level,
+                                  const double P[3], const double Lt[3]) {
+    orc_rdesc rd;
+    memset(&rd, 0, sizeof rd);
+    rd.radius = radius;
+    rd.reps = reps;
+    rd.shadow_level = level;
+    pixstate ps;
+    memset(&ps, 0, sizeof ps);
+    ps.margin = 1e300;
+    return shadow_reps(vs, &rd, P, Lt, &ps);
+}
+
 /* Shade one hit (reading S1) and composite it front to back (Sec. 5.1). */
 static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *rd,
                             const double *O, const double *D, const double *Lt,
@@ -487,7 +561,8 @@ static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rd
     double alpha = rd->opaque ? 1.0 : (double)tf[3];
 
     double V = 1.0, AO = 1.0;
-    if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
+    if (rd->shadows == 2 && rd->reps) V = shadow_reps(vs, rd, P, Lt, ps);
+    else if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
     if (rd->ao == 3 && L && rd->ao_field) {
         AO = orc_ao_field_sample(rd->ao_field, L->dims[0], P);
     } else if (rd->ao == 2 && L && rd->ao_params) {
@@ -756,7 +831,10 @@ static void trace_brute(const orc_voxset *vs, const orc_lod *L, const orc_rdesc 
 int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
                const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
                double *rgba, uint8_t *tie, double *margin, uint64_t *counters, int nthreads) {
-    if ((rd->shadows || rd->ao) && !L) return ORC_EINVAL;
+    if ((rd->shadows == 1 || rd->ao) && !L) return ORC_EINVAL;
+    if (rd->shadows == 2 && (!rd->reps || rd->shadow_level < 0 || rd->shadow_level >= rd->reps->levels))
+        return ORC_EINVAL;
+    if (rd->ao == 3 && !rd->ao_field) return ORC_EINVAL;
     if (view->width < 1 || view->height < 1 || !(rd->radius > 0.0f)) return ORC_EINVAL;
     cam32 cam;
     cam_setup(view, &cam);
