@@ -330,6 +330,27 @@ def still_frame(lvr, ctx, stream, dev, xyz, attr, offs, gdesc, sig, view, tf, la
                               "note": "per-voxel spherical AO for all 256^3 voxels, then the moving frame "
                                       "with soft shadows and the field's AO (the paper quotes ~9 ms for the "
                                       "precompute on a GTX 970)"}
+    # Sec. 5.2's first shadow approach: representative lines (Sec. 3.4) of every level, then the
+    # headline frame with hard shadows against one level's lines in place of the soft ones
+    lvr.lvr_lod_rep_lines(ctx, lod, s)
+    e0.record(stream)
+    for _ in range(3):
+        lvr.lvr_lod_rep_lines(ctx, lod, s)
+    e1.record(stream)
+    e1.synchronize()
+    rep = {"build_ms_all_levels": round(e0.elapsed_time(e1) / 3, 3)}
+    for level in range(LEVELS):
+        d = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, ao_mode=1, ao_rays=16, ao_radius=15.0, tile=tile,
+                          layout=layout, shadow_level=level)
+        lvr.lvr_render(ctx, s, lod, view, d, out)
+        e0.record(stream)
+        for _ in range(3):
+            lvr.lvr_render(ctx, s, lod, view, d, out)
+        e1.record(stream)
+        e1.synchronize()
+        rep[f"frame_ms_level{level}"] = round(e0.elapsed_time(e1) / 3, 3)
+    rep["note"] = "the headline frame (16 traced AO rays) with hard shadows against one level's lines"
+    res["rep_line_shadows"] = rep
     lod.free()
     s.free()
     res["note"] = ("same frame as the headline; at rest the hits that tubes overhanging into a voxel "

@@ -180,6 +180,25 @@ lvr_status lvr_lod_info_get(const lvr_lod *lod, lvr_lod_info *info);
 lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, float radius);
 /* The field, host or device float32 [voxels]. */
 lvr_status lvr_export_ao_field(lvr_ctx *ctx, const lvr_lod *lod, float *field);
+/* Representative lines (Sec. 3.4) for every level of `lod`, built from the
+ * line set it was built from (same grid; EINVAL otherwise) and stored with
+ * the LoD. Level 0: per voxel, its segments in canonical order, each flipped
+ * when its direction makes an obtuse angle with the running average line
+ * (sum of end points minus sum of start points); start and end points are
+ * averaged separately and each average is snapped to the nearest face of the
+ * cell (ties: the lower face id, -x +x -y +y -z +z) and the bin of that face
+ * holding its projection. Level l + 1: per cell, the lines of its 2^3
+ * children (z, y, x order), averaged the same way. After each level, two
+ * neighbours' end points on their shared face (a line's start point first
+ * when both lie there) both move to the bin of their average,
+ * floor((b1 + b2 + 1) / 2) per coordinate. Integer arithmetic throughout;
+ * results are exact. Used by lvr_render with shadows 2 (Sec. 5.2, first
+ * approach). */
+lvr_status lvr_lod_rep_lines(lvr_ctx *ctx, lvr_lod *lod, const lvr_lineset *ls);
+/* The lines of one level, host or device uint8 [cells][8]: byte 0 = 1 when
+ * the cell has a line, bytes 1-3 face, u, v of its start point, bytes 4-6 of
+ * its end point, byte 7 = 0 (bins of the line set's N x N face grid). */
+lvr_status lvr_export_rep_lines(lvr_ctx *ctx, const lvr_lod *lod, int level, uint8_t *out8);
 /* Copy one level out; any pointer may be NULL; host or device; each
  * dims[level] product elements. */
 lvr_status lvr_export_lod(lvr_ctx *ctx, const lvr_lod *lod, int level, uint32_t *cnt,
@@ -209,7 +228,11 @@ lvr_status lvr_lineset_layout(lvr_ctx *ctx, lvr_lineset *ls, int layout);
  * Sec. 5) and blended front to back with the transfer function's opacity
  * until the accumulated opacity reaches `ert_alpha` (Sec. 5.1); opaque mode
  * keeps the first hit. Optional soft shadows march the density LoD toward
- * a directional light, sampling coarser levels with distance (Sec. 5.2);
+ * a directional light, sampling coarser levels with distance (Sec. 5.2),
+ * or (shadows 2, Sec. 5.2's first approach) test a half-line toward the
+ * light, started one cell of level shadow_level away from the hit, against
+ * the representative lines of the cells of that level it crosses: visibility
+ * 0 when one passes within radius x 2^level of it, else 1;
  * optional ambient occlusion marches `ao_rays` hemisphere rays around the
  * normal up to `ao_radius` voxels (Sec. 5.3). Output pixel =
  * (C + (1 - A) * bg, A).
@@ -233,7 +256,9 @@ typedef struct lvr_render_desc {
     float   tf_rgba[1024]; /* transfer function: RGBA per attribute byte */
     int32_t opaque;        /* 1: alpha = 1, first hit only (Sec. 5) */
     float   ert_alpha;     /* early ray termination threshold (> 1: off) */
-    int32_t shadows;       /* 1: soft shadows (needs a LoD) */
+    int32_t shadows;       /* 0 off, 1 soft shadows (density-marched, needs a LoD),
+                              2 hard shadows against the representative lines of LoD level
+                              shadow_level (needs lvr_lod_rep_lines) */
     int32_t ao_mode;       /* 0 off, 1 traced (density-marched, needs a LoD),
                               2 learned surrogate (needs an lvr_ao_model),
                               3 spherical per-voxel field (needs lvr_lod_ao_field) */
@@ -249,6 +274,7 @@ typedef struct lvr_render_desc {
                               holding its entry point; no tube piece is missed for radii up to
                               half a voxel) and blends only the first hit of each 5-bit line id
                               (curve index mod 32) per voxel. Not with ao_mode 2 or batches. */
+    int32_t shadow_level;  /* shadows 2: LoD level whose representative lines cast shadows */
 } lvr_render_desc;
 
 /* rgba: host or device float32 [h * w * 4] for the crop rectangle (row-major,

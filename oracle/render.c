@@ -470,13 +470,44 @@ static int hit_cmp(const void *x, const void *y) {
  * crosses that level's cells; blocked if it comes within radius x 2^level
  * of the line of a crossed cell. Near-grazes and near-edge crossings are
  * flagged. */
-static const double EPS_R = 1e-5;   /* relative: distance vs radius, cell-edge crossings */
+/* Reading S5's visibility is binary, and the library finds hit points in
+ * float32, some 1e-5 voxel away from the exact ones. A pixel is a tie when
+ * a visited cell's line lies within EPS_SH x (cell size of the level) of the
+ * threshold distance, or when the walk's cell sequence is decided by less
+ * than EPS_SH (level cell units: the start cell, or two crossings of one
+ * step) and one of the cells the other choice would visit holds a line
+ * within that margin of blocking. */
+static const double EPS_SH = 1e-3;
+/* a quarter of the 2e-3 per-channel tolerance the parity tests use */
+static const double FLIP_MIN = 5e-4;
+
+/* distance from the half-line S + t Lt to the line of cell (x, y, z), or
+ * +inf when the cell is outside the level or has no line */
+static double rep_cell_distance(const orc_reps *R, int l, int N, const int64_t v[3], const double *S,
+                                const double *Lt) {
+    const int32_t *dm = R->dims[l];
+    for (int a = 0; a < 3; a++)
+        if (v[a] < 0 || v[a] >= dm[a]) return 1e300;
+    const int64_t cell = v[0] + (int64_t)dm[0] * (v[1] + (int64_t)dm[1] * v[2]);
+    if (!R->rep[l][7 * cell]) return 1e300;
+    double a[3], b[3];
+    orc_rep_world(R, l, cell, N, a, b);
+    return orc_halfline_segment_distance(S, Lt, a, b);
+}
+
+/* flag an owner tie when a cell that the other choice visits could block */
+static void note_alt(pixstate *ps, const orc_reps *R, int l, int N, const int64_t v[3], const double *S,
+                     const double *Lt, double rl, double tol) {
+    if (rep_cell_distance(R, l, N, v, S, Lt) <= rl + tol) note(ps, 0.0, TIE_OWNER);
+}
+
 static double shadow_reps(const orc_voxset *vs, const orc_rdesc *rd, const double *P, const double *Lt,
                           pixstate *ps) {
     const orc_reps *R = rd->reps;
     const int l = rd->shadow_level;
-    const double size = ldexp(1.0, l), rl = rd->radius * size;
+    const double size = ldexp(1.0, l), rl = rd->radius * size, tol = EPS_SH * size;
     const int32_t *dm = R->dims[l];
+    const int N = vs->grid.bins;
     double S[3], q[3];
     for (int a = 0; a < 3; a++) {
         S[a] = P[a] + size * Lt[a];
@@ -495,30 +526,45 @@ static double shadow_reps(const orc_voxset *vs, const orc_rdesc *rd, const doubl
     }
     if (!(tnear < tfar)) return 1.0;
     int64_t v[3], step[3];
-    double tmax[3];
+    double tmax[3], x[3];
     for (int a = 0; a < 3; a++) {
-        double x = q[a] + tnear * Lt[a];
-        int64_t vi = (int64_t)floor(x);
+        x[a] = q[a] + tnear * Lt[a];
+        int64_t vi = (int64_t)floor(x[a]);
         if (vi < 0) vi = 0;
         if (vi > dm[a] - 1) vi = dm[a] - 1;
         v[a] = vi;
         step[a] = Lt[a] > 0.0 ? 1 : (Lt[a] < 0.0 ? -1 : 0);
         tmax[a] = step[a] == 0 ? 1e300 : ((double)(step[a] > 0 ? vi + 1 : vi) - q[a]) / Lt[a];
     }
-    const int N = vs->grid.bins;
+    /* the start cell: a coordinate within EPS_SH of a cell boundary */
+    for (int a = 0; a < 3; a++) {
+        const double fr = x[a] - floor(x[a]);
+        if (fr < EPS_SH || fr > 1.0 - EPS_SH) {
+            int64_t w[3] = {v[0], v[1], v[2]};
+            w[a] += fr < EPS_SH ? -1 : 1;
+            note_alt(ps, R, l, N, w, S, Lt, rl, tol);
+        }
+    }
     for (;;) {
-        int64_t cell = v[0] + (int64_t)dm[0] * (v[1] + (int64_t)dm[1] * v[2]);
-        if (R->rep[l][7 * cell]) {
-            double a[3], b[3];
-            orc_rep_world(R, l, cell, N, a, b);
-            double dist = orc_halfline_segment_distance(S, Lt, a, b);
-            note(ps, fabs(dist - rl) / (EPS_R * rl), TIE_GRAZE);
+        const double dist = rep_cell_distance(R, l, N, v, S, Lt);
+        if (dist < 1e299) {
+            note(ps, fabs(dist - rl) / tol, TIE_GRAZE);
             if (dist <= rl) return 0.0;
         }
         int ax = 0;
         for (int a = 1; a < 3; a++) if (tmax[a] < tmax[ax]) ax = a;
+        /* near-simultaneous crossings: the other orders visit v + e_a (and,
+         * with three, v + e_a + e_b) instead of v + e_ax */
+        int tied[3], nt = 0;
         for (int a = 0; a < 3; a++)
-            if (a != ax && tmax[a] < 1e299) note(ps, fabs(tmax[a] - tmax[ax]) / EPS_R, TIE_OWNER);
+            if (tmax[a] < 1e299 && fabs(tmax[a] - tmax[ax]) < EPS_SH) tied[nt++] = a;
+        if (nt > 1)
+            for (int m = 1; m < (1 << nt) - 1; m++) {
+                int64_t w[3] = {v[0], v[1], v[2]};
+                for (int i = 0; i < nt; i++)
+                    if (m >> i & 1) w[tied[i]] += step[tied[i]];
+                note_alt(ps, R, l, N, w, S, Lt, rl, tol);
+            }
         v[ax] += step[ax];
         if (v[ax] < 0 || v[ax] >= dm[ax]) break;
         tmax[ax] = ((double)(step[ax] > 0 ? v[ax] + 1 : v[ax]) - q[ax]) / Lt[ax];
@@ -561,8 +607,21 @@ static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rd
     double alpha = rd->opaque ? 1.0 : (double)tf[3];
 
     double V = 1.0, AO = 1.0;
-    if (rd->shadows == 2 && rd->reps) V = shadow_reps(vs, rd, P, Lt, ps);
-    else if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
+    if (rd->shadows == 2 && rd->reps) {
+        /* a flip of this hit's binary visibility moves the pixel by at most
+         * w kd |n.L| max(rgb) (w: its compositing weight); near-ties of hits
+         * whose flip stays below FLIP_MIN are not flagged */
+        pixstate sh = *ps;
+        sh.tie = 0;
+        sh.margin = 1e300;
+        V = shadow_reps(vs, rd, P, Lt, &sh);
+        const double w = rd->opaque ? 1.0 : (1.0 - ps->A) * alpha;
+        const double cmax = fmax((double)tf[0], fmax((double)tf[1], (double)tf[2]));
+        if (w * rd->kd * fabs(dot3(n, Lt)) * cmax >= FLIP_MIN) {
+            ps->tie |= sh.tie;
+            ps->margin = fmin(ps->margin, sh.margin);
+        }
+    } else if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
     if (rd->ao == 3 && L && rd->ao_field) {
         AO = orc_ao_field_sample(rd->ao_field, L->dims[0], P);
     } else if (rd->ao == 2 && L && rd->ao_params) {

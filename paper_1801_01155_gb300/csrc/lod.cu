@@ -205,6 +205,187 @@ ao_field_tile_kernel(const float *__restrict__ dens, int dx, int dy, int dz, con
 
 }  // namespace
 
+// ------------------------------------------------------------------ representative lines
+// Sec. 3.4: one average line per cell of every level. Level 0 averages the
+// start points and the end points of a voxel's segments separately, in the
+// canonical segment order, flipping a segment first when it points against
+// the running average (sum of end points minus sum of start points); each
+// average is snapped to the nearest face of the cell (ties: the lower face
+// id) and the bin holding its projection. Coarser cells average their
+// children's lines (children in z, y, x order) the same way. After each
+// level, a line end point on a face shared with a neighbour's line end point
+// (start point taken first when both lie on that face) moves, with it, to
+// the bin of their average. Points are integers in units of 1/(2N) of a
+// cell (children: 1/(4N) of the parent), so every decision is exact.
+//
+// Joining is a gather: a face pair only changes the two end points on that
+// face, so each cell reads its neighbours from the unjoined copy and writes
+// its own word; the result equals joining the pairs one after another.
+namespace {
+
+__device__ __forceinline__ uint32_t rep_point(uint64_t w, int e) { return (uint32_t)(w >> (8 + 24 * e)) & 0xffffffu; }
+
+// nearest face and bins of the average point S / n (S in units 1 / U per cell edge)
+__device__ __forceinline__ uint32_t rep_snap(const long long S[3], long long n, long long U, long long N) {
+    int best = 0;
+    long long bd = S[0];
+    for (int f = 1; f < 6; f++) {
+        const long long d = (f & 1) ? U * n - S[f >> 1] : S[f >> 1];
+        if (d < bd) { bd = d; best = f; }
+    }
+    const int ax = best >> 1, b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+    uint32_t bin[2];
+    const int bx[2] = {b0, b1};
+    for (int i = 0; i < 2; i++) {
+        const long long s = S[bx[i]] < 0 ? 0 : S[bx[i]];
+        const long long b = (s * N) / (U * n);
+        bin[i] = (uint32_t)(b > N - 1 ? N - 1 : b);
+    }
+    return (uint32_t)best | bin[0] << 8 | bin[1] << 16;
+}
+
+__device__ __forceinline__ void rep_accumulate(int a[3], int b[3], long long SA[3], long long SB[3], long long &n) {
+    if (n > 0) {
+        long long dot = 0;
+        for (int c = 0; c < 3; c++) dot += (long long)(b[c] - a[c]) * (SB[c] - SA[c]);
+        if (dot < 0)
+            for (int c = 0; c < 3; c++) { const int t = a[c]; a[c] = b[c]; b[c] = t; }
+    }
+    for (int c = 0; c < 3; c++) { SA[c] += a[c]; SB[c] += b[c]; }
+    n++;
+}
+
+__device__ __forceinline__ uint64_t rep_word(uint32_t ps, uint32_t pe) {
+    return 1ull | (uint64_t)ps << 8 | (uint64_t)pe << 32;
+}
+
+__global__ void __launch_bounds__(256)
+rep_level0_kernel(const uint32_t *__restrict__ offset, const uint64_t *__restrict__ rec, int64_t nvox, int N,
+                  uint64_t *__restrict__ out) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    const uint32_t beg = offset[v], end = offset[v + 1];
+    long long SA[3] = {0, 0, 0}, SB[3] = {0, 0, 0}, n = 0;
+    for (uint32_t k = beg; k < end; k++) {
+        const uint64_t r = rec[k];
+        int a[3], b[3];
+        face_point_2n(rec_face_in(r), rec_u_in(r), rec_v_in(r), 2 * N, a);
+        face_point_2n(rec_face_out(r), rec_u_out(r), rec_v_out(r), 2 * N, b);
+        rep_accumulate(a, b, SA, SB, n);
+    }
+    out[v] = n ? rep_word(rep_snap(SA, n, 2 * N, N), rep_snap(SB, n, 2 * N, N)) : 0ull;
+}
+
+__global__ void __launch_bounds__(256)
+rep_pool_kernel(const uint64_t *__restrict__ child, int cx, int cy, int cz, uint64_t *__restrict__ out,
+                int px, int py, int pz, int N) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= (int64_t)px * py * pz) return;
+    const int x = (int)(c % px), y = (int)((c / px) % py), z = (int)(c / ((int64_t)px * py));
+    long long SA[3] = {0, 0, 0}, SB[3] = {0, 0, 0}, n = 0;
+    for (int dz = 0; dz < 2; dz++)
+        for (int dy = 0; dy < 2; dy++)
+            for (int dx = 0; dx < 2; dx++) {
+                const int X = 2 * x + dx, Y = 2 * y + dy, Z = 2 * z + dz;
+                if (X >= cx || Y >= cy || Z >= cz) continue;
+                const uint64_t w = child[X + (int64_t)cx * (Y + (int64_t)cy * Z)];
+                if (!(w & 1ull)) continue;
+                int a[3], b[3];
+                const uint32_t ps = rep_point(w, 0), pe = rep_point(w, 1);
+                face_point_2n(ps & 0xffu, (ps >> 8) & 0xffu, ps >> 16, 2 * N, a);
+                face_point_2n(pe & 0xffu, (pe >> 8) & 0xffu, pe >> 16, 2 * N, b);
+                const int off[3] = {dx, dy, dz};
+                for (int q = 0; q < 3; q++) {
+                    a[q] += off[q] * 2 * N;
+                    b[q] += off[q] * 2 * N;
+                }
+                rep_accumulate(a, b, SA, SB, n);
+            }
+    out[c] = n ? rep_word(rep_snap(SA, n, 4 * N, N), rep_snap(SB, n, 4 * N, N)) : 0ull;
+}
+
+// which end point (0 start, 1 end) of line word w lies on face f, start first; -1: none
+__device__ __forceinline__ int rep_end_on(uint64_t w, uint32_t f) {
+    if ((rep_point(w, 0) & 0xffu) == f) return 0;
+    if ((rep_point(w, 1) & 0xffu) == f) return 1;
+    return -1;
+}
+
+__global__ void __launch_bounds__(256)
+rep_join_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, int dx, int dy, int dz) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= (int64_t)dx * dy * dz) return;
+    uint64_t w = in[c];
+    if (w & 1ull) {
+        const int dm[3] = {dx, dy, dz};
+        const int p[3] = {(int)(c % dx), (int)((c / dx) % dy), (int)(c / ((int64_t)dx * dy))};
+        const int64_t stride[3] = {1, dx, (int64_t)dx * dy};
+        uint64_t res = w;
+        for (int e = 0; e < 2; e++) {
+            const uint32_t pt = rep_point(w, e), f = pt & 0xffu;
+            if (rep_end_on(w, f) != e) continue;   // the other end point on this face joins
+            const int ax = (int)(f >> 1), side = (int)(f & 1u);
+            const int q = p[ax] + (side ? 1 : -1);
+            if (q < 0 || q >= dm[ax]) continue;
+            const uint64_t nw = in[c + (side ? stride[ax] : -stride[ax])];
+            if (!(nw & 1ull)) continue;
+            const int ne = rep_end_on(nw, f ^ 1u);
+            if (ne < 0) continue;
+            const uint32_t np = rep_point(nw, ne);
+            const uint32_t u = (((pt >> 8) & 0xffu) + ((np >> 8) & 0xffu) + 1u) >> 1;
+            const uint32_t v = ((pt >> 16) + (np >> 16) + 1u) >> 1;
+            const int sh = 8 + 24 * e;
+            res = (res & ~(0xffffffull << sh)) | (uint64_t)(f | u << 8 | v << 16) << sh;
+        }
+        w = res;
+    }
+    out[c] = w;
+}
+
+}  // namespace
+
+extern "C" lvr_status lvr_lod_rep_lines(lvr_ctx *ctx, lvr_lod *lod, const lvr_lineset *ls) {
+    if (!ctx) return LVR_EINVAL;
+    if (!lod || !ls) return set_err(ctx, LVR_EINVAL, "lvr_lod_rep_lines: null argument");
+    for (int a = 0; a < 3; a++)
+        if (lod->dims[0][a] != ls->res[a]) return set_err(ctx, LVR_EINVAL, "LoD does not belong to this line set");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    lvr_status st = LVR_OK;
+    for (int l = 0; l < lod->levels && st == LVR_OK; l++)
+        if (!lod->rep[l]) {
+            const size_t n = (size_t)lod->dims[l][0] * lod->dims[l][1] * lod->dims[l][2];
+            st = dev_alloc(ctx, (void **)&lod->rep[l], n * 8);
+        }
+    uint64_t *tmp = nullptr;
+    const int64_t n0 = (int64_t)ls->res[0] * ls->res[1] * ls->res[2];
+    if (st == LVR_OK) st = dev_alloc(ctx, (void **)&tmp, (size_t)n0 * 8);
+    if (st != LVR_OK) return st;
+    const int N = ls->bins;
+    rep_level0_kernel<<<grid1d(n0, 256), 256, 0, s>>>(ls->offset, ls->rec, n0, N, tmp);
+    rep_join_kernel<<<grid1d(n0, 256), 256, 0, s>>>(tmp, lod->rep[0], ls->res[0], ls->res[1], ls->res[2]);
+    for (int l = 1; l < lod->levels; l++) {
+        const int32_t *c = lod->dims[l - 1], *p = lod->dims[l];
+        const int64_t np = (int64_t)p[0] * p[1] * p[2];
+        rep_pool_kernel<<<grid1d(np, 256), 256, 0, s>>>(lod->rep[l - 1], c[0], c[1], c[2], tmp, p[0], p[1], p[2], N);
+        rep_join_kernel<<<grid1d(np, 256), 256, 0, s>>>(tmp, lod->rep[l], p[0], p[1], p[2]);
+    }
+    const cudaError_t e = cudaGetLastError();
+    dev_free(ctx, tmp);   // stream-ordered
+    if (e != cudaSuccess) return cuda_err(ctx, e, "lvr_lod_rep_lines");
+    lod->rep_bins = N;
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_export_rep_lines(lvr_ctx *ctx, const lvr_lod *lod, int level, uint8_t *out8) {
+    if (!ctx) return LVR_EINVAL;
+    if (!lod || level < 0 || level >= lod->levels || !lod->rep[level] || !out8)
+        return set_err(ctx, LVR_EINVAL, "no representative lines at this level");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t n = (size_t)lod->dims[level][0] * lod->dims[level][1] * lod->dims[level][2];
+    return copy_out(ctx, out8, lod->rep[level], n * 8);
+}
+
 extern "C" lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, float radius) {
     if (!ctx) return LVR_EINVAL;
     if (!lod) return set_err(ctx, LVR_EINVAL, "lvr_lod_ao_field: null LoD");
@@ -362,5 +543,6 @@ extern "C" void lvr_free_lod(lvr_lod *lod) {
         dev_free(lod->ctx, lod->pk[l]);
     }
     dev_free(lod->ctx, lod->aof);
+    for (int l = 0; l < 4; l++) dev_free(lod->ctx, lod->rep[l]);
     delete lod;
 }

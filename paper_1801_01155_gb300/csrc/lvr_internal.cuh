@@ -66,6 +66,10 @@ struct lvr_lod {
     float4 *pk[4] = {};
     // spherical per-voxel AO (lvr_lod_ao_field), or null
     float *aof = nullptr;
+    // representative lines per level (lvr_lod_rep_lines), or null: per cell one
+    // word, bytes 0 valid, 1-3 face/u/v of the start point, 4-6 of the end point
+    uint64_t *rep[4] = {};
+    int rep_bins = 0;
 };
 
 struct lvr_ao_model {

@@ -81,6 +81,10 @@ struct RenderParams {
     int32_t learned;
     const float *aof;             // ao_mode 3: spherical per-voxel AO field (level-0 voxels), else null
     int32_t still;                // camera at rest: neighbouring voxels, one hit per line id
+    // shadows 2: representative lines of one LoD level (Sec. 5.2, first approach)
+    const uint64_t *rep;
+    int32_t rep_dims[3];
+    float rep_size, rep_inv, rep_r2;
     aomlp::Net net;
     const __nv_bfloat16 *vterm;
     // sample mode: per pixel the hit of index `target` (hash of seed and
@@ -560,6 +564,74 @@ __device__ __forceinline__ float march(const RenderParams &P, Vec p, Vec d, floa
     return O;
 }
 
+// Squared distance between the half-line o + t d (t >= 0, |d| = 1) and the
+// segment [a, b]: the least of the interior stationary point (when it lies
+// in range) and the optima on the three boundaries t = 0, h = 0, h = 1.
+// Every candidate is a pair of real points, so the result never falls below
+// the true distance.
+__device__ __forceinline__ float halfline_segment_d2(Vec o, Vec d, Vec a, Vec b) {
+    const Vec ba = sub(b, a), ao = sub(a, o);
+    const float L2 = dot(ba, ba), k = dot(d, ba), e = dot(d, ao), f = dot(ba, ao);
+    auto at = [&](float t, float h) {
+        const Vec q = sub(axpy(t, d, o), axpy(h, ba, a));
+        return dot(q, q);
+    };
+    float best = at(0.0f, L2 > 0.0f ? fminf(1.0f, fmaxf(0.0f, -f / L2)) : 0.0f);
+    best = fminf(best, at(fmaxf(0.0f, e), 0.0f));
+    best = fminf(best, at(fmaxf(0.0f, e + k), 1.0f));
+    const float det = L2 - k * k;
+    if (L2 > 0.0f && det > 1e-6f * L2) {
+        const float h = fmaf(k, e, -f) / det, t = fmaf(h, k, e);
+        if (t >= 0.0f && h >= 0.0f && h <= 1.0f) best = fminf(best, at(t, h));
+    }
+    return best;
+}
+
+// Hard shadow against the representative lines of one LoD level (Sec. 5.2,
+// first approach): from one cell size toward the light, walk the level's
+// cells (3D DDA, in cell units) and report 0 at the first cell whose line
+// passes within the scaled radius of the half-line, else 1.
+__device__ float rep_visibility(const RenderParams &P, Vec Pg, Vec Lt) {
+    const Vec q = scale(axpy(P.rep_size, Lt, Pg), P.rep_inv);
+    const float qa[3] = {q.x, q.y, q.z}, La[3] = {Lt.x, Lt.y, Lt.z};
+    float tnear = 0.0f, tfar = INFINITY;
+    for (int a = 0; a < 3; a++) {
+        if (La[a] != 0.0f) {
+            const float t1 = -qa[a] / La[a], t2 = ((float)P.rep_dims[a] - qa[a]) / La[a];
+            tnear = fmaxf(tnear, fminf(t1, t2));
+            tfar = fminf(tfar, fmaxf(t1, t2));
+        } else if (qa[a] < 0.0f || qa[a] > (float)P.rep_dims[a]) {
+            return 1.0f;
+        }
+    }
+    if (!(tnear < tfar)) return 1.0f;
+    int v[3], st[3];
+    float tm[3];
+    for (int a = 0; a < 3; a++) {
+        const int vi = (int)floorf(fmaf(tnear, La[a], qa[a]));
+        v[a] = min(max(vi, 0), P.rep_dims[a] - 1);
+        st[a] = La[a] > 0.0f ? 1 : (La[a] < 0.0f ? -1 : 0);
+        tm[a] = st[a] == 0 ? INFINITY : ((float)(st[a] > 0 ? v[a] + 1 : v[a]) - qa[a]) / La[a];
+    }
+    const int limit = P.rep_dims[0] + P.rep_dims[1] + P.rep_dims[2];
+    for (int it = 0; it < limit; it++) {
+        const uint64_t w = __ldg(reinterpret_cast<const unsigned long long *>(P.rep) +
+                                 (v[0] + (int64_t)P.rep_dims[0] * (v[1] + (int64_t)P.rep_dims[1] * v[2])));
+        if (w & 1ull) {
+            const uint32_t ps = (uint32_t)(w >> 8), pe = (uint32_t)(w >> 32);
+            const Vec a = face_point(ps & 0xffu, (ps >> 8) & 0xffu, (ps >> 16) & 0xffu, P.invN);
+            const Vec b = face_point(pe & 0xffu, (pe >> 8) & 0xffu, (pe >> 16) & 0xffu, P.invN);
+            const Vec o = mk(q.x - (float)v[0], q.y - (float)v[1], q.z - (float)v[2]);
+            if (halfline_segment_d2(o, Lt, a, b) <= P.rep_r2) return 0.0f;
+        }
+        const int ax = tm[0] <= tm[1] ? (tm[0] <= tm[2] ? 0 : 2) : (tm[1] <= tm[2] ? 1 : 2);
+        v[ax] += st[ax];
+        if (v[ax] < 0 || v[ax] >= P.rep_dims[ax]) break;
+        tm[ax] = ((float)(st[ax] > 0 ? v[ax] + 1 : v[ax]) - qa[ax]) / La[ax];
+    }
+    return 1.0f;
+}
+
 template <class SM>
 __device__ __forceinline__ int slot_owner(const SM &sm, int warp, int g) { return warp * 32 + (sm.item[warp][g] >> 3); }
 template <class SM>
@@ -581,7 +653,8 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
         for (int g = lane; g < total; g += 32) {
             const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
             const Vec Pg = mk(sm.slot[F_PX][q][o], sm.slot[F_PY][q][o], sm.slot[F_PZ][q][o]);
-            sm.slot[F_V][q][o] = 1.0f - fminf(1.0f, march(P, Pg, Lt, -1.0f, nsamp));
+            sm.slot[F_V][q][o] = P.shadows == 2 ? rep_visibility(P, Pg, Lt)
+                                                : 1.0f - fminf(1.0f, march(P, Pg, Lt, -1.0f, nsamp));
         }
     }
     if constexpr (MODE == MODE_LEARNED || MODE == MODE_JUDGE) {
@@ -937,6 +1010,10 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     if (desc->still && desc->ao_mode == 2) return set_err(ctx, LVR_EINVAL, "the camera-at-rest mode has no learned-AO variant");
     if ((desc->ao_mode == 2 || judge) && lod && lod->levels < 3)
         return set_err(ctx, LVR_EINVAL, "learned AO needs a LoD of >= 3 levels");
+    if (desc->shadows < 0 || desc->shadows > 2) return set_err(ctx, LVR_EINVAL, "bad shadows mode");
+    if (desc->shadows == 2 && !(lod && desc->shadow_level >= 0 && desc->shadow_level < lod->levels &&
+                                lod->rep[desc->shadow_level] && lod->rep_bins == ls->bins))
+        return set_err(ctx, LVR_EINVAL, "shadows 2 needs lvr_lod_rep_lines and a shadow_level of the LoD");
     const bool need_lod = desc->shadows || desc->ao_mode != 0;
     if (need_lod && !lod) return set_err(ctx, LVR_EINVAL, "shadows / AO need a LoD");
     if ((desc->ao_mode == 1 || judge) && (desc->ao_rays < 1 || desc->ao_rays > MAX_AO))
@@ -1000,14 +1077,22 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     for (int a = 0; a < 3; a++) P.Lt[a] = (float)(-ld[a]);
     P.opaque = desc->opaque ? 1 : 0;
     P.ert = desc->ert_alpha;
-    P.shadows = desc->shadows ? 1 : 0;
+    P.shadows = desc->shadows;
+    if (P.shadows == 2) {
+        const int l = desc->shadow_level;
+        P.rep = lod->rep[l];
+        for (int a = 0; a < 3; a++) P.rep_dims[a] = lod->dims[l][a];
+        P.rep_size = (float)(1 << l);
+        P.rep_inv = 1.0f / P.rep_size;
+        P.rep_r2 = desc->radius * desc->radius;   // radius x 2^l in cells of 2^l voxels
+    }
     P.ao = desc->ao_mode == 1 || judge ? 1 : 0;
     P.ao_rays = P.ao ? desc->ao_rays : 0;
     P.learned = desc->ao_mode == 2 ? 1 : 0;
     P.aof = desc->ao_mode == 3 && !judge ? lod->aof : nullptr;
     P.still = desc->still ? 1 : 0;
     if (judge) P.shadows = 0;   // the judge keeps the learned AO where the visibility would go
-    P.nrays = P.shadows + P.ao_rays + P.learned + (P.aof ? 1 : 0);
+    P.nrays = (P.shadows ? 1 : 0) + P.ao_rays + P.learned + (P.aof ? 1 : 0);
     P.ao_radius = desc->ao_radius;
     P.ka = desc->ka;
     P.kd = desc->kd;

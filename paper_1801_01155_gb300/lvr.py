@@ -61,7 +61,8 @@ class RenderDesc(C.Structure):
                 ("ert_alpha", C.c_float), ("shadows", C.c_int32), ("ao_mode", C.c_int32),
                 ("ao_rays", C.c_int32), ("ao_radius", C.c_float), ("ka", C.c_float),
                 ("kd", C.c_float), ("bg", C.c_float * 3), ("tile_w", C.c_int32),
-                ("tile_h", C.c_int32), ("layout", C.c_int32), ("still", C.c_int32)]
+                ("tile_h", C.c_int32), ("layout", C.c_int32), ("still", C.c_int32),
+                ("shadow_level", C.c_int32)]
 
 
 class BatchItem(C.Structure):
@@ -111,6 +112,8 @@ _SIGS = {
     "lvr_lineset_layout": ([_vp, _vp, C.c_int], C.c_int),
     "lvr_lod_ao_field": ([_vp, _vp, C.c_int, C.c_float], C.c_int),
     "lvr_export_ao_field": ([_vp, _vp, _vp], C.c_int),
+    "lvr_lod_rep_lines": ([_vp, _vp, _vp], C.c_int),
+    "lvr_export_rep_lines": ([_vp, _vp, C.c_int, _vp], C.c_int),
     "lvr_batch_create": ([_vp, C.POINTER(BatchItem), C.c_int, C.POINTER(_vp)], C.c_int),
     "lvr_batch_render": ([_vp, _vp], C.c_int),
     "lvr_batch_size": ([_vp, C.POINTER(_i64), C.POINTER(_i64)], C.c_int),
@@ -344,7 +347,9 @@ def make_view(eye, at, up, fovy_deg, width, height, light_dir, crop=None) -> Vie
 
 def make_desc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao_mode=0, ao_rays=16,
               ao_radius=15.0, ka=0.3, kd=0.7, bg=(1.0, 1.0, 1.0), tile=(0, 0), layout=0,
-              still=False) -> RenderDesc:
+              still=False, shadow_level=None) -> RenderDesc:
+    """shadows: False/0 off, True/1 soft (density LoD); shadow_level given: 2, hard
+    shadows against that LoD level's representative lines (lvr_lod_rep_lines)."""
     d = RenderDesc()
     d.radius = float(radius)
     tf = np.ascontiguousarray(np.asarray(tf, np.float32)).reshape(-1)
@@ -362,6 +367,9 @@ def make_desc(radius, tf, opaque=False, ert_alpha=0.99, shadows=False, ao_mode=0
     d.tile_w, d.tile_h = int(tile[0]), int(tile[1])
     d.layout = int(layout)
     d.still = int(bool(still))
+    if shadow_level is not None:
+        d.shadows = 2
+        d.shadow_level = int(shadow_level)
     return d
 
 
@@ -560,4 +568,17 @@ def export_ao_field_numpy(ctx: Context, lod: Lod) -> np.ndarray:
     d = lod.info().dims[0]
     out = np.empty(int(d[0]) * int(d[1]) * int(d[2]), np.float32)
     _check(ctx.handle, _L.lvr_export_ao_field(ctx.handle, lod.handle, _ptr(out)))
+    return out
+
+
+# ---------------------------------------------------------------- representative lines
+def lvr_lod_rep_lines(ctx: Context, lod: Lod, ls: LineSet):
+    _check(ctx.handle, _L.lvr_lod_rep_lines(ctx.handle, lod.handle, ls.handle))
+
+
+def export_rep_lines_numpy(ctx: Context, lod: Lod, level: int) -> np.ndarray:
+    """uint8 [cells][8] of one level (see lvr_export_rep_lines)."""
+    d = lod.info().dims[level]
+    out = np.empty((int(d[0]) * int(d[1]) * int(d[2]), 8), np.uint8)
+    _check(ctx.handle, _L.lvr_export_rep_lines(ctx.handle, lod.handle, int(level), _ptr(out)))
     return out

@@ -56,7 +56,7 @@ def test_structs_match_header_sizes(lib):
     import ctypes as C
     assert C.sizeof(lib.GridDesc) == 4 * 3 + 4 + 4 + 12 + 4 + 8
     assert C.sizeof(lib.View) == 12 * 3 + 4 + 8 + 16 + 12
-    assert C.sizeof(lib.RenderDesc) == 4 + 4096 + 4 + 4 + 4 + 4 + 4 + 4 + 8 + 12 + 8 + 4 + 4
+    assert C.sizeof(lib.RenderDesc) == 4 + 4096 + 4 + 4 + 4 + 4 + 4 + 4 + 8 + 12 + 8 + 4 + 4 + 4
 
 
 STRUCTS = {"lvr_grid_desc": "GridDesc", "lvr_lineset_info": "LineSetInfo", "lvr_lod_info": "LodInfo",
