@@ -339,16 +339,20 @@ def still_frame(lvr, ctx, stream, dev, xyz, attr, offs, gdesc, sig, view, tf, la
     e1.record(stream)
     e1.synchronize()
     rep = {"build_ms_all_levels": round(e0.elapsed_time(e1) / 3, 3)}
-    for level in range(LEVELS):
+    for level in [None] + list(range(LEVELS)):
         d = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, ao_mode=1, ao_rays=16, ao_radius=15.0, tile=tile,
                           layout=layout, shadow_level=level)
-        lvr.lvr_render(ctx, s, lod, view, d, out)
+        cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+        lvr.lvr_render(ctx, s, lod, view, d, out, counters=cnt)
         e0.record(stream)
         for _ in range(3):
             lvr.lvr_render(ctx, s, lod, view, d, out)
         e1.record(stream)
         e1.synchronize()
-        rep[f"frame_ms_level{level}"] = round(e0.elapsed_time(e1) / 3, 3)
+        c = cnt.cpu().numpy()
+        key = "no_shadows" if level is None else f"level{level}"
+        rep[f"frame_ms_{key}"] = round(e0.elapsed_time(e1) / 3, 3)
+        rep[f"samples_and_cells_per_hit_{key}"] = round(float(c[2]) / max(1.0, float(c[3])), 2)
     rep["note"] = "the headline frame (16 traced AO rays) with hard shadows against one level's lines"
     res["rep_line_shadows"] = rep
     lod.free()

@@ -279,7 +279,8 @@ typedef struct lvr_render_desc {
 
 /* rgba: host or device float32 [h * w * 4] for the crop rectangle (row-major,
  * row 0 = top of the crop). counters: NULL, or host or device uint64 [4]
- * receiving voxels visited, records tested, LoD trilinear samples and
+ * receiving voxels visited, records tested, LoD trilinear samples (with shadows 2 plus
+ * the representative-line cells tested) and
  * composited hits over the whole rectangle (costs one extra reduction).
  * `lod` may be NULL unless shadows or AO are on; `ao` may be NULL unless
  * ao_mode == 2, where the call evaluates the model's per-voxel layer-1 term

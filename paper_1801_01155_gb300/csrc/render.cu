@@ -239,7 +239,10 @@ __device__ __forceinline__ bool key_after(float t, uint32_t k, float lt, uint32_
 // samples (voxel, direction, traced AO) for the learned-AO trainer; image with
 // learned AO that also traces AO at every hit and records the difference;
 // image with the camera at rest (neighbouring voxels' segments, line ids).
-enum { MODE_IMAGE = 0, MODE_LEARNED = 1, MODE_SAMPLES = 2, MODE_JUDGE = 3, MODE_STILL = 4 };
+// MODE_REP: the image mode with hard shadows against representative lines,
+// a variant of its own so that the walk's registers do not weigh on the
+// other image kernels
+enum { MODE_IMAGE = 0, MODE_LEARNED = 1, MODE_SAMPLES = 2, MODE_JUDGE = 3, MODE_STILL = 4, MODE_REP = 5 };
 constexpr int JH = 4096;          // judge histogram bins over |e| in [0, 1]
 
 // Shared memory of one block: transfer function, per-lane sorted hit staging
@@ -275,7 +278,7 @@ struct Smem {
     static constexpr int kMode = MODE;
     static constexpr int kLayout = LAYOUT;
     static constexpr bool kBatch = BATCH;   // the transfer function is read from global memory
-    static constexpr bool kVid = MODE != MODE_IMAGE && MODE != MODE_STILL;
+    static constexpr bool kVid = MODE != MODE_IMAGE && MODE != MODE_STILL && MODE != MODE_REP;
     static constexpr bool kStill = MODE == MODE_STILL;
     float4 tf[BATCH ? 1 : 256];
     float4 hot[BATCH ? 4 : 1][BATCH ? HOT_BYTES / 16 : 1];   // batched: each warp's current view parameters
@@ -576,66 +579,206 @@ __device__ __forceinline__ float halfline_segment_d2(Vec o, Vec d, Vec a, Vec b)
         const Vec q = sub(axpy(t, d, o), axpy(h, ba, a));
         return dot(q, q);
     };
-    float best = at(0.0f, L2 > 0.0f ? fminf(1.0f, fmaxf(0.0f, -f / L2)) : 0.0f);
+    float best = at(0.0f, L2 > 0.0f ? fminf(1.0f, fmaxf(0.0f, __fdividef(-f, L2))) : 0.0f);
     best = fminf(best, at(fmaxf(0.0f, e), 0.0f));
     best = fminf(best, at(fmaxf(0.0f, e + k), 1.0f));
     const float det = L2 - k * k;
     if (L2 > 0.0f && det > 1e-6f * L2) {
-        const float h = fmaf(k, e, -f) / det, t = fmaf(h, k, e);
+        const float h = __fdividef(fmaf(k, e, -f), det), t = fmaf(h, k, e);
         if (t >= 0.0f && h >= 0.0f && h <= 1.0f) best = fminf(best, at(t, h));
     }
     return best;
 }
 
-// Hard shadow against the representative lines of one LoD level (Sec. 5.2,
-// first approach): from one cell size toward the light, walk the level's
-// cells (3D DDA, in cell units) and report 0 at the first cell whose line
-// passes within the scaled radius of the half-line, else 1.
-__device__ float rep_visibility(const RenderParams &P, Vec Pg, Vec Lt) {
-    const Vec q = scale(axpy(P.rep_size, Lt, Pg), P.rep_inv);
-    const float qa[3] = {q.x, q.y, q.z}, La[3] = {Lt.x, Lt.y, Lt.z};
-    float tnear = 0.0f, tfar = INFINITY;
-    for (int a = 0; a < 3; a++) {
-        if (La[a] != 0.0f) {
-            const float t1 = -qa[a] / La[a], t2 = ((float)P.rep_dims[a] - qa[a]) / La[a];
-            tnear = fmaxf(tnear, fminf(t1, t2));
-            tfar = fminf(tfar, fmaxf(t1, t2));
-        } else if (qa[a] < 0.0f || qa[a] > (float)P.rep_dims[a]) {
-            return 1.0f;
-        }
+// Does the line [a, b] pass within sqrt(r2) of the half-line o + t d? The
+// distance between the two infinite lines, |w . c| / |c| with w = a - o and
+// c = d x (b - a), bounds the answer from below and rejects most cells with
+// one cross product and no division. When it does not, and the lines' closest
+// points, t = (w x (b - a)) . c / |c|^2 and h = (w x d) . c / |c|^2, lie on
+// the half-line and the segment, that distance is the answer; otherwise the
+// optimum is on the boundary of the parameter range.
+__device__ __forceinline__ bool rep_blocks(Vec o, Vec d, Vec a, Vec b, float r2) {
+    const Vec ba = sub(b, a), c = cross(d, ba), w = sub(a, o);
+    const float c2 = dot(c, c), wc = dot(w, c);
+    if (wc * wc > r2 * c2) return false;
+    if (c2 > 1e-6f * dot(ba, ba)) {
+        const float t = dot(cross(w, ba), c), h = dot(cross(w, d), c);
+        if (t >= 0.0f && h >= 0.0f && h <= c2) return true;
     }
-    if (!(tnear < tfar)) return 1.0f;
-    int v[3], st[3];
-    float tm[3];
-    for (int a = 0; a < 3; a++) {
-        const int vi = (int)floorf(fmaf(tnear, La[a], qa[a]));
-        v[a] = min(max(vi, 0), P.rep_dims[a] - 1);
-        st[a] = La[a] > 0.0f ? 1 : (La[a] < 0.0f ? -1 : 0);
-        tm[a] = st[a] == 0 ? INFINITY : ((float)(st[a] > 0 ? v[a] + 1 : v[a]) - qa[a]) / La[a];
-    }
-    const int limit = P.rep_dims[0] + P.rep_dims[1] + P.rep_dims[2];
-    for (int it = 0; it < limit; it++) {
-        const uint64_t w = __ldg(reinterpret_cast<const unsigned long long *>(P.rep) +
-                                 (v[0] + (int64_t)P.rep_dims[0] * (v[1] + (int64_t)P.rep_dims[1] * v[2])));
-        if (w & 1ull) {
-            const uint32_t ps = (uint32_t)(w >> 8), pe = (uint32_t)(w >> 32);
-            const Vec a = face_point(ps & 0xffu, (ps >> 8) & 0xffu, (ps >> 16) & 0xffu, P.invN);
-            const Vec b = face_point(pe & 0xffu, (pe >> 8) & 0xffu, (pe >> 16) & 0xffu, P.invN);
-            const Vec o = mk(q.x - (float)v[0], q.y - (float)v[1], q.z - (float)v[2]);
-            if (halfline_segment_d2(o, Lt, a, b) <= P.rep_r2) return 0.0f;
-        }
-        const int ax = tm[0] <= tm[1] ? (tm[0] <= tm[2] ? 0 : 2) : (tm[1] <= tm[2] ? 1 : 2);
-        v[ax] += st[ax];
-        if (v[ax] < 0 || v[ax] >= P.rep_dims[ax]) break;
-        tm[ax] = ((float)(st[ax] > 0 ? v[ax] + 1 : v[ax]) - qa[ax]) / La[ax];
-    }
-    return 1.0f;
+    return halfline_segment_d2(o, d, a, b) <= r2;
 }
 
 template <class SM>
 __device__ __forceinline__ int slot_owner(const SM &sm, int warp, int g) { return warp * 32 + (sm.item[warp][g] >> 3); }
 template <class SM>
 __device__ __forceinline__ int slot_index(const SM &sm, int warp, int g) { return sm.item[warp][g] & 7; }
+
+// Hard shadow against the representative lines of one LoD level (Sec. 5.2,
+// first approach): from one cell size toward the light, walk the level's
+// cells (3D DDA, in cell units) and report 0 at the first cell whose line
+// passes within the scaled radius of the half-line, else 1.
+//
+// The walk's parameter range [tnear, tfar) inside the level's grid is cut
+// into pieces of REP_PIECE cell lengths (the last one open-ended) that are
+// walked independently: piece k starts in the cell holding its first point
+// and stops after the cell whose exit lies beyond its last, so the pieces
+// cover the walk's cells (a cell at a seam may be tested twice) and the
+// visibility is the minimum over the pieces. Each DDA step is decided by
+// the current cell alone, so two walks in the same cell take the same path.
+constexpr float REP_PIECE = 10.0f;
+
+struct RepRay {
+    float q[3], L[3], inv[3];
+    float tnear, tfar;
+};
+
+__device__ __forceinline__ bool rep_ray(const RenderParams &P, Vec Pg, Vec Lt, RepRay &r) {
+    const Vec q = scale(axpy(P.rep_size, Lt, Pg), P.rep_inv);
+    r.q[0] = q.x; r.q[1] = q.y; r.q[2] = q.z;
+    r.L[0] = Lt.x; r.L[1] = Lt.y; r.L[2] = Lt.z;
+    r.tnear = 0.0f;
+    r.tfar = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        r.inv[a] = __frcp_rn(r.L[a]);
+        if (r.L[a] != 0.0f) {
+            const float t1 = -r.q[a] * r.inv[a], t2 = ((float)P.rep_dims[a] - r.q[a]) * r.inv[a];
+            r.tnear = fmaxf(r.tnear, fminf(t1, t2));
+            r.tfar = fminf(r.tfar, fmaxf(t1, t2));
+        } else if (r.q[a] < 0.0f || r.q[a] > (float)P.rep_dims[a]) {
+            return false;
+        }
+    }
+    return r.tnear < r.tfar;
+}
+
+__device__ __forceinline__ int rep_pieces(const RepRay &r) {
+    return (int)fminf(32767.0f, ceilf((r.tfar - r.tnear) * (1.0f / REP_PIECE)));
+}
+
+// Walk piece `piece` of `pieces`: 0 if a line blocks, else 1. (The state
+// arrays are only ever indexed by unrolled constants, so they stay in
+// registers.)
+__device__ __forceinline__ float rep_piece(const RenderParams &P, const RepRay &r, int piece, int pieces, unsigned &ntested) {
+    const float t0 = fmaf(REP_PIECE, (float)piece, r.tnear);
+    const float t1 = piece + 1 < pieces ? fmaf(REP_PIECE, (float)(piece + 1), r.tnear) : INFINITY;
+    int v[3], st[3];
+    float tm[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int vi = (int)floorf(fmaf(t0, r.L[a], r.q[a]));
+        v[a] = min(max(vi, 0), P.rep_dims[a] - 1);
+        st[a] = r.L[a] > 0.0f ? 1 : (r.L[a] < 0.0f ? -1 : 0);
+        tm[a] = st[a] == 0 ? INFINITY : ((float)(st[a] > 0 ? v[a] + 1 : v[a]) - r.q[a]) * r.inv[a];
+    }
+    const unsigned long long *rep = reinterpret_cast<const unsigned long long *>(P.rep);
+    const uint32_t sy = (uint32_t)P.rep_dims[0], sz = sy * (uint32_t)P.rep_dims[1];   // cells < 2^32
+    const uint32_t stride[3] = {1u, sy, sz};
+    uint32_t cell = (uint32_t)v[0] + sy * (uint32_t)v[1] + sz * (uint32_t)v[2];
+    uint64_t w = __ldg(rep + cell);
+    const Vec d = mk(r.L[0], r.L[1], r.L[2]);
+    const int limit = P.rep_dims[0] + P.rep_dims[1] + P.rep_dims[2];
+    for (int it = 0; it < limit; it++) {
+        // the next cell, and its word loaded before this cell is tested
+        const int ax = tm[0] <= tm[1] ? (tm[0] <= tm[2] ? 0 : 2) : (tm[1] <= tm[2] ? 1 : 2);
+        bool more = false;
+        int nv = 0;
+        uint32_t ncell = cell;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (a != ax) continue;
+            nv = v[a] + st[a];
+            more = tm[a] < t1 && nv >= 0 && nv < P.rep_dims[a];
+            ncell = st[a] > 0 ? cell + stride[a] : cell - stride[a];
+        }
+        const uint64_t nw = more ? __ldg(rep + ncell) : 0ull;
+        ntested++;
+        if (w & 1ull) {
+            const uint32_t ps = (uint32_t)(w >> 8), pe = (uint32_t)(w >> 32);
+            const Vec a = face_point(ps & 0xffu, (ps >> 8) & 0xffu, (ps >> 16) & 0xffu, P.invN);
+            const Vec b = face_point(pe & 0xffu, (pe >> 8) & 0xffu, (pe >> 16) & 0xffu, P.invN);
+            const Vec o = mk(r.q[0] - (float)v[0], r.q[1] - (float)v[1], r.q[2] - (float)v[2]);
+            if (rep_blocks(o, d, a, b, P.rep_r2)) return 0.0f;
+        }
+        if (!more) break;
+        cell = ncell;
+        w = nw;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (a != ax) continue;
+            v[a] = nv;
+            tm[a] = ((float)(st[a] > 0 ? nv + 1 : nv) - r.q[a]) * r.inv[a];
+        }
+    }
+    return 1.0f;
+}
+
+// The warp's hits' representative-line shadows, balanced over the lanes:
+// every round, the hits still open (not blocked, pieces left; the first 32)
+// get 32 / (their number) adjacent lanes each (a power of two), which walk
+// the hit's next pieces side by side. Per-hit state lives in the staging
+// arrays, which are dead while a warp lights its hits: sk holds (next piece
+// << 16 | pieces) of hit g at [g / 32][warp * 32 + g % 32], st[0] the round's
+// list of open hits.
+template <class SM>
+__device__ __forceinline__ void rep_shadows(const RenderParams &P, SM &sm, int warp, int lane, int total, Vec Lt, unsigned &nsamp) {
+    auto hit_pos = [&](int g) {
+        const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
+        return mk(sm.slot[F_PX][q][o], sm.slot[F_PY][q][o], sm.slot[F_PZ][q][o]);
+    };
+    for (int g = lane; g < total; g += 32) {
+        RepRay r;
+        const int n = rep_ray(P, hit_pos(g), Lt, r) ? rep_pieces(r) : 0;
+        sm.sk[g >> 5][warp * 32 + (g & 31)] = (uint32_t)n;
+        sm.slot[F_V][slot_index(sm, warp, g)][slot_owner(sm, warp, g)] = 1.0f;
+    }
+    __syncwarp();
+    uint32_t *list = reinterpret_cast<uint32_t *>(&sm.st[0][warp * 32]);
+    for (int round = 0; round < 65536; round++) {
+        int K = 0;
+        for (int g0 = 0; g0 < total && K < 32; g0 += 32) {
+            const int g = g0 + lane;
+            bool open = false;
+            if (g < total) {
+                const uint32_t s = sm.sk[g >> 5][warp * 32 + (g & 31)];
+                open = (s >> 16) < (s & 0xffffu);   // a blocked hit's next piece is set past the end
+            }
+            const unsigned b = __ballot_sync(FULL, open);
+            const int pos = K + __popc(b & ((1u << lane) - 1u));
+            if (open && pos < 32) list[pos] = (uint32_t)g;
+            K += __popc(b);
+        }
+        if (K == 0) break;
+        K = min(K, 32);
+        __syncwarp();
+        int G = 1;
+        while (2 * G * K <= 32) G <<= 1;
+        const int i = lane / G, part = lane % G;
+        float vis = 1.0f;
+        int g = 0;
+        uint32_t s = 0;
+        if (i < K) {
+            g = (int)list[i];
+            s = sm.sk[g >> 5][warp * 32 + (g & 31)];
+            const int piece = (int)(s >> 16) + part, pieces = (int)(s & 0xffffu);
+            RepRay r;
+            if (piece < pieces && rep_ray(P, hit_pos(g), Lt, r)) vis = rep_piece(P, r, piece, pieces, nsamp);
+        }
+        for (int x = G >> 1; x > 0; x >>= 1) vis = fminf(vis, __shfl_xor_sync(FULL, vis, x));
+        __syncwarp();
+        if (i < K && part == 0) {
+            const uint32_t pieces = s & 0xffffu;
+            uint32_t next = (s >> 16) + (uint32_t)G;
+            if (vis == 0.0f) {
+                sm.slot[F_V][slot_index(sm, warp, g)][slot_owner(sm, warp, g)] = 0.0f;
+                next = pieces;
+            }
+            sm.sk[g >> 5][warp * 32 + (g & 31)] = pieces | min(next, pieces) << 16;
+        }
+        __syncwarp();
+    }
+}
+
 
 // Phase B: light the warp's collected hits.
 //  - Shadows: one lane per hit, a march toward the light (Sec. 5.2).
@@ -649,13 +792,14 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
                            unsigned long long js[4], float &jmax) {
     constexpr int MODE = SM::kMode;
     const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
-    if (P.shadows) {
+    if (P.shadows == 1) {
         for (int g = lane; g < total; g += 32) {
             const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
             const Vec Pg = mk(sm.slot[F_PX][q][o], sm.slot[F_PY][q][o], sm.slot[F_PZ][q][o]);
-            sm.slot[F_V][q][o] = P.shadows == 2 ? rep_visibility(P, Pg, Lt)
-                                                : 1.0f - fminf(1.0f, march(P, Pg, Lt, -1.0f, nsamp));
+            sm.slot[F_V][q][o] = 1.0f - fminf(1.0f, march(P, Pg, Lt, -1.0f, nsamp));
         }
+    } else if constexpr (MODE == MODE_REP) {
+        rep_shadows(P, sm, warp, lane, total, Lt, nsamp);
     }
     if constexpr (MODE == MODE_LEARNED || MODE == MODE_JUDGE) {
         // learned AO (Sec. 5.3 surrogate), 16 hits per step: per-hit inputs
@@ -1011,6 +1155,8 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     if ((desc->ao_mode == 2 || judge) && lod && lod->levels < 3)
         return set_err(ctx, LVR_EINVAL, "learned AO needs a LoD of >= 3 levels");
     if (desc->shadows < 0 || desc->shadows > 2) return set_err(ctx, LVR_EINVAL, "bad shadows mode");
+    if (desc->shadows == 2 && (desc->ao_mode == 2 || desc->still))
+        return set_err(ctx, LVR_EINVAL, "shadows 2 has no learned-AO or camera-at-rest variant");
     if (desc->shadows == 2 && !(lod && desc->shadow_level >= 0 && desc->shadow_level < lod->levels &&
                                 lod->rep[desc->shadow_level] && lod->rep_bins == ls->bins))
         return set_err(ctx, LVR_EINVAL, "shadows 2 needs lvr_lod_rep_lines and a shadow_level of the LoD");
@@ -1129,13 +1275,17 @@ static RenderKernel pick_kernel(int mode, int layout) {
     case MODE_JUDGE * 2: return render_kernel<MODE_JUDGE, LAYOUT_AOS8>;
     case MODE_STILL * 2: return render_kernel<MODE_STILL, LAYOUT_AOS8>;
     case MODE_STILL * 2 + 1: return render_kernel<MODE_STILL, LAYOUT_AOS16>;
+    case MODE_REP * 2: return render_kernel<MODE_REP, LAYOUT_AOS8>;
+    case MODE_REP * 2 + 1: return render_kernel<MODE_REP, LAYOUT_AOS16>;
     default: return nullptr;
     }
 }
 
 static int kernel_mode(const RenderParams &P) {
     return P.judge ? MODE_JUDGE
-                   : (P.learned ? MODE_LEARNED : (P.samp_vox ? MODE_SAMPLES : (P.still ? MODE_STILL : MODE_IMAGE)));
+                   : (P.learned ? MODE_LEARNED
+                                : (P.samp_vox ? MODE_SAMPLES
+                                              : (P.still ? MODE_STILL : (P.shadows == 2 ? MODE_REP : MODE_IMAGE))));
 }
 
 // Persistent grid size of a kernel: SMs x resident blocks (cached per variant).
@@ -1350,6 +1500,8 @@ BatchKernel pick_batch_kernel(int mode, int layout) {
     switch (mode * 2 + layout) {
     case MODE_IMAGE * 2: return render_batch_kernel<MODE_IMAGE, LAYOUT_AOS8>;
     case MODE_IMAGE * 2 + 1: return render_batch_kernel<MODE_IMAGE, LAYOUT_AOS16>;
+    case MODE_REP * 2: return render_batch_kernel<MODE_REP, LAYOUT_AOS8>;
+    case MODE_REP * 2 + 1: return render_batch_kernel<MODE_REP, LAYOUT_AOS16>;
     case MODE_LEARNED * 2: return render_batch_kernel<MODE_LEARNED, LAYOUT_AOS8>;
     case MODE_LEARNED * 2 + 1: return render_batch_kernel<MODE_LEARNED, LAYOUT_AOS16>;
     default: return nullptr;
@@ -1374,9 +1526,11 @@ lvr_status batch_build(lvr_ctx *ctx, const lvr_batch_item *items, int n, int til
         if (layout >= 0) d.layout = layout;
         lvr_status st = setup(ctx, it.ls, it.lod, &it.view, &d, it.ao, P[i]);
         if (st != LVR_OK) return st;
-        const int m = P[i].learned ? MODE_LEARNED : MODE_IMAGE;
+        const int m = P[i].learned ? MODE_LEARNED : (P[i].shadows == 2 ? MODE_REP : MODE_IMAGE);
         if (mode >= 0 && (m != mode || d.layout != lay))
-            return set_err(ctx, LVR_EINVAL, "batch items must share the AO kind and the record layout");
+            return set_err(ctx, LVR_EINVAL,
+                           "batch items must share the AO kind, representative-line shadows or not, and the "
+                           "record layout");
         mode = m;
         lay = d.layout;
         P[i].out = (float4 *)it.rgba;

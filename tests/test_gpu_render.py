@@ -388,7 +388,8 @@ def test_rep_line_shadows_invalid(env, c1t):
     bad = [(fresh, lvr.make_desc(0.2, c1t.tf, shadow_level=0)),          # lines not built
            (c1t.glod, lvr.make_desc(0.2, c1t.tf, shadow_level=3)),       # level outside the LoD
            (c1t.glod, lvr.make_desc(0.2, c1t.tf, shadow_level=-1)),
-           (None, lvr.make_desc(0.2, c1t.tf, shadow_level=0))]
+           (None, lvr.make_desc(0.2, c1t.tf, shadow_level=0)),
+           (c1t.glod, lvr.make_desc(0.2, c1t.tf, shadow_level=0, still=True))]   # no camera-at-rest variant
     lvr.lvr_lod_rep_lines(ctx, c1t.glod, c1t.gls)
     for lod, desc in bad:
         with pytest.raises(lvr.LVRError) as ei:
@@ -400,3 +401,22 @@ def test_rep_line_shadows_invalid(env, c1t):
         lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, d, out)
     with pytest.raises(lvr.LVRError):
         lvr.export_rep_lines_numpy(ctx, fresh, 0)
+
+
+def test_rep_line_shadows_tiles_agree(env, c1t):
+    """The lighting phase splits a walk over 1-8 lanes depending on how many
+    hits a warp holds, which changes with the ray tile: the images agree bit
+    for bit."""
+    import torch
+    lvr, O, ctx, dev = env
+    lvr.lvr_lod_rep_lines(ctx, c1t.glod, c1t.gls)
+    cam = synth.orbit_view((32, 32, 32), 160, 96)
+    lv, _, _ = S.views(cam)
+    outs = []
+    for tile in ((8, 4), (32, 1), (4, 8)):
+        out = torch.empty((96, 160, 4), dtype=torch.float32, device=dev)
+        lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, lvr.make_desc(0.2, c1t.tf, ert_alpha=0.99, shadow_level=1,
+                                                                  tile=tile), out)
+        ctx.sync()
+        outs.append(out.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
