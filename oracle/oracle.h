@@ -161,6 +161,16 @@ int orc_render(const orc_voxset *vs, const orc_lod *lod, const orc_view *view,
                const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
                double *rgba, uint8_t *tie, double *margin, uint64_t *counters, int nthreads);
 
+/* Reading K1, the rasterised comparison system: every capsule between two
+ * consecutive vertices of the input polylines (float32 grid coordinates, no
+ * voxel model), one fragment per capsule a pixel's ray enters, sorted by
+ * (entry, capsule index) and blended front to back (S1 shading, no shadows
+ * or AO) until the float32 opacity reaches ert_alpha; opaque: the nearest.
+ * counters[0..1]: fragments, blended fragments. */
+int orc_raster(const float *xyz, const float *attr, const int64_t *offsets, int64_t nc, const orc_grid *g,
+               const orc_view *view, const orc_rdesc *rd, const int32_t *pix, int64_t npix, double *rgba,
+               uint8_t *tie, uint64_t *counters, int nthreads);
+
 /* ---- pieces exposed for pin tests ---- */
 /* Primary ray of pixel (i, j) under the single-precision ray contract (reading R0). */
 void orc_primary_ray(const orc_view *view, int32_t i, int32_t j, float org[3], float dir[3]);

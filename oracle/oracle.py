@@ -74,6 +74,8 @@ def lib():
         L.orc_reps_export.argtypes = [vp, C.c_int, vp]
         L.orc_halfline_segment_distance.argtypes = [vp, vp, vp, vp]
         L.orc_halfline_segment_distance.restype = C.c_double
+        L.orc_raster.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int64, vp, vp, vp, C.c_int]
+        L.orc_raster.restype = C.c_int
         L.orc_shadow_reps_visibility.argtypes = [vp, vp, C.c_float, C.c_int, vp, vp]
         L.orc_shadow_reps_visibility.restype = C.c_double
         L.orc_ao_sphere_field.argtypes = [vp, C.c_int, C.c_double, vp]
@@ -448,3 +450,19 @@ def shadow_reps_visibility(vs: "VoxSet", reps: Reps, radius, level, P, Lt) -> fl
     P = np.ascontiguousarray(P, np.float64)
     Lt = np.ascontiguousarray(Lt, np.float64)
     return lib().orc_shadow_reps_visibility(vs.handle, reps.handle, float(radius), int(level), _p(P), _p(Lt))
+
+
+def raster(xyz, attr, offsets, grid: "Grid", view: "View", rd: "RDesc", pix, nthreads=0):
+    """Reading K1 (rasterised comparison system) for the listed pixels: rgba
+    (n, 4) f64, tie flags (n,) u8, counters [fragments, blended]."""
+    xyz = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+    attr = None if attr is None else np.ascontiguousarray(attr, np.float32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
+    n = len(pix)
+    rgba = np.empty((n, 4), np.float64)
+    tie = np.empty(n, np.uint8)
+    cnt = np.zeros(2, np.uint64)
+    _check(lib().orc_raster(_p(xyz), _p(attr), _p(offsets), len(offsets) - 1, C.byref(grid), C.byref(view),
+                            C.byref(rd), _p(pix), n, _p(rgba), _p(tie), _p(cnt), int(nthreads)))
+    return rgba, tie, cnt

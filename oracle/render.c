@@ -936,3 +936,157 @@ int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
     if (counters) { counters[0] = c0; counters[1] = c1; counters[2] = c2; counters[3] = c3; }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ rasterised comparison system
+ * Reading K1 (the paper's comparison system: tubes built around the input
+ * lines by the rasteriser, per-pixel fragment lists sorted by depth and
+ * blended front to back, Secs. 1 and 5.1). The input polylines are used
+ * directly (no voxel model). Vertex i of a curve maps to grid coordinates
+ * p = fl32(fl32(v - origin) * scale) (the voxeliser's float32 step, without
+ * its fixed-point snap); consecutive vertices (v_i, v_i+1) form one capsule
+ * of radius r (the tube piece closed by spheres at both ends), with the
+ * attribute byte floor(((A_i + A_i+1) 255 + 65535) / 131070) of the two
+ * vertices' 16-bit codes. A pixel's ray leaves one fragment per capsule it
+ * enters (entry parameter > 0, origin outside), with no voxel ownership;
+ * the fragments are sorted by (entry parameter, capsule index) and blended
+ * front to back with S1's shading (no shadows or AO) until the float32
+ * accumulated opacity reaches ert_alpha (> 1: every fragment, as the paper's
+ * lists do); opaque mode keeps the nearest fragment. */
+typedef struct { double a[3], b[3]; uint8_t attr; } rseg;
+
+static int raster_segments(const float *xyz, const float *attr, const int64_t *offsets, int64_t nc,
+                           const orc_grid *g, rseg **out, int64_t *nout) {
+    const int64_t nv = offsets[nc];
+    uint16_t *A = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)(nv > 0 ? nv : 1));
+    if (!A) return ORC_ENOMEM;
+    int st = orc_attr16(attr, nv, g->attr_min, g->attr_max, A);
+    if (st) { free(A); return st; }
+    int64_t n = 0;
+    for (int64_t c = 0; c < nc; c++)
+        if (offsets[c + 1] - offsets[c] > 1) n += offsets[c + 1] - offsets[c] - 1;
+    rseg *S = (rseg *)malloc(sizeof(rseg) * (size_t)(n > 0 ? n : 1));
+    if (!S) { free(A); return ORC_ENOMEM; }
+    int64_t k = 0;
+    for (int64_t c = 0; c < nc; c++)
+        for (int64_t i = offsets[c]; i + 1 < offsets[c + 1]; i++) {
+            rseg *s = &S[k++];
+            for (int a = 0; a < 3; a++) {
+                float d0 = xyz[3 * i + a] - g->origin[a], d1 = xyz[3 * (i + 1) + a] - g->origin[a];
+                float p0 = d0 * g->scale, p1 = d1 * g->scale;
+                s->a[a] = p0;
+                s->b[a] = p1;
+            }
+            s->attr = (uint8_t)(((int64_t)(A[i] + A[i + 1]) * 255 + 65535) / 131070);
+        }
+    free(A);
+    *out = S;
+    *nout = n;
+    return ORC_OK;
+}
+
+static int raster_hit_cmp(const void *x, const void *y) { return hit_cmp(x, y); }
+
+int orc_raster(const float *xyz, const float *attr, const int64_t *offsets, int64_t nc, const orc_grid *g,
+               const orc_view *view, const orc_rdesc *rd, const int32_t *pix, int64_t npix, double *rgba,
+               uint8_t *tie, uint64_t *counters, int nthreads) {
+    if (nc < 0 || !offsets || (!xyz && offsets[nc] > 0)) return ORC_EINVAL;
+    if (view->width < 1 || view->height < 1 || !(rd->radius > 0.0f)) return ORC_EINVAL;
+    rseg *S = NULL;
+    int64_t ns = 0;
+    int st = raster_segments(xyz, attr, offsets, nc, g, &S, &ns);
+    if (st) return st;
+    cam32 cam;
+    cam_setup(view, &cam);
+    double Lt[3];
+    {
+        double ld[3] = {view->light_dir[0], view->light_dir[1], view->light_dir[2]};
+        norm3(ld);
+        for (int a = 0; a < 3; a++) Lt[a] = (double)(float)(-ld[a]);
+    }
+    const double r = rd->radius;
+    uint64_t c0 = 0, c1 = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel reduction(+ : c0, c1)
+#endif
+    {
+        int64_t cap = 64;
+        hit *hs = (hit *)malloc(sizeof(hit) * (size_t)cap);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t p = 0; p < npix; p++) {
+            float o32[3], d32[3];
+            cam_ray(&cam, pix[2 * p], pix[2 * p + 1], o32, d32);
+            double O[3] = {o32[0], o32[1], o32[2]}, D[3] = {d32[0], d32[1], d32[2]};
+            pixstate ps;
+            memset(&ps, 0, sizeof ps);
+            ps.margin = 1e300;
+            int64_t nh = 0;
+            for (int64_t k = 0; k < ns; k++) {
+                double tc;
+                const double dist = line_segment_distance(O, D, S[k].a, S[k].b, &tc);
+                note(&ps, fabs(dist - r) / EPS_G, TIE_GRAZE);
+                entry E;
+                if (!capsule_entry_s(O, D, S[k].a, S[k].b, r, &E)) continue;
+                if (nh == cap) {
+                    cap *= 2;
+                    hs = (hit *)realloc(hs, sizeof(hit) * (size_t)cap);
+                }
+                hs[nh].t = E.t;
+                hs[nh].eps = EPS_T + ERR_Q * E.sens;
+                hs[nh].k = k;
+                hs[nh].e = E;
+                nh++;
+            }
+            qsort(hs, (size_t)nh, sizeof(hit), raster_hit_cmp);
+            /* neighbours in depth order closer than their error bounds may swap,
+             * unless both entered one joint sphere (bit-identical roots) */
+            for (int64_t i = 0; i + 1 < nh; i++) {
+                const entry *x = &hs[i].e, *y = &hs[i + 1].e;
+                if (x->part && y->part && x->c[0] == y->c[0] && x->c[1] == y->c[1] && x->c[2] == y->c[2]) continue;
+                note(&ps, (hs[i + 1].t - hs[i].t) / (hs[i].eps + hs[i + 1].eps), TIE_SORT);
+            }
+            for (int64_t i = 0; i < nh && !ps.done; i++) {
+                const rseg *s = &S[hs[i].k];
+                const double t = hs[i].t;
+                double P[3] = {O[0] + t * D[0], O[1] + t * D[1], O[2] + t * D[2]};
+                double ba[3] = {s->b[0] - s->a[0], s->b[1] - s->a[1], s->b[2] - s->a[2]};
+                double L2 = dot3(ba, ba), h = 0.0;
+                if (L2 > 0.0) {
+                    double pa[3] = {P[0] - s->a[0], P[1] - s->a[1], P[2] - s->a[2]};
+                    h = dot3(pa, ba) / L2;
+                    if (h < 0.0) h = 0.0;
+                    if (h > 1.0) h = 1.0;
+                }
+                double n[3] = {P[0] - (s->a[0] + h * ba[0]), P[1] - (s->a[1] + h * ba[1]), P[2] - (s->a[2] + h * ba[2])};
+                norm3(n);
+                const float *tf = rd->tf + 4 * s->attr;
+                const double kk = rd->ka + rd->kd * fabs(dot3(n, Lt));
+                ps.nhit++;
+                if (rd->opaque) {
+                    for (int c = 0; c < 3; c++) ps.C[c] = tf[c] * kk;
+                    ps.A = 1.0;
+                    ps.done = 1;
+                    break;
+                }
+                const double w = (1.0 - ps.A) * (double)tf[3];
+                for (int c = 0; c < 3; c++) ps.C[c] += w * tf[c] * kk;
+                ps.A += w;
+                float t1 = 1.0f - ps.A32;
+                float t2 = t1 * tf[3];
+                ps.A32 = ps.A32 + t2;
+                if (ps.A32 >= rd->ert_alpha) ps.done = 1;
+            }
+            for (int c = 0; c < 3; c++) rgba[4 * p + c] = ps.C[c] + (1.0 - ps.A) * rd->bg[c];
+            rgba[4 * p + 3] = ps.A;
+            if (tie) tie[p] = (uint8_t)ps.tie;
+            c0 += (uint64_t)nh;
+            c1 += ps.nhit;
+        }
+        free(hs);
+    }
+    free(S);
+    if (counters) { counters[0] = c0; counters[1] = c1; }
+    return ORC_OK;
+}
