@@ -290,6 +290,38 @@ lvr_status lvr_render(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
                       const lvr_view *view, const lvr_render_desc *desc,
                       lvr_ao_model *ao, float *rgba, uint64_t *counters);
 
+/* ------------------------------------------------------------------ rasterised comparison system
+ * The paper's baseline (Secs. 1 and 5.1): tubes around the input polylines
+ * rasterised into per-pixel fragment lists, sorted by depth and blended front
+ * to back; opaque tubes by a depth test. No voxel model is involved.
+ * Vertex i of a curve maps to p_i = fl32(fl32(v - origin) * scale) (the
+ * voxeliser's float32 step without the fixed-point snap; grid->fit must be
+ * 0, res and bins are ignored); each pair of consecutive vertices of a curve
+ * is a capsule of radius desc->radius (the tube piece closed by spheres) with
+ * attribute byte floor(((A_i + A_i+1) 255 + 65535) / 131070) of the two
+ * vertices' 16-bit codes (attr_min / attr_max as for lvr_voxelize). Pixel
+ * (i, j)'s primary ray is lvr_render's; it leaves one fragment per capsule it
+ * enters (entry > 0; an eye inside a capsule sees none of it). Fragments are
+ * sorted by (depth, capsule index), shaded as lvr_render does without shadows
+ * or AO (ka + kd |n . L|) and blended front to back with the transfer
+ * function's opacity until the float32 accumulated opacity reaches
+ * ert_alpha (> 1: every fragment, as fragment lists do); opaque mode shows
+ * the nearest fragment (ties: the lower capsule index). desc->shadows,
+ * ao_mode and still must be 0; tile and layout are ignored.
+ * xyz, attr (or NULL), curve_offsets: host or device, as for lvr_voxelize;
+ * rgba: host or device float32 [h * w * 4] of the crop; stats: NULL or host.
+ * Synchronises with the stream (the fragment count sizes the lists); the
+ * lists live in a grow-only buffer of the context. */
+typedef struct lvr_raster_stats {
+    uint64_t fragments;      /* fragments over the crop */
+    uint64_t max_per_pixel;  /* longest per-pixel list (transparent mode) */
+    uint64_t list_bytes;     /* bytes of the lists: 12 per fragment (0 in opaque mode) */
+} lvr_raster_stats;
+lvr_status lvr_raster(lvr_ctx *ctx, const float *xyz, const float *attr, const int64_t *curve_offsets,
+                      int64_t n_curves, int64_t n_vertices, const lvr_grid_desc *grid, const lvr_view *view,
+                      const lvr_render_desc *desc, float *rgba, lvr_raster_stats *stats);
+
+
 /* ------------------------------------------------------------------ batched rendering
  * Many views, possibly of different line sets, sizes and tile shapes, in one
  * persistent launch (the paper renders one view at a time): the work queue

@@ -986,6 +986,28 @@ static int raster_segments(const float *xyz, const float *attr, const int64_t *o
 
 static int raster_hit_cmp(const void *x, const void *y) { return hit_cmp(x, y); }
 
+/* S1 shading of capsule s entered at depth t: rgb * (ka + kd |n . Lt|) */
+static void raster_color(const rseg *s, const orc_rdesc *rd, const double *O, const double *D, double t,
+                         const double *Lt, double c[3]) {
+    double P[3] = {O[0] + t * D[0], O[1] + t * D[1], O[2] + t * D[2]};
+    double ba[3] = {s->b[0] - s->a[0], s->b[1] - s->a[1], s->b[2] - s->a[2]};
+    double L2 = dot3(ba, ba), h = 0.0;
+    if (L2 > 0.0) {
+        double pa[3] = {P[0] - s->a[0], P[1] - s->a[1], P[2] - s->a[2]};
+        h = dot3(pa, ba) / L2;
+        if (h < 0.0) h = 0.0;
+        if (h > 1.0) h = 1.0;
+    }
+    double n[3] = {P[0] - (s->a[0] + h * ba[0]), P[1] - (s->a[1] + h * ba[1]), P[2] - (s->a[2] + h * ba[2])};
+    norm3(n);
+    const float *tf = rd->tf + 4 * s->attr;
+    const double kk = rd->ka + rd->kd * fabs(dot3(n, Lt));
+    for (int q = 0; q < 3; q++) c[q] = tf[q] * kk;
+}
+
+/* a quarter of the 2e-3 per-channel tolerance the parity tests use */
+static const double SWAP_MIN = 5e-4;
+
 int orc_raster(const float *xyz, const float *attr, const int64_t *offsets, int64_t nc, const orc_grid *g,
                const orc_view *view, const orc_rdesc *rd, const int32_t *pix, int64_t npix, double *rgba,
                uint8_t *tie, uint64_t *counters, int nthreads) {
@@ -1023,10 +1045,12 @@ int orc_raster(const float *xyz, const float *attr, const int64_t *offsets, int6
             memset(&ps, 0, sizeof ps);
             ps.margin = 1e300;
             int64_t nh = 0;
+            double graze_t = 1e300, graze_m = 1e300;   /* nearest grazing approach and its margin */
             for (int64_t k = 0; k < ns; k++) {
                 double tc;
                 const double dist = line_segment_distance(O, D, S[k].a, S[k].b, &tc);
-                note(&ps, fabs(dist - r) / EPS_G, TIE_GRAZE);
+                const double gm = fabs(dist - r) / EPS_G;
+                if (gm < 1.0 && tc < graze_t) { graze_t = tc; graze_m = gm; }
                 entry E;
                 if (!capsule_entry_s(O, D, S[k].a, S[k].b, r, &E)) continue;
                 if (nh == cap) {
@@ -1040,44 +1064,50 @@ int orc_raster(const float *xyz, const float *attr, const int64_t *offsets, int6
                 nh++;
             }
             qsort(hs, (size_t)nh, sizeof(hit), raster_hit_cmp);
-            /* neighbours in depth order closer than their error bounds may swap,
-             * unless both entered one joint sphere (bit-identical roots) */
-            for (int64_t i = 0; i + 1 < nh; i++) {
-                const entry *x = &hs[i].e, *y = &hs[i + 1].e;
-                if (x->part && y->part && x->c[0] == y->c[0] && x->c[1] == y->c[1] && x->c[2] == y->c[2]) continue;
-                note(&ps, (hs[i + 1].t - hs[i].t) / (hs[i].eps + hs[i + 1].eps), TIE_SORT);
-            }
-            for (int64_t i = 0; i < nh && !ps.done; i++) {
-                const rseg *s = &S[hs[i].k];
-                const double t = hs[i].t;
-                double P[3] = {O[0] + t * D[0], O[1] + t * D[1], O[2] + t * D[2]};
-                double ba[3] = {s->b[0] - s->a[0], s->b[1] - s->a[1], s->b[2] - s->a[2]};
-                double L2 = dot3(ba, ba), h = 0.0;
-                if (L2 > 0.0) {
-                    double pa[3] = {P[0] - s->a[0], P[1] - s->a[1], P[2] - s->a[2]};
-                    h = dot3(pa, ba) / L2;
-                    if (h < 0.0) h = 0.0;
-                    if (h > 1.0) h = 1.0;
+            int64_t m = 0;   /* fragments blended */
+            double Tprev = 1.0, cprev[3] = {0.0, 0.0, 0.0};
+            for (int64_t i = 0; i <= nh; i++) {
+                double c[3] = {0.0, 0.0, 0.0};
+                const float *tf = i < nh ? rd->tf + 4 * S[hs[i].k].attr : NULL;
+                if (i < nh) raster_color(&S[hs[i].k], rd, O, D, hs[i].t, Lt, c);
+                /* Only decisions about the blended fragments matter: two
+                 * neighbours in depth order (the second may be the first one
+                 * not blended) closer than their error bounds may swap, unless
+                 * both entered one joint sphere (bit-identical roots); a swap
+                 * moves the pixel by T a_i a_i+1 (c_i - c_i+1), flagged from
+                 * SWAP_MIN on (opaque: c_0 - c_1). */
+                if (i > 0 && i < nh) {
+                    const entry *x = &hs[i - 1].e, *y = &hs[i].e;
+                    const int same = x->part && y->part && x->c[0] == y->c[0] && x->c[1] == y->c[1] &&
+                                     x->c[2] == y->c[2];
+                    const double aa = rd->opaque ? 1.0 : (double)rd->tf[4 * S[hs[i - 1].k].attr + 3] * tf[3];
+                    double dc = 0.0;
+                    for (int q = 0; q < 3; q++) dc = fmax(dc, fabs(c[q] - cprev[q]));
+                    if (!same && Tprev * aa * dc >= SWAP_MIN)
+                        note(&ps, (hs[i].t - hs[i - 1].t) / (hs[i - 1].eps + hs[i].eps), TIE_SORT);
                 }
-                double n[3] = {P[0] - (s->a[0] + h * ba[0]), P[1] - (s->a[1] + h * ba[1]), P[2] - (s->a[2] + h * ba[2])};
-                norm3(n);
-                const float *tf = rd->tf + 4 * s->attr;
-                const double kk = rd->ka + rd->kd * fabs(dot3(n, Lt));
+                if (i == nh || ps.done) break;
+                m++;
                 ps.nhit++;
+                for (int q = 0; q < 3; q++) cprev[q] = c[q];
+                Tprev = 1.0 - ps.A;
                 if (rd->opaque) {
-                    for (int c = 0; c < 3; c++) ps.C[c] = tf[c] * kk;
+                    for (int q = 0; q < 3; q++) ps.C[q] = c[q];
                     ps.A = 1.0;
                     ps.done = 1;
-                    break;
+                    continue;
                 }
                 const double w = (1.0 - ps.A) * (double)tf[3];
-                for (int c = 0; c < 3; c++) ps.C[c] += w * tf[c] * kk;
+                for (int q = 0; q < 3; q++) ps.C[q] += w * c[q];
                 ps.A += w;
                 float t1 = 1.0f - ps.A32;
                 float t2 = t1 * tf[3];
                 ps.A32 = ps.A32 + t2;
                 if (ps.A32 >= rd->ert_alpha) ps.done = 1;
             }
+            /* a capsule grazed in front of the last blended fragment may
+             * appear or vanish */
+            if (graze_m < 1.0 && (m == nh || graze_t <= hs[m - 1].t + 1e-3)) note(&ps, graze_m, TIE_GRAZE);
             for (int c = 0; c < 3; c++) rgba[4 * p + c] = ps.C[c] + (1.0 - ps.A) * rd->bg[c];
             rgba[4 * p + 3] = ps.A;
             if (tie) tie[p] = (uint8_t)ps.tie;

@@ -141,6 +141,8 @@ extern "C" void lvr_destroy(lvr_ctx *ctx) {
     dev_free(ctx, ctx->scratch);
     dev_free(ctx, ctx->stage_in);
     dev_free(ctx, ctx->stage_out);
+    dev_free(ctx, ctx->frag_t);
+    dev_free(ctx, ctx->frag_id);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_u64) cudaFree(ctx->d_u64);

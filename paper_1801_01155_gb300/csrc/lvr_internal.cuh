@@ -36,6 +36,10 @@ struct lvr_ctx {
     void *stage_out = nullptr;
     size_t stage_out_bytes = 0;
     int render_blocks[16] = {};            // persistent render grid per kernel variant (SMs x resident blocks)
+    // rasterised comparison system: grow-only fragment store (depths, capsule ids)
+    double *frag_t = nullptr;
+    uint32_t *frag_id = nullptr;
+    size_t frag_cap = 0;
 };
 
 struct lvr_lineset {
@@ -148,6 +152,15 @@ lvr_status dev_alloc(lvr_ctx *ctx, void **p, size_t bytes);
 void dev_free(lvr_ctx *ctx, void *p);
 // Copy `bytes` from device `src` into host-or-device `dst` (sync if host).
 lvr_status copy_out(lvr_ctx *ctx, void *dst, const void *src, size_t bytes);
+
+// Exclusive scan of n uint32 counts into offset[0..n] (offset[n] = total;
+// more than 2^32 - 1 sets ST_OVERFLOW in *status); tiles: scan_tile_count(n)
+// 64-bit words of scratch.
+int64_t scan_tile_count(int64_t n);
+void scan_counts(cudaStream_t s, const uint32_t *cnt, int64_t n, unsigned long long *tiles, uint32_t *offset,
+                 uint32_t *status);
+// Camera basis of a view (float64, rounded to float32); false if degenerate.
+bool camera_basis(const lvr_view *view, float F[3], float R[3], float U[3], float *th, float *tw, float Lt[3]);
 
 inline unsigned grid1d(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;

@@ -1136,6 +1136,37 @@ static void norm3(double *a) {
 
 // Validates the arguments and fills the launch parameters (all but outputs).
 // `judge`: learned AO for the image plus traced AO at every hit (ao_rays).
+// Camera basis (forward, right, up) and half-extents of the image plane in
+// float64, rounded to float32; Lt = toward the light. False: degenerate.
+bool camera_basis(const lvr_view *view, float F[3], float R[3], float U[3], float *th, float *tw, float Lt[3]) {
+    double f[3], up[3], r[3], u[3];
+    for (int a = 0; a < 3; a++) {
+        f[a] = (double)view->at[a] - (double)view->eye[a];
+        up[a] = view->up[a];
+    }
+    norm3(f);
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    if (!(fabs(r[0]) + fabs(r[1]) + fabs(r[2]) > 0.0)) return false;
+    norm3(r);
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    const double tanh_ = tan((double)view->fovy_deg * M_PI / 360.0);
+    for (int a = 0; a < 3; a++) {
+        F[a] = (float)f[a];
+        R[a] = (float)r[a];
+        U[a] = (float)u[a];
+    }
+    *th = (float)tanh_;
+    *tw = (float)(tanh_ * (double)view->width / (double)view->height);
+    double ld[3] = {view->light_dir[0], view->light_dir[1], view->light_dir[2]};
+    norm3(ld);
+    for (int a = 0; a < 3; a++) Lt[a] = (float)(-ld[a]);
+    return true;
+}
+
 static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
                         const lvr_render_desc *desc, lvr_ao_model *ao, RenderParams &P, bool judge = false) {
     if (!ls || !view || !desc) return set_err(ctx, LVR_EINVAL, "lvr_render: null argument");
@@ -1190,37 +1221,12 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
         P.lod_lo = -0.5f * cell;
         for (int a = 0; a < 3; a++) P.lod_hi[a] = ((float)lod->dims[lod->levels - 1][a] + 0.5f) * cell;
     }
-    // camera basis in float64, rounded to float32
-    double f[3], up[3], r[3], u[3];
-    for (int a = 0; a < 3; a++) {
-        f[a] = (double)view->at[a] - (double)view->eye[a];
-        up[a] = view->up[a];
-    }
-    norm3(f);
-    r[0] = f[1] * up[2] - f[2] * up[1];
-    r[1] = f[2] * up[0] - f[0] * up[2];
-    r[2] = f[0] * up[1] - f[1] * up[0];
-    if (!(fabs(r[0]) + fabs(r[1]) + fabs(r[2]) > 0.0)) return set_err(ctx, LVR_EINVAL, "degenerate camera");
-    norm3(r);
-    u[0] = r[1] * f[2] - r[2] * f[1];
-    u[1] = r[2] * f[0] - r[0] * f[2];
-    u[2] = r[0] * f[1] - r[1] * f[0];
-    const double tanh_ = tan((double)view->fovy_deg * M_PI / 360.0);
-    for (int a = 0; a < 3; a++) {
-        P.F[a] = (float)f[a];
-        P.R[a] = (float)r[a];
-        P.U[a] = (float)u[a];
-        P.eye[a] = view->eye[a];
-    }
-    P.th = (float)tanh_;
-    P.tw = (float)(tanh_ * (double)view->width / (double)view->height);
+    if (!camera_basis(view, P.F, P.R, P.U, &P.th, &P.tw, P.Lt)) return set_err(ctx, LVR_EINVAL, "degenerate camera");
+    for (int a = 0; a < 3; a++) P.eye[a] = view->eye[a];
     P.W = view->width; P.H = view->height; P.x0 = x0; P.y0 = y0; P.cw = cw; P.ch = ch;
     P.tile_w = tw; P.tile_h = th;
     P.tiles_x = (cw + tw - 1) / tw;
     P.ntiles = P.tiles_x * ((ch + th - 1) / th);
-    double ld[3] = {view->light_dir[0], view->light_dir[1], view->light_dir[2]};
-    norm3(ld);
-    for (int a = 0; a < 3; a++) P.Lt[a] = (float)(-ld[a]);
     P.opaque = desc->opaque ? 1 : 0;
     P.ert = desc->ert_alpha;
     P.shadows = desc->shadows;

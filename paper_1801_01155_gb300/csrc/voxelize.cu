@@ -456,6 +456,16 @@ bool valid_bins(int n) { return n >= 2 && n <= 128 && (n & (n - 1)) == 0; }
 
 }  // namespace
 
+int64_t scan_tile_count(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+
+void scan_counts(cudaStream_t s, const uint32_t *cnt, int64_t n, unsigned long long *tiles, uint32_t *offset,
+                 uint32_t *status) {
+    const int64_t ntiles = scan_tile_count(n);
+    scan_reduce_kernel<<<(unsigned)ntiles, SCAN_T, 0, s>>>(cnt, n, tiles);
+    scan_tiles_kernel<<<1, 1024, 0, s>>>(tiles, ntiles, offset + n, status);
+    scan_down_kernel<<<(unsigned)ntiles, SCAN_T, 0, s>>>(cnt, n, tiles, offset);
+}
+
 extern "C" lvr_status lvr_voxelize(lvr_ctx *ctx, const float *xyz, const float *attr,
                                    const int64_t *curve_offsets, int64_t n_curves,
                                    int64_t n_vertices, lvr_grid_desc *g, lvr_lineset **out) {

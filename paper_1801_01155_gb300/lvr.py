@@ -70,6 +70,10 @@ class BatchItem(C.Structure):
                 ("ao", C.c_void_p), ("rgba", C.c_void_p)]
 
 
+class RasterStats(C.Structure):
+    _fields_ = [("fragments", C.c_uint64), ("max_per_pixel", C.c_uint64), ("list_bytes", C.c_uint64)]
+
+
 class Tune(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("layout", C.c_int32), ("ms", C.c_float * 8)]
 
@@ -113,6 +117,8 @@ _SIGS = {
     "lvr_lod_ao_field": ([_vp, _vp, C.c_int, C.c_float], C.c_int),
     "lvr_export_ao_field": ([_vp, _vp, _vp], C.c_int),
     "lvr_lod_rep_lines": ([_vp, _vp, _vp], C.c_int),
+    "lvr_raster": ([_vp, _vp, _vp, _vp, _i64, _i64, C.POINTER(GridDesc), C.POINTER(View), C.POINTER(RenderDesc),
+                    _vp, C.POINTER(RasterStats)], C.c_int),
     "lvr_export_rep_lines": ([_vp, _vp, C.c_int, _vp], C.c_int),
     "lvr_batch_create": ([_vp, C.POINTER(BatchItem), C.c_int, C.POINTER(_vp)], C.c_int),
     "lvr_batch_render": ([_vp, _vp], C.c_int),
@@ -582,3 +588,15 @@ def export_rep_lines_numpy(ctx: Context, lod: Lod, level: int) -> np.ndarray:
     out = np.empty((int(d[0]) * int(d[1]) * int(d[2]), 8), np.uint8)
     _check(ctx.handle, _L.lvr_export_rep_lines(ctx.handle, lod.handle, int(level), _ptr(out)))
     return out
+
+
+# ---------------------------------------------------------------- rasterised comparison system
+def lvr_raster(ctx: Context, xyz, attr, curve_offsets, grid: GridDesc, view: View, desc: RenderDesc, rgba) -> dict:
+    """Per-pixel fragment lists of the input polylines' tubes (opaque: depth
+    test); rgba float32 (h, w, 4) for the crop. Returns the fragment stats."""
+    nv = int(xyz.shape[0]) if xyz is not None else 0
+    nc = int(curve_offsets.shape[0]) - 1
+    st = RasterStats()
+    _check(ctx.handle, _L.lvr_raster(ctx.handle, _ptr(xyz), _ptr(attr), _ptr(curve_offsets), nc, nv, C.byref(grid),
+                                     C.byref(view), C.byref(desc), _ptr(rgba), C.byref(st)))
+    return {"fragments": int(st.fragments), "max_per_pixel": int(st.max_per_pixel), "list_bytes": int(st.list_bytes)}

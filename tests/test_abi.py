@@ -61,7 +61,8 @@ def test_structs_match_header_sizes(lib):
 
 STRUCTS = {"lvr_grid_desc": "GridDesc", "lvr_lineset_info": "LineSetInfo", "lvr_lod_info": "LodInfo",
            "lvr_view": "View", "lvr_render_desc": "RenderDesc", "lvr_ao_train_desc": "AoTrainDesc",
-           "lvr_ao_error": "AoError", "lvr_batch_item": "BatchItem", "lvr_tune": "Tune"}
+           "lvr_ao_error": "AoError", "lvr_batch_item": "BatchItem", "lvr_tune": "Tune",
+           "lvr_raster_stats": "RasterStats"}
 
 
 def test_struct_layouts_match_the_c_compiler(lib, tmp_path):

@@ -1,0 +1,162 @@
+"""CUDA rasterised comparison system (per-pixel fragment lists, depth sort,
+front-to-back blending; opaque depth test) against the oracle's reading K1.
+
+RGBA within 2e-3 per channel outside the pixels the oracle flags (grazed
+silhouettes, fragments closer in depth than their error bounds whose swap
+would show), which are capped; fragment counts equal the oracle's up to the
+flagged decisions. Near a joint, one capsule's side and the next capsule's
+end sphere (tangent surfaces) are entered at depths that differ only to
+second order, so about 0.5 % of an opaque frame's pixels are such ties.
+"""
+import numpy as np
+import pytest
+
+from paper_1801_01155_gb300 import synth
+from tests import _scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from oracle import oracle as O
+    from paper_1801_01155_gb300 import lvr
+    dev = torch.device("cuda:0")
+    ctx = lvr.Context(0, torch.cuda.Stream(dev))
+    return lvr, O, ctx, dev
+
+
+def _raster(env, ls, R, cam, crop, radius, tf, pix=None, **kw):
+    import torch
+    lvr, O, ctx, dev = env
+    g = S.grid_args(ls, R, 32)
+    lv, ov, allpix = S.views(cam, crop)
+    w, h = (crop[2], crop[3]) if crop else (cam["width"], cam["height"])
+    out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+    xyz = torch.from_numpy(ls.xyz).to(dev)
+    attr = torch.from_numpy(ls.attr).to(dev)
+    offs = torch.from_numpy(ls.offsets).to(dev)
+    stats = lvr.lvr_raster(ctx, xyz, attr, offs, lvr.grid_desc(**g), lv, lvr.make_desc(radius, tf, **kw), out)
+    ctx.sync()
+    got = out.cpu().numpy().reshape(-1, 4)
+    okw = {k: v for k, v in kw.items() if k in ("opaque", "ert_alpha")}
+    if pix is None:
+        pix = allpix
+        sel = slice(None)
+    else:
+        x0, y0 = (crop[0], crop[1]) if crop else (0, 0)
+        sel = (pix[:, 1] - y0) * w + (pix[:, 0] - x0)
+    ref, tie, cnt = O.raster(ls.xyz, ls.attr, ls.offsets, O.make_grid(**g), ov, O.make_rdesc(radius, tf, **okw), pix)
+    return got[sel], ref, tie, stats, cnt
+
+
+def test_opaque_depth_test(env):
+    """c1 set (500 x 64 lines, 32^3 grid), r = 0.2, opaque, 128 x 128."""
+    ls = S.streamlines(500, 64, 0)
+    got, ref, tie, stats, cnt = _raster(env, ls, 32, synth.orbit_view((32, 32, 32), 128, 128), None, 0.2,
+                                        synth.tf_ramp(), opaque=True)
+    S.check_image(got, ref, tie, cap=1e-2, what="raster opaque")
+    assert (ref[:, 3] > 0).mean() > 0.3
+    assert abs(stats["fragments"] - int(cnt[0])) <= 2e-3 * cnt[0]
+
+
+@pytest.mark.parametrize("ert", [0.99, 2.0])
+def test_transparent_lists(env, ert):
+    """c1 set, alpha 0.05-0.3, blended until 0.99 and (ert 2) every fragment."""
+    ls = S.streamlines(500, 64, 0)
+    got, ref, tie, stats, cnt = _raster(env, ls, 32, synth.orbit_view((32, 32, 32), 128, 96), None, 0.2,
+                                        synth.tf_ramp(0.05, 0.3), ert_alpha=ert)
+    S.check_image(got, ref, tie, cap=5e-3, what=f"raster transparent ert {ert}")
+    assert abs(stats["fragments"] - int(cnt[0])) <= 2e-3 * cnt[0]
+    assert stats["list_bytes"] == 12 * stats["fragments"] and stats["max_per_pixel"] > 10
+
+
+def test_crop_and_host_output_agree(env):
+    import torch
+    lvr, O, ctx, dev = env
+    ls = S.streamlines(500, 64, 0)
+    g = lvr.grid_desc(**S.grid_args(ls, 32, 32))
+    cam = synth.orbit_view((32, 32, 32), 96, 64)
+    xyz, attr, offs = (torch.from_numpy(a).to(dev) for a in (ls.xyz, ls.attr, ls.offsets))
+    d = lvr.make_desc(0.2, synth.tf_ramp(0.05, 0.3), ert_alpha=0.99)
+    full = torch.empty((64, 96, 4), dtype=torch.float32, device=dev)
+    lvr.lvr_raster(ctx, xyz, attr, offs, g, S.views(cam)[0], d, full)
+    ctx.sync()
+    crop = torch.empty((20, 30, 4), dtype=torch.float32, device=dev)
+    lvr.lvr_raster(ctx, xyz, attr, offs, g, S.views(cam, (40, 30, 30, 20))[0], d, crop)
+    host = np.empty((64, 96, 4), np.float32)
+    lvr.lvr_raster(ctx, ls.xyz, ls.attr, ls.offsets, g, S.views(cam)[0], d, host)   # host inputs and output
+    ctx.sync()
+    f = full.cpu().numpy()
+    assert np.array_equal(f[30:50, 40:70], crop.cpu().numpy())
+    assert np.array_equal(f, host)
+
+
+def test_long_lists_sorted_in_global_memory(env):
+    """700 parallel tubes one behind the other: the centre pixels' lists
+    exceed the shared-memory sort and go through the global-memory path."""
+    import torch
+    lvr, O, ctx, dev = env
+    k = 700
+    z = np.linspace(1.0, 31.0, k)
+    xyz = np.stack([np.stack([np.full(k, 2.0), np.full(k, 16.0), z], 1),
+                    np.stack([np.full(k, 30.0), np.full(k, 16.0), z], 1)], 1).reshape(-1, 3).astype(np.float32)
+    attr = np.repeat(np.linspace(0.0, 1.0, k), 2).astype(np.float32)
+    offs = np.arange(0, 2 * k + 1, 2, dtype=np.int64)
+    g = dict(res=32, bins=32, origin=(0.0, 0.0, 0.0), scale=1.0, attr_min=0.0, attr_max=1.0)
+    cam = dict(eye=(16.0, 16.0, 200.0), at=(16.0, 16.0, 16.0), up=(0.0, 1.0, 0.0), fovy_deg=2.0, width=16,
+               height=16, light_dir=(0.0, -1.0, -1.0))
+    lv, ov, pix = S.views(cam)
+    tf = synth.tf_ramp(0.002, 0.01)
+    out = torch.empty((16, 16, 4), dtype=torch.float32, device=dev)
+    stats = lvr.lvr_raster(ctx, torch.from_numpy(xyz).to(dev), torch.from_numpy(attr).to(dev),
+                           torch.from_numpy(offs).to(dev), lvr.grid_desc(**g), lv,
+                           lvr.make_desc(0.45, tf, ert_alpha=2.0), out)
+    ctx.sync()
+    assert stats["max_per_pixel"] > 512
+    ref, tie, cnt = O.raster(xyz, attr, offs, O.make_grid(**g), ov, O.make_rdesc(0.45, tf, ert_alpha=2.0), pix)
+    S.check_image(out.cpu().numpy().reshape(-1, 4), ref, tie, cap=0.05, what="long lists")
+    assert stats["fragments"] == int(cnt[0])
+
+
+def test_c2_sampled_pixels(env):
+    """Config-2 set (100k x 200 lines, 256^3), r = 0.15, alpha 0.05-0.3, every
+    fragment blended, full 1080p frame as the benchmark runs it; the oracle
+    checks 48 sampled pixels of the centre."""
+    ls = S.streamlines(100_000, 200, 1)
+    rng = np.random.default_rng(5)
+    pix = np.stack([rng.integers(760, 1160, 48), rng.integers(340, 740, 48)], 1).astype(np.int32)
+    got, ref, tie, stats, cnt = _raster(env, ls, 256, synth.orbit_view((256, 256, 256), 1920, 1080), None, 0.15,
+                                        synth.tf_ramp(0.05, 0.3), pix=pix, ert_alpha=2.0)
+    ok = tie == 0
+    assert ok.mean() > 0.8
+    S.check_image(got, ref, tie, cap=0.2, what="c2 raster sampled")
+    assert (ref[:, 3] > 0.5).mean() > 0.5
+
+
+def test_invalid_arguments(env):
+    import torch
+    lvr, O, ctx, dev = env
+    ls = S.streamlines(500, 64, 0)
+    g = lvr.grid_desc(**S.grid_args(ls, 32, 32))
+    cam = synth.orbit_view((32, 32, 32), 16, 16)
+    lv = S.views(cam)[0]
+    out = torch.empty((16, 16, 4), dtype=torch.float32, device=dev)
+    xyz, attr, offs = (torch.from_numpy(a).to(dev) for a in (ls.xyz, ls.attr, ls.offsets))
+    tf = synth.tf_ramp()
+    for d in (lvr.make_desc(0.2, tf, shadows=True), lvr.make_desc(0.2, tf, ao_mode=1), lvr.make_desc(0.0, tf)):
+        with pytest.raises(lvr.LVRError) as ei:
+            lvr.lvr_raster(ctx, xyz, attr, offs, g, lv, d, out)
+        assert ei.value.code == lvr.EINVAL
+    bad = offs.clone()
+    bad[3] = bad[2] - 1
+    with pytest.raises(lvr.LVRError):
+        lvr.lvr_raster(ctx, xyz, attr, bad, g, lv, lvr.make_desc(0.2, tf), out)
+    gf = lvr.grid_desc(**S.grid_args(ls, 32, 32))
+    gf.fit = 1
+    with pytest.raises(lvr.LVRError):
+        lvr.lvr_raster(ctx, xyz, attr, offs, gf, lv, lvr.make_desc(0.2, tf), out)
