@@ -17,7 +17,7 @@
 //   network, in shared memory up to 512 entries, in place in global memory
 //   beyond), finds the termination index with the float32 opacity
 //   recurrence, shades the blended fragments across the lanes and sums them
-//   with a warp prefix product of (1 - alpha);
+//   with a warp prefix product of (1 - alpha) (float32);
 //   opaque: pass 1 takes the 64-bit minimum of the depth per pixel, pass 2
 //   the smallest capsule id among the fragments at that depth, and a thread
 //   per pixel shades the winner.
@@ -59,6 +59,7 @@ struct RasterParams {
     unsigned long long *zbuf;   // opaque: minimum depth bits per pixel
     uint32_t *zid;              // opaque: smallest capsule at that depth
     float4 *out;
+    float4 *dirs;               // per crop pixel: its primary ray direction
     unsigned long long *stats;  // [0] longest list, [1] fragments (opaque)
     uint32_t *status;
     float tf[1024];
@@ -177,6 +178,15 @@ __device__ bool capsule_rect(const RasterParams &P, V3 a, V3 b, int &i0, int &i1
     return true;
 }
 
+__global__ void __launch_bounds__(256)
+rs_rays_kernel(const __grid_constant__ RasterParams P) {
+    const int64_t npix = (int64_t)P.cw * P.ch;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const V3 D = ray_dir(P, (int)(p % P.cw) + P.x0, (int)(p / P.cw) + P.y0);
+        P.dirs[p] = make_float4(D.x, D.y, D.z, 0.0f);
+    }
+}
+
 // Per curve: grid coordinates and 16-bit attribute codes of its vertices,
 // one slot per vertex (the last vertex of a curve starts no capsule).
 __global__ void __launch_bounds__(256)
@@ -241,12 +251,21 @@ rs_frag_kernel(const __grid_constant__ RasterParams P) {
         }
         int i0, i1, j0, j1;
         if (!capsule_rect(P, a, b, i0, i1, j0, j1)) continue;
+        // bounding sphere of the capsule, for a cheap conservative reject
+        const V3 mrel = vsub(v3(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)),
+                             v3(P.eye[0], P.eye[1], P.eye[2]));
+        const V3 hb = vsub(b, a);
+        const float Rb = 0.5f * sqrtf(vdot(hb, hb)) + P.r;
+        const float Rb2 = (Rb * 1.0001f + 1e-3f) * (Rb * 1.0001f + 1e-3f);
         for (int j = j0; j <= j1; j++)
             for (int i = i0; i <= i1; i++) {
-                const V3 D = ray_dir(P, i, j);
+                const int64_t pix = (int64_t)(j - P.y0) * P.cw + (i - P.x0);
+                const float4 Dw = P.dirs[pix];
+                const V3 D = v3(Dw.x, Dw.y, Dw.z);
+                const V3 perp = vaxpy(-vdot(mrel, D), D, mrel);
+                if (vdot(perp, perp) > Rb2) continue;
                 const double t = capsule_depth(P, D, a, b);
                 if (!(t < INFINITY)) continue;
-                const int64_t pix = (int64_t)(j - P.y0) * P.cw + (i - P.x0);
                 if constexpr (PASS == PASS_COUNT) {
                     atomicAdd(P.count + pix, 1u);
                 } else if constexpr (PASS == PASS_WRITE) {
@@ -288,8 +307,11 @@ __device__ __forceinline__ float4 shade(const RasterParams &P, const float4 *tf,
     return make_float4(c.x * kk, c.y * kk, c.z * kk, c.w);
 }
 
+// depths are positive: their bit patterns order as unsigned integers
 __device__ __forceinline__ bool frag_less(double ta, uint32_t ia, double tb, uint32_t ib) {
-    return ta < tb || (ta == tb && ia < ib);
+    const unsigned long long ka = (unsigned long long)__double_as_longlong(ta),
+                             kb = (unsigned long long)__double_as_longlong(tb);
+    return ka < kb || (ka == kb && ia < ib);
 }
 
 // Ascending-only bitonic network over n entries (entries at or past n act as
@@ -362,22 +384,22 @@ rs_resolve_kernel(const __grid_constant__ RasterParams P) {
         }
         m = __shfl_sync(FULLW, m, 0);
         // blend fragments 0 .. m-1: weight = alpha x prod of (1 - alpha) before it
-        const int px = (int)(p % P.cw) + P.x0, py = (int)(p / P.cw) + P.y0;
-        const V3 D = ray_dir(P, px, py);
-        double carry = 1.0, C0 = 0.0, C1 = 0.0, C2 = 0.0, Asum = 0.0;
+        const float4 Dw = P.dirs[p];
+        const V3 D = v3(Dw.x, Dw.y, Dw.z);
+        float carry = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Asum = 0.0f;
         for (int k0 = 0; k0 < m; k0 += 32) {
             const int k = k0 + lane;
             float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (k < m) c = shade(P, tf, D, t[k], id[k]);
-            double x = 1.0 - (double)c.w;     // inclusive prefix product of (1 - alpha)
+            float x = 1.0f - c.w;              // inclusive prefix product of (1 - alpha)
             for (int o = 1; o < 32; o <<= 1) {
-                const double y = __shfl_up_sync(FULLW, x, o);
+                const float y = __shfl_up_sync(FULLW, x, o);
                 if (lane >= o) x *= y;
             }
-            double before = __shfl_up_sync(FULLW, x, 1);
-            if (lane == 0) before = 1.0;
-            const double w = k < m ? carry * before * (double)c.w : 0.0;
-            C0 += w * c.x; C1 += w * c.y; C2 += w * c.z; Asum += w;
+            float before = __shfl_up_sync(FULLW, x, 1);
+            if (lane == 0) before = 1.0f;
+            const float w = k < m ? carry * before * c.w : 0.0f;
+            C0 = fmaf(w, c.x, C0); C1 = fmaf(w, c.y, C1); C2 = fmaf(w, c.z, C2); Asum += w;
             carry *= __shfl_sync(FULLW, x, 31);
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -387,9 +409,8 @@ rs_resolve_kernel(const __grid_constant__ RasterParams P) {
             Asum += __shfl_xor_sync(FULLW, Asum, o);
         }
         if (lane == 0) {
-            const double rest = 1.0 - Asum;
-            P.out[p] = make_float4((float)(C0 + rest * P.bg[0]), (float)(C1 + rest * P.bg[1]),
-                                   (float)(C2 + rest * P.bg[2]), (float)Asum);
+            const float rest = 1.0f - Asum;
+            P.out[p] = make_float4(fmaf(rest, P.bg[0], C0), fmaf(rest, P.bg[1], C1), fmaf(rest, P.bg[2], C2), Asum);
         }
         __syncwarp();
     }
@@ -411,8 +432,8 @@ rs_opaque_kernel(const __grid_constant__ RasterParams P) {
             P.out[p] = make_float4(P.bg[0], P.bg[1], P.bg[2], 0.0f);
             continue;
         }
-        const int px = (int)(p % P.cw) + P.x0, py = (int)(p / P.cw) + P.y0;
-        const float4 c = shade(P, tf, ray_dir(P, px, py), __longlong_as_double((long long)P.zbuf[p]), k);
+        const float4 Dw = P.dirs[p];
+        const float4 c = shade(P, tf, v3(Dw.x, Dw.y, Dw.z), __longlong_as_double((long long)P.zbuf[p]), k);
         P.out[p] = make_float4(c.x, c.y, c.z, 1.0f);
     }
 }
@@ -475,8 +496,10 @@ extern "C" lvr_status lvr_raster(lvr_ctx *ctx, const float *xyz, const float *at
     const bool host_out = !is_device_ptr(rgba);
     const size_t b_slot = al((size_t)nslot * 16), b_cnt = al((size_t)npix * 4), b_off = al((size_t)(npix + 1) * 4),
                  b_tiles = al((size_t)ntiles * 8), b_z = al((size_t)npix * 8), b_zid = al((size_t)npix * 4),
+                 b_dir = al((size_t)npix * 16),
                  b_out = host_out ? al((size_t)npix * 16) : 0;
-    if ((st = ensure_scratch(ctx, 2 * b_slot + b_cnt + b_off + b_tiles + b_z + b_zid + b_out)) != LVR_OK) return st;
+    if ((st = ensure_scratch(ctx, 2 * b_slot + b_cnt + b_off + b_tiles + b_z + b_zid + b_dir + b_out)) != LVR_OK)
+        return st;
     char *sp = (char *)ctx->scratch;
     float4 *sa = (float4 *)sp; sp += b_slot;
     float4 *sb = (float4 *)sp; sp += b_slot;
@@ -485,9 +508,10 @@ extern "C" lvr_status lvr_raster(lvr_ctx *ctx, const float *xyz, const float *at
     unsigned long long *tiles = (unsigned long long *)sp; sp += b_tiles;
     unsigned long long *zbuf = (unsigned long long *)sp; sp += b_z;
     uint32_t *zid = (uint32_t *)sp; sp += b_zid;
+    float4 *dirs = (float4 *)sp; sp += b_dir;
     float4 *out = host_out ? (float4 *)sp : (float4 *)rgba;
     P.sa = sa; P.sb = sb; P.nslot = n_vertices;
-    P.count = count; P.offset = offset; P.zbuf = zbuf; P.zid = zid; P.out = out;
+    P.count = count; P.offset = offset; P.zbuf = zbuf; P.zid = zid; P.out = out; P.dirs = dirs;
     P.stats = ctx->d_u64;
     P.status = ctx->d_status;
 
@@ -499,6 +523,7 @@ extern "C" lvr_status lvr_raster(lvr_ctx *ctx, const float *xyz, const float *at
         (const float *)dx, (da && g->attr_max > g->attr_min) ? (const float *)da : nullptr, (const int64_t *)dof,
         n_curves, n_vertices, g->origin[0], g->origin[1], g->origin[2], g->scale, g->attr_min, aspan, sa, sb,
         ctx->d_status);
+    rs_rays_kernel<<<grid1d(npix, 256), 256, 0, s>>>(P);
     LVR_CUDA(ctx, cudaGetLastError());
     const unsigned gslot = grid1d(n_vertices, 256);
     uint32_t *h32 = (uint32_t *)ctx->h_pinned;
