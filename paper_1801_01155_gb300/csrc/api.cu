@@ -141,6 +141,7 @@ extern "C" void lvr_destroy(lvr_ctx *ctx) {
     dev_free(ctx, ctx->scratch);
     dev_free(ctx, ctx->stage_in);
     dev_free(ctx, ctx->stage_out);
+    dev_free(ctx, ctx->vox_pair);
     dev_free(ctx, ctx->frag_t);
     dev_free(ctx, ctx->frag_id);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);

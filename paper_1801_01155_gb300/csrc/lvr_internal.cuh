@@ -36,6 +36,9 @@ struct lvr_ctx {
     void *stage_out = nullptr;
     size_t stage_out_bytes = 0;
     int render_blocks[16] = {};            // persistent render grid per kernel variant (SMs x resident blocks)
+    // voxeliser: grow-only scatter target of (record, key) pairs
+    void *vox_pair = nullptr;
+    size_t vox_pair_bytes = 0;
     // rasterised comparison system: grow-only fragment store (depths, capsule ids)
     double *frag_t = nullptr;
     uint32_t *frag_id = nullptr;

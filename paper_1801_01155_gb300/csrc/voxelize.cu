@@ -98,11 +98,14 @@ __device__ __forceinline__ uint32_t face_bin(int64_t X0b, int64_t Db, int64_t vb
 }
 
 // One thread per curve. COUNT: per-voxel segment counts + total stored.
-// SCATTER: write records into their voxel's range at an atomic cursor.
+// SCATTER: write records into their voxel's range at an atomic cursor: as
+// one 16-byte (record, key) pair when `pair` is given (one partial sector
+// per scattered segment instead of two; the sort then writes the arrays),
+// else into rec / key directly.
 template <bool SCATTER>
 __global__ void __launch_bounds__(256)
 vox_curves_kernel(VoxParams P, uint32_t *cnt, const uint32_t *__restrict__ offset,
-                  uint64_t *__restrict__ rec, uint64_t *__restrict__ key,
+                  uint64_t *__restrict__ rec, uint64_t *__restrict__ key, ulonglong2 *__restrict__ pair,
                   unsigned long long *total) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= P.nc) return;
@@ -176,8 +179,14 @@ vox_curves_kernel(VoxParams P, uint32_t *cnt, const uint32_t *__restrict__ offse
                     if (SCATTER) {
                         const uint32_t at = offset[vox] + atomicAdd(cnt + vox, 1u);
                         const uint32_t attr8 = (uint32_t)(((pA + hA) * 255 + 65535) / 131070);
-                        rec[at] = rec_pack(pf, pu, pv, hf, hu, hv, attr8, prev_stored ? 1u : 0u, (uint32_t)c);
-                        key[at] = ((uint64_t)c << 32) | k;
+                        const uint64_t r = rec_pack(pf, pu, pv, hf, hu, hv, attr8, prev_stored ? 1u : 0u, (uint32_t)c);
+                        const uint64_t kk = ((uint64_t)c << 32) | k;
+                        if (pair) {
+                            pair[at] = make_ulonglong2(r, kk);
+                        } else {
+                            rec[at] = r;
+                            key[at] = kk;
+                        }
                     } else {
                         atomicAdd(cnt + vox, 1u);
                     }
@@ -362,20 +371,30 @@ scan_down_kernel(const uint32_t *__restrict__ cnt, int64_t n,
 }
 
 // ------------------------------------------------------------------ canonical per-voxel order
+// With `pair`, the scattered (record, key) pairs are read from there and
+// every list is written to rec / key; without, lists are sorted in place.
 __global__ void __launch_bounds__(256)
 sort_small_kernel(const uint32_t *__restrict__ offset, int64_t nvox, uint64_t *rec, uint64_t *key,
-                  uint32_t *long_list, uint32_t *long_count) {
+                  const ulonglong2 *__restrict__ pair, uint32_t *long_list, uint32_t *long_count) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nvox) return;
     const uint32_t beg = offset[v], n = offset[v + 1] - beg;
-    if (n <= 1) return;
+    if (n == 0 || (n == 1 && !pair)) return;
     if (n > SMALL_LIST) {
         long_list[atomicAdd(long_count, 1u)] = (uint32_t)v;
         return;
     }
     uint64_t k[SMALL_LIST], r[SMALL_LIST];
     for (uint32_t i = 0; i < n; i++) {
-        uint64_t kk = key[beg + i], rr = rec[beg + i];
+        uint64_t kk, rr;
+        if (pair) {
+            const ulonglong2 q = pair[beg + i];
+            rr = q.x;
+            kk = q.y;
+        } else {
+            kk = key[beg + i];
+            rr = rec[beg + i];
+        }
         int j = (int)i - 1;
         while (j >= 0 && k[j] > kk) {
             k[j + 1] = k[j];
@@ -418,7 +437,8 @@ __device__ void bitonic_block(uint32_t n, GetK getk, Swap swp) {
 
 __global__ void __launch_bounds__(256)
 sort_long_kernel(const uint32_t *__restrict__ offset, uint64_t *rec, uint64_t *key,
-                 const uint32_t *__restrict__ long_list, const uint32_t *__restrict__ long_count) {
+                 const ulonglong2 *__restrict__ pair, const uint32_t *__restrict__ long_list,
+                 const uint32_t *__restrict__ long_count) {
     extern __shared__ uint64_t sm[];
     uint64_t *sk = sm, *sr = sm + SMEM_LIST;
     const uint32_t nl = *long_count;
@@ -426,10 +446,24 @@ sort_long_kernel(const uint32_t *__restrict__ offset, uint64_t *rec, uint64_t *k
         const uint32_t v = long_list[li];
         const uint32_t beg = offset[v], n = offset[v + 1] - beg;
         uint64_t *gk = key + beg, *gr = rec + beg;
+        if (pair && n > SMEM_LIST) {   // sorted in place in the final arrays
+            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                const ulonglong2 q = pair[beg + i];
+                gr[i] = q.x;
+                gk[i] = q.y;
+            }
+            __syncthreads();
+        }
         if (n <= SMEM_LIST) {
             for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-                sk[i] = gk[i];
-                sr[i] = gr[i];
+                if (pair) {
+                    const ulonglong2 q = pair[beg + i];
+                    sr[i] = q.x;
+                    sk[i] = q.y;
+                } else {
+                    sk[i] = gk[i];
+                    sr[i] = gr[i];
+                }
             }
             __syncthreads();
             bitonic_block(n, [&](uint32_t i) { return sk[i]; },
@@ -572,7 +606,7 @@ extern "C" lvr_status lvr_voxelize(lvr_ctx *ctx, const float *xyz, const float *
     LVR_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s));
     LVR_CUDA(ctx, cudaMemsetAsync(total, 0, 8, s));
     if (n_curves > 0) {
-        vox_curves_kernel<false><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, total);
+        vox_curves_kernel<false><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, nullptr, total);
         LVR_CUDA(ctx, cudaGetLastError());
     }
     LVR_CUDA(ctx, cudaMemcpyAsync(h32, ctx->d_status, 4, cudaMemcpyDeviceToHost, s));
@@ -607,11 +641,25 @@ extern "C" lvr_status lvr_voxelize(lvr_ctx *ctx, const float *xyz, const float *
     scan_down_kernel<<<(unsigned)ntiles, SCAN_T, 0, s>>>(cnt, nvox, tiles, ls->offset);
     LVR_CUDA(ctx, cudaGetLastError());
     if (nseg > 0) {
+        if ((size_t)nseg * 16 > ctx->vox_pair_bytes) {   // grow-only scatter target
+            dev_free(ctx, ctx->vox_pair);
+            ctx->vox_pair = nullptr;
+            ctx->vox_pair_bytes = 0;
+            const size_t b = (size_t)nseg * 16 + (size_t)nseg * 2 + 4096;
+            if ((st = dev_alloc(ctx, &ctx->vox_pair, b)) != LVR_OK) {
+                lvr_free_lineset(ls);
+                return st;
+            }
+            ctx->vox_pair_bytes = b;
+        }
+        ulonglong2 *pair = (ulonglong2 *)ctx->vox_pair;
         LVR_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s));
-        vox_curves_kernel<true><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, ls->offset, ls->rec, ls->key, total);
+        vox_curves_kernel<true><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, ls->offset, ls->rec, ls->key, pair,
+                                                                      total);
         LVR_CUDA(ctx, cudaMemsetAsync(long_count, 0, 4, s));
-        sort_small_kernel<<<grid1d(nvox, 256), 256, 0, s>>>(ls->offset, nvox, ls->rec, ls->key, long_list, long_count);
-        sort_long_kernel<<<304, 256, 2 * SMEM_LIST * sizeof(uint64_t), s>>>(ls->offset, ls->rec, ls->key,
+        sort_small_kernel<<<grid1d(nvox, 256), 256, 0, s>>>(ls->offset, nvox, ls->rec, ls->key, pair, long_list,
+                                                            long_count);
+        sort_long_kernel<<<304, 256, 2 * SMEM_LIST * sizeof(uint64_t), s>>>(ls->offset, ls->rec, ls->key, pair,
                                                                          long_list, long_count);
         LVR_CUDA(ctx, cudaGetLastError());
     }
@@ -711,7 +759,7 @@ extern "C" lvr_status lvr_voxelize_static(const float *xyz, const float *attr, c
     if (cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s) != cudaSuccess ||
         cudaMemsetAsync(total, 0, 16, s) != cudaSuccess)
         return LVR_ECUDA;
-    if (n_curves > 0) vox_curves_kernel<false><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, total);
+    if (n_curves > 0) vox_curves_kernel<false><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, nullptr, total);
     if (cudaGetLastError() != cudaSuccess) return LVR_ECUDA;
     unsigned long long h_total = 0;
     uint32_t h_status = 0;
@@ -733,10 +781,12 @@ extern "C" lvr_status lvr_voxelize_static(const float *xyz, const float *attr, c
         if (cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s) != cudaSuccess ||
             cudaMemsetAsync(long_count, 0, 4, s) != cudaSuccess)
             return LVR_ECUDA;
-        vox_curves_kernel<true><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, offset, records, keys, total);
-        sort_small_kernel<<<grid1d(nvox, 256), 256, 0, s>>>(offset, nvox, records, keys, long_list, long_count);
-        sort_long_kernel<<<304, 256, 2 * SMEM_LIST * sizeof(uint64_t), s>>>(offset, records, keys, long_list,
-                                                                           long_count);
+        vox_curves_kernel<true><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, offset, records, keys, nullptr,
+                                                                      total);
+        sort_small_kernel<<<grid1d(nvox, 256), 256, 0, s>>>(offset, nvox, records, keys, nullptr, long_list,
+                                                            long_count);
+        sort_long_kernel<<<304, 256, 2 * SMEM_LIST * sizeof(uint64_t), s>>>(offset, records, keys, nullptr,
+                                                                           long_list, long_count);
     }
     if (cudaGetLastError() != cudaSuccess) return LVR_ECUDA;
     return LVR_OK;
