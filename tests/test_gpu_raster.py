@@ -160,3 +160,35 @@ def test_invalid_arguments(env):
     gf.fit = 1
     with pytest.raises(lvr.LVRError):
         lvr.lvr_raster(ctx, xyz, attr, offs, gf, lv, lvr.make_desc(0.2, tf), out)
+
+
+def test_degenerate_inputs(env):
+    """A curve of one vertex (no capsule), an empty curve, and a repeated
+    vertex (a zero-length capsule: a sphere) against the oracle; no vertices
+    at all gives the background."""
+    import torch
+    lvr, O, ctx, dev = env
+    xyz = np.array([[5.0, 5.0, 5.0],                                  # curve 0: one vertex
+                    [8.0, 8.0, 8.0], [8.0, 8.0, 8.0], [11.0, 9.0, 8.0],  # curve 2: repeated vertex
+                    [4.0, 11.0, 6.0], [12.0, 11.0, 10.0]], np.float32)
+    offs = np.array([0, 1, 1, 4, 6], np.int64)                         # curve 1 empty
+    attr = np.linspace(0.0, 1.0, len(xyz)).astype(np.float32)
+    g = dict(res=16, bins=32, origin=(0.0, 0.0, 0.0), scale=1.0, attr_min=0.0, attr_max=1.0)
+    cam = synth.orbit_view((16, 16, 16), 64, 48)
+    lv, ov, pix = S.views(cam)
+    for kw in (dict(opaque=True), dict(ert_alpha=0.99)):
+        tf = synth.tf_ramp() if kw.get("opaque") else synth.tf_ramp(0.2, 0.6)
+        out = torch.empty((48, 64, 4), dtype=torch.float32, device=dev)
+        stats = lvr.lvr_raster(ctx, torch.from_numpy(xyz).to(dev), torch.from_numpy(attr).to(dev),
+                               torch.from_numpy(offs).to(dev), lvr.grid_desc(**g), lv, lvr.make_desc(0.6, tf, **kw), out)
+        ctx.sync()
+        ref, tie, cnt = O.raster(xyz, attr, offs, O.make_grid(**g), ov, O.make_rdesc(0.6, tf, **kw), pix)
+        S.check_image(out.cpu().numpy().reshape(-1, 4), ref, tie, cap=0.02, what=f"degenerate {kw}")
+        assert stats["fragments"] == int(cnt[0]) > 0
+    out = torch.empty((48, 64, 4), dtype=torch.float32, device=dev)
+    empty = torch.zeros((0, 3), dtype=torch.float32, device=dev)
+    stats = lvr.lvr_raster(ctx, empty, None, torch.tensor([0, 0], dtype=torch.int64, device=dev), lvr.grid_desc(**g),
+                           lv, lvr.make_desc(0.6, synth.tf_ramp(0.2, 0.6)), out)
+    ctx.sync()
+    o = out.cpu().numpy()
+    assert stats["fragments"] == 0 and np.all(o[..., 3] == 0.0) and np.all(o[..., :3] == 1.0)

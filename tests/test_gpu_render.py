@@ -420,3 +420,22 @@ def test_rep_line_shadows_tiles_agree(env, c1t):
         ctx.sync()
         outs.append(out.cpu().numpy())
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_rep_lines_of_an_empty_line_set(env):
+    """Curves entirely outside the grid: no segments, no representative
+    lines, and shadows 2 leave the (empty) frame unshadowed."""
+    import torch
+    lvr, O, ctx, dev = env
+    xyz = torch.tensor([[40.0, 40.0, 40.0], [41.0, 40.5, 40.0]], dtype=torch.float32, device=dev)
+    offs = torch.tensor([0, 2], dtype=torch.int64, device=dev)
+    ls = lvr.lvr_voxelize(ctx, xyz, None, offs, lvr.grid_desc(res=16, bins=32, scale=1.0))
+    lod = lvr.lvr_build_lod(ctx, ls, 2, synth.sigma_lut(synth.tf_ramp()))
+    lvr.lvr_lod_rep_lines(ctx, lod, ls)
+    for level in (0, 1):
+        assert not lvr.export_rep_lines_numpy(ctx, lod, level).any()
+    out = torch.empty((16, 16, 4), dtype=torch.float32, device=dev)
+    lvr.lvr_render(ctx, ls, lod, S.views(synth.orbit_view((16, 16, 16), 16, 16))[0],
+                   lvr.make_desc(0.2, synth.tf_ramp(), shadow_level=1), out)
+    ctx.sync()
+    assert np.all(out.cpu().numpy()[..., 3] == 0.0)
