@@ -5,10 +5,11 @@
 // per-voxel segments to an append buffer tagged with voxel ids, the buffer
 // is sorted by voxel id, and an exclusive prefix sum gives each voxel's
 // start index (Sec. 3.3). Here the same store is built without a global
-// sort: one thread per curve counts its segments per voxel (atomics), an
-// exclusive scan turns the counts into the offset table, a second pass
-// scatters the packed records to their voxel's range, and a short per-voxel
-// sort by (curve, ordinal) makes every list's order canonical.
+// sort: one warp per curve (its edges on the lanes) counts its segments per
+// voxel (atomics), an exclusive scan turns the counts into the offset table,
+// a second pass scatters the packed records to their voxel's range, and a
+// short per-voxel sort by (curve, ordinal) makes every list's order
+// canonical.
 //
 // Every decision is exact integer arithmetic on the fixed-point vertices:
 // plane crossings are ordered by their rational edge parameter t = n / d
@@ -97,125 +98,209 @@ __device__ __forceinline__ uint32_t face_bin(int64_t X0b, int64_t Db, int64_t vb
     return (uint32_t)(b > N - 1 ? N - 1 : b);
 }
 
-// One thread per curve. COUNT: per-voxel segment counts + total stored.
-// SCATTER: write records into their voxel's range at an atomic cursor: as
-// one 16-byte (record, key) pair when `pair` is given (one partial sector
-// per scattered segment instead of two; the sort then writes the arrays),
-// else into rec / key directly.
+// One warp per curve, its edges spread over the lanes 32 at a time. Each
+// lane takes one edge (v_e, v_e+1): how many planes it crosses and its last
+// crossing (face point, attribute, the voxel before it) follow in closed
+// form; a warp scan numbers the crossings along the curve, each lane learns
+// the crossing before its first one from the nearest lower lane with one
+// (or from the previous window), and then walks its edge's crossings in the
+// sequential order (earliest first, ties x, y, z), emitting the segment
+// that ends at each. The voxel at the start of an edge is floor(v_e) on every
+// axis (the sequential walk's state there), so the result is the same
+// segment sequence, ordinals and flags as one thread walking the curve.
+// COUNT: per-voxel segment counts and the total stored. SCATTER: each
+// segment goes into its voxel's range at an atomic cursor, as one 16-byte
+// (record, key) pair when `pair` is given (one partial sector per scattered
+// segment instead of two; the sort then writes the arrays), else into rec /
+// key directly.
 template <bool SCATTER>
 __global__ void __launch_bounds__(256)
-vox_curves_kernel(VoxParams P, uint32_t *cnt, const uint32_t *__restrict__ offset,
-                  uint64_t *__restrict__ rec, uint64_t *__restrict__ key, ulonglong2 *__restrict__ pair,
-                  unsigned long long *total) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= P.nc) return;
-    const int64_t v0 = P.offs[c], v1 = P.offs[c + 1];
-    if (!SCATTER) {
-        bool bad = v0 < 0 || v1 < v0 || v1 > P.nv;
-        if (c == 0 && v0 != 0) bad = true;
-        if (c == P.nc - 1 && v1 != P.nv) bad = true;
-        if (bad) {
-            atomicOr(P.status, ST_BAD_OFFSETS);
-            return;
-        }
-    }
+vox_warp_kernel(VoxParams P, uint32_t *cnt, const uint32_t *__restrict__ offset, uint64_t *__restrict__ rec,
+                uint64_t *__restrict__ key, ulonglong2 *__restrict__ pair, unsigned long long *total) {
+    const unsigned FULLM = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int N = P.N;
-    int64_t X0[3], A0;
-    bool ok = true;
-    if (v1 > v0) ok = load_vertex(P, v0, X0, A0);
-    if (v1 - v0 < 2) {
-        if (!ok) atomicOr(P.status, ST_BAD_VERTEX);
-        return;
-    }
-    int64_t cur[3] = {X0[0] >> FXS, X0[1] >> FXS, X0[2] >> FXS};
-    bool have_prev = false, prev_stored = false;
-    uint32_t pf = 0, pu = 0, pv = 0;
-    int64_t pA = 0;
-    uint32_t k = 0, nstored = 0;
-    for (int64_t e = v0; e + 1 < v1; e++) {
-        int64_t X1[3], A1;
-        ok &= load_vertex(P, e + 1, X1, A1);
-        if (!ok) break;
-        int64_t D[3], den[3], nextp[3], lastp[3];
-        bool act[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            D[a] = X1[a] - X0[a];
-            const int64_t f0 = X0[a] >> FXS, f1 = X1[a] >> FXS;
-            if (D[a] > 0) {
-                nextp[a] = f0 + 1; lastp[a] = f1; den[a] = D[a]; act[a] = nextp[a] <= lastp[a];
-            } else if (D[a] < 0) {
-                nextp[a] = f0; lastp[a] = f1 + 1; den[a] = -D[a]; act[a] = nextp[a] >= lastp[a];
-            } else {
-                nextp[a] = lastp[a] = 0; den[a] = 1; act[a] = false;
+    unsigned long long nstored_all = 0;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < P.nc; c += nwarps) {
+        const int64_t v0 = P.offs[c], v1 = P.offs[c + 1];
+        if (!SCATTER) {
+            bool bad = v0 < 0 || v1 < v0 || v1 > P.nv;
+            if (c == 0 && v0 != 0) bad = true;
+            if (c == P.nc - 1 && v1 != P.nv) bad = true;
+            if (bad) {
+                if (lane == 0) atomicOr(P.status, ST_BAD_OFFSETS);
+                continue;
             }
         }
-        for (;;) {
-            // earliest crossing among the axes; ties keep the lower axis (x, y, z)
-            int ax = -1;
-            int64_t bn = 0, bd = 1;
+        if (v1 - v0 < 2) {
+            if (!SCATTER && v1 - v0 == 1 && lane == 0) {
+                int64_t X[3], A;
+                if (!load_vertex(P, v0, X, A)) atomicOr(P.status, ST_BAD_VERTEX);
+            }
+            continue;
+        }
+        // carried along the curve: crossings so far, the last one as the next segment's entry point
+        int64_t ncross = 0;
+        uint32_t cf = 0, cu = 0, cv = 0;
+        int64_t cA = 0;
+        bool cstored = false;          // the segment ending at the last crossing was stored
+        bool bad_vertex = false;
+        for (int64_t base = v0; base + 1 < v1; base += 32) {
+            const int64_t e = base + lane;
+            const bool has_edge = e + 1 < v1;
+            int64_t X0[3] = {0, 0, 0}, X1[3] = {0, 0, 0}, A0 = 0, A1 = 0;
+            if (has_edge) {
+                bad_vertex |= !load_vertex(P, e, X0, A0);
+                bad_vertex |= !load_vertex(P, e + 1, X1, A1);
+            }
+            int64_t D[3], den[3], nextp[3], lastp[3];
+            bool act[3];
+            int m = 0;
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                if (!act[a]) continue;
-                const int64_t n = D[a] > 0 ? nextp[a] * FX - X0[a] : X0[a] - nextp[a] * FX;
-                if (ax < 0 || n * bd < bn * den[a]) { ax = a; bn = n; bd = den[a]; }
-            }
-            if (ax < 0) break;
-            const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
-            const bool pos = D[ax] > 0;
-            const uint32_t hf = 2u * ax + (pos ? 1u : 0u);
-            uint32_t hu = 0, hv = 0;
-            int64_t hA = 0;
-            if (SCATTER) {   // the count pass needs only the voxel sequence
-                hu = face_bin(X0[b0], D[b0], cur[b0], bn, bd, N, P.status);
-                hv = face_bin(X0[b1], D[b1], cur[b1], bn, bd, N, P.status);
-                hA = A0 + floor_div((A1 - A0) * bn, bd);
-            }
-            if (have_prev) {
-                const bool st = cur[0] >= 0 && cur[0] < P.res[0] && cur[1] >= 0 &&
-                                cur[1] < P.res[1] && cur[2] >= 0 && cur[2] < P.res[2];
-                if (st) {
-                    const uint32_t vox = (uint32_t)(cur[0] + (int64_t)P.res[0] * (cur[1] + (int64_t)P.res[1] * cur[2]));
-                    if (SCATTER) {
-                        const uint32_t at = offset[vox] + atomicAdd(cnt + vox, 1u);
-                        const uint32_t attr8 = (uint32_t)(((pA + hA) * 255 + 65535) / 131070);
-                        const uint64_t r = rec_pack(pf, pu, pv, hf, hu, hv, attr8, prev_stored ? 1u : 0u, (uint32_t)c);
-                        const uint64_t kk = ((uint64_t)c << 32) | k;
-                        if (pair) {
-                            pair[at] = make_ulonglong2(r, kk);
-                        } else {
-                            rec[at] = r;
-                            key[at] = kk;
-                        }
-                    } else {
-                        atomicAdd(cnt + vox, 1u);
-                    }
-                    nstored++;
+                D[a] = X1[a] - X0[a];
+                const int64_t f0 = X0[a] >> FXS, f1 = X1[a] >> FXS;
+                if (D[a] > 0) {
+                    nextp[a] = f0 + 1; lastp[a] = f1; den[a] = D[a]; act[a] = nextp[a] <= lastp[a];
+                    if (act[a]) m += (int)(lastp[a] - nextp[a] + 1);
+                } else if (D[a] < 0) {
+                    nextp[a] = f0; lastp[a] = f1 + 1; den[a] = -D[a]; act[a] = nextp[a] >= lastp[a];
+                    if (act[a]) m += (int)(nextp[a] - lastp[a] + 1);
+                } else {
+                    nextp[a] = lastp[a] = 0; den[a] = 1; act[a] = false;
                 }
-                prev_stored = st;
-                k++;
             }
-            cur[ax] += pos ? 1 : -1;
-            pf = 2u * ax + (pos ? 0u : 1u);
-            pu = hu;
-            pv = hv;
-            pA = hA;
-            have_prev = true;
-            if (pos) { nextp[ax]++; act[ax] = nextp[ax] <= lastp[ax]; }
-            else     { nextp[ax]--; act[ax] = nextp[ax] >= lastp[ax]; }
-        }
+            if (!has_edge) m = 0;
+            // the edge's last crossing: the latest plane, ties to the higher axis (crossed last)
+            uint32_t lf = 0, lu = 0, lv = 0;
+            int64_t lA = 0;
+            bool lin = false;              // the voxel before it lies in the grid
+            if (m > 0) {
+                int ax = -1;
+                int64_t bn = 0, bd = 1;
 #pragma unroll
-        for (int a = 0; a < 3; a++) X0[a] = X1[a];
-        A0 = A1;
+                for (int a = 0; a < 3; a++) {
+                    if (!act[a]) continue;
+                    const int64_t n = D[a] > 0 ? lastp[a] * FX - X0[a] : X0[a] - lastp[a] * FX;
+                    if (ax < 0 || n * bd >= bn * den[a]) { ax = a; bn = n; bd = den[a]; }
+                }
+                const bool pos = D[ax] > 0;
+                int64_t before[3] = {X1[0] >> FXS, X1[1] >> FXS, X1[2] >> FXS};
+                before[ax] -= pos ? 1 : -1;
+                lin = before[0] >= 0 && before[0] < P.res[0] && before[1] >= 0 && before[1] < P.res[1] &&
+                      before[2] >= 0 && before[2] < P.res[2];
+                lf = 2u * ax + (pos ? 0u : 1u);   // entry face of the next segment
+                if (SCATTER) {
+                    const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+                    lu = face_bin(X0[b0], D[b0], before[b0], bn, bd, N, P.status);
+                    lv = face_bin(X0[b1], D[b1], before[b1], bn, bd, N, P.status);
+                    lA = A0 + floor_div((A1 - A0) * bn, bd);
+                }
+            }
+            int incl = m;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULLM, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int wtotal = __shfl_sync(FULLM, incl, 31);
+            const int64_t first = ncross + (incl - m);          // index of my first crossing on the curve
+            // the crossing before my first one: nearest lower lane with crossings, else the carry
+            const unsigned has = __ballot_sync(FULLM, m > 0);
+            const unsigned lower = has & ((1u << lane) - 1u);
+            const int src = lower ? 31 - __clz(lower) : lane;
+            uint32_t pf = __shfl_sync(FULLM, lf, src), pu = __shfl_sync(FULLM, lu, src),
+                     pv = __shfl_sync(FULLM, lv, src);
+            int64_t pA = __shfl_sync(FULLM, lA, src);
+            const int src_incl = __shfl_sync(FULLM, incl, src);
+            bool prev_stored = __shfl_sync(FULLM, lin ? 1 : 0, src) != 0;
+            if (lower) {
+                // the segment ending at src's last crossing exists iff that crossing is not the curve's first
+                prev_stored = prev_stored && ncross + src_incl - 1 >= 1;
+            } else {
+                pf = cf; pu = cu; pv = cv; pA = cA;
+                prev_stored = cstored;
+            }
+            // walk my crossings in order, emitting the segment that ends at each
+            if (m > 0) {
+                int64_t cur[3] = {X0[0] >> FXS, X0[1] >> FXS, X0[2] >> FXS};
+                int64_t j = first;
+                for (;;) {
+                    int ax = -1;
+                    int64_t bn = 0, bd = 1;
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        if (!act[a]) continue;
+                        const int64_t n = D[a] > 0 ? nextp[a] * FX - X0[a] : X0[a] - nextp[a] * FX;
+                        if (ax < 0 || n * bd < bn * den[a]) { ax = a; bn = n; bd = den[a]; }
+                    }
+                    if (ax < 0) break;
+                    const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+                    const bool pos = D[ax] > 0;
+                    const uint32_t hf = 2u * ax + (pos ? 1u : 0u);
+                    uint32_t hu = 0, hv = 0;
+                    int64_t hA = 0;
+                    if (SCATTER) {
+                        hu = face_bin(X0[b0], D[b0], cur[b0], bn, bd, N, P.status);
+                        hv = face_bin(X0[b1], D[b1], cur[b1], bn, bd, N, P.status);
+                        hA = A0 + floor_div((A1 - A0) * bn, bd);
+                    }
+                    bool st = false;
+                    if (j >= 1) {
+                        st = cur[0] >= 0 && cur[0] < P.res[0] && cur[1] >= 0 && cur[1] < P.res[1] && cur[2] >= 0 &&
+                             cur[2] < P.res[2];
+                        if (st) {
+                            const uint32_t vox =
+                                (uint32_t)(cur[0] + (int64_t)P.res[0] * (cur[1] + (int64_t)P.res[1] * cur[2]));
+                            if (SCATTER) {
+                                const uint32_t at = offset[vox] + atomicAdd(cnt + vox, 1u);
+                                const uint32_t attr8 = (uint32_t)(((pA + hA) * 255 + 65535) / 131070);
+                                const uint64_t r =
+                                    rec_pack(pf, pu, pv, hf, hu, hv, attr8, prev_stored ? 1u : 0u, (uint32_t)c);
+                                const uint64_t kk = ((uint64_t)c << 32) | (uint64_t)(j - 1);
+                                if (pair) {
+                                    pair[at] = make_ulonglong2(r, kk);
+                                } else {
+                                    rec[at] = r;
+                                    key[at] = kk;
+                                }
+                            } else {
+                                atomicAdd(cnt + vox, 1u);
+                            }
+                            nstored_all++;
+                        }
+                    }
+                    prev_stored = st;
+                    cur[ax] += pos ? 1 : -1;
+                    pf = 2u * ax + (pos ? 0u : 1u);
+                    pu = hu;
+                    pv = hv;
+                    pA = hA;
+                    j++;
+                    if (pos) { nextp[ax]++; act[ax] = nextp[ax] <= lastp[ax]; }
+                    else     { nextp[ax]--; act[ax] = nextp[ax] >= lastp[ax]; }
+                }
+            }
+            // carry: the window's last crossing
+            if (has) {
+                const int top = 31 - __clz(has);
+                cf = __shfl_sync(FULLM, lf, top);
+                cu = __shfl_sync(FULLM, lu, top);
+                cv = __shfl_sync(FULLM, lv, top);
+                cA = __shfl_sync(FULLM, lA, top);
+                const bool tl = __shfl_sync(FULLM, lin ? 1 : 0, top) != 0;
+                cstored = tl && ncross + wtotal - 1 >= 1;
+            } else {
+                // no crossing in this window: keep the carry (the shuffles above kept every lane converged)
+            }
+            ncross += wtotal;
+        }
+        if (__any_sync(FULLM, bad_vertex) && lane == 0) atomicOr(P.status, ST_BAD_VERTEX);
     }
-    if (!ok) atomicOr(P.status, ST_BAD_VERTEX);
-    if (!SCATTER && nstored) atomicAdd(total, (unsigned long long)nstored);
-}
-
-// ------------------------------------------------------------------ bounding box (fit mode)
-__device__ __forceinline__ int f2ord(float f) {
-    int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7fffffff;
+    if (!SCATTER) {
+        for (int o = 16; o > 0; o >>= 1) nstored_all += __shfl_xor_sync(0xffffffffu, nstored_all, o);
+        if (lane == 0 && nstored_all) atomicAdd(total, nstored_all);
+    }
 }
 
 __global__ void bbox_kernel(const float *__restrict__ xyz, int64_t nv, int *mn, int *mx,
@@ -606,7 +691,7 @@ extern "C" lvr_status lvr_voxelize(lvr_ctx *ctx, const float *xyz, const float *
     LVR_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s));
     LVR_CUDA(ctx, cudaMemsetAsync(total, 0, 8, s));
     if (n_curves > 0) {
-        vox_curves_kernel<false><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, nullptr, total);
+        vox_warp_kernel<false><<<grid1d(n_curves * 32, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, nullptr, total);
         LVR_CUDA(ctx, cudaGetLastError());
     }
     LVR_CUDA(ctx, cudaMemcpyAsync(h32, ctx->d_status, 4, cudaMemcpyDeviceToHost, s));
@@ -654,8 +739,8 @@ extern "C" lvr_status lvr_voxelize(lvr_ctx *ctx, const float *xyz, const float *
         }
         ulonglong2 *pair = (ulonglong2 *)ctx->vox_pair;
         LVR_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s));
-        vox_curves_kernel<true><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, ls->offset, ls->rec, ls->key, pair,
-                                                                      total);
+        vox_warp_kernel<true><<<grid1d(n_curves * 32, 256), 256, 0, s>>>(P, cnt, ls->offset, ls->rec, ls->key, pair,
+                                                                         total);
         LVR_CUDA(ctx, cudaMemsetAsync(long_count, 0, 4, s));
         sort_small_kernel<<<grid1d(nvox, 256), 256, 0, s>>>(ls->offset, nvox, ls->rec, ls->key, pair, long_list,
                                                             long_count);
@@ -759,7 +844,7 @@ extern "C" lvr_status lvr_voxelize_static(const float *xyz, const float *attr, c
     if (cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s) != cudaSuccess ||
         cudaMemsetAsync(total, 0, 16, s) != cudaSuccess)
         return LVR_ECUDA;
-    if (n_curves > 0) vox_curves_kernel<false><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, nullptr, total);
+    if (n_curves > 0) vox_warp_kernel<false><<<grid1d(n_curves * 32, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr, nullptr, nullptr, total);
     if (cudaGetLastError() != cudaSuccess) return LVR_ECUDA;
     unsigned long long h_total = 0;
     uint32_t h_status = 0;
@@ -781,8 +866,8 @@ extern "C" lvr_status lvr_voxelize_static(const float *xyz, const float *attr, c
         if (cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s) != cudaSuccess ||
             cudaMemsetAsync(long_count, 0, 4, s) != cudaSuccess)
             return LVR_ECUDA;
-        vox_curves_kernel<true><<<grid1d(n_curves, 256), 256, 0, s>>>(P, cnt, offset, records, keys, nullptr,
-                                                                      total);
+        vox_warp_kernel<true><<<grid1d(n_curves * 32, 256), 256, 0, s>>>(P, cnt, offset, records, keys, nullptr,
+                                                                         total);
         sort_small_kernel<<<grid1d(nvox, 256), 256, 0, s>>>(offset, nvox, records, keys, nullptr, long_list,
                                                             long_count);
         sort_long_kernel<<<304, 256, 2 * SMEM_LIST * sizeof(uint64_t), s>>>(offset, records, keys, nullptr,
