@@ -303,6 +303,12 @@ vox_warp_kernel(VoxParams P, uint32_t *cnt, const uint32_t *__restrict__ offset,
     }
 }
 
+// ------------------------------------------------------------------ bounding box (fit mode)
+__device__ __forceinline__ int f2ord(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+
 __global__ void bbox_kernel(const float *__restrict__ xyz, int64_t nv, int *mn, int *mx,
                             uint32_t *status) {
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
