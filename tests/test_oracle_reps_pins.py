@@ -46,17 +46,32 @@ def test_flip_rule_and_average(orc):
 
 
 def test_connectivity_meets_in_the_middle(orc):
-    """Voxel (1, 1, 1) holds curve 0 (y bin 10) and curve 1 (y bin 13); voxel
+    """Voxel (1, 1, 1) holds curve 0 (y bin 10) and curve 1 (y bin 12); voxel
     (2, 1, 1) only curve 0 (curve 1 ends inside it, and its last partial
-    piece is dropped). Their shared face: 12 in (1, 1, 1), 10 in (2, 1, 1),
-    joined at floor((12 + 10 + 1) / 2) = 11."""
-    y10, y13 = 1 + 10.5 / 32, 1 + 13.5 / 32
-    vs = _vs(orc, [[[0.2, y10, 1.5], [3.8, y10, 1.5]], [[0.2, y13, 1.5], [2.5, y13, 1.5]]])
+    piece is dropped). Averages in (1, 1, 1): y = (21 + 25) / (2 * 64) * 32
+    -> bin 11 at both ends. Their shared face: 11 in (1, 1, 1), 10 in
+    (2, 1, 1), joined at floor((11 + 10 + 1) / 2) = 11."""
+    y10, y12 = 1 + 10.5 / 32, 1 + 12.5 / 32
+    vs = _vs(orc, [[[0.2, y10, 1.5], [3.8, y10, 1.5]], [[0.2, y12, 1.5], [2.5, y12, 1.5]]])
     r = orc.Reps(vs, 1).export(0)
     a, b = r[_cell(4, 1, 1, 1)], r[_cell(4, 2, 1, 1)]
     assert a[4] == 1 and b[1] == 0          # A's +x end and B's -x start
     assert a[5] == 11 and b[2] == 11
-    assert a[2] == 12 and b[5] == 10         # ends without a neighbour line keep their bins
+    assert a[2] == 11 and b[5] == 10         # ends without a neighbour line keep their bins
+
+
+def test_connectivity_takes_the_start_point_first(orc):
+    """A curve makes a U-turn inside voxel (1, 1, 1): in and out through its
+    +x face (bins 8 and 20); a second curve crosses voxel (2, 1, 1) at bin
+    16. On the shared face the start point (bin 8) is joined with the
+    neighbour's: floor((8 + 16 + 1) / 2) = 12; the end point keeps 20."""
+    y8, y20, y16 = 1 + 8.5 / 32, 1 + 20.5 / 32, 1 + 16.5 / 32
+    u_turn = [[2.5, y8, 1.5], [1.6, y8, 1.5], [1.6, y20, 1.5], [2.5, y20, 1.5]]
+    vs = _vs(orc, [u_turn, [[1.9, y16, 1.5], [3.9, y16, 1.5]]])
+    r = orc.Reps(vs, 1).export(0)
+    a, b = r[_cell(4, 1, 1, 1)], r[_cell(4, 2, 1, 1)]
+    assert tuple(a) == (1, 1, 12, 16, 1, 20, 16)
+    assert tuple(b) == (1, 0, 12, 16, 1, 16, 16)
 
 
 def test_level_above_from_the_children(orc):
