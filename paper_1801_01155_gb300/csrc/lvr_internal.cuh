@@ -40,7 +40,7 @@ struct lvr_ctx {
     void *vox_pair = nullptr;
     size_t vox_pair_bytes = 0;
     // rasterised comparison system: grow-only fragment store (depths, capsule ids)
-    double *frag_t = nullptr;
+    uint64_t *frag_t = nullptr;
     uint32_t *frag_id = nullptr;
     size_t frag_cap = 0;
 };

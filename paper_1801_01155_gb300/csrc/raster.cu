@@ -21,11 +21,12 @@
 //   opaque: pass 1 takes the 64-bit minimum of the depth per pixel, pass 2
 //   the smallest capsule id among the fragments at that depth, and a thread
 //   per pixel shades the winner.
-// Depths are float64 sums T + s: T a float32 ray parameter near the surface
-// part hit, s the float32 entry computed from a local origin built in
-// float-float (as the ray caster does per voxel). Sphere entries use a frame
-// anchored at the sphere's centre, so the two capsules sharing a joint give
-// bit-identical depths there and keep capsule order.
+// Depths are float-float sums T + s (no float64 on the device): T a float32
+// ray parameter near the surface part hit, s the float32 entry computed from
+// a local origin built in float-float (as the ray caster does per voxel),
+// normalised to hi + lo and ordered as one 64-bit integer key. Sphere entries
+// use a frame anchored at the sphere's centre, so the two capsules sharing a
+// joint give bit-identical depths there and keep capsule order.
 #include <math.h>
 #include <string.h>
 
@@ -54,7 +55,7 @@ struct RasterParams {
     float ert, ka, kd, bg[3];
     uint32_t *count;            // per pixel: fragments (pass 1), then the write cursor
     const uint32_t *offset;     // [npix + 1]
-    double *ft;                 // fragment depths
+    unsigned long long *ft;     // fragment depth keys
     uint32_t *fid;              // fragment capsules
     unsigned long long *zbuf;   // opaque: minimum depth bits per pixel
     uint32_t *zid;              // opaque: smallest capsule at that depth
@@ -99,6 +100,25 @@ __device__ __forceinline__ V3 local_origin(const RasterParams &P, V3 D, float T,
     return v3(p[0], p[1], p[2]);
 }
 
+// A depth hi + lo (|lo| <= ulp(hi) / 2) as a 64-bit key ordered like the
+// value: the order-preserving images of hi and lo side by side.
+constexpr unsigned long long KEY_NONE = ~0ull;
+__device__ __forceinline__ uint32_t ford(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unford(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+// key of T + s, or KEY_NONE unless the sum is positive
+__device__ __forceinline__ unsigned long long depth_key(float T, float s) {
+    float hi, lo;
+    two_sum_f(T, s, hi, lo);
+    lo = __fadd_rn(lo, 0.0f);   // -0 -> +0
+    if (!(hi > 0.0f || (hi == 0.0f && lo > 0.0f))) return KEY_NONE;
+    return ((unsigned long long)ford(hi) << 32) | ford(lo);
+}
+
 // first entry of p + s D into the sphere of radius sqrt(r2) around the origin
 __device__ __forceinline__ float sphere_entry0(V3 p, V3 D, float r2) {
     const float sc = -vdot(p, D);
@@ -107,15 +127,15 @@ __device__ __forceinline__ float sphere_entry0(V3 p, V3 D, float r2) {
     return d2 > r2 ? INFINITY : sc - sqrtf(r2 - d2);
 }
 
-__device__ __forceinline__ double sphere_depth(const RasterParams &P, V3 D, V3 c) {
+__device__ __forceinline__ unsigned long long sphere_depth(const RasterParams &P, V3 D, V3 c) {
     const float T = vdot(vsub(c, v3(P.eye[0], P.eye[1], P.eye[2])), D);
     const float s = sphere_entry0(local_origin(P, D, T, c), D, P.r2);
-    return s < INFINITY ? (double)T + (double)s : INFINITY;
+    return s < INFINITY ? depth_key(T, s) : KEY_NONE;
 }
 
-// Depth of the ray's entry into capsule [a, b] (float64), or +inf.
-__device__ __forceinline__ double capsule_depth(const RasterParams &P, V3 D, V3 a, V3 b) {
-    double best = INFINITY;
+// Depth key of the ray's entry into capsule [a, b], or KEY_NONE.
+__device__ __forceinline__ unsigned long long capsule_depth(const RasterParams &P, V3 D, V3 a, V3 b) {
+    unsigned long long best = KEY_NONE;
     const V3 ba = vsub(b, a);
     const float L2 = vdot(ba, ba);
     if (L2 > 0.0f) {
@@ -131,17 +151,16 @@ __device__ __forceinline__ double capsule_depth(const RasterParams &P, V3 D, V3 
             const float sc = -vdot(Dp, Op) / A;
             const V3 q = vaxpy(sc, Dp, Op);
             const float d2 = vdot(q, q);
-            if (d2 > P.r2) return INFINITY;              // misses the infinite cylinder
+            if (d2 > P.r2) return KEY_NONE;              // misses the infinite cylinder
             const float s = sc - sqrtf((P.r2 - d2) / A);
             const float y = fmaf(s, dw, ow);
-            if (y > 0.0f && y < L) best = (double)Ta + (double)s;
+            if (y > 0.0f && y < L) best = depth_key(Ta, s);
         } else if (vdot(Op, Op) > P.r2) {
-            return INFINITY;
+            return KEY_NONE;
         }
-        best = fmin(best, sphere_depth(P, D, b));
+        best = min(best, sphere_depth(P, D, b));
     }
-    best = fmin(best, sphere_depth(P, D, a));
-    return best > 0.0 ? best : INFINITY;
+    return min(best, sphere_depth(P, D, a));
 }
 
 // Conservative pixel rectangle of the capsule (both end spheres); false if
@@ -264,8 +283,8 @@ rs_frag_kernel(const __grid_constant__ RasterParams P) {
                 const V3 D = v3(Dw.x, Dw.y, Dw.z);
                 const V3 perp = vaxpy(-vdot(mrel, D), D, mrel);
                 if (vdot(perp, perp) > Rb2) continue;
-                const double t = capsule_depth(P, D, a, b);
-                if (!(t < INFINITY)) continue;
+                const unsigned long long t = capsule_depth(P, D, a, b);
+                if (t == KEY_NONE) continue;
                 if constexpr (PASS == PASS_COUNT) {
                     atomicAdd(P.count + pix, 1u);
                 } else if constexpr (PASS == PASS_WRITE) {
@@ -278,10 +297,10 @@ rs_frag_kernel(const __grid_constant__ RasterParams P) {
                         atomicOr(P.status, ST_INTERNAL);
                     }
                 } else if constexpr (PASS == PASS_DEPTH) {
-                    atomicMin(P.zbuf + pix, (unsigned long long)__double_as_longlong(t));
+                    atomicMin(P.zbuf + pix, t);
                     nfrag++;
                 } else {
-                    if ((unsigned long long)__double_as_longlong(t) == P.zbuf[pix]) atomicMin(P.zid + pix, (uint32_t)k);
+                    if (t == P.zbuf[pix]) atomicMin(P.zid + pix, (uint32_t)k);
                 }
             }
     }
@@ -293,11 +312,13 @@ rs_frag_kernel(const __grid_constant__ RasterParams P) {
 
 // Shading of a fragment (S1: ka + kd |n . L|, no shadows or AO): colour
 // times the lighting factor in rgb, opacity in w.
-__device__ __forceinline__ float4 shade(const RasterParams &P, const float4 *tf, V3 D, double t, uint32_t k) {
+__device__ __forceinline__ float4 shade(const RasterParams &P, const float4 *tf, V3 D, unsigned long long t,
+                                        uint32_t k) {
     const float4 Aw = P.sa[k], B = P.sb[k];
     const V3 a = v3(Aw.x, Aw.y, Aw.z), ba = vsub(v3(B.x, B.y, B.z), a);
     const float Ta = vdot(vsub(a, v3(P.eye[0], P.eye[1], P.eye[2])), D);
-    const V3 pl = vaxpy((float)(t - (double)Ta), D, local_origin(P, D, Ta, a));   // entry point - a
+    const float hi = unford((uint32_t)(t >> 32)), lo = unford((uint32_t)t);
+    const V3 pl = vaxpy(__fadd_rn(__fsub_rn(hi, Ta), lo), D, local_origin(P, D, Ta, a));   // entry point - a
     const float L2 = vdot(ba, ba);
     const float h = L2 > 0.0f ? fminf(1.0f, fmaxf(0.0f, vdot(pl, ba) / L2)) : 0.0f;
     V3 n = vaxpy(-h, ba, pl);
@@ -307,10 +328,7 @@ __device__ __forceinline__ float4 shade(const RasterParams &P, const float4 *tf,
     return make_float4(c.x * kk, c.y * kk, c.z * kk, c.w);
 }
 
-// depths are positive: their bit patterns order as unsigned integers
-__device__ __forceinline__ bool frag_less(double ta, uint32_t ia, double tb, uint32_t ib) {
-    const unsigned long long ka = (unsigned long long)__double_as_longlong(ta),
-                             kb = (unsigned long long)__double_as_longlong(tb);
+__device__ __forceinline__ bool frag_less(unsigned long long ka, uint32_t ia, unsigned long long kb, uint32_t ib) {
     return ka < kb || (ka == kb && ia < ib);
 }
 
@@ -327,7 +345,7 @@ __device__ __forceinline__ void warp_sort(T *t, I *id, int n, int lane) {
             for (int i = lane; i < S; i += 32) {
                 const int j = i ^ mask;
                 if (j > i && j < n) {
-                    const double ti = t[i], tj = t[j];
+                    const unsigned long long ti = t[i], tj = t[j];
                     const uint32_t ii = id[i], ij = id[j];
                     if (frag_less(tj, ij, ti, ii)) {
                         t[i] = tj; t[j] = ti;
@@ -344,7 +362,7 @@ __device__ __forceinline__ void warp_sort(T *t, I *id, int n, int lane) {
 // blend the fragments before it.
 __global__ void __launch_bounds__(RS_WARPS * 32)
 rs_resolve_kernel(const __grid_constant__ RasterParams P) {
-    __shared__ double st[RS_WARPS][RS_CAP];
+    __shared__ unsigned long long st[RS_WARPS][RS_CAP];
     __shared__ uint32_t si[RS_WARPS][RS_CAP];
     __shared__ float4 tf[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x)
@@ -357,7 +375,7 @@ rs_resolve_kernel(const __grid_constant__ RasterParams P) {
         const uint32_t beg = P.offset[p];
         const int n = (int)(P.offset[p + 1] - beg);
         longest = max(longest, (unsigned)n);
-        double *t;
+        unsigned long long *t;
         uint32_t *id;
         if (n <= RS_CAP) {
             for (int i = lane; i < n; i += 32) {
@@ -433,7 +451,7 @@ rs_opaque_kernel(const __grid_constant__ RasterParams P) {
             continue;
         }
         const float4 Dw = P.dirs[p];
-        const float4 c = shade(P, tf, v3(Dw.x, Dw.y, Dw.z), __longlong_as_double((long long)P.zbuf[p]), k);
+        const float4 c = shade(P, tf, v3(Dw.x, Dw.y, Dw.z), P.zbuf[p], k);
         P.out[p] = make_float4(c.x, c.y, c.z, 1.0f);
     }
 }
@@ -566,7 +584,7 @@ extern "C" lvr_status lvr_raster(lvr_ctx *ctx, const float *xyz, const float *at
             if ((st = dev_alloc(ctx, (void **)&ctx->frag_id, cap * 4)) != LVR_OK) return st;
             ctx->frag_cap = cap;
         }
-        P.ft = ctx->frag_t;
+        P.ft = (unsigned long long *)ctx->frag_t;
         P.fid = ctx->frag_id;
         LVR_CUDA(ctx, cudaMemsetAsync(count, 0, (size_t)npix * 4, s));
         if (n_vertices > 0) rs_frag_kernel<PASS_WRITE><<<gslot, 256, 0, s>>>(P);
