@@ -159,17 +159,29 @@ def run_gpu(args):
     desc = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0,
                          tile=tune["tile"], layout=layout)
 
-    def step(counters=None, ev=None):
-        s = lvr.lvr_voxelize(ctx, xyz, attr, offs, gdesc())
+    # Consecutive steps alternate between two contexts on two streams, as a
+    # serving loop would: a step's voxelisation (which reads its segment count
+    # back to the host) overlaps the tail of the previous step's render.
+    streams = [stream, torch.cuda.Stream(dev)]
+    ctxs = [ctx, lvr.Context(local, streams[1])]
+    outs = [out, torch.empty((H, W, 4), dtype=torch.float32, device=dev)]
+
+    def step(k=0, counters=None, ev=None, src=(xyz, attr, offs), img=None):
+        i = k & 1
+        c, st = ctxs[i], streams[i]
+        s = lvr.lvr_voxelize(c, src[0], src[1], src[2], gdesc())
         if layout:
-            lvr.lvr_lineset_layout(ctx, s, layout)
-        lod = lvr.lvr_build_lod(ctx, s, LEVELS, sig)
+            lvr.lvr_lineset_layout(c, s, layout)
+        lod = lvr.lvr_build_lod(c, s, LEVELS, sig)
         if ev is not None:
-            ev[0].record(stream)
-        lvr.lvr_render(ctx, s, lod, view, desc, out, counters=counters)
+            ev[0].record(st)
+        lvr.lvr_render(c, s, lod, view, desc, outs[i], counters=counters)
         if ev is not None:
-            ev[1].record(stream)
-        lod.free()
+            ev[1].record(st)
+        if img is not None:   # the image back to pinned host memory
+            with torch.cuda.stream(st):
+                img[i].copy_(outs[i], non_blocking=True)
+        lod.free()   # stream-ordered
         s.free()
 
     # algorithmic bytes of one render launch (counted by the kernel itself, untimed)
@@ -179,8 +191,8 @@ def run_gpu(args):
     rec_bytes = 16 if layout else 8
     alg_bytes = 8 * nvox + rec_bytes * nrec + 32 * nsamp
 
-    for _ in range(args.warmup):
-        step()
+    for k in range(args.warmup):
+        step(k)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -189,8 +201,10 @@ def run_gpu(args):
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0.record(stream)
+    streams[1].wait_stream(stream)
     for k in range(args.steps):
-        step(ev=evs[k])
+        step(k, ev=evs[k])
+    stream.wait_stream(streams[1])
     t1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -203,36 +217,27 @@ def run_gpu(args):
     rays = W * H
     value = job_throughput(world, rays, args.steps, ms)
 
-    # end to end through the C ABI with host buffers: H2D of the step's inputs
-    # and D2H of the image inside the timed region
-    pin_xyz = torch.from_numpy(ls.xyz).pin_memory()
-    pin_attr = torch.from_numpy(ls.attr).pin_memory()
-    pin_offs = torch.from_numpy(ls.offsets).pin_memory()
-    pin_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
-
-    def step_e2e():
-        s = lvr.lvr_voxelize(ctx, pin_xyz, pin_attr, pin_offs, gdesc())
-        if layout:
-            lvr.lvr_lineset_layout(ctx, s, layout)
-        lod = lvr.lvr_build_lod(ctx, s, LEVELS, sig)
-        lvr.lvr_render(ctx, s, lod, view, desc, pin_out)
-        lod.free()
-        s.free()
-
-    for _ in range(args.warmup):
-        step_e2e()
+    # end to end through the C ABI: the same steps, each copying its inputs
+    # from pinned host memory (lvr_voxelize stages them) and its image back to
+    # pinned host memory, all inside the timed region
+    pin = (torch.from_numpy(ls.xyz).pin_memory(), torch.from_numpy(ls.attr).pin_memory(),
+           torch.from_numpy(ls.offsets).pin_memory())
+    pin_img = [torch.empty((H, W, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
+    for k in range(args.warmup):
+        step(k, src=pin, img=pin_img)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     e0 = time.perf_counter()
-    for _ in range(args.steps):
-        step_e2e()
+    for k in range(args.steps):
+        step(k, src=pin, img=pin_img)
     torch.cuda.synchronize()
     e_ms = (time.perf_counter() - e0) * 1e3
+    ctxs[1].close()
     e_ms = reduce_max(e_ms, dev)
     e2e_value = job_throughput(world, rays, args.steps, e_ms)
     h2d = ls.xyz.nbytes + ls.attr.nbytes + ls.offsets.nbytes
-    d2h = pin_out.numel() * 4
+    d2h = pin_img[0].numel() * 4
 
     if rank == 0:
         peak, which = peaks()
