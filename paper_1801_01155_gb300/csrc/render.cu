@@ -71,6 +71,7 @@ struct RenderParams {
     int32_t opaque;
     float ert;
     int32_t shadows, ao, ao_rays, nrays;
+    int32_t ao_fast;              // 3 levels, AO radius in [12, 16): the unrolled AO march
     float ao_radius, ka, kd, bg[3];
     float aod[MAX_AO][3];         // hemisphere directions in the (T, B, n) frame
     const float4 *gtf;            // batched views: this view's transfer function in global memory
@@ -546,6 +547,26 @@ __device__ __forceinline__ Vec ao_tangent(Vec n, Vec u) {
 // ... with step 2^l at level l = floor(log2 s) (capped); O += rho_l * 2^l
 // with rho_l = dens_l / 8^l; the ray ends at O >= 1, beyond max_dist (if
 // >= 0), or when the sample leaves the support of the density field.
+// The march of an AO ray with 3 levels and a radius in [12, 16): the
+// samples fall at s = 1, 2, 4, 8, 12 (levels 0, 1, 2, 2, 2), unrolled; the
+// same samples, order, weights and stopping rules as march().
+__device__ __forceinline__ float march_ao5(const RenderParams &P, Vec p, Vec d, unsigned &nsamp) {
+    float O = 0.0f;
+    const int ss[5] = {1, 2, 4, 8, 12}, ll[5] = {0, 1, 2, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        const Vec x = axpy((float)ss[k], d, p);
+        if (x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
+            x.z > P.lod_hi[2])
+            break;
+        const float wl = __int_as_float((127 - 2 * ll[k]) << 23);   // 2^l / 8^l
+        O = fmaf(sample_level(P, ll[k], x), wl, O);
+        nsamp++;
+        if (O >= 1.0f) break;
+    }
+    return O;
+}
+
 __device__ __forceinline__ float march(const RenderParams &P, Vec p, Vec d, float max_dist, unsigned &nsamp) {
     const int top = P.levels - 1;
     float O = 0.0f;
@@ -865,7 +886,7 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
                 const float dx = P.aod[ray][0], dy = P.aod[ray][1], dz = P.aod[ray][2];
                 const Vec d = mk(fmaf(T.x, dx, fmaf(B.x, dy, n.x * dz)), fmaf(T.y, dx, fmaf(B.y, dy, n.y * dz)),
                                  fmaf(T.z, dx, fmaf(B.z, dy, n.z * dz)));
-                o = fminf(1.0f, march(P, Pg, d, P.ao_radius, nsamp));
+                o = fminf(1.0f, P.ao_fast ? march_ao5(P, Pg, d, nsamp) : march(P, Pg, d, P.ao_radius, nsamp));
             }
             for (int x = G >> 1; x > 0; x >>= 1) o += __shfl_xor_sync(FULL, o, x);
             if (ray == 0 && g < total) {
@@ -1246,6 +1267,7 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     if (judge) P.shadows = 0;   // the judge keeps the learned AO where the visibility would go
     P.nrays = (P.shadows ? 1 : 0) + P.ao_rays + P.learned + (P.aof ? 1 : 0);
     P.ao_radius = desc->ao_radius;
+    P.ao_fast = lod && lod->levels == 3 && desc->ao_radius >= 12.0f && desc->ao_radius < 16.0f;
     P.ka = desc->ka;
     P.kd = desc->kd;
     for (int a = 0; a < 3; a++) P.bg[a] = desc->bg[a];
