@@ -567,6 +567,35 @@ __device__ __forceinline__ float march_ao5(const RenderParams &P, Vec p, Vec d, 
     return O;
 }
 
+// The unbounded march (shadows) with 3 levels: s = 1, 2 (levels 0, 1), then
+// s = 4, 8, 12, ... on level 2 until the sample leaves the density support
+// or O reaches 1; the same samples, order and weights as march().
+__device__ __forceinline__ float march_shadow3(const RenderParams &P, Vec p, Vec d, unsigned &nsamp) {
+    auto outside = [&](const Vec &x) {
+        return x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
+               x.z > P.lod_hi[2];
+    };
+    float O = 0.0f;
+    Vec x = axpy(1.0f, d, p);
+    if (outside(x)) return O;
+    O = sample_level(P, 0, x);
+    nsamp++;
+    if (O >= 1.0f) return O;
+    x = axpy(2.0f, d, p);
+    if (outside(x)) return O;
+    O = fmaf(sample_level(P, 1, x), 0.25f, O);
+    nsamp++;
+    if (O >= 1.0f) return O;
+    for (int s = 4; s < (1 << 30); s += 4) {
+        x = axpy((float)s, d, p);
+        if (outside(x)) break;
+        O = fmaf(sample_level(P, 2, x), 0.0625f, O);
+        nsamp++;
+        if (O >= 1.0f) break;
+    }
+    return O;
+}
+
 __device__ __forceinline__ float march(const RenderParams &P, Vec p, Vec d, float max_dist, unsigned &nsamp) {
     const int top = P.levels - 1;
     float O = 0.0f;
@@ -817,7 +846,8 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
         for (int g = lane; g < total; g += 32) {
             const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
             const Vec Pg = mk(sm.slot[F_PX][q][o], sm.slot[F_PY][q][o], sm.slot[F_PZ][q][o]);
-            sm.slot[F_V][q][o] = 1.0f - fminf(1.0f, march(P, Pg, Lt, -1.0f, nsamp));
+            sm.slot[F_V][q][o] =
+                1.0f - fminf(1.0f, P.levels == 3 ? march_shadow3(P, Pg, Lt, nsamp) : march(P, Pg, Lt, -1.0f, nsamp));
         }
     } else if constexpr (MODE == MODE_REP) {
         rep_shadows(P, sm, warp, lane, total, Lt, nsamp);
