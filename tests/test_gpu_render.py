@@ -137,20 +137,23 @@ def test_c2_crop_shadows_ao(env, c2):
 
 def test_c2_full_frame_sampled(env, c2):
     """Full 1080p frame of the benchmark workload in the benchmark's launch
-    configuration; 2000 sampled pixels checked by the oracle."""
+    configurations (the default one, and the autotuner's usual pick: 16-byte
+    records with 4x8 ray tiles); 2000 sampled pixels checked by the oracle."""
     import torch
     lvr, O, ctx, dev = env
+    lvr.lvr_lineset_layout(ctx, c2.gls, lvr.LAYOUT_AOS16)
     cam = synth.orbit_view((256, 256, 256), 1920, 1080)
     lv, ov, _ = S.views(cam)
-    out = torch.empty((1080, 1920, 4), dtype=torch.float32, device=dev)
-    desc = lvr.make_desc(0.15, c2.tf, ert_alpha=0.99, shadows=True, ao_mode=1)
-    lvr.lvr_render(ctx, c2.gls, c2.glod, lv, desc, out)
-    ctx.sync()
     rng = np.random.default_rng(1)
     pix = np.stack([rng.integers(0, 1920, 2000), rng.integers(0, 1080, 2000)], 1).astype(np.int32)
     ref, tie, _ = O.render(c2.ovs, c2.olod, ov, O.make_rdesc(0.15, c2.tf, ert_alpha=0.99, shadows=True, ao=True), pix)
-    got = out.cpu().numpy()[pix[:, 1], pix[:, 0]]
-    S.check_image(got, ref, tie, cap=3e-3, what="c2 sampled")
+    for kw in (dict(), dict(layout=lvr.LAYOUT_AOS16, tile=(4, 8))):
+        out = torch.empty((1080, 1920, 4), dtype=torch.float32, device=dev)
+        desc = lvr.make_desc(0.15, c2.tf, ert_alpha=0.99, shadows=True, ao_mode=1, **kw)
+        lvr.lvr_render(ctx, c2.gls, c2.glod, lv, desc, out)
+        ctx.sync()
+        got = out.cpu().numpy()[pix[:, 1], pix[:, 0]]
+        S.check_image(got, ref, tie, cap=3e-3, what=f"c2 sampled {kw}")
 
 
 def test_tile_shapes_bit_identical(env, c1t):
