@@ -150,8 +150,8 @@ constexpr int AOT_X = 32, AOT_Y = 4, AOT_Z = 2;   // a warp covers one row: conf
 // One stencil sample for the tiled kernel: the offset of its lower corner in
 // the shared tile and the eight trilinear weights of its corners.
 struct AoTap {
+    float4 wa, wb;       // corner (x, y, z) bits -> weight (bit 0 x, bit 1 y, bit 2 z): corners 0-3, 4-7
     int32_t off;
-    float w[8];          // corner (x, y, z) bits -> weight: bit 0 x, bit 1 y, bit 2 z
     int32_t pad[3];
 };
 constexpr int AOT_MAX_TAPS = 640;                  // stencil entries passed as a kernel parameter
@@ -188,15 +188,16 @@ ao_field_tile_kernel(const float *__restrict__ dens, int dx, int dy, int dz, con
 #pragma unroll
         for (int s = 0; s < STEPS; s++) {
             const AoTap &e = tab.t[k * STEPS + s];
+            const float4 wa = e.wa, wb = e.wb;   // two 16-byte constant loads
             const float *c = c0 + e.off;
-            O = fmaf(e.w[0], c[0], O);
-            O = fmaf(e.w[1], c[1], O);
-            O = fmaf(e.w[2], c[sy], O);
-            O = fmaf(e.w[3], c[sy + 1], O);
-            O = fmaf(e.w[4], c[sz], O);
-            O = fmaf(e.w[5], c[sz + 1], O);
-            O = fmaf(e.w[6], c[sz + sy], O);
-            O = fmaf(e.w[7], c[sz + sy + 1], O);
+            O = fmaf(wa.x, c[0], O);
+            O = fmaf(wa.y, c[1], O);
+            O = fmaf(wa.z, c[sy], O);
+            O = fmaf(wa.w, c[sy + 1], O);
+            O = fmaf(wb.x, c[sz], O);
+            O = fmaf(wb.y, c[sz + 1], O);
+            O = fmaf(wb.z, c[sz + sy], O);
+            O = fmaf(wb.w, c[sz + sy + 1], O);
         }
         occ += fminf(1.0f, O);
     }
@@ -429,8 +430,11 @@ extern "C" lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, flo
             const AoStep &e = tab[i];
             AoTap &t = taps.t[i];
             t.off = e.ix + TX * (e.iy + TY * e.iz);
+            float w[8];
             for (int c = 0; c < 8; c++)
-                t.w[c] = (c & 1 ? e.fx : 1.0f - e.fx) * (c & 2 ? e.fy : 1.0f - e.fy) * (c & 4 ? e.fz : 1.0f - e.fz);
+                w[c] = (c & 1 ? e.fx : 1.0f - e.fx) * (c & 2 ? e.fy : 1.0f - e.fy) * (c & 4 ? e.fz : 1.0f - e.fz);
+            t.wa = make_float4(w[0], w[1], w[2], w[3]);
+            t.wb = make_float4(w[4], w[5], w[6], w[7]);
             t.pad[0] = t.pad[1] = t.pad[2] = 0;
         }
         const dim3 grid((dm[0] + AOT_X - 1) / AOT_X, (dm[1] + AOT_Y - 1) / AOT_Y, (dm[2] + AOT_Z - 1) / AOT_Z);
