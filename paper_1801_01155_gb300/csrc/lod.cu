@@ -204,6 +204,82 @@ ao_field_tile_kernel(const float *__restrict__ dens, int dx, int dy, int dz, con
     field[vx + (int64_t)dx * (vy + (int64_t)dy * vz)] = 1.0f - occ / (float)rays;
 }
 
+// Two voxels per thread: a block covers 64 x 4 x 2 voxels, a thread the x
+// neighbours 2i and 2i + 1, whose trilinear corners share a column (the
+// upper x corners of the first are the lower ones of the second), so a tap
+// costs 12 shared loads for two voxels instead of 16. Even and odd tile
+// columns are stored in separate planes, so a warp's loads stay on distinct
+// banks. Each voxel sums its taps in the same order as the tiled kernel.
+constexpr int AOP_X = 64, AOP_Y = 4, AOP_Z = 2;
+
+struct AoPairTap {
+    float4 wa, wb;         // corner weights, as AoTap
+    int32_t off[3];        // per corner column d = 0, 1, 2: plane * plane size + offset in the plane
+    int32_t pad;
+};
+struct AoPairTaps {
+    AoPairTap t[AOT_MAX_TAPS];
+};
+
+template <int STEPS>
+__global__ void __launch_bounds__(AOP_X / 2 * AOP_Y * AOP_Z)
+ao_field_pair_kernel(const float *__restrict__ dens, int dx, int dy, int dz, const __grid_constant__ AoPairTaps tab,
+                     int rays, int H, float *field) {
+    extern __shared__ float tile[];
+    const int TX = AOP_X + 2 * H, TY = AOP_Y + 2 * H, TZ = AOP_Z + 2 * H;
+    const int TXh = (TX + 1) / 2, PS = TXh * TY * TZ;
+    const int tx0 = blockIdx.x * AOP_X, ty0 = blockIdx.y * AOP_Y, tz0 = blockIdx.z * AOP_Z;
+    for (int i = threadIdx.x; i < TX * TY * TZ; i += blockDim.x) {
+        const int X = i % TX, Y = (i / TX) % TY, Z = i / (TX * TY);
+        const int gx = tx0 - H + X, gy = ty0 - H + Y, gz = tz0 - H + Z;
+        tile[(X & 1) * PS + (X >> 1) + TXh * (Y + TY * Z)] =
+            (gx >= 0 && gy >= 0 && gz >= 0 && gx < dx && gy < dy && gz < dz)
+                ? __ldg(dens + (gx + (int64_t)dx * (gy + (int64_t)dy * gz))) : 0.0f;
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % (AOP_X / 2), ly = (threadIdx.x / (AOP_X / 2)) % AOP_Y,
+              lz = threadIdx.x / (AOP_X / 2 * AOP_Y);
+    const int vx = tx0 + 2 * lx, vy = ty0 + ly, vz = tz0 + lz;
+    if (vx >= dx || vy >= dy || vz >= dz) return;
+    const float *cb = tile + lx + TXh * ((ly + H) + TY * (lz + H));
+    const int sy = TXh, sz = TXh * TY;
+    float occ0 = 0.0f, occ1 = 0.0f;
+    for (int k = 0; k < rays; k++) {
+        float O0 = 0.0f, O1 = 0.0f;
+#pragma unroll
+        for (int s = 0; s < STEPS; s++) {
+            const AoPairTap &e = tab.t[k * STEPS + s];
+            const float4 wa = e.wa, wb = e.wb;
+            const float *c0 = cb + e.off[0], *c1 = cb + e.off[1], *c2 = cb + e.off[2];
+            const float p0 = c0[0], p1 = c1[0], p2 = c2[0];
+            const float q0 = c0[sy], q1 = c1[sy], q2 = c2[sy];
+            const float r0 = c0[sz], r1 = c1[sz], r2 = c2[sz];
+            const float u0 = c0[sz + sy], u1 = c1[sz + sy], u2 = c2[sz + sy];
+            O0 = fmaf(wa.x, p0, O0);
+            O0 = fmaf(wa.y, p1, O0);
+            O0 = fmaf(wa.z, q0, O0);
+            O0 = fmaf(wa.w, q1, O0);
+            O0 = fmaf(wb.x, r0, O0);
+            O0 = fmaf(wb.y, r1, O0);
+            O0 = fmaf(wb.z, u0, O0);
+            O0 = fmaf(wb.w, u1, O0);
+            O1 = fmaf(wa.x, p1, O1);
+            O1 = fmaf(wa.y, p2, O1);
+            O1 = fmaf(wa.z, q1, O1);
+            O1 = fmaf(wa.w, q2, O1);
+            O1 = fmaf(wb.x, r1, O1);
+            O1 = fmaf(wb.y, r2, O1);
+            O1 = fmaf(wb.z, u1, O1);
+            O1 = fmaf(wb.w, u2, O1);
+        }
+        occ0 += fminf(1.0f, O0);
+        occ1 += fminf(1.0f, O1);
+    }
+    const int64_t o = vx + (int64_t)dx * (vy + (int64_t)dy * vz);
+    field[o] = 1.0f - occ0 / (float)rays;
+    if (vx + 1 < dx) field[o + 1] = 1.0f - occ1 / (float)rays;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ representative lines
@@ -422,7 +498,32 @@ extern "C" lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, flo
     const int H = steps + 1;   // samples reach floor(s d) in [-steps, steps] plus one corner
     const int TX = AOT_X + 2 * H, TY = AOT_Y + 2 * H, TZ = AOT_Z + 2 * H;
     const size_t tile_bytes = (size_t)TX * TY * TZ * 4;
-    if (steps == 5 && tile_bytes <= 48 * 1024 && tab.size() <= (size_t)AOT_MAX_TAPS) {
+    const int PX = AOP_X + 2 * H, PY = AOP_Y + 2 * H, PZ = AOP_Z + 2 * H, PXh = (PX + 1) / 2;
+    const size_t pair_bytes = (size_t)2 * PXh * PY * PZ * 4;
+    if (steps == 5 && pair_bytes <= 200 * 1024 && tab.size() <= (size_t)AOT_MAX_TAPS) {
+        static AoPairTaps taps;   // host staging of the kernel parameter (copied at launch)
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lk(mu);
+        const int PS = PXh * PY * PZ;
+        for (size_t i = 0; i < tab.size(); i++) {
+            const AoStep &e = tab[i];
+            AoPairTap &t = taps.t[i];
+            const int m = H + e.ix;   // >= 1: column of the first corner, relative to 2 x (thread's x)
+            for (int d = 0; d < 3; d++)
+                t.off[d] = ((m + d) & 1) * PS + ((m + d) >> 1) + PXh * (e.iy + PY * e.iz);
+            float w[8];
+            for (int c = 0; c < 8; c++)
+                w[c] = (c & 1 ? e.fx : 1.0f - e.fx) * (c & 2 ? e.fy : 1.0f - e.fy) * (c & 4 ? e.fz : 1.0f - e.fz);
+            t.wa = make_float4(w[0], w[1], w[2], w[3]);
+            t.wb = make_float4(w[4], w[5], w[6], w[7]);
+            t.pad = 0;
+        }
+        LVR_CUDA(ctx, cudaFuncSetAttribute(ao_field_pair_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)pair_bytes));
+        const dim3 grid((dm[0] + AOP_X - 1) / AOP_X, (dm[1] + AOP_Y - 1) / AOP_Y, (dm[2] + AOP_Z - 1) / AOP_Z);
+        ao_field_pair_kernel<5><<<grid, AOP_X / 2 * AOP_Y * AOP_Z, pair_bytes, ctx->stream>>>(
+            lod->dens[0], dm[0], dm[1], dm[2], taps, rays, H, lod->aof);
+    } else if (steps == 5 && tile_bytes <= 48 * 1024 && tab.size() <= (size_t)AOT_MAX_TAPS) {
         static AoTaps taps;   // host staging of the kernel parameter (copied at launch)
         static std::mutex mu;
         std::lock_guard<std::mutex> lk(mu);
