@@ -145,75 +145,22 @@ ao_field_kernel(const float4 *__restrict__ pk, int dx, int dy, int dz, const AoS
 // H cells per side (zero outside the grid) into shared memory; the samples
 // then read shared memory, the stencil the constant bank (same values, same
 // lerps: identical results).
-constexpr int AOT_X = 32, AOT_Y = 4, AOT_Z = 2;   // a warp covers one row: conflict-free reads
 
-// One stencil sample for the tiled kernel: the offset of its lower corner in
-// the shared tile and the eight trilinear weights of its corners.
-struct AoTap {
-    float4 wa, wb;       // corner (x, y, z) bits -> weight (bit 0 x, bit 1 y, bit 2 z): corners 0-3, 4-7
-    int32_t off;
-    int32_t pad[3];
-};
 constexpr int AOT_MAX_TAPS = 640;                  // stencil entries passed as a kernel parameter
-struct AoTaps {
-    AoTap t[AOT_MAX_TAPS];
-};
-
-// The same field with the density staged per block: a block takes a tile of
-// 32 x 4 x 2 voxels and copies the level-0 density of the tile grown by H
-// cells per side (zero outside the grid) into shared memory; the stencil
-// (tile offsets and corner weights) comes from the constant bank. O is not
-// cut off at 1: min(1, O) is the same either way since density >= 0.
-template <int STEPS>
-__global__ void __launch_bounds__(AOT_X * AOT_Y * AOT_Z)
-ao_field_tile_kernel(const float *__restrict__ dens, int dx, int dy, int dz, const __grid_constant__ AoTaps tab,
-                     int rays, int H, float *field) {
-    extern __shared__ float tile[];
-    const int TX = AOT_X + 2 * H, TY = AOT_Y + 2 * H, TZ = AOT_Z + 2 * H;
-    const int tx0 = blockIdx.x * AOT_X, ty0 = blockIdx.y * AOT_Y, tz0 = blockIdx.z * AOT_Z;
-    for (int i = threadIdx.x; i < TX * TY * TZ; i += blockDim.x) {
-        const int X = tx0 - H + i % TX, Y = ty0 - H + (i / TX) % TY, Z = tz0 - H + i / (TX * TY);
-        tile[i] = (X >= 0 && Y >= 0 && Z >= 0 && X < dx && Y < dy && Z < dz)
-                      ? __ldg(dens + (X + (int64_t)dx * (Y + (int64_t)dy * Z))) : 0.0f;
-    }
-    __syncthreads();
-    const int lx = threadIdx.x % AOT_X, ly = (threadIdx.x / AOT_X) % AOT_Y, lz = threadIdx.x / (AOT_X * AOT_Y);
-    const int vx = tx0 + lx, vy = ty0 + ly, vz = tz0 + lz;
-    if (vx >= dx || vy >= dy || vz >= dz) return;
-    const float *c0 = tile + (lx + H) + TX * ((ly + H) + TY * (lz + H));
-    const int sy = TX, sz = TX * TY;
-    float occ = 0.0f;
-    for (int k = 0; k < rays; k++) {
-        float O = 0.0f;
-#pragma unroll
-        for (int s = 0; s < STEPS; s++) {
-            const AoTap &e = tab.t[k * STEPS + s];
-            const float4 wa = e.wa, wb = e.wb;   // two 16-byte constant loads
-            const float *c = c0 + e.off;
-            O = fmaf(wa.x, c[0], O);
-            O = fmaf(wa.y, c[1], O);
-            O = fmaf(wa.z, c[sy], O);
-            O = fmaf(wa.w, c[sy + 1], O);
-            O = fmaf(wb.x, c[sz], O);
-            O = fmaf(wb.y, c[sz + 1], O);
-            O = fmaf(wb.z, c[sz + sy], O);
-            O = fmaf(wb.w, c[sz + sy + 1], O);
-        }
-        occ += fminf(1.0f, O);
-    }
-    field[vx + (int64_t)dx * (vy + (int64_t)dy * vz)] = 1.0f - occ / (float)rays;
-}
 
 // Two voxels per thread: a block covers 64 x 4 x 2 voxels, a thread the x
 // neighbours 2i and 2i + 1, whose trilinear corners share a column (the
 // upper x corners of the first are the lower ones of the second), so a tap
 // costs 12 shared loads for two voxels instead of 16. Even and odd tile
 // columns are stored in separate planes, so a warp's loads stay on distinct
-// banks. Each voxel sums its taps in the same order as the tiled kernel.
+// banks. The density of the tile grown by H cells per side (zero outside the
+// grid) is staged once per block; the stencil (corner column offsets and
+// trilinear weights) comes from the constant bank. O is not cut off at 1:
+// min(1, O) is the same either way since density >= 0.
 constexpr int AOP_X = 64, AOP_Y = 4, AOP_Z = 2;
 
 struct AoPairTap {
-    float4 wa, wb;         // corner weights, as AoTap
+    float4 wa, wb;         // corner (x, y, z) bits -> weight (bit 0 x, bit 1 y, bit 2 z): corners 0-3, 4-7
     int32_t off[3];        // per corner column d = 0, 1, 2: plane * plane size + offset in the plane
     int32_t pad;
 };
@@ -496,8 +443,6 @@ extern "C" lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, flo
     if ((st = ensure_stage_in(ctx, tb)) != LVR_OK) return st;
     LVR_CUDA(ctx, cudaMemcpyAsync(ctx->stage_in, tab.data(), tb, cudaMemcpyHostToDevice, ctx->stream));
     const int H = steps + 1;   // samples reach floor(s d) in [-steps, steps] plus one corner
-    const int TX = AOT_X + 2 * H, TY = AOT_Y + 2 * H, TZ = AOT_Z + 2 * H;
-    const size_t tile_bytes = (size_t)TX * TY * TZ * 4;
     const int PX = AOP_X + 2 * H, PY = AOP_Y + 2 * H, PZ = AOP_Z + 2 * H, PXh = (PX + 1) / 2;
     const size_t pair_bytes = (size_t)2 * PXh * PY * PZ * 4;
     if (steps == 5 && pair_bytes <= 200 * 1024 && tab.size() <= (size_t)AOT_MAX_TAPS) {
@@ -522,24 +467,6 @@ extern "C" lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, flo
                                            (int)pair_bytes));
         const dim3 grid((dm[0] + AOP_X - 1) / AOP_X, (dm[1] + AOP_Y - 1) / AOP_Y, (dm[2] + AOP_Z - 1) / AOP_Z);
         ao_field_pair_kernel<5><<<grid, AOP_X / 2 * AOP_Y * AOP_Z, pair_bytes, ctx->stream>>>(
-            lod->dens[0], dm[0], dm[1], dm[2], taps, rays, H, lod->aof);
-    } else if (steps == 5 && tile_bytes <= 48 * 1024 && tab.size() <= (size_t)AOT_MAX_TAPS) {
-        static AoTaps taps;   // host staging of the kernel parameter (copied at launch)
-        static std::mutex mu;
-        std::lock_guard<std::mutex> lk(mu);
-        for (size_t i = 0; i < tab.size(); i++) {
-            const AoStep &e = tab[i];
-            AoTap &t = taps.t[i];
-            t.off = e.ix + TX * (e.iy + TY * e.iz);
-            float w[8];
-            for (int c = 0; c < 8; c++)
-                w[c] = (c & 1 ? e.fx : 1.0f - e.fx) * (c & 2 ? e.fy : 1.0f - e.fy) * (c & 4 ? e.fz : 1.0f - e.fz);
-            t.wa = make_float4(w[0], w[1], w[2], w[3]);
-            t.wb = make_float4(w[4], w[5], w[6], w[7]);
-            t.pad[0] = t.pad[1] = t.pad[2] = 0;
-        }
-        const dim3 grid((dm[0] + AOT_X - 1) / AOT_X, (dm[1] + AOT_Y - 1) / AOT_Y, (dm[2] + AOT_Z - 1) / AOT_Z);
-        ao_field_tile_kernel<5><<<grid, AOT_X * AOT_Y * AOT_Z, tile_bytes, ctx->stream>>>(
             lod->dens[0], dm[0], dm[1], dm[2], taps, rays, H, lod->aof);
     } else {
         const unsigned g = grid1d(n, 256) > 65535 ? 65535 : grid1d(n, 256);
