@@ -140,12 +140,6 @@ ao_field_kernel(const float4 *__restrict__ pk, int dx, int dy, int dz, const AoS
     }
 }
 
-// The same field with the density staged per block: a block takes a tile
-// of 32 x 4 x 2 voxels and copies the level-0 density of the tile grown by
-// H cells per side (zero outside the grid) into shared memory; the samples
-// then read shared memory, the stencil the constant bank (same values, same
-// lerps: identical results).
-
 constexpr int AOT_MAX_TAPS = 640;                  // stencil entries passed as a kernel parameter
 
 // Two voxels per thread: a block covers 64 x 4 x 2 voxels, a thread the x
