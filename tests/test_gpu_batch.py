@@ -181,3 +181,21 @@ def test_autotune_picks_a_candidate(env, sets):
     ms = r["ms"]
     assert all(m > 0 for m in ms)           # both layouts available: every candidate ran
     assert min(ms) == ms[r["layout"] * 4 + [(8, 4), (4, 8), (16, 2), (32, 1)].index(r["tile"])]
+
+
+def test_batch_with_rep_line_shadows(env, sets):
+    """Views with hard shadows against representative lines run in a batch
+    of their own kernel variant and equal their single renders bit for bit;
+    mixing them with soft-shadow views in one batch is refused."""
+    lvr, O, ctx, dev = env
+    for st in sets:
+        lvr.lvr_lod_rep_lines(ctx, st.glod, st.gls)
+    ents, singles = _entries(env, sets, dict(ert_alpha=0.99, ao_mode=1, shadow_level=1))
+    b = lvr.lvr_batch_create(ctx, ents)
+    b.render()
+    ctx.sync()
+    for e, ref in zip(ents, singles):
+        assert np.array_equal(e[5].cpu().numpy(), ref)
+    soft = _entries(env, sets, dict(ert_alpha=0.99, shadows=True, ao_mode=1))[0]
+    with pytest.raises(lvr.LVRError):
+        lvr.lvr_batch_create(ctx, [ents[0], soft[1]])
