@@ -565,7 +565,39 @@ def batched(args, lvr, synth, ctx, dev, stream, model):
     e1.record(stream)
     e1.synchronize()
     seq_ms = e0.elapsed_time(e1) / reps
+
+    # many small views (256 x 256, the two smaller sets): where one launch per
+    # view leaves the GPU partly idle, and the queue keeps it full
+    small = []
+    for i in range(128):
+        ls, lod, res, rad, _ = sets[i % 2]
+        cam = synth.orbit_views(1, (res,) * 3, [(256, 256)], seed=900 + i)[0]
+        view = lvr.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], 256, 256, cam["light_dir"])
+        small.append((ls, lod, view, lvr.make_desc(rad, tf, ert_alpha=ERT, ao_mode=2, tile=tune["tile"],
+                                                    layout=tune["layout"]), model,
+                      torch.empty((256, 256, 4), dtype=torch.float32, device=dev)))
+    bs = lvr.lvr_batch_create(ctx, small)
+    bs.render()
+    e0.record(stream)
+    for _ in range(reps):
+        bs.render()
+    e1.record(stream)
+    e1.synchronize()
+    small_batch_ms = e0.elapsed_time(e1) / reps
+    for (ls, lod, view, desc, m, out) in small:
+        lvr.lvr_render(ctx, ls, lod, view, desc, out, ao_model=m)
+    e0.record(stream)
+    for _ in range(reps):
+        for (ls, lod, view, desc, m, out) in small:
+            lvr.lvr_render(ctx, ls, lod, view, desc, out, ao_model=m)
+    e1.record(stream)
+    e1.synchronize()
+    small_seq_ms = e0.elapsed_time(e1) / reps
+    bs.free()
     return {
+        "small_views": {"views": len(small), "size": [256, 256], "sets": "64^3/20k and 256^3/100k",
+                        "batch_ms": round(small_batch_ms, 3), "sequential_ms": round(small_seq_ms, 3),
+                        "speedup_vs_sequential": round(small_seq_ms / small_batch_ms, 3)},
         "config": "config 5: 64 views (256^2 to 3840x2160) over three line sets (64^3/20k, 256^3/100k, 512^3/2M "
                   "lines x 150 vertices, r = 0.2/0.15/0.1), transparent (ERT 0.99) with learned AO, one persistent "
                   "launch from a CUDA graph",
