@@ -344,13 +344,22 @@ def raster_comparison(lvr, ctx, stream, dev, xyz, attr, offs, gdesc, sig, view, 
 # ---------------------------------------------------------------- camera at rest (Sec. 4.1)
 def still_frame(lvr, ctx, stream, dev, xyz, attr, offs, gdesc, sig, view, tf, layout, tile, out):
     """The headline frame with the camera at rest: every visited voxel also
-    tests its 26 neighbours' segments (one hit per line id per voxel)."""
+    tests those of its 26 neighbours' segments that reach into it (its
+    neighbour list, built once per line set and radius), and blends one hit
+    per line id per voxel."""
+    import time
+
     import torch
     s = lvr.lvr_voxelize(ctx, xyz, attr, offs, gdesc())
     if layout:
         lvr.lvr_lineset_layout(ctx, s, layout)
     lod = lvr.lvr_build_lod(ctx, s, LEVELS, sig)
-    res = {}
+    # the neighbour lists: one build per line set and radius (it reads the
+    # list size back, so it is timed on the host around a synchronised call)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    lvr.lvr_lineset_neighbours(ctx, s, RADIUS)
+    res = {"neighbour_lists_build_ms": round((time.perf_counter() - t0) * 1e3, 3)}
     for name, still in (("moving", False), ("still", True)):
         d = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0,
                           tile=tile, layout=layout, still=still)
@@ -614,7 +623,7 @@ def batched(args, lvr, synth, ctx, dev, stream, model):
 
 # voxelise: count, 3 scan kernels, scatter, 2 sort kernels; LoD: 1 + 2 pooling + 3 packing; render: 1
 LAUNCHES_PER_STEP = 7 + 3 + 3 + 1
-KERNEL_VERSION = "render-v5"
+KERNEL_VERSION = "render-v6"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_kernel_traffic_c2_1080p.md")
 
 

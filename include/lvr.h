@@ -218,6 +218,19 @@ void lvr_free_lod(lvr_lod *lod);
 #define LVR_LAYOUT_AOS16 1
 lvr_status lvr_lineset_layout(lvr_ctx *ctx, lvr_lineset *ls, int layout);
 
+/* ------------------------------------------------------------------ camera at rest
+ * Neighbour lists for the camera-at-rest mode (render desc `still`, Sec.
+ * 4.1): per voxel, every segment of its 3 x 3 x 3 neighbourhood (itself
+ * included) whose box, grown by the tube radius plus a rounding margin of
+ * 1e-4 radius + 1e-5, reaches into the voxel. A tube whose box misses a
+ * voxel cannot enter it, so testing only these gives the image the search
+ * over all 26 neighbours gives. Kept in the line set (8 bytes per entry plus
+ * 4 per voxel) and used by every later lvr_render at rest with a radius up
+ * to `radius`; lvr_render builds them itself when they are missing or were
+ * built for a smaller radius. Returns LVR_EOVERFLOW (nothing kept) when the
+ * lists would hold more than 2^32 - 1 entries. Synchronises the stream. */
+lvr_status lvr_lineset_neighbours(lvr_ctx *ctx, lvr_lineset *ls, float radius);
+
 /* ------------------------------------------------------------------ rendering
  * Secs. 4-5. One ray per pixel (pinhole camera, pixel centres, row 0 at the
  * top) is traversed through the grid by 3D-DDA; the segments stored in each
@@ -273,13 +286,17 @@ typedef struct lvr_render_desc {
                               segments of its 26 neighbours (a hit still belongs to the voxel
                               holding its entry point; no tube piece is missed for radii up to
                               half a voxel) and blends only the first hit of each 5-bit line id
-                              (curve index mod 32) per voxel. Not with ao_mode 2 or batches. */
+                              (curve index mod 32) per voxel. Reads the line set's neighbour
+                              lists (lvr_lineset_neighbours; built on first use, the one call
+                              that then allocates and synchronises). Not with ao_mode 2 or
+                              batches. */
     int32_t shadow_level;  /* shadows 2: LoD level whose representative lines cast shadows */
 } lvr_render_desc;
 
 /* rgba: host or device float32 [h * w * 4] for the crop rectangle (row-major,
  * row 0 = top of the crop). counters: NULL, or host or device uint64 [4]
- * receiving voxels visited, records tested, LoD trilinear samples (with shadows 2 plus
+ * receiving voxels visited, records tested (at rest: the neighbour-list
+ * entries of the visited voxels), LoD trilinear samples (with shadows 2 plus
  * the representative-line cells tested) and
  * composited hits over the whole rectangle (costs one extra reduction).
  * `lod` may be NULL unless shadows or AO are on; `ao` may be NULL unless

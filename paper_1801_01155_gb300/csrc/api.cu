@@ -239,5 +239,7 @@ extern "C" void lvr_free_lineset(lvr_lineset *ls) {
     dev_free(ctx, ls->rec);
     dev_free(ctx, ls->key);
     dev_free(ctx, ls->rec16);
+    dev_free(ctx, ls->halo_off);
+    dev_free(ctx, ls->halo);
     delete ls;
 }

@@ -57,6 +57,13 @@ struct lvr_lineset {
     uint64_t *rec = nullptr;      // [nseg] packed segment records
     uint64_t *key = nullptr;      // [nseg] (curve << 32) | ordinal
     void *rec16 = nullptr;        // [nseg] 16-byte records (lvr_lineset_layout), or null
+    // camera at rest (lvr_lineset_neighbours): per voxel, the records of its
+    // 3x3x3 neighbourhood whose grown box reaches into it, as
+    // (neighbour index 0..26 << 32) | record; built for radius^2 <= halo_r2
+    uint32_t *halo_off = nullptr; // [nvox + 1], or null
+    uint64_t *halo = nullptr;     // [halo_n]
+    int64_t halo_n = 0;
+    float halo_r2 = 0.0f;
 };
 
 struct lvr_lod {
@@ -163,6 +170,8 @@ int64_t scan_tile_count(int64_t n);
 void scan_counts(cudaStream_t s, const uint32_t *cnt, int64_t n, unsigned long long *tiles, uint32_t *offset,
                  uint32_t *status);
 // Camera basis of a view (float64, rounded to float32); false if degenerate.
+// Build (or keep) the camera-at-rest neighbour lists of `ls` for radius^2 r2.
+lvr_status ensure_neighbours(lvr_ctx *ctx, lvr_lineset *ls, float r2);
 bool camera_basis(const lvr_view *view, float F[3], float R[3], float U[3], float *th, float *tw, float Lt[3]);
 
 inline unsigned grid1d(int64_t n, int block) {

@@ -82,6 +82,8 @@ struct RenderParams {
     int32_t learned;
     const float *aof;             // ao_mode 3: spherical per-voxel AO field (level-0 voxels), else null
     int32_t still;                // camera at rest: neighbouring voxels, one hit per line id
+    const uint32_t *halo_off;     // camera at rest: per voxel its neighbour-list entries
+    const uint64_t *halo;         //   (neighbour << 32) | record
     // shadows 2: representative lines of one LoD level (Sec. 5.2, first approach)
     const uint64_t *rep;
     int32_t rep_dims[3];
@@ -124,6 +126,14 @@ __device__ __forceinline__ Vec face_point(uint32_t face, uint32_t u, uint32_t v,
     const float side = (face & 1u) ? 1.0f : 0.0f;
     const float cu = ((float)u + 0.5f) * invN, cv = ((float)v + 0.5f) * invN;
     return {ax == 0 ? side : cu, ax == 1 ? side : (ax == 0 ? cu : cv), ax == 2 ? side : cv};
+}
+
+// Camera at rest: rounding margin of the neighbour lists' box cull: sqrt(r2) x (1 + 1e-4) + 1e-5.
+__device__ __forceinline__ float cull_margin(float r2) { return sqrtf(r2) * 1.0001f + 1e-5f; }
+
+// Neighbour `nc` (0..26, x fastest) of a voxel as an offset in voxels.
+__device__ __forceinline__ Vec neighbour_offset(uint32_t nc) {
+    return mk((float)((int)(nc % 3u) - 1), (float)((int)((nc / 3u) % 3u) - 1), (float)((int)(nc / 9u) - 1));
 }
 
 // First entry of ray p + s D into the sphere |x - c| = r; INF if none.
@@ -322,14 +332,15 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
         }
         se = fmaxf(se, 0.0f);
         const uint32_t vid = (uint32_t)ray.v[0] + (uint32_t)P.res[0] * ((uint32_t)ray.v[1] + (uint32_t)P.res[1] * (uint32_t)ray.v[2]);
-        const uint32_t beg = __ldg(P.offset + vid), end = __ldg(P.offset + vid + 1);
+        // with the camera at rest (reading R2) the candidates are the voxel's
+        // neighbour list: its own records and its neighbours' that reach into it
+        const uint32_t *const offs = SM::kStill ? P.halo_off : P.offset;
+        const uint32_t beg = __ldg(offs + vid), end = __ldg(offs + vid + 1);
         if (!ray.resume) {
             nvox++;
-            if constexpr (!SM::kStill) nrec += end - beg;
+            nrec += end - beg;
         }
-        // with the camera at rest (reading R2) every voxel is searched: its
-        // neighbours' tubes may reach into it
-        if (SM::kStill || end > beg) {
+        if (end > beg) {
             // accurate local origin: eye + T D - v in float-float, rounded once
             float po[3];
 #pragma unroll
@@ -379,31 +390,17 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                 nh++;
             };
             if constexpr (SM::kStill) {
-                const float rm = sqrtf(P.r2) * 1.0001f + 1e-5f;
-                for (int nc = 0; nc < 27; nc++) {
-                    const int dx = nc % 3 - 1, dy = (nc / 3) % 3 - 1, dz = nc / 9 - 1;
-                    const int X = ray.v[0] + dx, Y = ray.v[1] + dy, Z = ray.v[2] + dz;
-                    if ((unsigned)X >= (unsigned)P.res[0] || (unsigned)Y >= (unsigned)P.res[1] ||
-                        (unsigned)Z >= (unsigned)P.res[2])
-                        continue;
-                    const uint32_t nv = (uint32_t)X + (uint32_t)P.res[0] * ((uint32_t)Y + (uint32_t)P.res[1] * (uint32_t)Z);
-                    const uint32_t nb = __ldg(P.offset + nv), ne = __ldg(P.offset + nv + 1);
-                    if (!ray.resume) nrec += ne - nb;
-                    const Vec o = mk((float)dx, (float)dy, (float)dz);
-                    for (uint32_t k = nb; k < ne; k++) {
-                        Vec a, b;
-                        uint32_t attr;
-                        fetch_record<SM::kLayout>(P, k, a, b, attr);
-                        // the neighbour's face points in this voxel's frame (exact: binary fractions + integers)
-                        a = mk(a.x + o.x, a.y + o.y, a.z + o.z);
-                        b = mk(b.x + o.x, b.y + o.y, b.z + o.z);
-                        // a tube whose box (segment box grown by the radius, with a margin for
-                        // rounding) misses this voxel cannot have its entry point in it
-                        if (fmaxf(a.x, b.x) + rm < 0.0f || fminf(a.x, b.x) - rm > 1.0f || fmaxf(a.y, b.y) + rm < 0.0f ||
-                            fminf(a.y, b.y) - rm > 1.0f || fmaxf(a.z, b.z) + rm < 0.0f || fminf(a.z, b.z) - rm > 1.0f)
-                            continue;
-                        stage(capsule_entry(p, ray.D, a, b, P.r2), k, ((attr >> 8) << 5) | (uint32_t)nc);
-                    }
+                for (uint32_t j = beg; j < end; j++) {
+                    const uint64_t e = __ldg(P.halo + j);
+                    const uint32_t k = (uint32_t)e, nc = (uint32_t)(e >> 32);
+                    Vec a, b;
+                    uint32_t attr;
+                    fetch_record<SM::kLayout>(P, k, a, b, attr);
+                    // the neighbour's face points in this voxel's frame (exact: binary fractions + integers)
+                    const Vec o = neighbour_offset(nc);
+                    a = mk(a.x + o.x, a.y + o.y, a.z + o.z);
+                    b = mk(b.x + o.x, b.y + o.y, b.z + o.z);
+                    stage(capsule_entry(p, ray.D, a, b, P.r2), k, ((attr >> 8) << 5) | nc);
                 }
             } else {
                 for (uint32_t k = beg; k < end; k++) {
@@ -421,8 +418,7 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                 uint32_t attr;
                 fetch_record<SM::kLayout>(P, k, a, b, attr);
                 if constexpr (SM::kStill) {
-                    const int nc = sm.sa[q][tid] & 31;
-                    const Vec o = mk((float)(nc % 3 - 1), (float)((nc / 3) % 3 - 1), (float)(nc / 9 - 1));
+                    const Vec o = neighbour_offset(sm.sa[q][tid] & 31u);
                     a = mk(a.x + o.x, a.y + o.y, a.z + o.z);
                     b = mk(b.x + o.x, b.y + o.y, b.z + o.z);
                     ray.idmask |= 1u << (attr >> 8);
@@ -1218,6 +1214,117 @@ bool camera_basis(const lvr_view *view, float F[3], float R[3], float U[3], floa
     return true;
 }
 
+// ------------------------------------------------------------------ camera at rest: neighbour lists
+// One thread per voxel: the records of the 27 voxels around it (neighbour
+// order x fastest, records ascending) whose segment box grown by the cull
+// margin reaches into it. Count pass (halo null): per voxel the number into
+// cnt and the sum into *total; fill pass: the entries at halo + hoff[voxel].
+// Face points and the offsets are binary fractions and small integers, so
+// the shifted end points are exact and the cull decides as the at-rest
+// search over all neighbours would.
+__global__ void __launch_bounds__(256) neighbours_kernel(const uint32_t *__restrict__ offset,
+                                                         const uint64_t *__restrict__ rec, int rx, int ry, int rz,
+                                                         float invN, float r2, uint32_t *__restrict__ cnt,
+                                                         unsigned long long *total,
+                                                         const uint32_t *__restrict__ hoff,
+                                                         uint64_t *__restrict__ halo) {
+    const int64_t nvox = (int64_t)rx * ry * rz;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t n = 0;
+    if (v < nvox) {
+        const float rm = cull_margin(r2);
+        const int x = (int)(v % rx), y = (int)((v / rx) % ry), z = (int)(v / ((int64_t)rx * ry));
+        uint64_t *out = halo ? halo + hoff[v] : nullptr;
+        for (uint32_t nc = 0; nc < 27; nc++) {
+            const int X = x + (int)(nc % 3u) - 1, Y = y + (int)((nc / 3u) % 3u) - 1, Z = z + (int)(nc / 9u) - 1;
+            if ((unsigned)X >= (unsigned)rx || (unsigned)Y >= (unsigned)ry || (unsigned)Z >= (unsigned)rz) continue;
+            const int64_t nv = X + (int64_t)rx * (Y + (int64_t)ry * Z);
+            const uint32_t nb = offset[nv], ne = offset[nv + 1];
+            const Vec o = neighbour_offset(nc);
+            for (uint32_t k = nb; k < ne; k++) {
+                const uint64_t r = rec[k];
+                Vec a = face_point(rec_face_in(r), rec_u_in(r), rec_v_in(r), invN);
+                Vec b = face_point(rec_face_out(r), rec_u_out(r), rec_v_out(r), invN);
+                a = mk(a.x + o.x, a.y + o.y, a.z + o.z);
+                b = mk(b.x + o.x, b.y + o.y, b.z + o.z);
+                if (fmaxf(a.x, b.x) + rm < 0.0f || fminf(a.x, b.x) - rm > 1.0f || fmaxf(a.y, b.y) + rm < 0.0f ||
+                    fminf(a.y, b.y) - rm > 1.0f || fmaxf(a.z, b.z) + rm < 0.0f || fminf(a.z, b.z) - rm > 1.0f)
+                    continue;
+                if (out) out[n] = (uint64_t)nc << 32 | k;
+                n++;
+            }
+        }
+        if (!halo) cnt[v] = n;
+    }
+    if (!halo) {
+        const unsigned long long w = __reduce_add_sync(0xffffffffu, n);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, w);
+    }
+}
+
+lvr_status ensure_neighbours(lvr_ctx *ctx, lvr_lineset *ls, float r2) {
+    if (ls->halo_off && ls->halo_r2 >= r2) return LVR_OK;
+    cudaStream_t s = ctx->stream;
+    dev_free(ctx, ls->halo_off);
+    dev_free(ctx, ls->halo);
+    ls->halo_off = nullptr;
+    ls->halo = nullptr;
+    ls->halo_n = 0;
+    ls->halo_r2 = 0.0f;
+    const int64_t nvox = ls->nvox;
+    const size_t cnt_bytes = ((size_t)nvox * 4 + 255) & ~(size_t)255;
+    lvr_status st = ensure_scratch(ctx, cnt_bytes + (size_t)scan_tile_count(nvox) * 8);
+    if (st != LVR_OK) return st;
+    uint32_t *cnt = (uint32_t *)ctx->scratch;
+    unsigned long long *tiles = (unsigned long long *)((char *)ctx->scratch + cnt_bytes);
+    uint32_t *hoff = nullptr;
+    if ((st = dev_alloc(ctx, (void **)&hoff, (size_t)(nvox + 1) * 4)) != LVR_OK) return st;
+    unsigned long long *total = ctx->d_u64 + 6;
+    LVR_CUDA(ctx, cudaMemsetAsync(total, 0, 8, s));
+    const unsigned grid = grid1d(nvox, 256);
+    neighbours_kernel<<<grid, 256, 0, s>>>(ls->offset, ls->rec, ls->res[0], ls->res[1], ls->res[2],
+                                           1.0f / (float)ls->bins, r2, cnt, total, nullptr, nullptr);
+    LVR_CUDA(ctx, cudaGetLastError());
+    // the total decides overflow here, so the scan's overflow bit goes to a
+    // word of its own instead of the context's status
+    scan_counts(s, cnt, nvox, tiles, hoff, ctx->d_status + 2);
+    LVR_CUDA(ctx, cudaGetLastError());
+    unsigned long long *h = (unsigned long long *)ctx->h_pinned;
+    LVR_CUDA(ctx, cudaMemcpyAsync(h, total, 8, cudaMemcpyDeviceToHost, s));
+    LVR_CUDA(ctx, cudaStreamSynchronize(s));
+    const unsigned long long n = h[0];
+    if (n > 0xffffffffull) {
+        dev_free(ctx, hoff);
+        return set_err(ctx, LVR_EOVERFLOW, "neighbour lists: %llu entries (more than 2^32 - 1)", n);
+    }
+    uint64_t *halo = nullptr;
+    if (n > 0 && (st = dev_alloc(ctx, (void **)&halo, (size_t)n * 8)) != LVR_OK) {
+        dev_free(ctx, hoff);
+        return st;
+    }
+    if (n > 0) {
+        neighbours_kernel<<<grid, 256, 0, s>>>(ls->offset, ls->rec, ls->res[0], ls->res[1], ls->res[2],
+                                               1.0f / (float)ls->bins, r2, nullptr, nullptr, hoff, halo);
+        LVR_CUDA(ctx, cudaGetLastError());
+    }
+    ls->halo_off = hoff;
+    ls->halo = halo;
+    ls->halo_n = (int64_t)n;
+    ls->halo_r2 = r2;
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_lineset_neighbours(lvr_ctx *ctx, lvr_lineset *ls, float radius) {
+    if (!ctx) return LVR_EINVAL;
+    if (!ls) return set_err(ctx, LVR_EINVAL, "lvr_lineset_neighbours: null line set");
+    if (!(radius > 0.0f) || !(radius < 1e3f)) return set_err(ctx, LVR_EINVAL, "radius must be > 0");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    lvr_status st = ensure_neighbours(ctx, ls, radius * radius);
+    if (st != LVR_OK) return st;
+    LVR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LVR_OK;
+}
+
 static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod, const lvr_view *view,
                         const lvr_render_desc *desc, lvr_ao_model *ao, RenderParams &P, bool judge = false) {
     if (!ls || !view || !desc) return set_err(ctx, LVR_EINVAL, "lvr_render: null argument");
@@ -1294,6 +1401,13 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
     P.learned = desc->ao_mode == 2 ? 1 : 0;
     P.aof = desc->ao_mode == 3 && !judge ? lod->aof : nullptr;
     P.still = desc->still ? 1 : 0;
+    if (P.still) {
+        // the line set's neighbour lists are a cache inside the handle
+        lvr_status st = ensure_neighbours(ctx, const_cast<lvr_lineset *>(ls), P.r2);
+        if (st != LVR_OK) return st;
+        P.halo_off = ls->halo_off;
+        P.halo = ls->halo;
+    }
     if (judge) P.shadows = 0;   // the judge keeps the learned AO where the visibility would go
     P.nrays = (P.shadows ? 1 : 0) + P.ao_rays + P.learned + (P.aof ? 1 : 0);
     P.ao_radius = desc->ao_radius;

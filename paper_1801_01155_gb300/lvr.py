@@ -114,6 +114,7 @@ _SIGS = {
     "lvr_voxelize_static": ([_vp, _vp, _vp, _i64, _i64, C.POINTER(GridDesc), _vp, _vp, _vp, _i64,
                              C.POINTER(_i64), _vp], C.c_int),
     "lvr_lineset_layout": ([_vp, _vp, C.c_int], C.c_int),
+    "lvr_lineset_neighbours": ([_vp, _vp, C.c_float], C.c_int),
     "lvr_lod_ao_field": ([_vp, _vp, C.c_int, C.c_float], C.c_int),
     "lvr_export_ao_field": ([_vp, _vp, _vp], C.c_int),
     "lvr_lod_rep_lines": ([_vp, _vp, _vp], C.c_int),
@@ -502,6 +503,11 @@ def ao_train_desc(n_samples, epochs, batch, lr, seed, render: RenderDesc, view_s
 # ---------------------------------------------------------------- record layouts, batches, autotuner
 def lvr_lineset_layout(ctx: Context, ls: LineSet, layout: int):
     _check(ctx.handle, _L.lvr_lineset_layout(ctx.handle, ls.handle, int(layout)))
+
+
+def lvr_lineset_neighbours(ctx: Context, ls: LineSet, radius: float):
+    """Camera-at-rest neighbour lists of `ls` for tube radii up to `radius`."""
+    _check(ctx.handle, _L.lvr_lineset_neighbours(ctx.handle, ls.handle, float(radius)))
 
 
 class Batch:
