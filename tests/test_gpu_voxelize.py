@@ -171,6 +171,52 @@ def test_512_grid_bit_exact(env):
     S.compare_lineset(lvr, ctx, S.gpu_lineset(lvr, ctx, ls, dev, **g), S.oracle_lineset(O, ls, **g))
 
 
+def test_512_full_set_sampled_curves(env):
+    """The batched workload's largest set at full size: 2M streamlines x 150
+    vertices (seed 23) in a 512^3 grid (N = 32), voxelised in one call as the
+    benchmark does. Every segment of 2000 sampled curves, located in the full
+    voxelisation, equals the oracle's voxelisation of those curves alone, bit
+    for bit (voxel, fields, ordinal, canonical order), and each sampled curve
+    has exactly the segments the oracle gives it."""
+    import torch
+
+    from paper_1801_01155_gb300 import synth
+    lvr, O, ctx, dev = env
+    n, nv = 2_000_000, 150
+    xyz, attr, offs = synth.make_streamlines_device(n, nv, 23, dev)
+    g = dict(res=512, bins=32, origin=(0.0, 0.0, 0.0), scale=512.0,
+             attr_min=float(attr.min()), attr_max=float(attr.max()))
+    gls = lvr.lvr_voxelize(ctx, xyz, attr, offs, lvr.grid_desc(**g))
+    inf = gls.info()
+    nseg, nvox = int(inf.n_segments), int(inf.n_voxels)
+    assert nseg > 300_000_000
+    off = torch.empty(nvox + 1, dtype=torch.int32, device=dev)
+    fields = torch.empty((nseg, 8), dtype=torch.uint8, device=dev)
+    curve = torch.empty(nseg, dtype=torch.int32, device=dev)
+    ordn = torch.empty(nseg, dtype=torch.int32, device=dev)
+    lvr.lvr_export_lineset(ctx, gls, off, fields, curve, ordn)
+    ctx.sync()
+    gls.free()
+    sample = np.sort(np.random.default_rng(7).choice(n, 2000, replace=False))
+    pick = torch.isin(curve, torch.from_numpy(sample.astype(np.int32)).to(dev)).nonzero().squeeze(1)
+    gvox = torch.searchsorted(off[1:].to(torch.int64), pick, right=True).cpu().numpy()
+    gfields = fields[pick].cpu().numpy()
+    gcurve = curve[pick].cpu().numpy().astype(np.int64)
+    gord = ordn[pick].cpu().numpy()
+    del fields, curve, ordn, off
+    sub = torch.from_numpy(sample).to(dev)
+    sxyz = xyz.view(n, nv, 3)[sub].reshape(-1, 3).cpu().numpy()
+    sattr = attr.view(n, nv)[sub].reshape(-1).cpu().numpy()
+    soffs = np.arange(0, (len(sample) + 1) * nv, nv, dtype=np.int64)
+    o = O.VoxSet(sxyz, sattr, soffs, O.make_grid(**g)).export()
+    ovox = np.repeat(np.arange(nvox, dtype=np.int64), np.diff(o["offset"].astype(np.int64)))
+    assert len(ovox) == len(gvox) > 100_000
+    np.testing.assert_array_equal(gvox, ovox)
+    np.testing.assert_array_equal(gfields, o["fields"])
+    np.testing.assert_array_equal(gcurve, sample[o["curve"].astype(np.int64)])
+    np.testing.assert_array_equal(gord, o["ordinal"])
+
+
 @pytest.mark.parametrize("R,levels", [(32, 3), (37, 4), (256, 3)])
 def test_lod(env, R, levels):
     """Counts bit-exact. Float32 sums of n positive terms carry a relative error
