@@ -206,6 +206,132 @@ __device__ __forceinline__ void mlp_tile(const Net &net, const __nv_bfloat16 *vt
     ao_hi = 1.0f / (1.0f + __expf(-(hi + b4)));
 }
 
+// ---- the same model with short code: activations in shared memory
+// A warp's 16 x 64 bf16 activation tile: rows of 128 bytes whose 16-byte
+// chunks (8 features each) are XOR-swizzled by the row, so the ldmatrix row
+// reads and the fragment stores both touch distinct banks.
+constexpr int ACT_BYTES = 16 * 128;
+
+__device__ __forceinline__ int act_off(int row, int chunk) { return row * 128 + ((chunk ^ (row & 7)) << 4); }
+
+// Per-hit inputs of one hit (16 bf16, input 15 zero) into row `row` of the tile.
+__device__ __forceinline__ void store_hit_inputs_act(const float h[NHIT], uint8_t *act, int row) {
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 7; i++) w[i] = pack_bf16x2(h[2 * i], h[2 * i + 1]);
+    w[7] = pack_bf16x2(h[14], 0.0f);
+    *reinterpret_cast<uint4 *>(act + act_off(row, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(act + act_off(row, 1)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// A fragments of k-step k (features 16k .. 16k + 15) of the tile: matrices
+// (rows 0-7 | 8-15) x (features 16k .. 16k + 7 | 16k + 8 .. 16k + 15).
+__device__ __forceinline__ void act_a(const uint8_t *act, int k, uint32_t a[4]) {
+    const int lane = threadIdx.x & 31;
+    const int row = (lane & 7) + ((lane >> 3) & 1) * 8, chunk = 2 * k + (lane >> 4);
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(act + act_off(row, chunk));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr));
+}
+
+// ReLU + bf16 of one n-tile's accumulators (features 8n .. 8n + 7) into the tile.
+__device__ __forceinline__ void act_store(uint8_t *act, int n, const float acc[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    *reinterpret_cast<uint32_t *>(act + act_off(g, n) + 4 * t) =
+        pack_bf16x2(fmaxf(acc[0], 0.0f), fmaxf(acc[1], 0.0f));
+    *reinterpret_cast<uint32_t *>(act + act_off(g + 8, n) + 4 * t) =
+        pack_bf16x2(fmaxf(acc[2], 0.0f), fmaxf(acc[3], 0.0f));
+}
+
+// The model for the 16 hits whose per-hit inputs are in rows 0..15 of the
+// warp's tile (vt_lo / vt_hi and the result lanes as in mlp_tile). Each layer
+// takes its input fragments into registers, then walks its 8 n-tiles in a
+// loop that is not unrolled, writing each n-tile's activations back into the
+// tile: the code stays small and few registers are live. Every mma, rounding
+// and sum is the one mlp_tile performs, in the same order, so the results are
+// identical.
+__device__ __forceinline__ void mlp_tile_smem(const Net &net, const __nv_bfloat16 *vt_lo,
+                                              const __nv_bfloat16 *vt_hi, uint8_t *act, float &ao_lo,
+                                              float &ao_hi) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    {   // layer 1: b1 + voxel term + the per-hit part (one k-step)
+        uint32_t x[4];
+        act_a(act, 0, x);
+        __syncwarp();   // every lane holds its inputs before the tile is overwritten
+#pragma unroll 2
+        for (int n = 0; n < 8; n++) {
+            const int f = n * 8 + 2 * t;
+            const float b0 = __ldg(net.b1 + f), b1 = __ldg(net.b1 + f + 1);
+            float lo0 = 0.0f, lo1 = 0.0f, hi0 = 0.0f, hi1 = 0.0f;
+            if (vt_lo) {
+                const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_lo + f));
+                const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&u);
+                lo0 = __bfloat162float(pr.x);
+                lo1 = __bfloat162float(pr.y);
+            }
+            if (vt_hi) {
+                const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_hi + f));
+                const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162 *>(&u);
+                hi0 = __bfloat162float(pr.x);
+                hi1 = __bfloat162float(pr.y);
+            }
+            float acc[4] = {b0 + lo0, b1 + lo1, b0 + hi0, b1 + hi1};
+            const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w1 + (n * 8 + g) * NIN);
+            mma16816(acc, x, __ldg(wr + t), __ldg(wr + t + 4));
+            act_store(act, n, acc);
+        }
+        __syncwarp();
+    }
+    uint32_t a[4][4];
+    {   // layer 2
+#pragma unroll
+        for (int k = 0; k < 4; k++) act_a(act, k, a[k]);
+        __syncwarp();
+#pragma unroll 2
+        for (int n = 0; n < 8; n++) {
+            float acc[4];
+            acc[0] = acc[2] = __ldg(net.b2 + n * 8 + 2 * t);
+            acc[1] = acc[3] = __ldg(net.b2 + n * 8 + 2 * t + 1);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w2 + (n * 8 + g) * NH + k * 16);
+                mma16816(acc, a[k], __ldg(wr + t), __ldg(wr + t + 4));
+            }
+            act_store(act, n, acc);
+        }
+        __syncwarp();
+    }
+    // layer 3, and layer 4 from its fragments: bf16(ReLU(z3)) . w4, summed over the quad
+#pragma unroll
+    for (int k = 0; k < 4; k++) act_a(act, k, a[k]);
+    __syncwarp();   // the tile's last reads are done before the caller reuses it
+    float lo = 0.0f, hi = 0.0f;
+#pragma unroll 2
+    for (int n = 0; n < 8; n++) {
+        float acc[4];
+        acc[0] = acc[2] = __ldg(net.b3 + n * 8 + 2 * t);
+        acc[1] = acc[3] = __ldg(net.b3 + n * 8 + 2 * t + 1);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w3 + (n * 8 + g) * NH + k * 16);
+            mma16816(acc, a[k], __ldg(wr + t), __ldg(wr + t + 4));
+        }
+        const float w0 = __ldg(net.w4 + n * 8 + 2 * t), w1 = __ldg(net.w4 + n * 8 + 2 * t + 1);
+        lo = fmaf(bf16_round(fmaxf(acc[0], 0.0f)), w0, lo);
+        lo = fmaf(bf16_round(fmaxf(acc[1], 0.0f)), w1, lo);
+        hi = fmaf(bf16_round(fmaxf(acc[2], 0.0f)), w0, hi);
+        hi = fmaf(bf16_round(fmaxf(acc[3], 0.0f)), w1, hi);
+    }
+    lo += __shfl_xor_sync(0xffffffffu, lo, 1);
+    lo += __shfl_xor_sync(0xffffffffu, lo, 2);
+    hi += __shfl_xor_sync(0xffffffffu, hi, 1);
+    hi += __shfl_xor_sync(0xffffffffu, hi, 2);
+    const float b4 = __ldg(net.b4);
+    ao_lo = 1.0f / (1.0f + __expf(-(lo + b4)));
+    ao_hi = 1.0f / (1.0f + __expf(-(hi + b4)));
+}
+
 }  // namespace aomlp
 
 struct lvr_ao_model;

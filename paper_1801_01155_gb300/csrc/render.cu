@@ -40,6 +40,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "ao_mlp.cuh"
@@ -293,12 +294,40 @@ struct Smem {
     static constexpr bool kStill = MODE == MODE_STILL;
     float4 tf[BATCH ? 1 : 256];
     float4 hot[BATCH ? 4 : 1][BATCH ? HOT_BYTES / 16 : 1];   // batched: each warp's current view parameters
-    float st[KS][RT];             // staged (t, k) of the current voxel, ascending
-    uint32_t sk[KS][RT];
+    // the staged (t, k) of each lane's current voxel, ascending: slot-major,
+    // lane-minor columns; the single-view learned variant keeps them per
+    // warp, because they are dead while a warp lights its hits and it
+    // overlays the warp's activation tile on its own entries
+    static constexpr bool kActTile = MODE == MODE_LEARNED && !BATCH;
+    struct ColStage {
+        float st[KS][RT];
+        uint32_t sk[KS][RT];
+    };
+    struct WarpStage {
+        union {
+            struct {
+                float st[KS][32];
+                uint32_t sk[KS][32];
+            };
+            __align__(16) uint8_t act[aomlp::ACT_BYTES];
+        };
+    };
+    std::conditional_t<kActTile, WarpStage[RT / 32], ColStage> stage;
+    __device__ __forceinline__ float &st_(int q, int tid) {
+        if constexpr (kActTile) return stage[tid >> 5].st[q][tid & 31];
+        else return stage.st[q][tid];
+    }
+    __device__ __forceinline__ uint32_t &sk_(int q, int tid) {
+        if constexpr (kActTile) return stage[tid >> 5].sk[q][tid & 31];
+        else return stage.sk[q][tid];
+    }
+    // 32 words of warp `warp`'s staging entries (slot 0 of its lanes)
+    __device__ __forceinline__ uint32_t *warp_words(int warp) { return reinterpret_cast<uint32_t *>(&st_(0, warp * 32)); }
     uint16_t sa[MODE == MODE_STILL ? KS : 1][MODE == MODE_STILL ? RT : 2];   // at rest: (line id << 5) | neighbour
     float slot[kVid ? NF : NF - 1][KS][RT];
     uint8_t item[4][32 * KS];     // per warp: (owner lane, slot) of each collected hit
-    __align__(16) __nv_bfloat16 hin[MODE == MODE_LEARNED || MODE == MODE_JUDGE ? 4 * 16 * aomlp::HIN_STRIDE : 8];   // per warp: per-hit inputs of 16 hits
+    // judge and batched learned variant, per warp: per-hit inputs of 16 hits
+    __align__(16) __nv_bfloat16 hin[MODE == MODE_JUDGE || (MODE == MODE_LEARNED && BATCH) ? 4 * 16 * aomlp::HIN_STRIDE : 8];
 };
 
 struct Ray {
@@ -365,26 +394,26 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                     int ns = nh < room ? nh : room;
                     for (int j = 0; j < ns; j++) {
                         if ((uint32_t)(sm.sa[j][tid] >> 5) != id) continue;
-                        if (!key_after(sm.st[j][tid], sm.sk[j][tid], t, k)) return;   // staged one is first
+                        if (!key_after(sm.st_(j, tid), sm.sk_(j, tid), t, k)) return;   // staged one is first
                         for (int q = j; q + 1 < ns; q++) {                            // drop the staged one
-                            sm.st[q][tid] = sm.st[q + 1][tid];
-                            sm.sk[q][tid] = sm.sk[q + 1][tid];
+                            sm.st_(q, tid) = sm.st_(q + 1, tid);
+                            sm.sk_(q, tid) = sm.sk_(q + 1, tid);
                             sm.sa[q][tid] = sm.sa[q + 1][tid];
                         }
                         nh--;
                         break;
                     }
                 }
-                if (nh < room || t < sm.st[room - 1][tid]) {
+                if (nh < room || t < sm.st_(room - 1, tid)) {
                     int q = nh < room ? nh : room - 1;
-                    while (q > 0 && t < sm.st[q - 1][tid]) {
-                        sm.st[q][tid] = sm.st[q - 1][tid];
-                        sm.sk[q][tid] = sm.sk[q - 1][tid];
+                    while (q > 0 && t < sm.st_(q - 1, tid)) {
+                        sm.st_(q, tid) = sm.st_(q - 1, tid);
+                        sm.sk_(q, tid) = sm.sk_(q - 1, tid);
                         if constexpr (SM::kStill) sm.sa[q][tid] = sm.sa[q - 1][tid];
                         q--;
                     }
-                    sm.st[q][tid] = t;
-                    sm.sk[q][tid] = k;
+                    sm.st_(q, tid) = t;
+                    sm.sk_(q, tid) = k;
                     if constexpr (SM::kStill) sm.sa[q][tid] = (uint16_t)aux;
                 }
                 nh++;
@@ -412,8 +441,8 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
             }
             const int take = nh < room ? nh : room;
             for (int q = 0; q < take; q++) {
-                const float t = sm.st[q][tid];
-                const uint32_t k = sm.sk[q][tid];
+                const float t = sm.st_(q, tid);
+                const uint32_t k = sm.sk_(q, tid);
                 Vec a, b;
                 uint32_t attr;
                 fetch_record<SM::kLayout>(P, k, a, b, attr);
@@ -775,18 +804,18 @@ __device__ __forceinline__ void rep_shadows(const RenderParams &P, SM &sm, int w
     for (int g = lane; g < total; g += 32) {
         RepRay r;
         const int n = rep_ray(P, hit_pos(g), Lt, r) ? rep_pieces(r) : 0;
-        sm.sk[g >> 5][warp * 32 + (g & 31)] = (uint32_t)n;
+        sm.sk_(g >> 5, warp * 32 + (g & 31)) = (uint32_t)n;
         sm.slot[F_V][slot_index(sm, warp, g)][slot_owner(sm, warp, g)] = 1.0f;
     }
     __syncwarp();
-    uint32_t *list = reinterpret_cast<uint32_t *>(&sm.st[0][warp * 32]);
+    uint32_t *list = sm.warp_words(warp);
     for (int round = 0; round < 65536; round++) {
         int K = 0;
         for (int g0 = 0; g0 < total && K < 32; g0 += 32) {
             const int g = g0 + lane;
             bool open = false;
             if (g < total) {
-                const uint32_t s = sm.sk[g >> 5][warp * 32 + (g & 31)];
+                const uint32_t s = sm.sk_(g >> 5, warp * 32 + (g & 31));
                 open = (s >> 16) < (s & 0xffffu);   // a blocked hit's next piece is set past the end
             }
             const unsigned b = __ballot_sync(FULL, open);
@@ -805,7 +834,7 @@ __device__ __forceinline__ void rep_shadows(const RenderParams &P, SM &sm, int w
         uint32_t s = 0;
         if (i < K) {
             g = (int)list[i];
-            s = sm.sk[g >> 5][warp * 32 + (g & 31)];
+            s = sm.sk_(g >> 5, warp * 32 + (g & 31));
             const int piece = (int)(s >> 16) + part, pieces = (int)(s & 0xffffu);
             RepRay r;
             if (piece < pieces && rep_ray(P, hit_pos(g), Lt, r)) vis = rep_piece(P, r, piece, pieces, nsamp);
@@ -819,7 +848,7 @@ __device__ __forceinline__ void rep_shadows(const RenderParams &P, SM &sm, int w
                 sm.slot[F_V][slot_index(sm, warp, g)][slot_owner(sm, warp, g)] = 0.0f;
                 next = pieces;
             }
-            sm.sk[g >> 5][warp * 32 + (g & 31)] = pieces | min(next, pieces) << 16;
+            sm.sk_(g >> 5, warp * 32 + (g & 31)) = pieces | min(next, pieces) << 16;
         }
         __syncwarp();
     }
@@ -850,11 +879,18 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
     }
     if constexpr (MODE == MODE_LEARNED || MODE == MODE_JUDGE) {
         // learned AO (Sec. 5.3 surrogate), 16 hits per step: per-hit inputs
-        // into a shared tile, then the model on tensor cores with the
-        // activations in registers. The judge keeps it in F_V (no shadows
-        // there) beside the traced AO.
+        // into a shared tile, then the model on tensor cores. The single-view
+        // variant keeps the activations in the warp's tile (short code that
+        // shares the instruction cache with the traversal: faster where a
+        // warp lights few hits at a time); the batched variant and the judge
+        // keep them in registers (fully unrolled: faster on dense frames).
+        // Both give the same bits. The judge keeps its result in F_V (no
+        // shadows there) beside the traced AO.
         constexpr int FL = MODE == MODE_JUDGE ? F_V : F_AO;
-        __nv_bfloat16 *h = sm.hin + warp * 16 * aomlp::HIN_STRIDE;
+        constexpr bool kAct = SM::kActTile;
+        __nv_bfloat16 *h = sm.hin + (kAct ? 0 : warp * 16 * aomlp::HIN_STRIDE);
+        uint8_t *act = nullptr;
+        if constexpr (kAct) act = sm.stage[warp].act;
         const uint32_t rx = (uint32_t)P.res[0], ry = (uint32_t)P.res[1];
         for (int g0 = 0; g0 < total; g0 += 16) {
             if (lane < 16) {   // per-hit inputs of hit g0 + lane into row lane
@@ -871,7 +907,8 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
 #pragma unroll
                     for (int k = 0; k < aomlp::NHIT; k++) hx[k] = 0.0f;
                 }
-                aomlp::store_hit_inputs(hx, h + lane * aomlp::HIN_STRIDE);
+                if constexpr (kAct) aomlp::store_hit_inputs_act(hx, act, lane);
+                else aomlp::store_hit_inputs(hx, h + lane * aomlp::HIN_STRIDE);
             }
             __syncwarp();
             const int gl = g0 + (lane >> 2), gh = gl + 8;
@@ -881,7 +918,8 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
             if (gh < total)
                 vhi = P.vterm + (size_t)__float_as_uint(sm.slot[F_VID][slot_index(sm, warp, gh)][slot_owner(sm, warp, gh)]) * 64;
             float lo, hi;
-            aomlp::mlp_tile(P.net, vlo, vhi, h, lo, hi);
+            if constexpr (kAct) aomlp::mlp_tile_smem(P.net, vlo, vhi, act, lo, hi);
+            else aomlp::mlp_tile(P.net, vlo, vhi, h, lo, hi);
             if ((lane & 3) == 0) {
                 const int g = lane >> 2;
                 if (g0 + g < total) sm.slot[FL][slot_index(sm, warp, g0 + g)][slot_owner(sm, warp, g0 + g)] = lo;
@@ -1108,8 +1146,10 @@ __device__ __forceinline__ void flush_stats(const RenderParams &P, int lane, Sta
 }
 
 constexpr int min_blocks(int mode) {
-    return mode == MODE_LEARNED || mode == MODE_JUDGE ? 4 : (mode == MODE_STILL ? 5 : 6);
+    return mode == MODE_JUDGE ? 4 : (mode == MODE_STILL || mode == MODE_LEARNED ? 5 : 6);
 }
+// batched: the learned variant's register-resident model needs 128 registers
+constexpr int min_blocks_batch(int mode) { return mode == MODE_LEARNED ? 4 : min_blocks(mode); }
 
 // One view: a persistent grid takes 32-ray tiles from a global counter.
 template <int MODE, int LAYOUT>
@@ -1143,7 +1183,7 @@ struct BatchParams {
 };
 
 template <int MODE, int LAYOUT>
-__global__ void __launch_bounds__(RT, min_blocks(MODE))
+__global__ void __launch_bounds__(RT, min_blocks_batch(MODE))
 render_batch_kernel(const __grid_constant__ BatchParams B) {
     __shared__ Smem<MODE, LAYOUT, true> sm;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
