@@ -221,10 +221,10 @@ lvr_status lvr_lineset_layout(lvr_ctx *ctx, lvr_lineset *ls, int layout);
 /* ------------------------------------------------------------------ camera at rest
  * Neighbour lists for the camera-at-rest mode (render desc `still`, Sec.
  * 4.1): per voxel, every segment of its 3 x 3 x 3 neighbourhood (itself
- * included) whose box, grown by the tube radius plus a rounding margin of
- * 1e-4 radius + 1e-5, reaches into the voxel. A tube whose box misses a
- * voxel cannot enter it, so testing only these gives the image the search
- * over all 26 neighbours gives. Kept in the line set (8 bytes per entry plus
+ * included) that comes within the tube radius plus a rounding margin of
+ * 1e-4 radius + 1e-5 of the voxel. A tube farther away cannot enter it, so
+ * testing only these gives the image the search over all 26 neighbours
+ * gives. Kept in the line set (8 bytes per entry plus
  * 4 per voxel) and used by every later lvr_render at rest with a radius up
  * to `radius`; lvr_render builds them itself when they are missing or were
  * built for a smaller radius. Returns LVR_EOVERFLOW (nothing kept) when the
