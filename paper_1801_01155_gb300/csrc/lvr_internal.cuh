@@ -58,7 +58,7 @@ struct lvr_lineset {
     uint64_t *key = nullptr;      // [nseg] (curve << 32) | ordinal
     void *rec16 = nullptr;        // [nseg] 16-byte records (lvr_lineset_layout), or null
     // camera at rest (lvr_lineset_neighbours): per voxel, the records of its
-    // 3x3x3 neighbourhood whose grown box reaches into it, as
+    // 3x3x3 neighbourhood that come within the radius of it, as
     // (neighbour index 0..26 << 32) | record; built for radius^2 <= halo_r2
     uint32_t *halo_off = nullptr; // [nvox + 1], or null
     uint64_t *halo = nullptr;     // [halo_n]
