@@ -154,12 +154,17 @@ typedef struct orc_rdesc {
 /* counters[0..3]: voxels visited, records tested, LoD trilinear samples,
  * composited hits (summed over the listed pixels). */
 enum { ORC_RENDER_DDA = 0, ORC_RENDER_BRUTE = 1 };
-/* tie: per-pixel bit mask of near-tie decisions (may be NULL); margin: per
- * pixel, the smallest decision margin in units of its tie threshold (< 1
- * exactly when tie != 0; may be NULL). */
+/* tie: per-pixel bit mask of near-tie decisions (may be NULL): 1 silhouette
+ * graze, 2 voxel ownership, 4 depth order, 16 AO frame, 32 slab entry, 64 a
+ * hit's hard-shadow visibility (shadows 2); margin: per pixel, the smallest
+ * decision margin in units of its tie threshold (may be NULL); flip: per
+ * pixel, the sum over hits whose hard-shadow visibility is a near-tie of
+ * w kd |n.L| max(rgb), the most a flip of each can move any colour channel
+ * (may be NULL). */
 int orc_render(const orc_voxset *vs, const orc_lod *lod, const orc_view *view,
                const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
-               double *rgba, uint8_t *tie, double *margin, uint64_t *counters, int nthreads);
+               double *rgba, uint8_t *tie, double *margin, double *flip, uint64_t *counters,
+               int nthreads);
 
 /* Reading K1, the rasterised comparison system: every capsule between two
  * consecutive vertices of the input polylines (float32 grid coordinates, no

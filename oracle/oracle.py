@@ -61,7 +61,7 @@ def lib():
         L.orc_lod_free.argtypes = [vp]
         L.orc_lod_dims.argtypes = [vp, C.c_int, vp]
         L.orc_lod_export.argtypes = [vp, C.c_int, vp, vp, vp]
-        L.orc_render.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int, vp, vp, vp, vp, C.c_int]
+        L.orc_render.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int, vp, vp, vp, vp, vp, C.c_int]
         L.orc_primary_ray.argtypes = [vp, i32, i32, vp, vp]
         L.orc_capsule_entry.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
         L.orc_march.argtypes = [vp, vp, vp, C.c_double]
@@ -285,23 +285,30 @@ def pixel_grid(x0, y0, w, h):
     return np.stack([ii.reshape(-1), jj.reshape(-1)], 1).astype(np.int32)
 
 
+# tie flag bits of render()
+TIE_GRAZE, TIE_OWNER, TIE_SORT, TIE_FRAME, TIE_SLAB, TIE_SHADOW = 1, 2, 4, 16, 32, 64
+
+
 def render(vs: VoxSet, lod: Lod | None, view: View, rd: RDesc, pix, mode="dda", nthreads=0,
-           margins=False):
+           margins=False, flips=False):
     """Render the listed pixels (int32 (n, 2) of (i, j)); returns rgba (n,4) f64,
     tie flags (n,) u8 and counters [voxels, records, lod samples, hits]; with
-    margins=True also the per-pixel smallest normalised decision margin."""
+    margins=True also the per-pixel smallest normalised decision margin; with
+    flips=True also the per-pixel bound on what near-tie hard-shadow
+    visibilities can move a colour channel (both in that order)."""
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
     n = len(pix)
     rgba = np.empty((n, 4), np.float64)
     tie = np.empty(n, np.uint8)
     mg = np.empty(n, np.float64) if margins else None
+    fl = np.empty(n, np.float64) if flips else None
     cnt = np.zeros(4, np.uint64)
     m = 1 if mode == "brute" else 0
     _check(lib().orc_render(vs.handle, lod.handle if lod is not None else None, C.byref(view),
-                            C.byref(rd), _p(pix), n, m, _p(rgba), _p(tie), _p(mg), _p(cnt), int(nthreads)))
-    if margins:
-        return rgba, tie, cnt, mg
-    return rgba, tie, cnt
+                            C.byref(rd), _p(pix), n, m, _p(rgba), _p(tie), _p(mg), _p(fl), _p(cnt),
+                            int(nthreads)))
+    out = (rgba, tie, cnt) + ((mg,) if margins else ()) + ((fl,) if flips else ())
+    return out
 
 
 def primary_ray(view: View, i, j):

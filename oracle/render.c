@@ -42,6 +42,7 @@
 #define TIE_SORT  4
 #define TIE_FRAME 16
 #define TIE_SLAB  32
+#define TIE_SHADOW 64   /* a hit's binary visibility (shadows 2) is a near-tie */
 
 static const double EPS_G = 7.5e-7;   /* |distance - radius| at a silhouette */
 static const double EPS_T = 7.5e-7;   /* entry parameter vs voxel faces / other hits */
@@ -448,6 +449,8 @@ typedef struct {
     int done;
     int tie;
     double margin;      /* smallest decision margin, in units of its tie threshold */
+    double flip;        /* shadows 2: sum over hits whose visibility is a near-tie of
+                           the most a flip of it can move the pixel's colour */
     uint64_t nvox, nrec, nsamp, nhit;
 } pixstate;
 
@@ -608,17 +611,20 @@ static void shade_composite(const orc_voxset *vs, const orc_lod *L, const orc_rd
 
     double V = 1.0, AO = 1.0;
     if (rd->shadows == 2 && rd->reps) {
-        /* a flip of this hit's binary visibility moves the pixel by at most
-         * w kd |n.L| max(rgb) (w: its compositing weight); near-ties of hits
-         * whose flip stays below FLIP_MIN are not flagged */
+        /* the visibility is binary and enters only this hit's diffuse term
+         * (S1), so a flip of it moves the pixel by at most w kd |n.L| max(rgb)
+         * (w: its compositing weight); near-ties add that to the pixel's flip
+         * budget, and those whose flip reaches FLIP_MIN also flag the pixel */
         pixstate sh = *ps;
         sh.tie = 0;
         sh.margin = 1e300;
         V = shadow_reps(vs, rd, P, Lt, &sh);
         const double w = rd->opaque ? 1.0 : (1.0 - ps->A) * alpha;
         const double cmax = fmax((double)tf[0], fmax((double)tf[1], (double)tf[2]));
-        if (w * rd->kd * fabs(dot3(n, Lt)) * cmax >= FLIP_MIN) {
-            ps->tie |= sh.tie;
+        const double dmax = w * rd->kd * fabs(dot3(n, Lt)) * cmax;
+        if (sh.tie) ps->flip += dmax;
+        if (dmax >= FLIP_MIN) {
+            if (sh.tie) ps->tie |= TIE_SHADOW;
             ps->margin = fmin(ps->margin, sh.margin);
         }
     } else if (rd->shadows && L) V = 1.0 - fmin(1.0, march(L, P, Lt, -1.0, &ps->nsamp));
@@ -889,7 +895,8 @@ static void trace_brute(const orc_voxset *vs, const orc_lod *L, const orc_rdesc 
 
 int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
                const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
-               double *rgba, uint8_t *tie, double *margin, uint64_t *counters, int nthreads) {
+               double *rgba, uint8_t *tie, double *margin, double *flip, uint64_t *counters,
+               int nthreads) {
     if ((rd->shadows == 1 || rd->ao) && !L) return ORC_EINVAL;
     if (rd->shadows == 2 && (!rd->reps || rd->shadow_level < 0 || rd->shadow_level >= rd->reps->levels))
         return ORC_EINVAL;
@@ -929,6 +936,7 @@ int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
             rgba[4 * p + 3] = ps.A;
             if (tie) tie[p] = (uint8_t)ps.tie;
             if (margin) margin[p] = ps.margin;
+            if (flip) flip[p] = ps.flip;
             c0 += ps.nvox; c1 += ps.nrec; c2 += ps.nsamp; c3 += ps.nhit;
         }
         free(buf);

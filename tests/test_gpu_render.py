@@ -39,7 +39,7 @@ class Scene:
         self.glod = lvr.lvr_build_lod(ctx, self.gls, levels, sig)
         self.olod = O.Lod(self.ovs, levels, sig)
 
-    def render(self, env, cam, crop=None, radius=0.15, tile=(0, 0), counters=False, **kw):
+    def render(self, env, cam, crop=None, radius=0.15, tile=(0, 0), counters=False, flips=False, **kw):
         import torch
         lvr, O, ctx, dev = env
         lv, ov, pix = S.views(cam, crop)
@@ -56,7 +56,10 @@ class Scene:
         lvr.lvr_render(ctx, self.gls, self.glod, lv, desc, out, counters=cnt)
         ctx.sync()
         rd = O.make_rdesc(radius, self.tf, **okw)
-        ref, tie, ocnt = O.render(self.ovs, self.olod, ov, rd, pix)
+        if flips:   # the oracle's flip budget of hard-shadow near-ties, kept for check_image
+            ref, tie, ocnt, self.flip = O.render(self.ovs, self.olod, ov, rd, pix, flips=True)
+        else:
+            ref, tie, ocnt = O.render(self.ovs, self.olod, ov, rd, pix)
         got = out.cpu().numpy().reshape(-1, 4)
         return got, ref, tie, (cnt.cpu().numpy() if counters else None), ocnt
 
@@ -390,11 +393,13 @@ def test_rep_line_shadows_match_oracle(env, c1, c1t, level):
         out = torch.empty((128, 128, 4), dtype=torch.float32, device=dev)
         lvr.lvr_render(ctx, sc.gls, sc.glod, lv, lvr.make_desc(0.2, sc.tf, shadow_level=level, **dkw), out)
         ctx.sync()
-        ref, tie, _ = O.render(sc.ovs, sc.olod, ov, O.make_rdesc(0.2, sc.tf, reps=sc.oreps, shadow_level=level,
-                                                                   **okw), pix)
+        ref, tie, _, flip = O.render(sc.ovs, sc.olod, ov,
+                                     O.make_rdesc(0.2, sc.tf, reps=sc.oreps, shadow_level=level, **okw), pix,
+                                     flips=True)
         got = out.cpu().numpy().reshape(-1, 4)
-        # binary visibility: hits within 1e-3 voxel of a shadow edge are flagged too
-        S.check_image(got, ref, tie, cap=5e-3, what=f"rep shadows level {level}")
+        # binary visibility: pixels with a hit within 1e-3 voxel of a shadow
+        # edge are compared within the oracle's flip budget
+        S.check_image(got, ref, tie, flip=flip, what=f"rep shadows level {level}")
         # the shadows are there: against the unshadowed frame some pixels darken
         plain, _, _ = O.render(sc.ovs, sc.olod, ov, O.make_rdesc(0.2, sc.tf, **okw), pix)
         assert (ref[:, :3] < plain[:, :3] - 1e-3).any(1).mean() > 0.01
@@ -405,17 +410,20 @@ def test_rep_line_shadows_c2_crop(env, c2):
     128 x 128 crop of the 1080p view. Opaque: about 1 % of the pixels hold a
     hit within 1e-3 voxel of a shadow edge. Transparent: 20-40 hits per pixel
     each walk tens of densely filled cells, so about 40 % of the pixels hold
-    such a hit; the others are compared."""
+    such a hit. A hit's visibility is binary and enters only its own diffuse
+    term, so those pixels are compared within 2e-3 plus the oracle's bound on
+    what their near-tie visibilities can change (Sec. 5.2, first approach);
+    pixels with any other near-tie stay under the usual 0.1 % cap."""
     lvr, O, ctx, dev = env
     lvr.lvr_lod_rep_lines(ctx, c2.glod, c2.gls)
     reps = O.Reps(c2.ovs, 3)
     cam = synth.orbit_view((256, 256, 256), 1920, 1080)
     got, ref, tie, _, _ = c2.render(env, cam, crop=(896, 476, 128, 128), opaque=True, shadow_level=1,
-                                    reps_oracle=reps)
-    S.check_image(got, ref, tie, cap=0.02, what="c2 crop rep shadows, opaque")
+                                    reps_oracle=reps, flips=True)
+    S.check_image(got, ref, tie, flip=c2.flip, what="c2 crop rep shadows, opaque")
     got, ref, tie, _, _ = c2.render(env, cam, crop=(896, 476, 128, 128), ert_alpha=0.99, shadow_level=1,
-                                    reps_oracle=reps)
-    S.check_image(got, ref, tie, cap=0.5, what="c2 crop rep shadows, transparent")
+                                    reps_oracle=reps, flips=True)
+    S.check_image(got, ref, tie, flip=c2.flip, what="c2 crop rep shadows, transparent")
 
 
 def test_rep_line_shadows_invalid(env, c1t):
