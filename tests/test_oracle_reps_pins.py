@@ -203,3 +203,37 @@ def test_image_with_rep_shadows_only_darkens(orc):
         np.testing.assert_array_equal(sh[ok, 3], base[ok, 3])
         dark = (sh[ok, :3] < base[ok, :3] - 1e-6).any(1).mean()
         assert 0.02 < dark < 0.9
+
+
+def test_flip_budget_is_the_diffuse_term(orc):
+    """Opaque frame, uniform grey transfer function, no AO: a pixel's colour
+    is c (ka + kd V |n.L|) with a binary V, so the most a flip of V can move
+    it is kd |n.L| c, which the same frame without shadows gives as its
+    colour minus ka c. Every pixel flagged with a near-tie visibility (bit
+    64) carries exactly that budget; unflagged pixels carry at most the
+    threshold below which near-ties are not flagged; each flagged pixel is
+    either lit (colour without shadows) or dark (ka c)."""
+    from paper_1801_01155_gb300 import synth
+    ls = synth.make_streamlines(150, 48, seed=5)
+    g = orc.make_grid(16, 32, scale=16.0, attr_min=float(ls.attr.min()), attr_max=float(ls.attr.max()))
+    vs = orc.VoxSet(ls.xyz, ls.attr, ls.offsets, g)
+    W, H = 160, 120
+    cam = synth.orbit_view((16, 16, 16), W, H)
+    v = orc.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"])
+    pix = orc.pixel_grid(0, 0, W, H)
+    reps = orc.Reps(vs, 3)
+    c, ka = float(np.float32(0.8)), float(np.float32(0.3))
+    tf = np.tile(np.array([c, c, c, 1.0], np.float32), 256)
+    plain, tp, _ = orc.render(vs, None, v, orc.make_rdesc(0.2, tf, opaque=True), pix)
+    flagged = 0
+    for level in (0, 1, 2):
+        rgba, tie, _, flip = orc.render(vs, None, v, orc.make_rdesc(0.2, tf, opaque=True, reps=reps,
+                                                                     shadow_level=level), pix, flips=True)
+        sh = (tie & orc.TIE_SHADOW) != 0
+        flagged += int(sh.sum())
+        assert np.all(flip[~sh] < 5e-4)
+        np.testing.assert_allclose(flip[sh], plain[sh, 0] - ka * c, rtol=0, atol=1e-12)
+        lit = np.isclose(rgba[sh, 0], plain[sh, 0], rtol=0, atol=1e-12)
+        dark = np.isclose(rgba[sh, 0], ka * c, rtol=0, atol=1e-12)
+        assert np.all(lit | dark)
+    assert flagged >= 10
