@@ -83,7 +83,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -191,12 +191,14 @@ def run_gpu(args):
     rec_bytes = 16 if layout else 8
     alg_bytes = 8 * nvox + rec_bytes * nrec + 32 * nsamp
 
+    # the clock sampler starts before the warm-up steps, so that it is running
+    # (and sampling a loaded GPU) when the timed region begins
+    clocks = Clocks(local) if rank == 0 else None
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = Clocks(local) if rank == 0 else None
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -714,7 +716,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lvr", choices=["lvr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
