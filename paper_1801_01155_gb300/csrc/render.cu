@@ -44,6 +44,7 @@
 #include <vector>
 
 #include "ao_mlp.cuh"
+#include "geom.cuh"
 #include "lvr_internal.cuh"
 
 namespace {
@@ -1255,62 +1256,6 @@ bool camera_basis(const lvr_view *view, float F[3], float R[3], float U[3], floa
 }
 
 // ------------------------------------------------------------------ camera at rest: neighbour lists
-// Squared distance from the segment a + s (b - a), 0 <= s <= 1, to the unit
-// box [0, 1]^3. Along the segment the squared distance is a convex piecewise
-// quadratic whose pieces end where a coordinate crosses 0 or 1; on each piece
-// the axes outside the box are fixed, and its minimum is the piece's
-// stationary point clamped to the piece. Float rounding moves the result by
-// a few units in the last place, far below the cull margin.
-__device__ float segment_box_dist2(Vec a, Vec b) {
-    const float A[3] = {a.x, a.y, a.z}, d[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
-    auto f = [&](float s) {
-        float q = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            const float x = fmaf(s, d[i], A[i]);
-            const float e = fmaxf(fmaxf(-x, x - 1.0f), 0.0f);
-            q = fmaf(e, e, q);
-        }
-        return q;
-    };
-    float bp[8];
-    int nb = 0;
-    bp[nb++] = 0.0f;
-    bp[nb++] = 1.0f;
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        if (d[i] == 0.0f) continue;
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const float sb = ((float)c - A[i]) / d[i];
-            if (sb > 0.0f && sb < 1.0f) bp[nb++] = sb;
-        }
-    }
-    for (int i = 1; i < nb; i++)   // insertion sort of at most 8 values
-        for (int j = i; j > 0 && bp[j] < bp[j - 1]; j--) {
-            const float tmp = bp[j];
-            bp[j] = bp[j - 1];
-            bp[j - 1] = tmp;
-        }
-    float best = f(1.0f);
-    for (int k = 0; k + 1 < nb; k++) {
-        const float s0 = bp[k], s1 = bp[k + 1], mid = 0.5f * (s0 + s1);
-        best = fminf(best, f(s0));
-        float num = 0.0f, den = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            const float x = fmaf(mid, d[i], A[i]);
-            if (x < 0.0f || x > 1.0f) {
-                const float c = x < 0.0f ? 0.0f : 1.0f;
-                num = fmaf(d[i], c - A[i], num);
-                den = fmaf(d[i], d[i], den);
-            }
-        }
-        if (den > 0.0f) best = fminf(best, f(fminf(fmaxf(num / den, s0), s1)));
-    }
-    return best;
-}
-
 // One thread per voxel: the records of the 27 voxels around it (neighbour
 // order x fastest, records ascending) whose segment comes within the cull
 // margin of it (a box test first, then the exact distance). Count pass (halo null): per voxel the number into
@@ -1347,7 +1292,10 @@ __global__ void __launch_bounds__(256) neighbours_kernel(const uint32_t *__restr
                 if (fmaxf(a.x, b.x) + rm < 0.0f || fminf(a.x, b.x) - rm > 1.0f || fmaxf(a.y, b.y) + rm < 0.0f ||
                     fminf(a.y, b.y) - rm > 1.0f || fmaxf(a.z, b.z) + rm < 0.0f || fminf(a.z, b.z) - rm > 1.0f)
                     continue;
-                if (nc != 13 && segment_box_dist2(a, b) > rm * rm) continue;
+                if (nc != 13) {
+                    const float pa[3] = {a.x, a.y, a.z}, pb[3] = {b.x, b.y, b.z};
+                    if (lvr_geom::segment_box_dist2(pa, pb) > rm * rm) continue;
+                }
                 if (out) out[n] = (uint64_t)nc << 32 | k;
                 n++;
             }
