@@ -237,3 +237,31 @@ def test_flip_budget_is_the_diffuse_term(orc):
         dark = np.isclose(rgba[sh, 0], ka * c, rtol=0, atol=1e-12)
         assert np.all(lit | dark)
     assert flagged >= 10
+
+
+def test_flip_budget_adds_up_along_the_ray(orc):
+    """Transparent frames: the budget sums over every composited hit whose
+    visibility is a near-tie, so terminating later (more hits composited)
+    never lowers it, and it never exceeds the pixel's whole diffuse part
+    (the frame without shadows minus its ambient part ka c A)."""
+    from paper_1801_01155_gb300 import synth
+    ls = synth.make_streamlines(1500, 64, seed=6)
+    g = orc.make_grid(16, 32, scale=16.0, attr_min=float(ls.attr.min()), attr_max=float(ls.attr.max()))
+    vs = orc.VoxSet(ls.xyz, ls.attr, ls.offsets, g)
+    W, H = 160, 120
+    cam = synth.orbit_view((16, 16, 16), W, H)
+    v = orc.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"])
+    pix = orc.pixel_grid(0, 0, W, H)
+    reps = orc.Reps(vs, 3)
+    c, ka = float(np.float32(0.8)), float(np.float32(0.3))
+    tf = np.tile(np.array([c, c, c, 0.2], np.float32), 256)
+    plain, _, _ = orc.render(vs, None, v, orc.make_rdesc(0.2, tf, ert_alpha=2.0), pix)
+    diffuse = plain[:, 0] - (1.0 - plain[:, 3]) * 1.0 - ka * c * plain[:, 3]   # minus background and ambient
+    flips = []
+    for ert in (0.5, 0.9, 2.0):
+        _, tie, _, flip = orc.render(vs, None, v, orc.make_rdesc(0.2, tf, ert_alpha=ert, reps=reps,
+                                                               shadow_level=1), pix, flips=True)
+        flips.append(flip)
+    assert np.all(flips[0] <= flips[1] + 1e-12) and np.all(flips[1] <= flips[2] + 1e-12)
+    assert np.all(flips[2] <= diffuse + 1e-9)
+    assert (flips[2] > flips[0] + 1e-6).sum() > 20
