@@ -39,7 +39,8 @@ typedef enum lvr_status {
     LVR_EINVAL = 1,     /* bad argument or input data */
     LVR_ENOMEM = 2,     /* device or host allocation failed */
     LVR_ECUDA = 3,      /* CUDA runtime error */
-    LVR_EOVERFLOW = 4,  /* more than 2^32 - 1 segments */
+    LVR_EOVERFLOW = 4,  /* a count beyond 2^32 - 1 (segments, neighbour-list entries,
+                           fragments) or beyond a caller-owned capacity */
     LVR_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
     LVR_EDEVICE = 6     /* no usable sm_103 device */
 } lvr_status;
