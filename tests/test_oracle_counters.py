@@ -1,0 +1,43 @@
+"""Pins of the oracle's traversal counters, which fix the algorithmic bytes of
+the roofline (8 B per voxel visited, one record per record tested).
+
+With early termination off and translucent tubes every primary ray walks
+the grid from entry to exit, so the voxels it visits are exactly the cells
+whose box the ray crosses over an interval of positive length after leaving
+the eye, and the records it tests are those cells' stored segments. Both are
+recounted here by a slab test of the ray against every cell of the grid.
+"""
+import numpy as np
+
+from paper_1801_01155_gb300 import synth
+
+
+def test_voxels_and_records_equal_a_slab_test_over_all_cells(orc):
+    R = 12
+    ls = synth.make_streamlines(200, 48, seed=4)
+    g = orc.make_grid(R, 32, scale=float(R), attr_min=float(ls.attr.min()), attr_max=float(ls.attr.max()))
+    vs = orc.VoxSet(ls.xyz, ls.attr, ls.offsets, g)
+    counts = np.diff(vs.export()["offset"].astype(np.int64))
+    W, H = 40, 30
+    cam = synth.orbit_view((R, R, R), W, H)
+    view = orc.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"])
+    pix = orc.pixel_grid(0, 0, W, H)
+    tf = synth.tf_ramp(0.01, 0.02)
+    _, tie, cnt = orc.render(vs, None, view, orc.make_rdesc(0.2, tf, ert_alpha=2.0), pix)
+    idx = np.arange(R ** 3)
+    lo = np.stack([idx % R, (idx // R) % R, idx // (R * R)], 1).astype(np.float64)
+    hi = lo + 1.0
+    nvox = nrec = 0
+    for i, j in pix:
+        o, d = orc.primary_ray(view, int(i), int(j))
+        o, d = o.astype(np.float64), d.astype(np.float64)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1, t2 = (lo - o) / d, (hi - o) / d
+        tn = np.maximum(np.nanmax(np.minimum(t1, t2), 1), 0.0)
+        tf_ = np.nanmin(np.maximum(t1, t2), 1)
+        crossed = tf_ - tn > 1e-9
+        nvox += int(crossed.sum())
+        nrec += int(counts[crossed].sum())
+    assert nvox > 5000 and nrec > 1000
+    assert int(cnt[0]) == nvox
+    assert int(cnt[1]) == nrec
