@@ -41,3 +41,25 @@ def test_voxels_and_records_equal_a_slab_test_over_all_cells(orc):
     assert nvox > 5000 and nrec > 1000
     assert int(cnt[0]) == nvox
     assert int(cnt[1]) == nrec
+
+
+def test_lod_samples_of_shadow_marches_in_closed_form(orc):
+    """One straight opaque tube along x at y = z = 8 + 16.5/32 (its quantised
+    axis) in a 16^3 grid with a 3-level LoD, lit straight from +y, at a density
+    so low that no march reaches O = 1. By the soft-shadow reading (samples at
+    s = 1, 2, 4 on levels 0, 1, 2, then every 4 voxels, ending where a sample
+    would leave the density's support [-2, 18]) every hit, whose y lies in
+    [axis - r, axis + r], takes its samples at y + 1, 2, 4 and 8 and stops
+    before y + 12: exactly 4 per hit."""
+    R, r = 16, 0.2
+    xyz = np.array([[0.5, 8.5, 8.5], [15.5, 8.5, 8.5]], np.float32)
+    attr = np.zeros(2, np.float32)
+    vs = orc.VoxSet(xyz, attr, np.array([0, 2], np.int64), orc.make_grid(R, 32, scale=1.0))
+    tf = synth.tf_ramp(1.0, 1.0)
+    lod = orc.Lod(vs, 3, np.full(256, 1e-3, np.float32))
+    W, H = 64, 48
+    view = orc.make_view((8.0, 8.5, 40.0), (8.0, 8.5, 8.5), (0.0, 1.0, 0.0), 20.0, W, H, (0.0, -1.0, 0.0))
+    pix = orc.pixel_grid(0, 0, W, H)
+    _, tie, cnt = orc.render(vs, lod, view, orc.make_rdesc(r, tf, opaque=True, shadows=True), pix)
+    assert int(cnt[3]) > 100
+    assert int(cnt[2]) == 4 * int(cnt[3])
