@@ -63,3 +63,23 @@ def test_lod_samples_of_shadow_marches_in_closed_form(orc):
     _, tie, cnt = orc.render(vs, lod, view, orc.make_rdesc(r, tf, opaque=True, shadows=True), pix)
     assert int(cnt[3]) > 100
     assert int(cnt[2]) == 4 * int(cnt[3])
+
+
+def test_lod_samples_with_ao_in_closed_form(orc):
+    """The same kind of tube in the middle of a 32^3 grid (support [-2, 34]),
+    now with 16 AO rays of radius 15 per hit as well: an AO ray samples at
+    s = 1, 2, 4, 8, 12 and stops because s = 16 exceeds the radius (no sample
+    point can leave the support), a shadow march toward +y at s = 1, 2, 4,
+    8, 12, 16 and stops before leaving at y + 20: 6 + 16 x 5 = 86 per hit."""
+    R, r = 32, 0.2
+    xyz = np.array([[12.5, 16.5, 16.5], [20.5, 16.5, 16.5]], np.float32)
+    attr = np.zeros(2, np.float32)
+    vs = orc.VoxSet(xyz, attr, np.array([0, 2], np.int64), orc.make_grid(R, 32, scale=1.0))
+    lod = orc.Lod(vs, 3, np.full(256, 1e-3, np.float32))
+    W, H = 64, 48
+    view = orc.make_view((16.5, 16.5, 60.0), (16.5, 16.5, 16.5), (0.0, 1.0, 0.0), 6.0, W, H, (0.0, -1.0, 0.0))
+    pix = orc.pixel_grid(0, 0, W, H)
+    rd = orc.make_rdesc(r, synth.tf_ramp(1.0, 1.0), opaque=True, shadows=True, ao=True, ao_rays=16, ao_radius=15.0)
+    _, tie, cnt = orc.render(vs, lod, view, rd, pix)
+    assert int(cnt[3]) > 100
+    assert int(cnt[2]) == 86 * int(cnt[3])
