@@ -80,14 +80,13 @@ lod_pool_kernel(int cx, int cy, int cz, const uint32_t *__restrict__ ccnt, const
 }
 
 // Corner-packed copy of one level for trilinear sampling: padded cell
-// (i, j, k) -> X = i - 1, Y = j - 1, Z = k - 1; .x = v(X, Y), .y = v(X+1, Y),
+// (i, j, k) -> X = i - lo, Y = j - lo, Z = k - lo; .x = v(X, Y), .y = v(X+1, Y),
 // .z = v(X, Y+1), .w = v(X+1, Y+1) in slice Z, zero outside the grid.
 __global__ void __launch_bounds__(256)
-lod_pack_kernel(const float *__restrict__ d, int dx, int dy, int dz, float4 *pk) {
-    const int px = dx + 2, py = dy + 2;
-    const int64_t np = (int64_t)px * py * (dz + 2);
+lod_pack_kernel(const float *__restrict__ d, int dx, int dy, int dz, int lo, int px, int py, int pz, float4 *pk) {
+    const int64_t np = (int64_t)px * py * pz;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < np; c += (int64_t)gridDim.x * blockDim.x) {
-        const int X = (int)(c % px) - 1, Y = (int)((c / px) % py) - 1, Z = (int)(c / ((int64_t)px * py)) - 1;
+        const int X = (int)(c % px) - lo, Y = (int)((c / px) % py) - lo, Z = (int)(c / ((int64_t)px * py)) - lo;
         auto v = [&](int x, int y) {
             return (x >= 0 && y >= 0 && Z >= 0 && x < dx && y < dy && Z < dz)
                        ? d[x + (int64_t)dx * (y + (int64_t)dy * Z)] : 0.0f;
@@ -109,10 +108,9 @@ struct AoStep {
 // mean min(1, O). A sample at c + s d has the same fractional position in
 // every voxel, so the stencil (integer offsets, fractions) is one table.
 __global__ void __launch_bounds__(256)
-ao_field_kernel(const float4 *__restrict__ pk, int dx, int dy, int dz, const AoStep *__restrict__ tab, int rays,
-                int steps, float *field) {
+ao_field_kernel(const float4 *__restrict__ pk0, int64_t px, int64_t sz, int dx, int dy, int dz,
+                const AoStep *__restrict__ tab, int rays, int steps, float *field) {
     const int64_t n = (int64_t)dx * dy * dz;
-    const unsigned px = (unsigned)dx + 2u, sz = px * ((unsigned)dy + 2u);
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int vx = (int)(v % dx), vy = (int)((v / dx) % dy), vz = (int)(v / ((int64_t)dx * dy));
         float occ = 0.0f;
@@ -124,7 +122,7 @@ ao_field_kernel(const float4 *__restrict__ pk, int dx, int dy, int dz, const AoS
                 float val = 0.0f;
                 if ((unsigned)(ix + 1) <= (unsigned)dx && (unsigned)(iy + 1) <= (unsigned)dy &&
                     (unsigned)(iz + 1) <= (unsigned)dz) {
-                    const float4 *c = pk + ((unsigned)(ix + 1) + px * (unsigned)(iy + 1) + sz * (unsigned)(iz + 1));
+                    const float4 *c = pk0 + (ix + px * iy + sz * iz);
                     const float4 a = __ldg(c), b = __ldg(c + sz);
                     const float x00 = fmaf(e.fx, a.y - a.x, a.x), x10 = fmaf(e.fx, a.w - a.z, a.z);
                     const float x01 = fmaf(e.fx, b.y - b.x, b.x), x11 = fmaf(e.fx, b.w - b.z, b.z);
@@ -464,7 +462,8 @@ extern "C" lvr_status lvr_lod_ao_field(lvr_ctx *ctx, lvr_lod *lod, int rays, flo
             lod->dens[0], dm[0], dm[1], dm[2], taps, rays, H, lod->aof);
     } else {
         const unsigned g = grid1d(n, 256) > 65535 ? 65535 : grid1d(n, 256);
-        ao_field_kernel<<<g, 256, 0, ctx->stream>>>(lod->pk[0], dm[0], dm[1], dm[2], (const AoStep *)ctx->stage_in,
+        ao_field_kernel<<<g, 256, 0, ctx->stream>>>(lod->pk0[0], lod->pstride[0][0], lod->pstride[0][1], dm[0], dm[1],
+                                                    dm[2], (const AoStep *)ctx->stage_in,
                                                    rays, steps, lod->aof);
     }
     LVR_CUDA(ctx, cudaGetLastError());
@@ -503,8 +502,25 @@ extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int lev
         if ((st = dev_alloc(ctx, (void **)&L->cnt[l], n * 4)) != LVR_OK) break;
         if ((st = dev_alloc(ctx, (void **)&L->len[l], n * 4)) != LVR_OK) break;
         if ((st = dev_alloc(ctx, (void **)&L->dens[l], n * 4)) != LVR_OK) break;
-        const size_t np = (size_t)(L->dims[l][0] + 2) * (L->dims[l][1] + 2) * (L->dims[l][2] + 2);
-        st = dev_alloc(ctx, (void **)&L->pk[l], np * 16);
+    }
+    // padding of the sampling copies: the support of the density field is
+    // [-c/2, (top + 1/2) c] per axis in level-0 units (c = 2^(levels-1), top =
+    // the coarsest level's dims); at level l its sample points fall in cells
+    // floor(x / 2^l - 1/2), whose corners reach one cell further
+    for (int l = 0; l < levels && st == LVR_OK; l++) {
+        const double m = ldexp(1.0, levels - 1 - l);
+        L->pad_lo[l] = -(int)floor(-0.5 * m - 0.5);
+        int64_t pd[3];
+        for (int a = 0; a < 3; a++) {
+            const int64_t hi = (int64_t)floor(((double)L->dims[levels - 1][a] + 0.5) * m - 0.5) + 1;
+            L->pad_hi[l][a] = (int32_t)(hi - (L->dims[l][a] - 1));
+            pd[a] = (int64_t)L->dims[l][a] + L->pad_lo[l] + L->pad_hi[l][a];
+        }
+        L->pstride[l][0] = pd[0];
+        L->pstride[l][1] = pd[0] * pd[1];
+        st = dev_alloc(ctx, (void **)&L->pk[l], (size_t)(pd[0] * pd[1] * pd[2]) * 16);
+        if (st == LVR_OK)
+            L->pk0[l] = L->pk[l] + L->pad_lo[l] * (1 + L->pstride[l][0] + L->pstride[l][1]);
     }
     if (st == LVR_OK) st = ensure_stage_in(ctx, 1024);
     if (st != LVR_OK) {
@@ -525,9 +541,12 @@ extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int lev
         }
         for (int l = 0; l < levels; l++) {
             const int32_t *dm = L->dims[l];
-            const int64_t np = (int64_t)(dm[0] + 2) * (dm[1] + 2) * (dm[2] + 2);
+            const int lo = L->pad_lo[l];
+            const int px = dm[0] + lo + L->pad_hi[l][0], py = dm[1] + lo + L->pad_hi[l][1],
+                      pz = dm[2] + lo + L->pad_hi[l][2];
+            const int64_t np = (int64_t)px * py * pz;
             const unsigned g = grid1d(np, 256) > 65535 ? 65535 : grid1d(np, 256);
-            lod_pack_kernel<<<g, 256, 0, s>>>(L->dens[l], dm[0], dm[1], dm[2], L->pk[l]);
+            lod_pack_kernel<<<g, 256, 0, s>>>(L->dens[l], dm[0], dm[1], dm[2], lo, px, py, pz, L->pk[l]);
         }
         e = cudaGetLastError();
     }

@@ -74,10 +74,19 @@ struct lvr_lod {
     uint32_t *cnt[4] = {};
     float *len[4] = {};
     float *dens[4] = {};
-    // sampling copy of dens: per cell (i, j, k) of the grid padded by one cell
-    // on every side, the four x/y corners (i, j), (i+1, j), (i, j+1), (i+1, j+1)
-    // of z-slice k as one float4 (zero outside the grid)
+    // sampling copy of dens: per cell (i, j, k) of the padded grid, the four
+    // x/y corners (i, j), (i+1, j), (i, j+1), (i+1, j+1) of z-slice k as one
+    // float4 (zero outside the grid). Level l is padded by pad_lo[l] cells
+    // below and pad_hi[l][a] above on each axis, enough that every sample
+    // point of the density field's support (the grid enlarged by half a
+    // coarsest-level cell) has its eight corners inside the copy, so a
+    // sampler that checks the support needs no per-corner range check.
+    // pk0[l] points at cell (0, 0, 0); strides pstride[l] = {row, slice}.
     float4 *pk[4] = {};
+    const float4 *pk0[4] = {};
+    int32_t pad_lo[4] = {};
+    int32_t pad_hi[4][3] = {};
+    int64_t pstride[4][2] = {};
     // spherical per-voxel AO (lvr_lod_ao_field), or null
     float *aof = nullptr;
     // representative lines per level (lvr_lod_rep_lines), or null: per cell one

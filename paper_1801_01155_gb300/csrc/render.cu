@@ -50,7 +50,7 @@
 namespace {
 
 constexpr int RT = 128;       // threads per block (4 warps)
-constexpr int KS = 4;         // hit slots per lane per lighting round
+constexpr int KS = 3;         // hit slots per lane per lighting round
 constexpr unsigned ROUND_TARGET = 16;   // a warp lights its hits once it holds this many
 constexpr int MAX_AO = 32;
 constexpr unsigned FULL = 0xffffffffu;
@@ -64,7 +64,8 @@ struct RenderParams {
     float r2;
     int32_t levels;
     int32_t ldims[4][3];
-    const float4 *pk[4];          // corner-packed levels, padded by one cell per side
+    const float4 *pk0[4];         // corner-packed levels at cell (0, 0, 0), padded to cover the support
+    int64_t pstr[4][2];           //   their row and slice strides in cells
     float lod_lo, lod_hi[3];      // support of the density field (level-0 voxels)
     float F[3], R[3], U[3], th, tw, eye[3];
     int32_t W, H, x0, y0, cw, ch;
@@ -159,6 +160,18 @@ __device__ __forceinline__ float sphere_entry(Vec p, Vec D, Vec c, float r2) {
 __device__ __forceinline__ float capsule_entry(Vec p, Vec D, Vec a, Vec b, float r2) {
     const Vec ba = sub(b, a);
     const float L2 = dot(ba, ba);
+    // Early reject: every point of the capsule lies within the radius of the
+    // axis line, so a ray whose line passes farther from it misses. The
+    // squared line distance is (w . c)^2 / |c|^2 with w = a - p, c = D x ba;
+    // rejecting only beyond 1.001 r^2, and only when the lines are not
+    // near-parallel (|c|^2 > 1e-4 L2, so c has a small relative error), keeps
+    // every capsule the full test below accepts.
+    const Vec c = cross(D, ba);
+    const float c2 = dot(c, c);
+    if (c2 > 1e-4f * L2) {
+        const float wc = dot(sub(a, p), c);
+        if (wc * wc > 1.001f * r2 * c2) return INFINITY;
+    }
     if (L2 > 0.0f) {
         const float L = sqrtf(L2), iL = 1.0f / L;
         const Vec w = scale(ba, iL);
@@ -184,24 +197,33 @@ __device__ __forceinline__ float capsule_entry(Vec p, Vec D, Vec a, Vec b, float
 
 // Cell-centred trilinear density at level l, zero outside the grid: two
 // 16-byte loads of the corner-packed level (slices iz and iz + 1), the same
-// lerps in the same order as eight scalar corner loads would feed.
-__device__ __forceinline__ float sample_level(const RenderParams &P, int l, Vec x) {
+// lerps in the same order as eight scalar corner loads would feed. The
+// packed copy is padded to cover the support of the density field, so a
+// point inside the support (which every caller checks) needs no range check.
+struct Corners {
+    float4 a, b;                  // the x/y corners of slices iz and iz + 1
+    float fx, fy, fz;             // position inside the cell
+};
+__device__ __forceinline__ const float4 *corner_addr(const RenderParams &P, int l, Vec x, float &fx, float &fy,
+                                                     float &fz) {
     const float inv = __int_as_float((127 - l) << 23);         // 2^-l
     const float qx = fmaf(x.x, inv, -0.5f), qy = fmaf(x.y, inv, -0.5f), qz = fmaf(x.z, inv, -0.5f);
     const float fx0 = floorf(qx), fy0 = floorf(qy), fz0 = floorf(qz);
-    const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
-    const int dx = P.ldims[l][0], dy = P.ldims[l][1], dz = P.ldims[l][2];
-    // cells with both corners outside on some axis sample zero
-    if ((unsigned)(ix + 1) > (unsigned)dx || (unsigned)(iy + 1) > (unsigned)dy || (unsigned)(iz + 1) > (unsigned)dz)
-        return 0.0f;
-    const float fx = qx - fx0, fy = qy - fy0, fz = qz - fz0;
-    const unsigned px = (unsigned)dx + 2u, sz = px * ((unsigned)dy + 2u);
-    const float4 *c = P.pk[l] + ((unsigned)(ix + 1) + px * (unsigned)(iy + 1) + sz * (unsigned)(iz + 1));
-    const float4 a = __ldg(c), b = __ldg(c + sz);
+    fx = qx - fx0;
+    fy = qy - fy0;
+    fz = qz - fz0;
+    return P.pk0[l] + ((int64_t)(int)fx0 + P.pstr[l][0] * (int)fy0 + P.pstr[l][1] * (int)fz0);
+}
+__device__ __forceinline__ float trilerp(float4 a, float4 b, float fx, float fy, float fz) {
     const float x00 = fmaf(fx, a.y - a.x, a.x), x10 = fmaf(fx, a.w - a.z, a.z);
     const float x01 = fmaf(fx, b.y - b.x, b.x), x11 = fmaf(fx, b.w - b.z, b.z);
     const float y0 = fmaf(fy, x10 - x00, x00), y1 = fmaf(fy, x11 - x01, x01);
     return fmaf(fz, y1 - y0, y0);
+}
+__device__ __forceinline__ float sample_level(const RenderParams &P, int l, Vec x) {
+    float fx, fy, fz;
+    const float4 *c = corner_addr(P, l, x, fx, fy, fz);
+    return trilerp(__ldg(c), __ldg(c + P.pstr[l][1]), fx, fy, fz);
 }
 
 // Spherical AO field at x: cell-centred trilinear, coordinates clamped to
@@ -575,50 +597,78 @@ __device__ __forceinline__ Vec ao_tangent(Vec n, Vec u) {
 // >= 0), or when the sample leaves the support of the density field.
 // The march of an AO ray with 3 levels and a radius in [12, 16): the
 // samples fall at s = 1, 2, 4, 8, 12 (levels 0, 1, 2, 2, 2), unrolled; the
-// same samples, order, weights and stopping rules as march().
+// same samples, weights and sample count as march(), and the same
+// min(1, O).
 __device__ __forceinline__ float march_ao5(const RenderParams &P, Vec p, Vec d, unsigned &nsamp) {
-    float O = 0.0f;
     const int ss[5] = {1, 2, 4, 8, 12}, ll[5] = {0, 1, 2, 2, 2};
+    // every sample's corners are requested before the first is used (one
+    // memory round trip per ray instead of five); samples past the support
+    // read nothing and are zero
+    float4 A[5], B[5];
+    float fx[5], fy[5], fz[5];
+    bool in[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
         const Vec x = axpy((float)ss[k], d, p);
-        if (x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
-            x.z > P.lod_hi[2])
-            break;
+        in[k] = (k == 0 || in[k - 1]) && !(x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo ||
+                                            x.x > P.lod_hi[0] || x.y > P.lod_hi[1] || x.z > P.lod_hi[2]);
+        const float4 *c = corner_addr(P, ll[k], x, fx[k], fy[k], fz[k]);
+        A[k] = in[k] ? __ldg(c) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        B[k] = in[k] ? __ldg(c + P.pstr[ll[k]][1]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    // the march stops at O >= 1 or when a sample leaves the support; terms
+    // added after O >= 1 are non-negative and leave min(1, O) = 1, terms past
+    // the support are zero, so summing all five gives the same min(1, O)
+    float O = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        nsamp += (in[k] && O < 1.0f) ? 1u : 0u;
         const float wl = __int_as_float((127 - 2 * ll[k]) << 23);   // 2^l / 8^l
-        O = fmaf(sample_level(P, ll[k], x), wl, O);
-        nsamp++;
-        if (O >= 1.0f) break;
+        O = fmaf(trilerp(A[k], B[k], fx[k], fy[k], fz[k]), wl, O);
     }
     return O;
 }
 
 // The unbounded march (shadows) with 3 levels: s = 1, 2 (levels 0, 1), then
 // s = 4, 8, 12, ... on level 2 until the sample leaves the density support
-// or O reaches 1; the same samples, order and weights as march().
-__device__ __forceinline__ float march_shadow3(const RenderParams &P, Vec p, Vec d, unsigned &nsamp) {
-    auto outside = [&](const Vec &x) {
-        return x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
-               x.z > P.lod_hi[2];
-    };
-    float O = 0.0f;
-    Vec x = axpy(1.0f, d, p);
-    if (outside(x)) return O;
-    O = sample_level(P, 0, x);
-    nsamp++;
-    if (O >= 1.0f) return O;
-    x = axpy(2.0f, d, p);
-    if (outside(x)) return O;
-    O = fmaf(sample_level(P, 1, x), 0.25f, O);
-    nsamp++;
-    if (O >= 1.0f) return O;
-    for (int s = 4; s < (1 << 30); s += 4) {
-        x = axpy((float)s, d, p);
-        if (outside(x)) break;
-        O = fmaf(sample_level(P, 2, x), 0.0625f, O);
-        nsamp++;
-        if (O >= 1.0f) break;
+// or O reaches 1; the same samples, weights and sample count as march(), and
+// the same min(1, O). The corners of four samples at a time are requested
+// before the first of them is used.
+__device__ __forceinline__ bool in_support(const RenderParams &P, const Vec &x) {
+    return !(x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
+             x.z > P.lod_hi[2]);
+}
+template <int L0, int L1, int L2, int L3>
+__device__ __forceinline__ void march4(const RenderParams &P, Vec p, Vec d, float s0, float s1, float s2, float s3,
+                                       bool &alive, float &O, unsigned &nsamp) {
+    constexpr int ll[4] = {L0, L1, L2, L3};
+    const float ss[4] = {s0, s1, s2, s3};
+    float4 A[4], B[4];
+    float fx[4], fy[4], fz[4];
+    bool in[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const Vec x = axpy(ss[j], d, p);
+        in[j] = (j == 0 ? alive : in[j - 1]) && in_support(P, x);
+        const float4 *c = corner_addr(P, ll[j], x, fx[j], fy[j], fz[j]);
+        A[j] = in[j] ? __ldg(c) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        B[j] = in[j] ? __ldg(c + P.pstr[ll[j]][1]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        nsamp += (in[j] && O < 1.0f) ? 1u : 0u;
+        const float wl = __int_as_float((127 - 2 * ll[j]) << 23);   // 2^l / 8^l
+        O = fmaf(trilerp(A[j], B[j], fx[j], fy[j], fz[j]), wl, O);
+    }
+    alive = in[3] && O < 1.0f;
+}
+__device__ __forceinline__ float march_shadow3(const RenderParams &P, Vec p, Vec d, unsigned &nsamp) {
+    float O = 0.0f;
+    bool alive = true;
+    // s = 1, 2, 4, 8 (levels 0, 1, 2, 2), then s = 12 + 16 g + 4 j on level 2
+    march4<0, 1, 2, 2>(P, p, d, 1.0f, 2.0f, 4.0f, 8.0f, alive, O, nsamp);
+    for (int s = 12; alive && s < (1 << 24); s += 16)
+        march4<2, 2, 2, 2>(P, p, d, (float)s, (float)(s + 4), (float)(s + 8), (float)(s + 12), alive, O, nsamp);
     return O;
 }
 
@@ -1147,10 +1197,13 @@ __device__ __forceinline__ void flush_stats(const RenderParams &P, int lane, Sta
 }
 
 constexpr int min_blocks(int mode) {
-    return mode == MODE_JUDGE ? 4 : (mode == MODE_STILL || mode == MODE_LEARNED ? 5 : 6);
+    return mode == MODE_IMAGE ? 7 : (mode == MODE_JUDGE ? 4 : (mode == MODE_STILL || mode == MODE_LEARNED ? 5 : 6));
 }
-// batched: the learned variant's register-resident model needs 128 registers
-constexpr int min_blocks_batch(int mode) { return mode == MODE_LEARNED ? 4 : min_blocks(mode); }
+// batched: the learned variant's register-resident model needs 128 registers;
+// the image variant reads its view from shared memory and needs 80
+constexpr int min_blocks_batch(int mode) {
+    return mode == MODE_LEARNED ? 4 : (mode == MODE_IMAGE ? 6 : min_blocks(mode));
+}
 
 // One view: a persistent grid takes 32-ray tiles from a global counter.
 template <int MODE, int LAYOUT>
@@ -1419,7 +1472,9 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
         P.levels = lod->levels;
         for (int l = 0; l < lod->levels; l++) {
             for (int a = 0; a < 3; a++) P.ldims[l][a] = lod->dims[l][a];
-            P.pk[l] = lod->pk[l];
+            P.pk0[l] = lod->pk0[l];
+            P.pstr[l][0] = lod->pstride[l][0];
+            P.pstr[l][1] = lod->pstride[l][1];
         }
         const float cell = (float)(1 << (lod->levels - 1));
         P.lod_lo = -0.5f * cell;
