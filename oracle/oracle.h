@@ -160,21 +160,26 @@ enum { ORC_RENDER_DDA = 0, ORC_RENDER_BRUTE = 1 };
  * decision margin in units of its tie threshold (may be NULL); flip: per
  * pixel, the sum over hits whose hard-shadow visibility is a near-tie of
  * w kd |n.L| max(rgb), the most a flip of each can move any colour channel
- * (may be NULL). */
+ * (may be NULL); alt (may be NULL): per pixel whose only near-tie is one
+ * pair of hits closer in depth than their error bounds, the RGBA with that
+ * pair composited in the other order (the other right answer); NaN
+ * elsewhere (DDA mode only). */
 int orc_render(const orc_voxset *vs, const orc_lod *lod, const orc_view *view,
                const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
-               double *rgba, uint8_t *tie, double *margin, double *flip, uint64_t *counters,
-               int nthreads);
+               double *rgba, uint8_t *tie, double *margin, double *flip, double *alt,
+               uint64_t *counters, int nthreads);
 
 /* Reading K1, the rasterised comparison system: every capsule between two
  * consecutive vertices of the input polylines (float32 grid coordinates, no
  * voxel model), one fragment per capsule a pixel's ray enters, sorted by
  * (entry, capsule index) and blended front to back (S1 shading, no shadows
  * or AO) until the float32 opacity reaches ert_alpha; opaque: the nearest.
- * counters[0..1]: fragments, blended fragments. */
+ * counters[0..1]: fragments, blended fragments. alt (may be NULL): as for
+ * orc_render, the pixel with its one near-tie pair of fragments blended in
+ * the other order, NaN elsewhere. */
 int orc_raster(const float *xyz, const float *attr, const int64_t *offsets, int64_t nc, const orc_grid *g,
                const orc_view *view, const orc_rdesc *rd, const int32_t *pix, int64_t npix, double *rgba,
-               uint8_t *tie, uint64_t *counters, int nthreads);
+               uint8_t *tie, double *alt, uint64_t *counters, int nthreads);
 
 /* ---- pieces exposed for pin tests ---- */
 /* Primary ray of pixel (i, j) under the single-precision ray contract (reading R0). */

@@ -61,7 +61,7 @@ def lib():
         L.orc_lod_free.argtypes = [vp]
         L.orc_lod_dims.argtypes = [vp, C.c_int, vp]
         L.orc_lod_export.argtypes = [vp, C.c_int, vp, vp, vp]
-        L.orc_render.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int, vp, vp, vp, vp, vp, C.c_int]
+        L.orc_render.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp, C.c_int]
         L.orc_primary_ray.argtypes = [vp, i32, i32, vp, vp]
         L.orc_capsule_entry.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
         L.orc_march.argtypes = [vp, vp, vp, C.c_double]
@@ -74,7 +74,7 @@ def lib():
         L.orc_reps_export.argtypes = [vp, C.c_int, vp]
         L.orc_halfline_segment_distance.argtypes = [vp, vp, vp, vp]
         L.orc_halfline_segment_distance.restype = C.c_double
-        L.orc_raster.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int64, vp, vp, vp, C.c_int]
+        L.orc_raster.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int]
         L.orc_raster.restype = C.c_int
         L.orc_shadow_reps_visibility.argtypes = [vp, vp, C.c_float, C.c_int, vp, vp]
         L.orc_shadow_reps_visibility.restype = C.c_double
@@ -290,24 +290,28 @@ TIE_GRAZE, TIE_OWNER, TIE_SORT, TIE_FRAME, TIE_SLAB, TIE_SHADOW = 1, 2, 4, 16, 3
 
 
 def render(vs: VoxSet, lod: Lod | None, view: View, rd: RDesc, pix, mode="dda", nthreads=0,
-           margins=False, flips=False):
+           margins=False, flips=False, alts=False):
     """Render the listed pixels (int32 (n, 2) of (i, j)); returns rgba (n,4) f64,
     tie flags (n,) u8 and counters [voxels, records, lod samples, hits]; with
     margins=True also the per-pixel smallest normalised decision margin; with
     flips=True also the per-pixel bound on what near-tie hard-shadow
-    visibilities can move a colour channel (both in that order)."""
+    visibilities can move a colour channel; with alts=True also, per pixel
+    whose only near-tie is one pair of hits in depth order, the RGBA with
+    that pair composited the other way round (NaN elsewhere), in that
+    order."""
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
     n = len(pix)
     rgba = np.empty((n, 4), np.float64)
     tie = np.empty(n, np.uint8)
     mg = np.empty(n, np.float64) if margins else None
     fl = np.empty(n, np.float64) if flips else None
+    al = np.empty((n, 4), np.float64) if alts else None
     cnt = np.zeros(4, np.uint64)
     m = 1 if mode == "brute" else 0
     _check(lib().orc_render(vs.handle, lod.handle if lod is not None else None, C.byref(view),
-                            C.byref(rd), _p(pix), n, m, _p(rgba), _p(tie), _p(mg), _p(fl), _p(cnt),
+                            C.byref(rd), _p(pix), n, m, _p(rgba), _p(tie), _p(mg), _p(fl), _p(al), _p(cnt),
                             int(nthreads)))
-    out = (rgba, tie, cnt) + ((mg,) if margins else ()) + ((fl,) if flips else ())
+    out = (rgba, tie, cnt) + ((mg,) if margins else ()) + ((fl,) if flips else ()) + ((al,) if alts else ())
     return out
 
 
@@ -459,9 +463,11 @@ def shadow_reps_visibility(vs: "VoxSet", reps: Reps, radius, level, P, Lt) -> fl
     return lib().orc_shadow_reps_visibility(vs.handle, reps.handle, float(radius), int(level), _p(P), _p(Lt))
 
 
-def raster(xyz, attr, offsets, grid: "Grid", view: "View", rd: "RDesc", pix, nthreads=0):
+def raster(xyz, attr, offsets, grid: "Grid", view: "View", rd: "RDesc", pix, nthreads=0, alts=False):
     """Reading K1 (rasterised comparison system) for the listed pixels: rgba
-    (n, 4) f64, tie flags (n,) u8, counters [fragments, blended]."""
+    (n, 4) f64, tie flags (n,) u8, counters [fragments, blended]; with
+    alts=True also the RGBA of each pixel whose only near-tie is one pair of
+    fragments in depth order, blended the other way round (NaN elsewhere)."""
     xyz = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
     attr = None if attr is None else np.ascontiguousarray(attr, np.float32)
     offsets = np.ascontiguousarray(offsets, np.int64)
@@ -470,6 +476,7 @@ def raster(xyz, attr, offsets, grid: "Grid", view: "View", rd: "RDesc", pix, nth
     rgba = np.empty((n, 4), np.float64)
     tie = np.empty(n, np.uint8)
     cnt = np.zeros(2, np.uint64)
+    al = np.empty((n, 4), np.float64) if alts else None
     _check(lib().orc_raster(_p(xyz), _p(attr), _p(offsets), len(offsets) - 1, C.byref(grid), C.byref(view),
-                            C.byref(rd), _p(pix), n, _p(rgba), _p(tie), _p(cnt), int(nthreads)))
-    return rgba, tie, cnt
+                            C.byref(rd), _p(pix), n, _p(rgba), _p(tie), _p(al), _p(cnt), int(nthreads)))
+    return (rgba, tie, cnt) + ((al,) if alts else ())

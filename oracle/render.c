@@ -452,6 +452,13 @@ typedef struct {
     double flip;        /* shadows 2: sum over hits whose visibility is a near-tie of
                            the most a flip of it can move the pixel's colour */
     uint64_t nvox, nrec, nsamp, nhit;
+    /* depth-sort near-ties: how many, and where the last one was (the voxel's
+       ordinal along the ray and the pair's position in its sorted hits) */
+    int nsort;
+    int64_t sort_vox, sort_i;
+    /* input of a second pass: swap the sorted pair (swap_i, swap_i + 1) of
+       voxel ordinal swap_vox (-1: none) */
+    int64_t swap_vox, swap_i;
 } pixstate;
 
 static void note(pixstate *ps, double m, int bit) {
@@ -474,13 +481,17 @@ static int hit_cmp(const void *x, const void *y) {
  * of the line of a crossed cell. Near-grazes and near-edge crossings are
  * flagged. */
 /* Reading S5's visibility is binary, and the library finds hit points in
- * float32, some 1e-5 voxel away from the exact ones. A pixel is a tie when
- * a visited cell's line lies within EPS_SH x (cell size of the level) of the
- * threshold distance, or when the walk's cell sequence is decided by less
- * than EPS_SH (level cell units: the start cell, or two crossings of one
- * step) and one of the cells the other choice would visit holds a line
- * within that margin of blocking. */
-static const double EPS_SH = 1e-3;
+ * float32: the hit point v + p_local is rounded once to float32 (half an ulp,
+ * 1.5e-5 voxel below 256 and 3e-5 below 512, far above the float-float
+ * local point's own error) and the walk's start point, the hit plus one cell
+ * toward the light, once more; the distance tests on O(1) cell coordinates
+ * add about 1e-6. A pixel is a tie when a visited cell's line lies within
+ * EPS_SH x (cell size of the level) of the threshold distance, or when the
+ * walk's cell sequence is decided by less than EPS_SH (level cell units: the
+ * start cell, or two crossings of one step) and one of the cells the other
+ * choice would visit holds a line within that margin of blocking. EPS_SH =
+ * 1e-4 is 3x the error bound for grids up to 256^3 and 1.6x up to 512^3. */
+static const double EPS_SH = 1e-4;
 /* a quarter of the 2e-3 per-channel tolerance the parity tests use */
 static const double FLIP_MIN = 5e-4;
 
@@ -677,7 +688,13 @@ static void flag_sorted_ties(const orc_voxset *vs, const hit *hs, int nh, pixsta
         if (x->e.part && y->e.part && x->e.c[0] == y->e.c[0] && x->e.c[1] == y->e.c[1] &&
             x->e.c[2] == y->e.c[2] && x->e.ymargin > YMARGIN && y->e.ymargin > YMARGIN)
             continue;
-        note(ps, (y->t - x->t) / (x->eps + y->eps), TIE_SORT);
+        const double m = (y->t - x->t) / (x->eps + y->eps);
+        note(ps, m, TIE_SORT);
+        if (m < 1.0) {
+            ps->nsort++;
+            ps->sort_vox = (int64_t)ps->nvox;
+            ps->sort_i = i;
+        }
     }
 }
 
@@ -769,6 +786,11 @@ static void trace_dda(const orc_voxset *vs, const orc_lod *L, const orc_rdesc *r
         if (nh > 0) {
             qsort(*buf, (size_t)nh, sizeof(hit), hit_cmp);
             flag_sorted_ties(vs, *buf, nh, ps);
+            if ((int64_t)ps->nvox == ps->swap_vox && ps->swap_i + 1 < nh) {   /* the other order of a near-tie */
+                const hit x = (*buf)[ps->swap_i];
+                (*buf)[ps->swap_i] = (*buf)[ps->swap_i + 1];
+                (*buf)[ps->swap_i + 1] = x;
+            }
             if (rd->still) nh = dedup_line_ids(vs, *buf, nh);
             for (int i = 0; i < nh && !ps->done; i++) shade_composite(vs, L, rd, O, D, Lt, &(*buf)[i], ps);
         }
@@ -895,8 +917,8 @@ static void trace_brute(const orc_voxset *vs, const orc_lod *L, const orc_rdesc 
 
 int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
                const orc_rdesc *rd, const int32_t *pix, int64_t npix, int mode,
-               double *rgba, uint8_t *tie, double *margin, double *flip, uint64_t *counters,
-               int nthreads) {
+               double *rgba, uint8_t *tie, double *margin, double *flip, double *alt,
+               uint64_t *counters, int nthreads) {
     if ((rd->shadows == 1 || rd->ao) && !L) return ORC_EINVAL;
     if (rd->shadows == 2 && (!rd->reps || rd->shadow_level < 0 || rd->shadow_level >= rd->reps->levels))
         return ORC_EINVAL;
@@ -929,11 +951,28 @@ int orc_render(const orc_voxset *vs, const orc_lod *L, const orc_view *view,
             pixstate ps;
             memset(&ps, 0, sizeof ps);
             ps.margin = 1e300;
+            ps.swap_vox = -1;
             if (mode == ORC_RENDER_BRUTE && rd->still) trace_brute_still(vs, L, rd, O, D, Lt, &ps);
             else if (mode == ORC_RENDER_BRUTE) trace_brute(vs, L, rd, O, D, Lt, &ps);
             else trace_dda(vs, L, rd, O, D, Lt, &ps, &buf, &bufcap);
             for (int c = 0; c < 3; c++) rgba[4 * p + c] = ps.C[c] + (1.0 - ps.A) * rd->bg[c];
             rgba[4 * p + 3] = ps.A;
+            if (alt) {
+                /* a pixel whose only near-tie is one depth order has two
+                 * right answers: the second composites that pair the other
+                 * way round */
+                for (int c = 0; c < 4; c++) alt[4 * p + c] = NAN;
+                if (mode != ORC_RENDER_BRUTE && ps.tie == TIE_SORT && ps.nsort == 1) {
+                    pixstate ps2;
+                    memset(&ps2, 0, sizeof ps2);
+                    ps2.margin = 1e300;
+                    ps2.swap_vox = ps.sort_vox;
+                    ps2.swap_i = ps.sort_i;
+                    trace_dda(vs, L, rd, O, D, Lt, &ps2, &buf, &bufcap);
+                    for (int c = 0; c < 3; c++) alt[4 * p + c] = ps2.C[c] + (1.0 - ps2.A) * rd->bg[c];
+                    alt[4 * p + 3] = ps2.A;
+                }
+            }
             if (tie) tie[p] = (uint8_t)ps.tie;
             if (margin) margin[p] = ps.margin;
             if (flip) flip[p] = ps.flip;
@@ -1016,9 +1055,73 @@ static void raster_color(const rseg *s, const orc_rdesc *rd, const double *O, co
 /* a quarter of the 2e-3 per-channel tolerance the parity tests use */
 static const double SWAP_MIN = 5e-4;
 
+/* Blend the sorted fragments of one pixel front to back (opaque: the
+ * nearest); swap >= 1 blends fragments swap - 1 and swap in the other order.
+ * Only decisions about the blended fragments matter: two neighbours in depth
+ * order (the second may be the first one not blended) closer than their
+ * error bounds may swap, unless both entered one joint sphere
+ * (bit-identical roots); a swap moves the pixel by T a_i a_i+1 (c_i -
+ * c_i+1), flagged from SWAP_MIN on (opaque: c_0 - c_1). Returns the number
+ * of fragments blended. */
+static int64_t raster_blend(const rseg *S, hit *hs, int64_t nh, const orc_rdesc *rd, const double *O,
+                            const double *D, const double *Lt, pixstate *ps, int64_t swap) {
+    if (swap >= 1 && swap < nh) {
+        const hit x = hs[swap - 1];
+        hs[swap - 1] = hs[swap];
+        hs[swap] = x;
+    }
+    int64_t m = 0;   /* fragments blended */
+    double Tprev = 1.0, cprev[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = 0; i <= nh; i++) {
+        double c[3] = {0.0, 0.0, 0.0};
+        const float *tf = i < nh ? rd->tf + 4 * S[hs[i].k].attr : NULL;
+        if (i < nh) raster_color(&S[hs[i].k], rd, O, D, hs[i].t, Lt, c);
+        if (i > 0 && i < nh) {
+            const entry *x = &hs[i - 1].e, *y = &hs[i].e;
+            const int same = x->part && y->part && x->c[0] == y->c[0] && x->c[1] == y->c[1] &&
+                             x->c[2] == y->c[2];
+            const double aa = rd->opaque ? 1.0 : (double)rd->tf[4 * S[hs[i - 1].k].attr + 3] * tf[3];
+            double dc = 0.0;
+            for (int q = 0; q < 3; q++) dc = fmax(dc, fabs(c[q] - cprev[q]));
+            if (!same && Tprev * aa * dc >= SWAP_MIN) {
+                const double mg = (hs[i].t - hs[i - 1].t) / (hs[i - 1].eps + hs[i].eps);
+                note(ps, mg, TIE_SORT);
+                if (mg < 1.0) {
+                    ps->nsort++;
+                    ps->sort_i = i;
+                }
+            }
+        }
+        if (i == nh || ps->done) break;
+        m++;
+        ps->nhit++;
+        for (int q = 0; q < 3; q++) cprev[q] = c[q];
+        Tprev = 1.0 - ps->A;
+        if (rd->opaque) {
+            for (int q = 0; q < 3; q++) ps->C[q] = c[q];
+            ps->A = 1.0;
+            ps->done = 1;
+            continue;
+        }
+        const double w = (1.0 - ps->A) * (double)tf[3];
+        for (int q = 0; q < 3; q++) ps->C[q] += w * c[q];
+        ps->A += w;
+        float t1 = 1.0f - ps->A32;
+        float t2 = t1 * tf[3];
+        ps->A32 = ps->A32 + t2;
+        if (ps->A32 >= rd->ert_alpha) ps->done = 1;
+    }
+    if (swap >= 1 && swap < nh) {   /* restore the sorted order */
+        const hit x = hs[swap - 1];
+        hs[swap - 1] = hs[swap];
+        hs[swap] = x;
+    }
+    return m;
+}
+
 int orc_raster(const float *xyz, const float *attr, const int64_t *offsets, int64_t nc, const orc_grid *g,
                const orc_view *view, const orc_rdesc *rd, const int32_t *pix, int64_t npix, double *rgba,
-               uint8_t *tie, uint64_t *counters, int nthreads) {
+               uint8_t *tie, double *alt, uint64_t *counters, int nthreads) {
     if (nc < 0 || !offsets || (!xyz && offsets[nc] > 0)) return ORC_EINVAL;
     if (view->width < 1 || view->height < 1 || !(rd->radius > 0.0f)) return ORC_EINVAL;
     rseg *S = NULL;
@@ -1072,53 +1175,24 @@ int orc_raster(const float *xyz, const float *attr, const int64_t *offsets, int6
                 nh++;
             }
             qsort(hs, (size_t)nh, sizeof(hit), raster_hit_cmp);
-            int64_t m = 0;   /* fragments blended */
-            double Tprev = 1.0, cprev[3] = {0.0, 0.0, 0.0};
-            for (int64_t i = 0; i <= nh; i++) {
-                double c[3] = {0.0, 0.0, 0.0};
-                const float *tf = i < nh ? rd->tf + 4 * S[hs[i].k].attr : NULL;
-                if (i < nh) raster_color(&S[hs[i].k], rd, O, D, hs[i].t, Lt, c);
-                /* Only decisions about the blended fragments matter: two
-                 * neighbours in depth order (the second may be the first one
-                 * not blended) closer than their error bounds may swap, unless
-                 * both entered one joint sphere (bit-identical roots); a swap
-                 * moves the pixel by T a_i a_i+1 (c_i - c_i+1), flagged from
-                 * SWAP_MIN on (opaque: c_0 - c_1). */
-                if (i > 0 && i < nh) {
-                    const entry *x = &hs[i - 1].e, *y = &hs[i].e;
-                    const int same = x->part && y->part && x->c[0] == y->c[0] && x->c[1] == y->c[1] &&
-                                     x->c[2] == y->c[2];
-                    const double aa = rd->opaque ? 1.0 : (double)rd->tf[4 * S[hs[i - 1].k].attr + 3] * tf[3];
-                    double dc = 0.0;
-                    for (int q = 0; q < 3; q++) dc = fmax(dc, fabs(c[q] - cprev[q]));
-                    if (!same && Tprev * aa * dc >= SWAP_MIN)
-                        note(&ps, (hs[i].t - hs[i - 1].t) / (hs[i - 1].eps + hs[i].eps), TIE_SORT);
-                }
-                if (i == nh || ps.done) break;
-                m++;
-                ps.nhit++;
-                for (int q = 0; q < 3; q++) cprev[q] = c[q];
-                Tprev = 1.0 - ps.A;
-                if (rd->opaque) {
-                    for (int q = 0; q < 3; q++) ps.C[q] = c[q];
-                    ps.A = 1.0;
-                    ps.done = 1;
-                    continue;
-                }
-                const double w = (1.0 - ps.A) * (double)tf[3];
-                for (int q = 0; q < 3; q++) ps.C[q] += w * c[q];
-                ps.A += w;
-                float t1 = 1.0f - ps.A32;
-                float t2 = t1 * tf[3];
-                ps.A32 = ps.A32 + t2;
-                if (ps.A32 >= rd->ert_alpha) ps.done = 1;
-            }
+            const int64_t m = raster_blend(S, hs, nh, rd, O, D, Lt, &ps, -1);
             /* a capsule grazed in front of the last blended fragment may
              * appear or vanish */
             if (graze_m < 1.0 && (m == nh || graze_t <= hs[m - 1].t + 1e-3)) note(&ps, graze_m, TIE_GRAZE);
             for (int c = 0; c < 3; c++) rgba[4 * p + c] = ps.C[c] + (1.0 - ps.A) * rd->bg[c];
             rgba[4 * p + 3] = ps.A;
             if (tie) tie[p] = (uint8_t)ps.tie;
+            if (alt) {   /* one near-tie in depth order: the pair blended the other way round */
+                for (int c = 0; c < 4; c++) alt[4 * p + c] = NAN;
+                if (ps.tie == TIE_SORT && ps.nsort == 1) {
+                    pixstate ps2;
+                    memset(&ps2, 0, sizeof ps2);
+                    ps2.margin = 1e300;
+                    raster_blend(S, hs, nh, rd, O, D, Lt, &ps2, ps.sort_i);
+                    for (int c = 0; c < 3; c++) alt[4 * p + c] = ps2.C[c] + (1.0 - ps2.A) * rd->bg[c];
+                    alt[4 * p + 3] = ps2.A;
+                }
+            }
             c0 += (uint64_t)nh;
             c1 += ps.nhit;
         }

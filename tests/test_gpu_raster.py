@@ -3,10 +3,12 @@ front-to-back blending; opaque depth test) against the oracle's reading K1.
 
 RGBA within 2e-3 per channel outside the pixels the oracle flags (grazed
 silhouettes, fragments closer in depth than their error bounds whose swap
-would show), which are capped; fragment counts equal the oracle's up to the
-flagged decisions. Near a joint, one capsule's side and the next capsule's
-end sphere (tangent surfaces) are entered at depths that differ only to
-second order, so about 0.5 % of an opaque frame's pixels are such ties.
+would show), which are capped at 0.1 %; fragment counts equal the oracle's
+up to the flagged decisions. Near a joint, one capsule's side and the next
+capsule's end sphere (tangent surfaces) are entered at depths that differ
+only to second order, so about 0.5 % of an opaque frame's pixels hold such a
+pair: where it is the pixel's only near-tie, either order is right and the
+pixel must match one of the oracle's two answers.
 """
 import numpy as np
 import pytest
@@ -30,6 +32,9 @@ def env():
     return lvr, O, ctx, dev
 
 
+env_alt = [None]   # the oracle's second answers of the last _raster call
+
+
 def _raster(env, ls, R, cam, crop, radius, tf, pix=None, **kw):
     import torch
     lvr, O, ctx, dev = env
@@ -50,7 +55,9 @@ def _raster(env, ls, R, cam, crop, radius, tf, pix=None, **kw):
     else:
         x0, y0 = (crop[0], crop[1]) if crop else (0, 0)
         sel = (pix[:, 1] - y0) * w + (pix[:, 0] - x0)
-    ref, tie, cnt = O.raster(ls.xyz, ls.attr, ls.offsets, O.make_grid(**g), ov, O.make_rdesc(radius, tf, **okw), pix)
+    ref, tie, cnt, alt = O.raster(ls.xyz, ls.attr, ls.offsets, O.make_grid(**g), ov, O.make_rdesc(radius, tf, **okw),
+                                  pix, alts=True)
+    env_alt[0] = alt
     return got[sel], ref, tie, stats, cnt
 
 
@@ -59,7 +66,7 @@ def test_opaque_depth_test(env):
     ls = S.streamlines(500, 64, 0)
     got, ref, tie, stats, cnt = _raster(env, ls, 32, synth.orbit_view((32, 32, 32), 128, 128), None, 0.2,
                                         synth.tf_ramp(), opaque=True)
-    S.check_image(got, ref, tie, cap=1e-2, what="raster opaque")
+    S.check_image(got, ref, tie, what="raster opaque", alt=env_alt[0])
     assert (ref[:, 3] > 0).mean() > 0.3
     assert abs(stats["fragments"] - int(cnt[0])) <= 2e-3 * cnt[0]
 
@@ -70,7 +77,7 @@ def test_transparent_lists(env, ert):
     ls = S.streamlines(500, 64, 0)
     got, ref, tie, stats, cnt = _raster(env, ls, 32, synth.orbit_view((32, 32, 32), 128, 96), None, 0.2,
                                         synth.tf_ramp(0.05, 0.3), ert_alpha=ert)
-    S.check_image(got, ref, tie, cap=5e-3, what=f"raster transparent ert {ert}")
+    S.check_image(got, ref, tie, what=f"raster transparent ert {ert}", alt=env_alt[0])
     assert abs(stats["fragments"] - int(cnt[0])) <= 2e-3 * cnt[0]
     assert stats["list_bytes"] == 12 * stats["fragments"] and stats["max_per_pixel"] > 10
 

@@ -56,10 +56,9 @@ class Scene:
         lvr.lvr_render(ctx, self.gls, self.glod, lv, desc, out, counters=cnt)
         ctx.sync()
         rd = O.make_rdesc(radius, self.tf, **okw)
-        if flips:   # the oracle's flip budget of hard-shadow near-ties, kept for check_image
-            ref, tie, ocnt, self.flip = O.render(self.ovs, self.olod, ov, rd, pix, flips=True)
-        else:
-            ref, tie, ocnt = O.render(self.ovs, self.olod, ov, rd, pix)
+        # kept for check_image: the oracle's flip budget of hard-shadow
+        # near-ties and its second right answer of one-pair depth ties
+        ref, tie, ocnt, self.flip, self.alt = O.render(self.ovs, self.olod, ov, rd, pix, flips=True, alts=True)
         got = out.cpu().numpy().reshape(-1, 4)
         return got, ref, tie, (cnt.cpu().numpy() if counters else None), ocnt
 
@@ -83,7 +82,7 @@ def test_c1_opaque_full_image(env, c1):
     """Config 1: 500 x 64 streamlines, 32^3, r = 0.2, opaque, 128 x 128."""
     cam = synth.orbit_view((32, 32, 32), 128, 128)
     got, ref, tie, gc, oc = c1.render(env, cam, radius=0.2, opaque=True, counters=True)
-    S.check_image(got, ref, tie, what="c1 opaque")
+    S.check_image(got, ref, tie, what="c1 opaque", alt=c1.alt)
     assert (ref[:, 3] > 0).mean() > 0.3
     # the same voxels and records are read (float32 may pass a voxel edge on
     # the other side, so allow a few extra or fewer)
@@ -96,7 +95,7 @@ def test_c3_illumination_small(env, c1t):
     cam = synth.orbit_view((32, 32, 32), 192, 108)
     got, ref, tie, gc, oc = c1t.render(env, cam, radius=0.2, ert_alpha=0.99, shadows=True, ao_mode=1,
                                        counters=True)
-    S.check_image(got, ref, tie, what="c3 small")
+    S.check_image(got, ref, tie, what="c3 small", alt=c1t.alt)
     # traversal counters match the oracle's within the tie pixels' share
     np.testing.assert_allclose(gc, oc.astype(np.float64), rtol=2e-3)
 
@@ -113,9 +112,10 @@ def test_c3_full_frame_sampled(env, c1t):
     ctx.sync()
     rng = np.random.default_rng(0)
     pix = np.stack([rng.integers(0, 1920, 3000), rng.integers(0, 1080, 3000)], 1).astype(np.int32)
-    ref, tie, _ = O.render(c1t.ovs, c1t.olod, ov, O.make_rdesc(0.2, c1t.tf, ert_alpha=0.99, shadows=True, ao=True), pix)
+    ref, tie, _, alt = O.render(c1t.ovs, c1t.olod, ov, O.make_rdesc(0.2, c1t.tf, ert_alpha=0.99, shadows=True, ao=True),
+                                pix, alts=True)
     got = out.cpu().numpy()[pix[:, 1], pix[:, 0]]
-    S.check_image(got, ref, tie, cap=3e-3, what="c3 sampled")
+    S.check_image(got, ref, tie, what="c3 sampled", alt=alt)
 
 
 def test_c2_crop_transparent(env, c2):
@@ -123,7 +123,7 @@ def test_c2_crop_transparent(env, c2):
     termination at 0.99, 1920 x 1080 view; the central 256 x 256 crop."""
     cam = synth.orbit_view((256, 256, 256), 1920, 1080)
     got, ref, tie, gc, oc = c2.render(env, cam, crop=(832, 412, 256, 256), ert_alpha=0.99, counters=True)
-    S.check_image(got, ref, tie, what="c2 crop")
+    S.check_image(got, ref, tie, what="c2 crop", alt=c2.alt)
     assert (ref[:, 3] > 0.9).mean() > 0.5
     np.testing.assert_allclose(gc, oc.astype(np.float64), rtol=2e-3)
 
@@ -134,7 +134,7 @@ def test_c2_crop_shadows_ao(env, c2):
     cam = synth.orbit_view((256, 256, 256), 1920, 1080)
     got, ref, tie, gc, oc = c2.render(env, cam, crop=(896, 476, 128, 128), ert_alpha=0.99, shadows=True,
                                       ao_mode=1, counters=True)
-    S.check_image(got, ref, tie, what="c2 crop AO")
+    S.check_image(got, ref, tie, what="c2 crop AO", alt=c2.alt)
     np.testing.assert_allclose(gc, oc.astype(np.float64), rtol=2e-3)
 
 
@@ -149,14 +149,15 @@ def test_c2_full_frame_sampled(env, c2):
     lv, ov, _ = S.views(cam)
     rng = np.random.default_rng(1)
     pix = np.stack([rng.integers(0, 1920, 2000), rng.integers(0, 1080, 2000)], 1).astype(np.int32)
-    ref, tie, _ = O.render(c2.ovs, c2.olod, ov, O.make_rdesc(0.15, c2.tf, ert_alpha=0.99, shadows=True, ao=True), pix)
+    ref, tie, _, alt = O.render(c2.ovs, c2.olod, ov, O.make_rdesc(0.15, c2.tf, ert_alpha=0.99, shadows=True, ao=True),
+                                pix, alts=True)
     for kw in (dict(), dict(layout=lvr.LAYOUT_AOS16, tile=(4, 8))):
         out = torch.empty((1080, 1920, 4), dtype=torch.float32, device=dev)
         desc = lvr.make_desc(0.15, c2.tf, ert_alpha=0.99, shadows=True, ao_mode=1, **kw)
         lvr.lvr_render(ctx, c2.gls, c2.glod, lv, desc, out)
         ctx.sync()
         got = out.cpu().numpy()[pix[:, 1], pix[:, 0]]
-        S.check_image(got, ref, tie, cap=3e-3, what=f"c2 sampled {kw}")
+        S.check_image(got, ref, tie, what=f"c2 sampled {kw}", alt=alt)
 
 
 def test_tile_shapes_bit_identical(env, c1t):
@@ -203,7 +204,7 @@ def test_edge_cases(env, c1t):
                   up=np.array([0, 1, 0], np.float32), fovy_deg=70.0, width=64, height=48,
                   light_dir=np.array([0.2, -1, 0.1], np.float32))
     got, ref, tie, _, _ = c1t.render(env, inside, radius=0.2, ert_alpha=0.99, shadows=True, ao_mode=1)
-    S.check_image(got, ref, tie, cap=5e-3, what="camera inside")
+    S.check_image(got, ref, tie, what="camera inside", alt=c1t.alt)
     away = dict(inside, eye=np.array([100.0, 100.0, 100.0], np.float32), at=np.array([200.0, 100, 100], np.float32))
     got, ref, tie, _, _ = c1t.render(env, away, radius=0.2)
     np.testing.assert_array_equal(got, np.tile([1, 1, 1, 0], (64 * 48, 1)).astype(np.float32))
@@ -240,9 +241,9 @@ def test_many_hits_in_one_voxel(env):
     lv, ovw, pix = S.views(cam)
     out = np.empty((32, 48, 4), np.float32)
     lvr.lvr_render(ctx, gl, None, lv, lvr.make_desc(0.3, tf, ert_alpha=2.0), out)
-    ref, tie, cnt = O.render(ov, None, ovw, O.make_rdesc(0.3, tf, ert_alpha=2.0), pix)
+    ref, tie, cnt, alt = O.render(ov, None, ovw, O.make_rdesc(0.3, tf, ert_alpha=2.0), pix, alts=True)
     assert cnt[3] / len(pix) > 10
-    S.check_image(out, ref, tie, cap=2e-2, what="overflow path")
+    S.check_image(out, ref, tie, what="overflow path", alt=alt)
 
 
 def test_invalid_render_arguments(env, c1t):
@@ -270,7 +271,7 @@ def test_still_camera_mode_matches_oracle(env, c1t, c1):
     cam = synth.orbit_view((32, 32, 32), 192, 108)
     got, ref, tie, gc, oc = c1t.render(env, cam, radius=0.2, ert_alpha=0.99, shadows=True, ao_mode=1,
                                        still=True, counters=True)
-    S.check_image(got, ref, tie, what="still transparent")
+    S.check_image(got, ref, tie, what="still transparent", alt=c1t.alt)
     # voxels visited, LoD samples, hits; records tested at rest are the
     # neighbour-list entries, a subset of the 27-voxel neighbourhoods
     # the oracle counts
@@ -278,7 +279,7 @@ def test_still_camera_mode_matches_oracle(env, c1t, c1):
     assert 0 < gc[1] <= oc[1] * 1.002
     got, ref, tie, _, _ = c1.render(env, synth.orbit_view((32, 32, 32), 128, 128), radius=0.2, opaque=True,
                                     still=True)
-    S.check_image(got, ref, tie, what="still opaque")
+    S.check_image(got, ref, tie, what="still opaque", alt=c1.alt)
 
 
 def test_still_camera_neighbour_lists(env, c1t):
@@ -306,8 +307,9 @@ def test_still_camera_neighbour_lists(env, c1t):
     assert np.array_equal(frame(narrow, 0.45), frame(wide, 0.45))
     got, ref, tie, _, _ = c1t.render(env, cam, radius=0.45, ert_alpha=0.99, shadows=True, still=True)
     # tubes of radius 0.45 overlap their neighbours' heavily, so more hits
-    # have near-equal entry depths: 12 of these 6144 pixels carry a tie flag
-    S.check_image(got, ref, tie, cap=0.004, what="still r=0.45")
+    # have near-equal entry depths: 12 of these 6144 pixels hold one such
+    # pair, and either order is right
+    S.check_image(got, ref, tie, what="still r=0.45", alt=c1t.alt)
     for r in (0.0, -1.0, float("nan")):
         with pytest.raises(lvr.LVRError) as ei:
             lvr.lvr_lineset_neighbours(ctx, wide, r)
@@ -420,10 +422,10 @@ def test_rep_line_shadows_c2_crop(env, c2):
     cam = synth.orbit_view((256, 256, 256), 1920, 1080)
     got, ref, tie, _, _ = c2.render(env, cam, crop=(896, 476, 128, 128), opaque=True, shadow_level=1,
                                     reps_oracle=reps, flips=True)
-    S.check_image(got, ref, tie, flip=c2.flip, what="c2 crop rep shadows, opaque")
+    S.check_image(got, ref, tie, flip=c2.flip, what="c2 crop rep shadows, opaque", alt=c2.alt)
     got, ref, tie, _, _ = c2.render(env, cam, crop=(896, 476, 128, 128), ert_alpha=0.99, shadow_level=1,
                                     reps_oracle=reps, flips=True)
-    S.check_image(got, ref, tie, flip=c2.flip, what="c2 crop rep shadows, transparent")
+    S.check_image(got, ref, tie, flip=c2.flip, what="c2 crop rep shadows, transparent", alt=c2.alt)
 
 
 def test_rep_line_shadows_invalid(env, c1t):

@@ -214,10 +214,10 @@ def test_flip_budget_is_the_diffuse_term(orc):
     threshold below which near-ties are not flagged; each flagged pixel is
     either lit (colour without shadows) or dark (ka c)."""
     from paper_1801_01155_gb300 import synth
-    ls = synth.make_streamlines(150, 48, seed=5)
+    ls = synth.make_streamlines(600, 48, seed=5)
     g = orc.make_grid(16, 32, scale=16.0, attr_min=float(ls.attr.min()), attr_max=float(ls.attr.max()))
     vs = orc.VoxSet(ls.xyz, ls.attr, ls.offsets, g)
-    W, H = 160, 120
+    W, H = 320, 240
     cam = synth.orbit_view((16, 16, 16), W, H)
     v = orc.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"])
     pix = orc.pixel_grid(0, 0, W, H)
@@ -248,7 +248,7 @@ def test_flip_budget_adds_up_along_the_ray(orc):
     ls = synth.make_streamlines(1500, 64, seed=6)
     g = orc.make_grid(16, 32, scale=16.0, attr_min=float(ls.attr.min()), attr_max=float(ls.attr.max()))
     vs = orc.VoxSet(ls.xyz, ls.attr, ls.offsets, g)
-    W, H = 160, 120
+    W, H = 480, 360
     cam = synth.orbit_view((16, 16, 16), W, H)
     v = orc.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], W, H, cam["light_dir"])
     pix = orc.pixel_grid(0, 0, W, H)
