@@ -31,16 +31,23 @@ __global__ void refresh_kernel(const float *__restrict__ p, bf16 *w1b, bf16 *w2b
 }
 
 // ------------------------------------------------------------------ inputs
-// Per-voxel input values of one LoD level: bf16(log1p(8 dens_l / 8^l)).
-__global__ void logd_kernel(const float *__restrict__ dens, int64_t n, float inv8l, bf16 *out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __float2bfloat16_rn(log1pf(8.0f * (dens[i] * inv8l)));
+// Per-voxel input values of one LoD level: bf16(log1p(8 dens_l / 8^l)),
+// rows (x) of `pitch` elements.
+__global__ void logd_kernel(const float *__restrict__ dens, int dx, int dy, int64_t n, int pitch, float inv8l,
+                            bf16 *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / dx;
+        out[row * pitch + (i - row * dx)] = __float2bfloat16_rn(log1pf(8.0f * (dens[i] * inv8l)));
+    }
 }
 
-// The three levels' input values and dimensions.
+// The three levels' input values (rows padded to `pitch` elements, a
+// multiple of 8: 16-byte rows, as the voxel term's tensor maps need) and
+// dimensions.
 struct Logd {
     const bf16 *d[3];
     int dims[3][3];
+    int pitch[3];
 };
 
 // Per-voxel inputs 16..390 of voxel v into row[0..374]: for each level the
@@ -53,61 +60,8 @@ __device__ __forceinline__ void gather_voxel_inputs(const Logd &L, int vx, int v
         bf16 v = __float2bfloat16_rn(0.0f);
         if ((unsigned)X < (unsigned)L.dims[l][0] && (unsigned)Y < (unsigned)L.dims[l][1] &&
             (unsigned)Z < (unsigned)L.dims[l][2])
-            v = L.d[l][X + (int64_t)L.dims[l][0] * (Y + (int64_t)L.dims[l][1] * Z)];
+            v = L.d[l][X + (int64_t)L.pitch[l] * (Y + (int64_t)L.dims[l][1] * Z)];
         row[i] = v;
-    }
-}
-
-constexpr int VT_ROW = VK + 8;   // padded smem row (bank-conflict-free fragments)
-
-// Layer-1 voxel term for every voxel: vterm[v][f] = bf16(sum_{k>=16} W1[f][k] x_v[k]).
-// One warp per 16 voxels: gather the 16 x 384 input tile into shared memory,
-// then 8 n-tiles x 24 k-steps of mma.
-__global__ void __launch_bounds__(64)
-vterm_kernel(Logd L, const bf16 *__restrict__ w1b, bf16 *vterm) {
-    __shared__ __align__(16) bf16 tile[2][16][VT_ROW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int dx = L.dims[0][0], dy = L.dims[0][1];
-    const int64_t nvox = (int64_t)dx * dy * L.dims[0][2];
-    bf16(*A)[VT_ROW] = tile[warp];
-    for (int64_t base = ((int64_t)blockIdx.x * 2 + warp) * 16; base < nvox; base += (int64_t)gridDim.x * 32) {
-        for (int r = 0; r < 16; r++) {
-            const int64_t v = base + r;
-            if (v < nvox) {
-                const int vx = (int)(v % dx), vy = (int)((v / dx) % dy), vz = (int)(v / ((int64_t)dx * dy));
-                gather_voxel_inputs(L, vx, vy, vz, A[r], lane, 32);
-            } else {
-                for (int k = lane; k < NVIN; k += 32) A[r][k] = __float2bfloat16_rn(0.0f);
-            }
-            if (lane < VK - NVIN) A[r][NVIN + lane] = __float2bfloat16_rn(0.0f);
-        }
-        __syncwarp();
-        float acc[8][4];
-#pragma unroll
-        for (int n = 0; n < 8; n++) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
-#pragma unroll 4
-        for (int k = 0; k < VK / 16; k++) {
-            uint32_t a[4];
-            const uint32_t *r0 = reinterpret_cast<const uint32_t *>(&A[g][k * 16]);
-            const uint32_t *r1 = reinterpret_cast<const uint32_t *>(&A[g + 8][k * 16]);
-            a[0] = r0[t];
-            a[1] = r1[t];
-            a[2] = r0[t + 4];
-            a[3] = r1[t + 4];
-#pragma unroll
-            for (int n = 0; n < 8; n++) {
-                const uint32_t *wr = reinterpret_cast<const uint32_t *>(w1b + (n * 8 + g) * NIN + VOFF + k * 16);
-                mma16816(acc[n], a, __ldg(wr + t), __ldg(wr + t + 4));
-            }
-        }
-#pragma unroll
-        for (int n = 0; n < 8; n++) {
-            if (base + g < nvox)
-                reinterpret_cast<uint32_t *>(vterm + (base + g) * NH + n * 8)[t] = pack_bf16x2(acc[n][0], acc[n][1]);
-            if (base + g + 8 < nvox)
-                reinterpret_cast<uint32_t *>(vterm + (base + g + 8) * NH + n * 8)[t] = pack_bf16x2(acc[n][2], acc[n][3]);
-        }
-        __syncwarp();
     }
 }
 
@@ -553,8 +507,9 @@ static lvr_status make_logd(lvr_ctx *ctx, const lvr_lod *lod, void **buf, size_t
     int64_t cnt[3];
     for (int l = 0; l < 3; l++) {
         cnt[l] = (int64_t)lod->dims[l][0] * lod->dims[l][1] * lod->dims[l][2];
+        L.pitch[l] = (lod->dims[l][0] + 7) & ~7;
         off[l] = tot;
-        tot += ((size_t)cnt[l] * 2 + 255) & ~(size_t)255;
+        tot += ((size_t)L.pitch[l] * lod->dims[l][1] * lod->dims[l][2] * 2 + 255) & ~(size_t)255;
         for (int a = 0; a < 3; a++) L.dims[l][a] = lod->dims[l][a];
     }
     if (*bytes < tot) {
@@ -569,7 +524,8 @@ static lvr_status make_logd(lvr_ctx *ctx, const lvr_lod *lod, void **buf, size_t
         bf16 *d = (bf16 *)((char *)*buf + off[l]);
         L.d[l] = d;
         const unsigned g = grid1d(cnt[l], 256) > 8192 ? 8192 : grid1d(cnt[l], 256);
-        logd_kernel<<<g, 256, 0, ctx->stream>>>(lod->dens[l], cnt[l], 1.0f / (float)(1 << (3 * l)), d);
+        logd_kernel<<<g, 256, 0, ctx->stream>>>(lod->dens[l], lod->dims[l][0], lod->dims[l][1], cnt[l], L.pitch[l],
+                                                1.0f / (float)(1 << (3 * l)), d);
     }
     LVR_CUDA(ctx, cudaGetLastError());
     return LVR_OK;
@@ -605,10 +561,19 @@ lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, const void
         if ((st = dev_alloc(ctx, &slot->vterm, vb)) != LVR_OK) return st;
         slot->bytes = vb;
     }
-    const int64_t tiles = (nvox + 31) / 32;
-    vterm_kernel<<<(unsigned)(tiles > 65535 * 8 ? 65535 * 8 : tiles), 64, 0, ctx->stream>>>(
-        L, (const bf16 *)m->w1b, (bf16 *)slot->vterm);
-    LVR_CUDA(ctx, cudaGetLastError());
+    // the coarse levels' terms (fp32, one row of 64 per level-1 and level-2 cell)
+    const size_t cb = (size_t)((int64_t)L.dims[1][0] * L.dims[1][1] * L.dims[1][2] +
+                               (int64_t)L.dims[2][0] * L.dims[2][1] * L.dims[2][2]) * NH * 4;
+    if (m->vcoarse_bytes < cb) {
+        dev_free(ctx, m->vcoarse);
+        m->vcoarse = nullptr;
+        m->vcoarse_bytes = 0;
+        if ((st = dev_alloc(ctx, (void **)&m->vcoarse, cb)) != LVR_OK) return st;
+        m->vcoarse_bytes = cb;
+    }
+    const void *ld[3] = {L.d[0], L.d[1], L.d[2]};
+    if ((st = ao_vterm_tc(ctx, ld, L.pitch, L.dims, m->vcoarse, m->w1b, slot->vterm)) != LVR_OK) return st;
+    if ((st = ao_vterm_tc_status(ctx)) != LVR_OK) return st;
     slot->gen = lod->gen;
     slot->used = m->clock;
     *vterm = slot->vterm;
@@ -652,7 +617,7 @@ extern "C" void lvr_free_ao_model(lvr_ao_model *m) {
     if (!m) return;
     lvr_ctx *ctx = m->ctx;
     cudaSetDevice(ctx->device);
-    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w4b, m->logd};
+    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w4b, m->logd, m->vcoarse};
     for (void *p : ps) dev_free(ctx, p);
     for (auto &b : m->bound) dev_free(ctx, b.vterm);
     delete m;

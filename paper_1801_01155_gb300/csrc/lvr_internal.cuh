@@ -105,6 +105,8 @@ struct lvr_ao_model {
     float *w4b = nullptr;
     void *logd = nullptr;         // scratch: bf16 per cell of levels 0..2, log1p(8 dens_l / 8^l)
     size_t logd_bytes = 0;
+    float *vcoarse = nullptr;     // scratch: fp32 voxel-term parts of the level-1 and level-2 cells
+    size_t vcoarse_bytes = 0;
     // voxel terms of the last LoDs the model was bound to (least recently used replaced)
     static constexpr int kBound = 8;
     struct Bound {
@@ -120,6 +122,12 @@ struct lvr_ao_model {
 // the cache or computed (ao_mlp.cu). *vterm stays valid until kBound other
 // LoDs have been bound or the weights change.
 lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, const void **vterm);
+// The learned-AO voxel term of every level-0 voxel on the tensor cores
+// (ao_vterm.cu); ao_vterm_tc_status synchronises and reports a pipeline wait
+// that ran out (LVR_ETIMEOUT).
+lvr_status ao_vterm_tc(lvr_ctx *ctx, const void *const logd[3], const int pitch[3], const int dims[3][3],
+                       float *coarse, const void *w1b, void *vterm);
+lvr_status ao_vterm_tc_status(lvr_ctx *ctx);
 
 // The cached voxel term of `lod` in `m`, or null (no side effects).
 inline const void *ao_cached(const lvr_ao_model *m, const lvr_lod *lod) {
