@@ -506,10 +506,48 @@ def learned_ao(args, lvr, synth, ctx, dev, stream, main):
     le2 = _frame_ms(lvr, ctx, stream, big, big_lod, view2, d2_le, out, model, n=5)
     err2 = lvr.lvr_ao_judge(ctx, big, big_lod, view2, d2_tr, model)
     res["frame_1080p_c2"] = {"traced_ms": round(tr2, 3), "learned_ms": round(le2, 3),
-                             "speedup": round(tr2 / le2, 3), "first_learned_frame_ms": round(first_ms, 2),
+                             "speedup": round(tr2 / le2, 3), "learned_beats_traced": bool(le2 < tr2),
+                             "first_learned_frame_ms": round(first_ms, 2),
                              "mean_abs_error": round(err2["mean_abs"], 5), "p99_abs_error": round(err2["p99_abs"], 5),
                              "note": "model trained on the small sets only"}
+    res["voxel_term_bind_256c"] = bind_time(lvr, ctx, stream, big, sig2, model)
+    big_lod.free()
+    big.free()
     return res, model
+
+
+def bind_time(lvr, ctx, stream, ls, sig, model, reps=3):
+    """The model's per-voxel layer-1 term for a 256^3 LoD (the tensor-core
+    convolutions of the three levels), timed by CUDA events around a one-hit
+    inference on a LoD the model has not seen. The model keeps the terms of
+    its last 8 LoDs, so 8 binds first fill those slots; the timed binds then
+    reuse a slot's buffer (no allocation inside the timed region)."""
+    import numpy as np
+    import torch
+    hit = [np.zeros(1, np.int32), np.ones((1, 3), np.float32), np.full((1, 3), 0.5, np.float32),
+           np.array([[0.0, 0.0, 1.0]], np.float32)]
+    d_hit = [torch.from_numpy(a).to(ls_device(torch)) for a in hit]
+    ao = torch.empty(1, dtype=torch.float32, device=ls_device(torch))
+    ms = []
+    for k in range(8 + reps):
+        lod = lvr.lvr_build_lod(ctx, ls, LEVELS, sig)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        lvr.lvr_ao_infer(ctx, model, lod, *d_hit, ao)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 8:
+            ms.append(e0.elapsed_time(e1))
+        lod.free()
+    return {"ms": round(float(np.median(ms)), 3), "reps": reps,
+            "note": "voxel term of every voxel: 5^3-tap convolutions of levels 2, 1, 0 on tcgen05 tensor cores "
+                    "(TMA halo loads, TMEM accumulators) plus one inference; ~45 ms with the mma.sync kernel it "
+                    "replaced"}
+
+
+def ls_device(torch):
+    return torch.device("cuda", torch.cuda.current_device())
 
 
 # ---------------------------------------------------------------- batched views (config 5)
@@ -675,9 +713,10 @@ def cpu_baseline(ls, tf, cam, budget_s=20.0):
     nthreads = O.num_threads()
     full, parts = oracle_step(O, ls, tf, cam, 20000, nthreads)
     return {"value": round(W * H / full / 1e6, 5), "unit": "Mrays/s", "cores": nthreads, "kind": "oracle",
+            "cores_per_phase": {"voxelize": 1, "lod": 1, "render": nthreads},
             "sample": (f"full oracle voxelise ({parts['voxelize_s']:.2f} s, 1 thread) + LoD "
-                       f"({parts['lod_s']:.2f} s) + render of {parts['sample_pixels']} random pixels of the "
-                       f"frame ({parts['render_sample_s']:.2f} s, {nthreads} threads), render time scaled "
+                       f"({parts['lod_s']:.2f} s, 1 thread) + render of {parts['sample_pixels']} random pixels of "
+                       f"the frame ({parts['render_sample_s']:.2f} s, {nthreads} threads), render time scaled "
                        f"to {W*H} rays")}
 
 
@@ -694,18 +733,25 @@ def run_reference(args):
     npix = 4000
     for k in range(args.warmup):
         oracle_step(O, ls, tf, cam, npix, nthreads, rng_seed=100 + k)
-    tot, parts = 0.0, None
+    tot, wall, parts = 0.0, 0.0, None
     for k in range(args.steps):
+        w0 = time.perf_counter()
         full, parts = oracle_step(O, ls, tf, cam, npix, nthreads, rng_seed=k)
+        wall += time.perf_counter() - w0
         tot += full
     value = args.steps * W * H / tot / 1e6
-    sample = (f"each step: full oracle voxelise + LoD, render of {npix} random pixels scaled to {W*H} rays "
-              f"({nthreads} threads)")
+    sample = (f"each step: full oracle voxelise (1 thread) + LoD (1 thread), render of {npix} random pixels "
+              f"({nthreads} threads) with the render time scaled to {W*H} rays")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Mrays/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
+            "scaled": True,
+            "measured_ms_per_step": round(wall / args.steps * 1e3, 2),
+            "scaling_note": ("ms_per_step and value are the full 1080p step extrapolated from the rendered pixel "
+                             "sample; measured_ms_per_step is the wall time each sampled step took"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": round(value, 5), "unit": "Mrays/s", "cores": nthreads, "kind": "oracle",
+                             "cores_per_phase": {"voxelize": 1, "lod": 1, "render": nthreads},
                              "sample": sample},
             "e2e": {"value": round(value, 5), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}

@@ -41,7 +41,8 @@ typedef enum lvr_status {
     LVR_ECUDA = 3,      /* CUDA runtime error */
     LVR_EOVERFLOW = 4,  /* a count beyond 2^32 - 1 (segments, neighbour-list entries,
                            fragments) or beyond a caller-owned capacity */
-    LVR_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    LVR_ETIMEOUT = 5,   /* a bounded device-side wait gave up (the learned-AO voxel term's
+                           tensor-core pipeline: lvr_render, lvr_ao_infer, lvr_batch_create) */
     LVR_EDEVICE = 6     /* no usable sm_103 device */
 } lvr_status;
 
@@ -129,8 +130,9 @@ void lvr_free_lineset(lvr_lineset *ls);
  * process exits, which limits grids to LVR_STATIC_MAX_VOXELS voxels
  * (128^3).
  *
- * All pointers are device pointers (host pointers: LVR_EINVAL; nothing is
- * staged). grid->fit must be 0. offset: uint32 [voxels + 1]; records and
+ * All pointers are device pointers of the current device (host pointers or
+ * another device's memory: LVR_EINVAL; nothing is staged). grid->fit must
+ * be 0. offset: uint32 [voxels + 1]; records and
  * keys: uint64 [capacity] receive the segments, voxel-major and by (curve,
  * position along the curve) within a voxel. Record bits: 0-2 entry face
  * (0=-x,1=+x,2=-y,3=+y,4=-z,5=+z), 3-9 / 10-16 entry bins on the two other
@@ -144,7 +146,8 @@ void lvr_free_lineset(lvr_lineset *ls);
  *
  * The first call on a device looks up the static array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream
- * capture. Every call on a device shares the one array, which keeps the
+ * capture. The address is kept for the process: after a cudaDeviceReset of
+ * that device the library must be reloaded before this call is used again. Every call on a device shares the one array, which keeps the
  * previous call's contents (the call clears what must start at zero):
  * calls that overlap on the GPU (from several streams or host threads)
  * race and must be serialised by the caller. Errors are reported by the

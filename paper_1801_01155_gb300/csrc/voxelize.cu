@@ -798,6 +798,16 @@ cudaError_t static_scratch(int dev, unsigned char **out) {
 
 }  // namespace
 
+// True when p is device memory of device `dev`, or managed memory.
+static bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
 extern "C" lvr_status lvr_voxelize_static(const float *xyz, const float *attr, const int64_t *curve_offsets,
                                           int64_t n_curves, int64_t n_vertices, const lvr_grid_desc *g,
                                           uint32_t *offset, uint64_t *records, uint64_t *keys,
@@ -814,12 +824,13 @@ extern "C" lvr_status lvr_voxelize_static(const float *xyz, const float *attr, c
     if (!(g->scale > 0.0f) || !isfinite(g->scale)) return LVR_EINVAL;
     const int64_t nvox = (int64_t)g->res[0] * g->res[1] * g->res[2];
     if (nvox > (int64_t)STATIC_MAX_VOXELS) return LVR_EINVAL;
-    // every buffer must already be on the device: nothing is staged
-    const void *ptrs[6] = {xyz, attr, curve_offsets, offset, records, keys};
-    for (const void *p : ptrs)
-        if (p && !is_device_ptr(p)) return LVR_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return LVR_EDEVICE;
+    // every buffer must already be in the current device's memory: nothing is
+    // staged, and the kernels run on this device
+    const void *ptrs[6] = {xyz, attr, curve_offsets, offset, records, keys};
+    for (const void *p : ptrs)
+        if (p && !on_device(p, dev)) return LVR_EINVAL;
     unsigned char *base = nullptr;
     if (static_scratch(dev, &base) != cudaSuccess) return LVR_ECUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -406,8 +406,15 @@ def lvr_voxelize_static(xyz, attr, curve_offsets, grid: GridDesc, offset, record
     raw = None
     if stream is not None:
         raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    rc = _L.lvr_voxelize_static(_ptr(xyz), _ptr(attr), _ptr(curve_offsets), nc, nv, C.byref(grid),
-                                _ptr(offset), _ptr(records), _ptr(keys), cap, C.byref(n), raw)
+    dev = getattr(curve_offsets, "device", None)
+    if dev is not None and getattr(dev, "type", None) == "cuda":
+        import torch   # the call runs on the current device: make it the buffers' device
+        with torch.cuda.device(dev):
+            rc = _L.lvr_voxelize_static(_ptr(xyz), _ptr(attr), _ptr(curve_offsets), nc, nv, C.byref(grid),
+                                        _ptr(offset), _ptr(records), _ptr(keys), cap, C.byref(n), raw)
+    else:
+        rc = _L.lvr_voxelize_static(_ptr(xyz), _ptr(attr), _ptr(curve_offsets), nc, nv, C.byref(grid),
+                                    _ptr(offset), _ptr(records), _ptr(keys), cap, C.byref(n), raw)
     if rc != OK:
         err = LVRError(rc, "lvr_voxelize_static failed")
         err.n_segments = n.value

@@ -56,6 +56,37 @@ def test_static_voxelize_matches_allocating_entry_point():
         np.testing.assert_array_equal(_decode(r), ref["fields"])
         np.testing.assert_array_equal((k >> np.uint64(32)).astype(np.uint32), ref["curve"])
         np.testing.assert_array_equal((k & np.uint64(0xffffffff)).astype(np.uint32), ref["ordinal"])
+    # a dense bundle: 3000 curves through one voxel, whose list is longer than
+    # the shared-memory sort limit and is sorted in place in the caller's buffers
+    rng = np.random.default_rng(3)
+    n_b = 3000
+    xyz_b = np.zeros((n_b, 2, 3), np.float32)
+    xyz_b[:, 0, 0], xyz_b[:, 1, 0] = 0.5, 2.5
+    xyz_b[:, :, 1] = (0.5 + 0.49 * (rng.random(n_b) - 0.5))[:, None]
+    xyz_b[:, :, 2] = (0.5 + 0.49 * (rng.random(n_b) - 0.5))[:, None]
+    xyz_b = xyz_b.reshape(-1, 3)
+    offs_b = np.arange(0, 2 * n_b + 1, 2, dtype=np.int64)
+    g_b = dict(res=(3, 1, 1), bins=128, scale=1.0)
+    ref = lvr.export_lineset_numpy(ctx, lvr.lvr_voxelize(ctx, xyz_b, None, offs_b, lvr.grid_desc(**g_b)))
+    assert len(ref["curve"]) == n_b
+    off = torch.empty(4, dtype=torch.int32, device=dev)
+    rec = torch.empty(n_b, dtype=torch.int64, device=dev)
+    key = torch.empty(n_b, dtype=torch.int64, device=dev)
+    for _ in range(2):
+        n = lvr.lvr_voxelize_static(torch.from_numpy(xyz_b).to(dev), None, torch.from_numpy(offs_b).to(dev),
+                                    lvr.grid_desc(**g_b), off, rec, key, stream)
+        stream.synchronize()
+        assert n == n_b
+        np.testing.assert_array_equal(off.cpu().numpy().view(np.uint32), ref["offset"])
+        np.testing.assert_array_equal(_decode(rec.cpu().numpy().view(np.uint64)), ref["fields"])
+        k = key.cpu().numpy().view(np.uint64)
+        np.testing.assert_array_equal((k >> np.uint64(32)).astype(np.uint32), ref["curve"])
+        np.testing.assert_array_equal((k & np.uint64(0xffffffff)).astype(np.uint32), ref["ordinal"])
+    # buffers outside the current device's memory are refused before anything runs
+    with pytest.raises(lvr.LVRError) as ei:
+        lvr.lvr_voxelize_static(torch.from_numpy(xyz_b), None, torch.from_numpy(offs_b).to(dev), lvr.grid_desc(**g_b),
+                                off, rec, key, stream)
+    assert ei.value.code == lvr.EINVAL
     # too large a grid for the static scratch
     ls = S.streamlines(50, 16, 0)
     with pytest.raises(lvr.LVRError) as ei:
