@@ -209,6 +209,32 @@ lvr_status lvr_export_lod(lvr_ctx *ctx, const lvr_lod *lod, int level, uint32_t 
                           float *len, float *dens);
 void lvr_free_lod(lvr_lod *lod);
 
+/* ------------------------------------------------------------------ saving and restoring
+ * The paper has no counterpart: a voxel model, a density LoD and a learned-AO
+ * model in training can be written out (lvr_export_lineset, lvr_export_lod,
+ * lvr_ao_model_state) and restored later without re-running the voxeliser or
+ * the trainer.
+ *
+ * lvr_import_lineset: a line set from the arrays lvr_export_lineset writes.
+ * info: res, bins, origin, scale, n_voxels (= res product) and n_segments
+ * (bytes is ignored); offset: uint32 [n_voxels + 1]; fields: uint8
+ * [n_segments * 8] (face_in, u_in, v_in, face_out, u_out, v_out, attribute
+ * byte, continues flag); curve, ordinal: uint32 [n_segments]; all host or
+ * device, only read. The arrays are checked (offsets from 0, non-decreasing,
+ * ending at n_segments; faces < 6, bins < N, flag 0 or 1; within a voxel
+ * strictly increasing (curve, ordinal), the voxeliser's order):
+ * LVR_EINVAL otherwise, with nothing kept. Synchronises the stream. */
+lvr_status lvr_import_lineset(lvr_ctx *ctx, const lvr_lineset_info *info, const uint32_t *offset,
+                              const uint8_t *fields, const uint32_t *curve, const uint32_t *ordinal,
+                              lvr_lineset **out);
+/* lvr_import_lod: a LoD of `levels` levels (1..4) over a grid of dims0
+ * voxels (level l: ceil(dims0 / 2^l) cells) from the per-level arrays
+ * lvr_export_lod writes: cnt[l] uint32, len[l] and dens[l] float32 (finite,
+ * >= 0, else LVR_EINVAL), each host or device. It renders exactly as the LoD
+ * it was exported from. Synchronises the stream. */
+lvr_status lvr_import_lod(lvr_ctx *ctx, int levels, const int32_t dims0[3], const uint32_t *const *cnt,
+                          const float *const *len, const float *const *dens, lvr_lod **out);
+
 /* ------------------------------------------------------------------ record layouts
  * The ray caster reads each segment as the packed 8-byte record of the
  * voxelisation (LVR_LAYOUT_AOS8) or, after lvr_lineset_layout, as a 16-byte
@@ -454,6 +480,17 @@ typedef struct lvr_ao_error {
 lvr_status lvr_ao_judge(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
                         const lvr_view *view, const lvr_render_desc *desc, lvr_ao_model *ao,
                         float *rgba, lvr_ao_error *err);
+/* Training checkpoint of a model trained with lvr_ao_train_step: its float32
+ * parameters, Adam moments m and v (float32 [lvr_ao_nparams()] each; zero
+ * before the first Adam step) and the number of Adam steps taken, into host
+ * or device buffers (synchronises). lvr_ao_model_set_state puts such a state
+ * into a model (parameters finite; the cached per-voxel terms are dropped):
+ * training continued from it takes the same steps as training that never
+ * stopped. */
+lvr_status lvr_ao_model_state(lvr_ctx *ctx, const lvr_ao_model *m, float *params, float *adam_m, float *adam_v,
+                              int64_t *step);
+lvr_status lvr_ao_model_set_state(lvr_ctx *ctx, lvr_ao_model *m, const float *params, const float *adam_m,
+                                  const float *adam_v, int64_t step);
 /* One step on a batch of n rows (1..2^20; device X bf16 bits [n][400],
  * device y float32 [n]): forward, mean squared error, backward, and, if
  * lr > 0, one Adam update (beta 0.9 / 0.999, eps 1e-8, bias-corrected)
@@ -485,6 +522,17 @@ typedef struct lvr_ao_train_desc {
  * over all samples (training forward pass). */
 lvr_status lvr_train_ao(lvr_ctx *ctx, const lvr_lineset *const *sets, const lvr_lod *const *lods,
                         int nsets, const lvr_ao_train_desc *td, lvr_ao_model **out, float *final_mse);
+
+/* ------------------------------------------------------------------ test hooks
+ * For tests of the failure paths; not for production use. Every device
+ * allocation the library makes goes through one allocator:
+ * lvr_test_fail_allocation(n) makes the allocation after the next n ones
+ * fail once with LVR_ENOMEM (n < 0: off), and lvr_test_live_allocations()
+ * returns how many of the library's device allocations are held right now
+ * (a call that fails must leave it where it was, apart from the context's
+ * grow-only buffers). Process-wide; not thread-safe with other calls. */
+void lvr_test_fail_allocation(int64_t n);
+int64_t lvr_test_live_allocations(void);
 
 #ifdef __cplusplus
 }

@@ -607,6 +607,35 @@ extern "C" lvr_status lvr_ao_model_create(lvr_ctx *ctx, const float *params, lvr
     return LVR_OK;
 }
 
+// Restore a model's training state (lvr_ao_model_set_state): parameters,
+// Adam moments and step count; the bf16 copies are refreshed and the cached
+// voxel terms dropped.
+lvr_status ao_set_state(lvr_ctx *ctx, lvr_ao_model *m, const float *params, const float *am, const float *av,
+                        int64_t step) {
+    if (!m->adam_m || !m->adam_v) {
+        float *mm = nullptr, *vv = nullptr;
+        lvr_status st = dev_alloc(ctx, (void **)&mm, NPARAM * 4);
+        if (st == LVR_OK) st = dev_alloc(ctx, (void **)&vv, NPARAM * 4);
+        if (st != LVR_OK) {
+            dev_free(ctx, mm);
+            dev_free(ctx, vv);
+            return st;
+        }
+        dev_free(ctx, m->adam_m);
+        dev_free(ctx, m->adam_v);
+        m->adam_m = mm;
+        m->adam_v = vv;
+    }
+    LVR_CUDA(ctx, cudaMemcpyAsync(m->params, params, NPARAM * 4, cudaMemcpyDefault, ctx->stream));
+    LVR_CUDA(ctx, cudaMemcpyAsync(m->adam_m, am, NPARAM * 4, cudaMemcpyDefault, ctx->stream));
+    LVR_CUDA(ctx, cudaMemcpyAsync(m->adam_v, av, NPARAM * 4, cudaMemcpyDefault, ctx->stream));
+    m->adam_t = step;
+    lvr_status st = refresh(ctx, m);
+    if (st != LVR_OK) return st;
+    LVR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // inputs may be caller memory
+    return LVR_OK;
+}
+
 extern "C" lvr_status lvr_ao_model_params(lvr_ctx *ctx, const lvr_ao_model *m, float *params) {
     if (!ctx) return LVR_EINVAL;
     if (!m || !params) return set_err(ctx, LVR_EINVAL, "lvr_ao_model_params: null argument");

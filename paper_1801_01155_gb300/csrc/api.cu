@@ -1,5 +1,7 @@
 // Context, memory staging, error reporting and export entry points.
 #include <stdarg.h>
+
+#include <atomic>
 #include <stdio.h>
 
 #include "lvr_internal.cuh"
@@ -32,19 +34,35 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Test hooks: a one-shot allocation failure after n more allocations, and
+// the count of device allocations held (every device allocation of the
+// library goes through dev_alloc / dev_free).
+static std::atomic<int64_t> g_fail_after{-1};
+static std::atomic<int64_t> g_live{0};
+void alloc_fail_after(int64_t n) { g_fail_after.store(n < 0 ? -1 : n); }
+int64_t alloc_live() { return g_live.load(); }
+
 lvr_status dev_alloc(lvr_ctx *ctx, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    int64_t f = g_fail_after.load();
+    while (f >= 0 && !g_fail_after.compare_exchange_weak(f, f - 1)) {
+    }
+    if (f == 0) return set_err(ctx, LVR_ENOMEM, "device allocation of %zu bytes refused (test hook)", bytes);
     cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
     if (e != cudaSuccess) {
         *p = nullptr;
         return cuda_err(ctx, e, "device allocation");
     }
+    g_live.fetch_add(1);
     return LVR_OK;
 }
 
 void dev_free(lvr_ctx *ctx, void *p) {
-    if (p) cudaFreeAsync(p, ctx->stream);
+    if (p) {
+        cudaFreeAsync(p, ctx->stream);
+        g_live.fetch_sub(1);
+    }
 }
 
 static lvr_status grow(lvr_ctx *ctx, void **buf, size_t *have, size_t want) {

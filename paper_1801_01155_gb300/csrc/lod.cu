@@ -479,17 +479,9 @@ extern "C" lvr_status lvr_export_ao_field(lvr_ctx *ctx, const lvr_lod *lod, floa
     return copy_out(ctx, field, lod->aof, n * 4);
 }
 
-extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int levels,
-                                    const float *sigma256, lvr_lod **out) {
-    if (!ctx) return LVR_EINVAL;
-    if (!ls || !out || !sigma256) return set_err(ctx, LVR_EINVAL, "lvr_build_lod: null argument");
-    *out = nullptr;
-    if (levels < 1 || levels > 4) return set_err(ctx, LVR_EINVAL, "levels must be in [1,4]");
-    for (int i = 0; i < 256; i++)
-        if (!(sigma256[i] >= 0.0f) || !(sigma256[i] < 1e30f))
-            return set_err(ctx, LVR_EINVAL, "sigma must be finite and >= 0");
-    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t s = ctx->stream;
+// A LoD handle with its level arrays and padded sampling copies allocated
+// (contents undefined): dims of level l = ceil(dims0 / 2^l).
+lvr_status lod_alloc(lvr_ctx *ctx, int levels, const int32_t dims0[3], lvr_lod **out) {
     static uint64_t next_gen = 0;
     lvr_lod *L = new lvr_lod();
     L->ctx = ctx;
@@ -497,11 +489,11 @@ extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int lev
     L->levels = levels;
     lvr_status st = LVR_OK;
     for (int l = 0; l < levels && st == LVR_OK; l++) {
-        for (int a = 0; a < 3; a++) L->dims[l][a] = l == 0 ? ls->res[a] : (L->dims[l - 1][a] + 1) / 2;
+        for (int a = 0; a < 3; a++) L->dims[l][a] = l == 0 ? dims0[a] : (L->dims[l - 1][a] + 1) / 2;
         const size_t n = (size_t)L->dims[l][0] * L->dims[l][1] * L->dims[l][2];
         if ((st = dev_alloc(ctx, (void **)&L->cnt[l], n * 4)) != LVR_OK) break;
         if ((st = dev_alloc(ctx, (void **)&L->len[l], n * 4)) != LVR_OK) break;
-        if ((st = dev_alloc(ctx, (void **)&L->dens[l], n * 4)) != LVR_OK) break;
+        st = dev_alloc(ctx, (void **)&L->dens[l], n * 4);
     }
     // padding of the sampling copies: the support of the density field is
     // [-c/2, (top + 1/2) c] per axis in level-0 units (c = 2^(levels-1), top =
@@ -522,6 +514,41 @@ extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int lev
         if (st == LVR_OK)
             L->pk0[l] = L->pk[l] + L->pad_lo[l] * (1 + L->pstride[l][0] + L->pstride[l][1]);
     }
+    if (st != LVR_OK) {
+        lvr_free_lod(L);
+        return st;
+    }
+    *out = L;
+    return LVR_OK;
+}
+
+// The corner-packed sampling copy of every level from its densities.
+lvr_status lod_pack(lvr_ctx *ctx, lvr_lod *L) {
+    for (int l = 0; l < L->levels; l++) {
+        const int32_t *dm = L->dims[l];
+        const int lo = L->pad_lo[l];
+        const int px = dm[0] + lo + L->pad_hi[l][0], py = dm[1] + lo + L->pad_hi[l][1], pz = dm[2] + lo + L->pad_hi[l][2];
+        const int64_t np = (int64_t)px * py * pz;
+        const unsigned g = grid1d(np, 256) > 65535 ? 65535 : grid1d(np, 256);
+        lod_pack_kernel<<<g, 256, 0, ctx->stream>>>(L->dens[l], dm[0], dm[1], dm[2], lo, px, py, pz, L->pk[l]);
+    }
+    LVR_CUDA(ctx, cudaGetLastError());
+    return LVR_OK;
+}
+
+extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int levels,
+                                    const float *sigma256, lvr_lod **out) {
+    if (!ctx) return LVR_EINVAL;
+    if (!ls || !out || !sigma256) return set_err(ctx, LVR_EINVAL, "lvr_build_lod: null argument");
+    *out = nullptr;
+    if (levels < 1 || levels > 4) return set_err(ctx, LVR_EINVAL, "levels must be in [1,4]");
+    for (int i = 0; i < 256; i++)
+        if (!(sigma256[i] >= 0.0f) || !(sigma256[i] < 1e30f))
+            return set_err(ctx, LVR_EINVAL, "sigma must be finite and >= 0");
+    LVR_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    lvr_lod *L = nullptr;
+    lvr_status st = lod_alloc(ctx, levels, ls->res, &L);
     if (st == LVR_OK) st = ensure_stage_in(ctx, 1024);
     if (st != LVR_OK) {
         lvr_free_lod(L);
@@ -539,20 +566,16 @@ extern "C" lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int lev
                                                              L->dens[l - 1], p[0], p[1], p[2], L->cnt[l],
                                                              L->len[l], L->dens[l]);
         }
-        for (int l = 0; l < levels; l++) {
-            const int32_t *dm = L->dims[l];
-            const int lo = L->pad_lo[l];
-            const int px = dm[0] + lo + L->pad_hi[l][0], py = dm[1] + lo + L->pad_hi[l][1],
-                      pz = dm[2] + lo + L->pad_hi[l][2];
-            const int64_t np = (int64_t)px * py * pz;
-            const unsigned g = grid1d(np, 256) > 65535 ? 65535 : grid1d(np, 256);
-            lod_pack_kernel<<<g, 256, 0, s>>>(L->dens[l], dm[0], dm[1], dm[2], lo, px, py, pz, L->pk[l]);
-        }
         e = cudaGetLastError();
     }
-    if (e != cudaSuccess) {
+    if (e == cudaSuccess) {
+        st = lod_pack(ctx, L);
+    } else {
+        st = cuda_err(ctx, e, "lvr_build_lod");
+    }
+    if (st != LVR_OK) {
         lvr_free_lod(L);
-        return cuda_err(ctx, e, "lvr_build_lod");
+        return st;
     }
     *out = L;
     return LVR_OK;

@@ -128,6 +128,18 @@ lvr_status ao_bind(lvr_ctx *ctx, lvr_ao_model *m, const lvr_lod *lod, const void
 lvr_status ao_vterm_tc(lvr_ctx *ctx, const void *const logd[3], const int pitch[3], const int dims[3][3],
                        float *coarse, const void *w1b, void *vterm);
 lvr_status ao_vterm_tc_status(lvr_ctx *ctx);
+// LoD handle allocation and the packed sampling copies (lod.cu), shared by
+// lvr_build_lod and lvr_import_lod.
+lvr_status lod_alloc(lvr_ctx *ctx, int levels, const int32_t dims0[3], lvr_lod **out);
+lvr_status lod_pack(lvr_ctx *ctx, lvr_lod *L);
+// Restore a learned-AO model's training state (ao_mlp.cu).
+lvr_status ao_set_state(lvr_ctx *ctx, lvr_ao_model *m, const float *params, const float *adam_m, const float *adam_v,
+                        int64_t step);
+// Device-allocation test hooks (api.cu): the n-th next allocation (0: the
+// next one) fails once with LVR_ENOMEM, n < 0 switches that off; and the
+// number of the library's device allocations currently held.
+void alloc_fail_after(int64_t n);
+int64_t alloc_live();
 
 // The cached voxel term of `lod` in `m`, or null (no side effects).
 inline const void *ao_cached(const lvr_ao_model *m, const lvr_lod *lod) {

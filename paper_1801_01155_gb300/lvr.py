@@ -139,6 +139,12 @@ _SIGS = {
     "lvr_ao_train_step": ([_vp, _vp, _i64, _vp, _vp, C.c_float, C.POINTER(C.c_float), _vp], C.c_int),
     "lvr_train_ao": ([_vp, _vp, _vp, C.c_int, C.POINTER(AoTrainDesc), C.POINTER(_vp),
                       C.POINTER(C.c_float)], C.c_int),
+    "lvr_import_lineset": ([_vp, C.POINTER(LineSetInfo), _vp, _vp, _vp, _vp, C.POINTER(_vp)], C.c_int),
+    "lvr_import_lod": ([_vp, C.c_int, _vp, _vp, _vp, _vp, C.POINTER(_vp)], C.c_int),
+    "lvr_ao_model_state": ([_vp, _vp, _vp, _vp, _vp, C.POINTER(_i64)], C.c_int),
+    "lvr_ao_model_set_state": ([_vp, _vp, _vp, _vp, _vp, _i64], C.c_int),
+    "lvr_test_fail_allocation": ([_i64], None),
+    "lvr_test_live_allocations": ([], _i64),
 }
 STATIC_MAX_VOXELS = 2097152
 for _n, (_a, _r) in _SIGS.items():
@@ -309,6 +315,22 @@ def export_lineset_numpy(ctx: Context, ls: LineSet) -> dict:
     return dict(offset=off, fields=fields, curve=curve, ordinal=ordn)
 
 
+def lvr_import_lineset(ctx: Context, res, bins, origin, scale, offset, fields, curve, ordinal) -> LineSet:
+    """A line set from the arrays lvr_export_lineset writes (host or device)."""
+    inf = LineSetInfo()
+    r = (res, res, res) if np.isscalar(res) else tuple(res)
+    inf.res[:] = [int(x) for x in r]
+    inf.bins = int(bins)
+    inf.origin[:] = [float(x) for x in origin]
+    inf.scale = float(scale)
+    inf.n_voxels = int(r[0]) * int(r[1]) * int(r[2])
+    inf.n_segments = int(len(curve)) if curve is not None else 0
+    h = _vp()
+    _check(ctx.handle, _L.lvr_import_lineset(ctx.handle, C.byref(inf), _ptr(offset), _ptr(fields), _ptr(curve),
+                                            _ptr(ordinal), C.byref(h)))
+    return LineSet(ctx, h)
+
+
 def lvr_free_lineset(ls: LineSet):
     ls.free()
 
@@ -333,6 +355,16 @@ def export_lod_numpy(ctx: Context, lod: Lod, level: int) -> dict:
     dn = np.empty(n, np.float32)
     lvr_export_lod(ctx, lod, level, cnt, ln, dn)
     return dict(cnt=cnt, len=ln, dens=dn, dims=d)
+
+
+def lvr_import_lod(ctx: Context, dims0, cnt, len_, dens) -> Lod:
+    """A LoD from per-level arrays (lists of host or device arrays, level 0 first)."""
+    levels = len(cnt)
+    d = (C.c_int32 * 3)(*[int(x) for x in dims0])
+    arr = lambda xs: (_vp * levels)(*[_ptr(x) for x in xs])   # noqa: E731
+    h = _vp()
+    _check(ctx.handle, _L.lvr_import_lod(ctx.handle, levels, d, arr(cnt), arr(len_), arr(dens), C.byref(h)))
+    return Lod(ctx, h)
 
 
 def lvr_free_lod(lod: Lod):
@@ -435,6 +467,28 @@ def lvr_ao_model_create(ctx: Context, params) -> AoModel:
     h = _vp()
     _check(ctx.handle, _L.lvr_ao_model_create(ctx.handle, _ptr(p), C.byref(h)))
     return AoModel(ctx, h)
+
+
+def lvr_ao_model_state(ctx: Context, m: AoModel):
+    """Training checkpoint: (params, adam_m, adam_v, step), float32 host arrays."""
+    n = lvr_ao_nparams()
+    p, mm, vv = (np.empty(n, np.float32) for _ in range(3))
+    step = _i64(0)
+    _check(ctx.handle, _L.lvr_ao_model_state(ctx.handle, m.handle, _ptr(p), _ptr(mm), _ptr(vv), C.byref(step)))
+    return p, mm, vv, step.value
+
+
+def lvr_ao_model_set_state(ctx: Context, m: AoModel, params, adam_m, adam_v, step: int):
+    args = [np.ascontiguousarray(x, np.float32) if isinstance(x, np.ndarray) else x for x in (params, adam_m, adam_v)]
+    _check(ctx.handle, _L.lvr_ao_model_set_state(ctx.handle, m.handle, *[_ptr(x) for x in args], int(step)))
+
+
+def lvr_test_fail_allocation(n: int):
+    _L.lvr_test_fail_allocation(int(n))
+
+
+def lvr_test_live_allocations() -> int:
+    return int(_L.lvr_test_live_allocations())
 
 
 def lvr_free_ao_model(m: AoModel):
