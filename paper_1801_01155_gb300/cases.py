@@ -1,0 +1,105 @@
+"""Named GPU cases for profiling one kernel on a reduced workload.
+
+    python -m paper_1801_01155_gb300.cases render-crop [--reps K]
+        the benchmark's render (config-2 set: 100k x 200 lines in 256^3,
+        transparency with termination at 0.99, soft shadows, 16 traced AO
+        rays, 16-byte records, 4x8 ray tiles) on the central 640 x 360 crop of
+        the 1920 x 1080 view: one warm-up render, then K renders
+    python -m paper_1801_01155_gb300.cases voxel-term [--reps K]
+        the learned-AO model bound to K fresh 3-level LoDs of the config-2 set
+        (each bind computes the per-voxel term of every voxel on the tensor
+        cores), after one warm-up bind
+
+Each prints one line with its CUDA-event times. The inputs are the seeded
+synthetic sets of the benchmark.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _setup(torch, lvr, synth):
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(dev)
+    ctx = lvr.Context(0, st)
+    ls = synth.make_streamlines(100_000, 200, 1)
+    tf = synth.tf_ramp(0.05, 0.3)
+    sig = synth.sigma_lut(tf)
+    g = lvr.grid_desc(256, 32, scale=256.0, attr_min=float(ls.attr.min()), attr_max=float(ls.attr.max()))
+    with torch.cuda.stream(st):
+        xyz, attr, offs = (torch.from_numpy(a).to(dev) for a in (ls.xyz, ls.attr, ls.offsets))
+    s = lvr.lvr_voxelize(ctx, xyz, attr, offs, g)
+    return dev, st, ctx, s, tf, sig
+
+
+def render_crop(reps):
+    import torch
+
+    from paper_1801_01155_gb300 import lvr, synth
+    dev, st, ctx, s, tf, sig = _setup(torch, lvr, synth)
+    lvr.lvr_lineset_layout(ctx, s, lvr.LAYOUT_AOS16)
+    lod = lvr.lvr_build_lod(ctx, s, 3, sig)
+    cam = synth.orbit_view((256, 256, 256), 1920, 1080)
+    view = lvr.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], 1920, 1080, cam["light_dir"],
+                         crop=(640, 360, 640, 360))
+    desc = lvr.make_desc(0.15, tf, ert_alpha=0.99, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0,
+                         tile=(4, 8), layout=lvr.LAYOUT_AOS16)
+    out = torch.empty((360, 640, 4), dtype=torch.float32, device=dev)
+    lvr.lvr_render(ctx, s, lod, view, desc, out)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lvr.lvr_render(ctx, s, lod, view, desc, out)
+        e1.record(st)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(f"render-crop: {np.median(ms):.3f} ms per 640x360 crop render (median of {reps})")
+
+
+def voxel_term(reps):
+    import torch
+
+    from paper_1801_01155_gb300 import lvr, synth
+    dev, st, ctx, s, tf, sig = _setup(torch, lvr, synth)
+    rng = np.random.default_rng(7)
+    m = lvr.lvr_ao_model_create(ctx, (rng.standard_normal(lvr.lvr_ao_nparams()) * 0.05).astype(np.float32))
+    hit = [torch.from_numpy(a).to(dev) for a in (np.zeros(1, np.int32), np.ones((1, 3), np.float32),
+                                                 np.full((1, 3), 0.5, np.float32),
+                                                 np.array([[0.0, 0.0, 1.0]], np.float32))]
+    ao = torch.empty(1, dtype=torch.float32, device=dev)
+    ms = []
+    for k in range(reps + 1):
+        lod = lvr.lvr_build_lod(ctx, s, 3, sig)
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lvr.lvr_ao_infer(ctx, m, lod, *hit, ao)   # binds the model to the new LoD
+        e1.record(st)
+        e1.synchronize()
+        if k > 0:
+            ms.append(e0.elapsed_time(e1))
+        lod.free()
+    print(f"voxel-term: {np.median(ms):.3f} ms per bind to a 256^3 LoD (median of {reps}, allocation included)")
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["render-crop", "voxel-term"])
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args(argv)
+    import __graft_entry__ as g
+    g.build()
+    (render_crop if a.case == "render-crop" else voxel_term)(a.reps)
+
+
+if __name__ == "__main__":
+    main()
