@@ -109,14 +109,28 @@ __device__ __forceinline__ uint32_t face_bin(int64_t X0b, int64_t Db, int64_t vb
 // axis (the sequential walk's state there), so the result is the same
 // segment sequence, ordinals and flags as one thread walking the curve.
 // COUNT: per-voxel segment counts and the total stored. SCATTER: each
-// segment goes into its voxel's range at an atomic cursor, as one 16-byte
-// (record, key) pair when `pair` is given (one partial sector per scattered
-// segment instead of two; the sort then writes the arrays), else into rec /
-// key directly.
+// segment goes into its voxel's range at an atomic cursor, as one 32-byte
+// slot holding the (record, key) pair when `pair` is given (one whole sector
+// per scattered segment, written by one store: the cache never fills a
+// partly written sector from DRAM; the sort then writes the arrays), else
+// into rec / key directly.
+// The scatter target of one segment: its record and key in the first half of
+// a 32-byte sector.
+struct __align__(32) PairSlot {
+    unsigned long long r, k, pad0, pad1;
+};
+__device__ __forceinline__ void store_slot(PairSlot *p, uint64_t r, uint64_t k) {
+    // streaming store (read once, by the sort): it should not push the cursors out of L2
+    asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"((uint32_t)r),
+                 "r"((uint32_t)(r >> 32)), "r"((uint32_t)k), "r"((uint32_t)(k >> 32)), "r"(0u), "r"(0u), "r"(0u),
+                 "r"(0u)
+                 : "memory");
+}
+
 template <bool SCATTER>
 __global__ void __launch_bounds__(256)
 vox_warp_kernel(VoxParams P, uint32_t *cnt, const uint32_t *__restrict__ offset, uint64_t *__restrict__ rec,
-                uint64_t *__restrict__ key, ulonglong2 *__restrict__ pair, unsigned long long *total) {
+                uint64_t *__restrict__ key, PairSlot *__restrict__ pair, unsigned long long *total) {
     const unsigned FULLM = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -253,13 +267,14 @@ vox_warp_kernel(VoxParams P, uint32_t *cnt, const uint32_t *__restrict__ offset,
                             const uint32_t vox =
                                 (uint32_t)(cur[0] + (int64_t)P.res[0] * (cur[1] + (int64_t)P.res[1] * cur[2]));
                             if (SCATTER) {
-                                const uint32_t at = offset[vox] + atomicAdd(cnt + vox, 1u);
+                                // with `pair`, cnt holds the cursors (the offsets to begin with)
+                                const uint32_t at = pair ? atomicAdd(cnt + vox, 1u) : offset[vox] + atomicAdd(cnt + vox, 1u);
                                 const uint32_t attr8 = (uint32_t)(((pA + hA) * 255 + 65535) / 131070);
                                 const uint64_t r =
                                     rec_pack(pf, pu, pv, hf, hu, hv, attr8, prev_stored ? 1u : 0u, (uint32_t)c);
                                 const uint64_t kk = ((uint64_t)c << 32) | (uint64_t)(j - 1);
                                 if (pair) {
-                                    pair[at] = make_ulonglong2(r, kk);
+                                    store_slot(pair + at, r, kk);
                                 } else {
                                     rec[at] = r;
                                     key[at] = kk;
@@ -466,7 +481,7 @@ scan_down_kernel(const uint32_t *__restrict__ cnt, int64_t n,
 // every list is written to rec / key; without, lists are sorted in place.
 __global__ void __launch_bounds__(256)
 sort_small_kernel(const uint32_t *__restrict__ offset, int64_t nvox, uint64_t *rec, uint64_t *key,
-                  const ulonglong2 *__restrict__ pair, uint32_t *long_list, uint32_t *long_count) {
+                  const PairSlot *__restrict__ pair, uint32_t *long_list, uint32_t *long_count) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nvox) return;
     const uint32_t beg = offset[v], n = offset[v + 1] - beg;
@@ -479,9 +494,8 @@ sort_small_kernel(const uint32_t *__restrict__ offset, int64_t nvox, uint64_t *r
     for (uint32_t i = 0; i < n; i++) {
         uint64_t kk, rr;
         if (pair) {
-            const ulonglong2 q = pair[beg + i];
-            rr = q.x;
-            kk = q.y;
+            rr = pair[beg + i].r;
+            kk = pair[beg + i].k;
         } else {
             kk = key[beg + i];
             rr = rec[beg + i];
@@ -528,7 +542,7 @@ __device__ void bitonic_block(uint32_t n, GetK getk, Swap swp) {
 
 __global__ void __launch_bounds__(256)
 sort_long_kernel(const uint32_t *__restrict__ offset, uint64_t *rec, uint64_t *key,
-                 const ulonglong2 *__restrict__ pair, const uint32_t *__restrict__ long_list,
+                 const PairSlot *__restrict__ pair, const uint32_t *__restrict__ long_list,
                  const uint32_t *__restrict__ long_count) {
     extern __shared__ uint64_t sm[];
     uint64_t *sk = sm, *sr = sm + SMEM_LIST;
@@ -539,18 +553,16 @@ sort_long_kernel(const uint32_t *__restrict__ offset, uint64_t *rec, uint64_t *k
         uint64_t *gk = key + beg, *gr = rec + beg;
         if (pair && n > SMEM_LIST) {   // sorted in place in the final arrays
             for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-                const ulonglong2 q = pair[beg + i];
-                gr[i] = q.x;
-                gk[i] = q.y;
+                gr[i] = pair[beg + i].r;
+                gk[i] = pair[beg + i].k;
             }
             __syncthreads();
         }
         if (n <= SMEM_LIST) {
             for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
                 if (pair) {
-                    const ulonglong2 q = pair[beg + i];
-                    sr[i] = q.x;
-                    sk[i] = q.y;
+                    sr[i] = pair[beg + i].r;
+                    sk[i] = pair[beg + i].k;
                 } else {
                     sk[i] = gk[i];
                     sr[i] = gr[i];
@@ -732,19 +744,20 @@ extern "C" lvr_status lvr_voxelize(lvr_ctx *ctx, const float *xyz, const float *
     scan_down_kernel<<<(unsigned)ntiles, SCAN_T, 0, s>>>(cnt, nvox, tiles, ls->offset);
     LVR_CUDA(ctx, cudaGetLastError());
     if (nseg > 0) {
-        if ((size_t)nseg * 16 > ctx->vox_pair_bytes) {   // grow-only scatter target
+        if ((size_t)nseg * sizeof(PairSlot) > ctx->vox_pair_bytes) {   // grow-only scatter target
             dev_free(ctx, ctx->vox_pair);
             ctx->vox_pair = nullptr;
             ctx->vox_pair_bytes = 0;
-            const size_t b = (size_t)nseg * 16 + (size_t)nseg * 2 + 4096;
+            const size_t b = (size_t)nseg * sizeof(PairSlot) + (size_t)nseg * 4 + 4096;
             if ((st = dev_alloc(ctx, &ctx->vox_pair, b)) != LVR_OK) {
                 lvr_free_lineset(ls);
                 return st;
             }
             ctx->vox_pair_bytes = b;
         }
-        ulonglong2 *pair = (ulonglong2 *)ctx->vox_pair;
-        LVR_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)nvox * 4, s));
+        PairSlot *pair = (PairSlot *)ctx->vox_pair;
+        // the scatter's cursors start at the offsets (one random atomic per segment)
+        LVR_CUDA(ctx, cudaMemcpyAsync(cnt, ls->offset, (size_t)nvox * 4, cudaMemcpyDeviceToDevice, s));
         vox_warp_kernel<true><<<grid1d(n_curves * 32, 256), 256, 0, s>>>(P, cnt, ls->offset, ls->rec, ls->key, pair,
                                                                          total);
         LVR_CUDA(ctx, cudaMemsetAsync(long_count, 0, 4, s));
