@@ -5,6 +5,10 @@
         transparency with termination at 0.99, soft shadows, 16 traced AO
         rays, 16-byte records, 4x8 ray tiles) on the central 640 x 360 crop of
         the 1920 x 1080 view: one warm-up render, then K renders
+    python -m paper_1801_01155_gb300.cases render-crop-learned [--reps K]
+        the same crop with the learned AO surrogate in place of the traced AO
+        rays (a model with seeded random weights: the work does not depend on
+        them), after the model is bound to the LoD
     python -m paper_1801_01155_gb300.cases voxel-term [--reps K]
         the learned-AO model bound to K fresh 3-level LoDs of the config-2 set
         (each bind computes the per-voxel term of every voxel on the tensor
@@ -40,29 +44,34 @@ def _setup(torch, lvr, synth):
     return dev, st, ctx, s, tf, sig
 
 
-def render_crop(reps):
+def render_crop(reps, learned=False):
     import torch
 
     from paper_1801_01155_gb300 import lvr, synth
     dev, st, ctx, s, tf, sig = _setup(torch, lvr, synth)
+    model = None
+    if learned:
+        rng = np.random.default_rng(7)
+        model = lvr.lvr_ao_model_create(ctx, (rng.standard_normal(lvr.lvr_ao_nparams()) * 0.05).astype(np.float32))
     lvr.lvr_lineset_layout(ctx, s, lvr.LAYOUT_AOS16)
     lod = lvr.lvr_build_lod(ctx, s, 3, sig)
     cam = synth.orbit_view((256, 256, 256), 1920, 1080)
     view = lvr.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], 1920, 1080, cam["light_dir"],
                          crop=(640, 360, 640, 360))
-    desc = lvr.make_desc(0.15, tf, ert_alpha=0.99, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0,
-                         tile=(4, 8), layout=lvr.LAYOUT_AOS16)
+    desc = lvr.make_desc(0.15, tf, ert_alpha=0.99, shadows=True, ao_mode=2 if learned else 1, ao_rays=16,
+                         ao_radius=15.0, tile=(4, 8), layout=lvr.LAYOUT_AOS16)
     out = torch.empty((360, 640, 4), dtype=torch.float32, device=dev)
-    lvr.lvr_render(ctx, s, lod, view, desc, out)
+    lvr.lvr_render(ctx, s, lod, view, desc, out, ao_model=model)
     ms = []
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        lvr.lvr_render(ctx, s, lod, view, desc, out)
+        lvr.lvr_render(ctx, s, lod, view, desc, out, ao_model=model)
         e1.record(st)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-    print(f"render-crop: {np.median(ms):.3f} ms per 640x360 crop render (median of {reps})")
+    print(f"render-crop{'-learned' if learned else ''}: {np.median(ms):.3f} ms per 640x360 crop render "
+          f"(median of {reps})")
 
 
 def voxel_term(reps):
@@ -93,12 +102,15 @@ def voxel_term(reps):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["render-crop", "voxel-term"])
+    ap.add_argument("case", choices=["render-crop", "render-crop-learned", "voxel-term"])
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args(argv)
     import __graft_entry__ as g
     g.build()
-    (render_crop if a.case == "render-crop" else voxel_term)(a.reps)
+    if a.case == "voxel-term":
+        voxel_term(a.reps)
+    else:
+        render_crop(a.reps, learned=a.case == "render-crop-learned")
 
 
 if __name__ == "__main__":

@@ -321,7 +321,7 @@ struct Smem {
     // lane-minor columns; the single-view learned variant keeps them per
     // warp, because they are dead while a warp lights its hits and it
     // overlays the warp's activation tile on its own entries
-    static constexpr bool kActTile = MODE == MODE_LEARNED && !BATCH;
+    static constexpr bool kActTile = MODE == MODE_LEARNED;
     struct ColStage {
         float st[KS][RT];
         uint32_t sk[KS][RT];
@@ -350,7 +350,7 @@ struct Smem {
     float slot[kVid ? NF : NF - 1][KS][RT];
     uint8_t item[4][32 * KS];     // per warp: (owner lane, slot) of each collected hit
     // judge and batched learned variant, per warp: per-hit inputs of 16 hits
-    __align__(16) __nv_bfloat16 hin[MODE == MODE_JUDGE || (MODE == MODE_LEARNED && BATCH) ? 4 * 16 * aomlp::HIN_STRIDE : 8];
+    __align__(16) __nv_bfloat16 hin[MODE == MODE_JUDGE ? 4 * 16 * aomlp::HIN_STRIDE : 8];
 };
 
 struct Ray {
@@ -1199,11 +1199,9 @@ __device__ __forceinline__ void flush_stats(const RenderParams &P, int lane, Sta
 constexpr int min_blocks(int mode) {
     return mode == MODE_IMAGE ? 7 : (mode == MODE_JUDGE ? 4 : (mode == MODE_STILL || mode == MODE_LEARNED ? 5 : 6));
 }
-// batched: the learned variant's register-resident model needs 128 registers;
-// the image variant reads its view from shared memory and needs 80
-constexpr int min_blocks_batch(int mode) {
-    return mode == MODE_LEARNED ? 4 : (mode == MODE_IMAGE ? 6 : min_blocks(mode));
-}
+// batched: the image variant reads its view from shared memory and needs 80
+// registers
+constexpr int min_blocks_batch(int mode) { return mode == MODE_IMAGE ? 6 : min_blocks(mode); }
 
 // One view: a persistent grid takes 32-ray tiles from a global counter.
 template <int MODE, int LAYOUT>
