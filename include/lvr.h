@@ -164,7 +164,9 @@ lvr_status lvr_voxelize_static(const float *xyz, const float *attr, const int64_
  * function's opacity); then 2^3 pooling into `levels` levels (1..4),
  * dims ceil(d / 2). Each level stores sums: segment count (uint32), summed
  * length and summed length * sigma (float32); the density sampled at level
- * l is dens_l / 8^l, the paper's 2^3 average. */
+ * l is dens_l / 8^l, the paper's 2^3 average. Beside them the renderer's
+ * sampling copy: 32 bytes per cell of each level padded by 1-3 cells per
+ * side (a level with 2^32 - 1 or more padded cells: LVR_EINVAL). */
 lvr_status lvr_build_lod(lvr_ctx *ctx, const lvr_lineset *ls, int levels,
                          const float *sigma256, lvr_lod **out);
 typedef struct lvr_lod_info {

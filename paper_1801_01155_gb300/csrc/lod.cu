@@ -80,18 +80,27 @@ lod_pool_kernel(int cx, int cy, int cz, const uint32_t *__restrict__ ccnt, const
 }
 
 // Corner-packed copy of one level for trilinear sampling: padded cell
-// (i, j, k) -> X = i - lo, Y = j - lo, Z = k - lo; .x = v(X, Y), .y = v(X+1, Y),
-// .z = v(X, Y+1), .w = v(X+1, Y+1) in slice Z, zero outside the grid.
+// (i, j, k) -> X = i - lo, Y = j - lo, Z = k - lo; per z-slice Z and Z + 1 a
+// float4 (v(X, Y), v(X+1, Y) - v(X, Y), v(X, Y+1), v(X+1, Y+1) - v(X, Y+1)),
+// zero outside the grid; the two slices of a cell are adjacent (32 bytes).
 __global__ void __launch_bounds__(256)
 lod_pack_kernel(const float *__restrict__ d, int dx, int dy, int dz, int lo, int px, int py, int pz, float4 *pk) {
     const int64_t np = (int64_t)px * py * pz;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < np; c += (int64_t)gridDim.x * blockDim.x) {
         const int X = (int)(c % px) - lo, Y = (int)((c / px) % py) - lo, Z = (int)(c / ((int64_t)px * py)) - lo;
-        auto v = [&](int x, int y) {
-            return (x >= 0 && y >= 0 && Z >= 0 && x < dx && y < dy && Z < dz)
-                       ? d[x + (int64_t)dx * (y + (int64_t)dy * Z)] : 0.0f;
+        auto v = [&](int x, int y, int z) {
+            return (x >= 0 && y >= 0 && z >= 0 && x < dx && y < dy && z < dz)
+                       ? __ldg(d + (x + (int64_t)dx * (y + (int64_t)dy * z))) : 0.0f;
         };
-        pk[c] = make_float4(v(X, Y), v(X + 1, Y), v(X, Y + 1), v(X + 1, Y + 1));
+        float4 s[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const float v00 = v(X, Y, Z + h), v10 = v(X + 1, Y, Z + h), v01 = v(X, Y + 1, Z + h),
+                        v11 = v(X + 1, Y + 1, Z + h);
+            s[h] = make_float4(v00, v10 - v00, v01, v11 - v01);
+        }
+        pk[2 * c] = s[0];
+        pk[2 * c + 1] = s[1];
     }
 }
 
@@ -122,10 +131,10 @@ ao_field_kernel(const float4 *__restrict__ pk0, int64_t px, int64_t sz, int dx, 
                 float val = 0.0f;
                 if ((unsigned)(ix + 1) <= (unsigned)dx && (unsigned)(iy + 1) <= (unsigned)dy &&
                     (unsigned)(iz + 1) <= (unsigned)dz) {
-                    const float4 *c = pk0 + (ix + px * iy + sz * iz);
-                    const float4 a = __ldg(c), b = __ldg(c + sz);
-                    const float x00 = fmaf(e.fx, a.y - a.x, a.x), x10 = fmaf(e.fx, a.w - a.z, a.z);
-                    const float x01 = fmaf(e.fx, b.y - b.x, b.x), x11 = fmaf(e.fx, b.w - b.z, b.z);
+                    const float4 *c = pk0 + 2 * (ix + px * iy + sz * iz);
+                    const float4 a = __ldg(c), b = __ldg(c + 1);
+                    const float x00 = fmaf(e.fx, a.y, a.x), x10 = fmaf(e.fx, a.w, a.z);
+                    const float x01 = fmaf(e.fx, b.y, b.x), x11 = fmaf(e.fx, b.w, b.z);
                     const float y0 = fmaf(e.fy, x10 - x00, x00), y1 = fmaf(e.fy, x11 - x01, x01);
                     val = fmaf(e.fz, y1 - y0, y0);
                 }
@@ -510,9 +519,19 @@ lvr_status lod_alloc(lvr_ctx *ctx, int levels, const int32_t dims0[3], lvr_lod *
         }
         L->pstride[l][0] = pd[0];
         L->pstride[l][1] = pd[0] * pd[1];
-        st = dev_alloc(ctx, (void **)&L->pk[l], (size_t)(pd[0] * pd[1] * pd[2]) * 16);
-        if (st == LVR_OK)
-            L->pk0[l] = L->pk[l] + L->pad_lo[l] * (1 + L->pstride[l][0] + L->pstride[l][1]);
+        const int64_t ncell = pd[0] * pd[1] * pd[2];
+        if (ncell >= ((int64_t)1 << 32) - 1) {
+            st = set_err(ctx, LVR_EINVAL, "LoD: a padded level must have fewer than 2^32 - 1 cells");
+            break;
+        }
+        L->pzero[l] = (uint32_t)ncell;
+        st = dev_alloc(ctx, (void **)&L->pk[l], (size_t)(ncell + 1) * 32);
+        if (st == LVR_OK) {
+            const int64_t c0 = L->pad_lo[l] * (1 + L->pstride[l][0] + L->pstride[l][1]);
+            L->pk0[l] = L->pk[l] + 2 * c0;
+            L->pbias[l] = (uint32_t)((0x4B400000u - (uint32_t)L->pad_lo[l]) *
+                                     (uint32_t)(1 + L->pstride[l][0] + L->pstride[l][1]));
+        }
     }
     if (st != LVR_OK) {
         lvr_free_lod(L);
@@ -531,6 +550,7 @@ lvr_status lod_pack(lvr_ctx *ctx, lvr_lod *L) {
         const int64_t np = (int64_t)px * py * pz;
         const unsigned g = grid1d(np, 256) > 65535 ? 65535 : grid1d(np, 256);
         lod_pack_kernel<<<g, 256, 0, ctx->stream>>>(L->dens[l], dm[0], dm[1], dm[2], lo, px, py, pz, L->pk[l]);
+        LVR_CUDA(ctx, cudaMemsetAsync(L->pk[l] + 2 * (size_t)np, 0, 32, ctx->stream));   // the zero cell
     }
     LVR_CUDA(ctx, cudaGetLastError());
     return LVR_OK;

@@ -74,19 +74,29 @@ struct lvr_lod {
     uint32_t *cnt[4] = {};
     float *len[4] = {};
     float *dens[4] = {};
-    // sampling copy of dens: per cell (i, j, k) of the padded grid, the four
-    // x/y corners (i, j), (i+1, j), (i, j+1), (i+1, j+1) of z-slice k as one
-    // float4 (zero outside the grid). Level l is padded by pad_lo[l] cells
-    // below and pad_hi[l][a] above on each axis, enough that every sample
-    // point of the density field's support (the grid enlarged by half a
-    // coarsest-level cell) has its eight corners inside the copy, so a
-    // sampler that checks the support needs no per-corner range check.
-    // pk0[l] points at cell (0, 0, 0); strides pstride[l] = {row, slice}.
+    // sampling copy of dens: per cell (i, j, k) of the padded grid 32 bytes,
+    // two float4 for z-slices k and k + 1, each holding the x/y corners as
+    // (v(i, j), v(i+1, j) - v(i, j), v(i, j+1), v(i+1, j+1) - v(i, j+1))
+    // (zero outside the grid): one aligned 32-byte load per trilinear
+    // sample, its x differences already taken. Level l is padded by
+    // pad_lo[l] cells below and pad_hi[l][a] above on each axis, enough that
+    // every sample point of the density field's support (the grid enlarged
+    // by half a coarsest-level cell) has its eight corners inside the copy,
+    // so a sampler that checks the support needs no per-corner range check.
+    // pk[l] is the padded cell (0, 0, 0), pk0[l] the grid's cell (0, 0, 0);
+    // strides pstride[l] = {row, slice} in cells; fewer than 2^32 padded
+    // cells per level, so cell indices are 32-bit. pbias[l] folds the
+    // padding and the float-to-integer offset of the sampler's floor
+    // (bit pattern 0x4B400000 + n for the integer n) into one constant:
+    // cell index = bx + row * by + slice * bz - pbias (mod 2^32). One more
+    // cell, all zeros, follows the last (index pzero[l]).
     float4 *pk[4] = {};
     const float4 *pk0[4] = {};
     int32_t pad_lo[4] = {};
     int32_t pad_hi[4][3] = {};
     int64_t pstride[4][2] = {};
+    uint32_t pbias[4] = {};
+    uint32_t pzero[4] = {};
     // spherical per-voxel AO (lvr_lod_ao_field), or null
     float *aof = nullptr;
     // representative lines per level (lvr_lod_rep_lines), or null: per cell one

@@ -64,8 +64,10 @@ struct RenderParams {
     float r2;
     int32_t levels;
     int32_t ldims[4][3];
-    const float4 *pk0[4];         // corner-packed levels at cell (0, 0, 0), padded to cover the support
-    int64_t pstr[4][2];           //   their row and slice strides in cells
+    const float4 *pk[4];          // corner-packed levels (32-byte cells), padded to cover the support
+    uint32_t pstr[4][2];          //   their row and slice strides in cells
+    uint32_t pbias[4];            //   the floor's bit offset and the padding, folded (see corner_cell)
+    uint32_t pzero[4];            //   index of the all-zero cell past the last
     float lod_lo, lod_hi[3];      // support of the density field (level-0 voxels)
     float F[3], R[3], U[3], th, tw, eye[3];
     int32_t W, H, x0, y0, cw, ch;
@@ -195,35 +197,52 @@ __device__ __forceinline__ float capsule_entry(Vec p, Vec D, Vec a, Vec b, float
     return sphere_entry(p, D, a, r2);
 }
 
-// Cell-centred trilinear density at level l, zero outside the grid: two
-// 16-byte loads of the corner-packed level (slices iz and iz + 1), the same
-// lerps in the same order as eight scalar corner loads would feed. The
-// packed copy is padded to cover the support of the density field, so a
-// point inside the support (which every caller checks) needs no range check.
-struct Corners {
-    float4 a, b;                  // the x/y corners of slices iz and iz + 1
-    float fx, fy, fz;             // position inside the cell
-};
-__device__ __forceinline__ const float4 *corner_addr(const RenderParams &P, int l, Vec x, float &fx, float &fy,
-                                                     float &fz) {
+// Cell-centred trilinear density at level l, zero outside the grid: one
+// 32-byte load of the corner-packed level (the x/y corners of slices iz and
+// iz + 1, x differences precomputed), the same lerps in the same order as
+// eight scalar corner loads would feed. The packed copy is padded to cover
+// the support of the density field, so a point inside the support (which
+// every caller checks) needs no range check.
+//
+// The cell is found without a conversion instruction: for |q| < 2^22,
+// q + 1.5 * 2^23 rounded toward -infinity is the integer 1.5 * 2^23 +
+// floor(q) exactly, and its bit pattern is 0x4B400000 + floor(q); the
+// padded cell index is then a 32-bit sum of the three bit patterns times
+// the strides, less a per-level constant (pbias) that removes the offsets
+// and adds the padding. Subtracting the rounded sum back gives floor(q) as
+// a float, so the fractions are q - floor(q), as with floorf.
+constexpr float FLOOR_MAGIC = 12582912.0f;   // 1.5 * 2^23
+__device__ __forceinline__ uint32_t corner_cell(const RenderParams &P, int l, Vec x, float &fx, float &fy,
+                                                float &fz) {
     const float inv = __int_as_float((127 - l) << 23);         // 2^-l
     const float qx = fmaf(x.x, inv, -0.5f), qy = fmaf(x.y, inv, -0.5f), qz = fmaf(x.z, inv, -0.5f);
-    const float fx0 = floorf(qx), fy0 = floorf(qy), fz0 = floorf(qz);
-    fx = qx - fx0;
-    fy = qy - fy0;
-    fz = qz - fz0;
-    return P.pk0[l] + ((int64_t)(int)fx0 + P.pstr[l][0] * (int)fy0 + P.pstr[l][1] * (int)fz0);
+    const float tx = __fadd_rd(qx, FLOOR_MAGIC), ty = __fadd_rd(qy, FLOOR_MAGIC), tz = __fadd_rd(qz, FLOOR_MAGIC);
+    fx = qx - (tx - FLOOR_MAGIC);
+    fy = qy - (ty - FLOOR_MAGIC);
+    fz = qz - (tz - FLOOR_MAGIC);
+    return __float_as_uint(tx) + P.pstr[l][0] * __float_as_uint(ty) + P.pstr[l][1] * __float_as_uint(tz) -
+           P.pbias[l];
+}
+// Cell i of level l (a: slice iz, b: slice iz + 1): two 16-byte loads at
+// one address (two 16-byte loads issue faster here than one 32-byte load).
+// The cell past the last (index pzero) is all zeros, the stand-in for a
+// sample that is not taken.
+__device__ __forceinline__ void load_cell(const RenderParams &P, int l, uint32_t i, float4 &a, float4 &b) {
+    const float4 *c = P.pk[l] + 2 * (size_t)i;
+    a = __ldg(c);
+    b = __ldg(c + 1);
 }
 __device__ __forceinline__ float trilerp(float4 a, float4 b, float fx, float fy, float fz) {
-    const float x00 = fmaf(fx, a.y - a.x, a.x), x10 = fmaf(fx, a.w - a.z, a.z);
-    const float x01 = fmaf(fx, b.y - b.x, b.x), x11 = fmaf(fx, b.w - b.z, b.z);
+    const float x00 = fmaf(fx, a.y, a.x), x10 = fmaf(fx, a.w, a.z);
+    const float x01 = fmaf(fx, b.y, b.x), x11 = fmaf(fx, b.w, b.z);
     const float y0 = fmaf(fy, x10 - x00, x00), y1 = fmaf(fy, x11 - x01, x01);
     return fmaf(fz, y1 - y0, y0);
 }
 __device__ __forceinline__ float sample_level(const RenderParams &P, int l, Vec x) {
     float fx, fy, fz;
-    const float4 *c = corner_addr(P, l, x, fx, fy, fz);
-    return trilerp(__ldg(c), __ldg(c + P.pstr[l][1]), fx, fy, fz);
+    float4 a, b;
+    load_cell(P, l, corner_cell(P, l, x, fx, fy, fz), a, b);
+    return trilerp(a, b, fx, fy, fz);
 }
 
 // Spherical AO field at x: cell-centred trilinear, coordinates clamped to
@@ -599,22 +618,26 @@ __device__ __forceinline__ Vec ao_tangent(Vec n, Vec u) {
 // samples fall at s = 1, 2, 4, 8, 12 (levels 0, 1, 2, 2, 2), unrolled; the
 // same samples, weights and sample count as march(), and the same
 // min(1, O).
+__device__ __forceinline__ bool in_support(const RenderParams &P, const Vec &x) {
+    return !(x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
+             x.z > P.lod_hi[2]);
+}
 __device__ __forceinline__ float march_ao5(const RenderParams &P, Vec p, Vec d, unsigned &nsamp) {
     const int ss[5] = {1, 2, 4, 8, 12}, ll[5] = {0, 1, 2, 2, 2};
     // every sample's corners are requested before the first is used (one
     // memory round trip per ray instead of five); samples past the support
-    // read nothing and are zero
+    // read the zero cell. The support is a box that holds p, and each
+    // coordinate of the rounded p + s d is monotone in s, so the samples
+    // inside it are a prefix of s = 1, 2, 4, 8, 12.
     float4 A[5], B[5];
     float fx[5], fy[5], fz[5];
     bool in[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
         const Vec x = axpy((float)ss[k], d, p);
-        in[k] = (k == 0 || in[k - 1]) && !(x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo ||
-                                            x.x > P.lod_hi[0] || x.y > P.lod_hi[1] || x.z > P.lod_hi[2]);
-        const float4 *c = corner_addr(P, ll[k], x, fx[k], fy[k], fz[k]);
-        A[k] = in[k] ? __ldg(c) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        B[k] = in[k] ? __ldg(c + P.pstr[ll[k]][1]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        in[k] = in_support(P, x);
+        const uint32_t i = corner_cell(P, ll[k], x, fx[k], fy[k], fz[k]);
+        load_cell(P, ll[k], in[k] ? i : P.pzero[ll[k]], A[k], B[k]);
     }
     // the march stops at O >= 1 or when a sample leaves the support; terms
     // added after O >= 1 are non-negative and leave min(1, O) = 1, terms past
@@ -634,10 +657,6 @@ __device__ __forceinline__ float march_ao5(const RenderParams &P, Vec p, Vec d, 
 // or O reaches 1; the same samples, weights and sample count as march(), and
 // the same min(1, O). The corners of four samples at a time are requested
 // before the first of them is used.
-__device__ __forceinline__ bool in_support(const RenderParams &P, const Vec &x) {
-    return !(x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
-             x.z > P.lod_hi[2]);
-}
 template <int L0, int L1, int L2, int L3>
 __device__ __forceinline__ void march4(const RenderParams &P, Vec p, Vec d, float s0, float s1, float s2, float s3,
                                        bool &alive, float &O, unsigned &nsamp) {
@@ -650,9 +669,8 @@ __device__ __forceinline__ void march4(const RenderParams &P, Vec p, Vec d, floa
     for (int j = 0; j < 4; j++) {
         const Vec x = axpy(ss[j], d, p);
         in[j] = (j == 0 ? alive : in[j - 1]) && in_support(P, x);
-        const float4 *c = corner_addr(P, ll[j], x, fx[j], fy[j], fz[j]);
-        A[j] = in[j] ? __ldg(c) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        B[j] = in[j] ? __ldg(c + P.pstr[ll[j]][1]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const uint32_t i = corner_cell(P, ll[j], x, fx[j], fy[j], fz[j]);
+        load_cell(P, ll[j], in[j] ? i : P.pzero[ll[j]], A[j], B[j]);
     }
 #pragma unroll
     for (int j = 0; j < 4; j++) {
@@ -1470,9 +1488,11 @@ static lvr_status setup(lvr_ctx *ctx, const lvr_lineset *ls, const lvr_lod *lod,
         P.levels = lod->levels;
         for (int l = 0; l < lod->levels; l++) {
             for (int a = 0; a < 3; a++) P.ldims[l][a] = lod->dims[l][a];
-            P.pk0[l] = lod->pk0[l];
-            P.pstr[l][0] = lod->pstride[l][0];
-            P.pstr[l][1] = lod->pstride[l][1];
+            P.pk[l] = lod->pk[l];
+            P.pstr[l][0] = (uint32_t)lod->pstride[l][0];
+            P.pstr[l][1] = (uint32_t)lod->pstride[l][1];
+            P.pbias[l] = lod->pbias[l];
+            P.pzero[l] = lod->pzero[l];
         }
         const float cell = (float)(1 << (lod->levels - 1));
         P.lod_lo = -0.5f * cell;

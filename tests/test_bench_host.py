@@ -44,11 +44,21 @@ def test_no_sampler_no_clocks():
     assert c.stop() is None
 
 
-def test_traffic_only_for_the_profiled_kernel():
-    t = bench.measured_traffic(1, (4, 8))
-    assert isinstance(t, int) and t > 100_000_000
-    assert bench.measured_traffic(0, (4, 8)) is None
-    assert bench.measured_traffic(1, (8, 4)) is None
+def test_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
+    """The DRAM bytes are taken only from a summary of this kernel version
+    and record layout (the tile does not change them)."""
+    f = tmp_path / "traffic.md"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.measured_traffic(1, (4, 8)) is None            # no summary
+    f.write_text(f"# x\n\n- kernel_version: {bench.KERNEL_VERSION}\n- layout: aos16\n- tile: 8x4\n"
+                 "- dram_bytes_per_launch: 647810560\n")
+    assert bench.measured_traffic(1, (4, 8)) == 647810560
+    assert bench.measured_traffic(1, (8, 4)) == 647810560
+    assert bench.measured_traffic(0, (4, 8)) is None            # other layout
+    f.write_text("- kernel_version: render-v0\n- layout: aos16\n- dram_bytes_per_launch: 1\n")
+    assert bench.measured_traffic(1, (4, 8)) is None            # other kernel version
+    f.write_text(f"- kernel_version: {bench.KERNEL_VERSION}\n- layout: aos16\n- dram_bytes_per_launch: n/a\n")
+    assert bench.measured_traffic(1, (4, 8)) is None
 
 
 def test_job_throughput_counts_every_rank():
