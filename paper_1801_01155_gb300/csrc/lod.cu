@@ -7,6 +7,7 @@
 // float32 sqrt of I is correctly rounded and the division by 2N is exact.
 // Sums run in the canonical segment order (level 0) and in the fixed child
 // order z, y, x (coarser levels), so results are deterministic.
+#include <algorithm>
 #include <math.h>
 #include <string.h>
 
@@ -512,8 +513,14 @@ lvr_status lod_alloc(lvr_ctx *ctx, int levels, const int32_t dims0[3], lvr_lod *
         const double m = ldexp(1.0, levels - 1 - l);
         L->pad_lo[l] = -(int)floor(-0.5 * m - 0.5);
         int64_t pd[3];
+        // with 3 levels the coarsest copy also holds every point within 13
+        // voxels of the grid: the AO march of radius 12 then needs no support
+        // test (its samples there read zeros)
+        const bool reach = levels == 3 && l == 2;
+        if (reach) L->pad_lo[l] = std::max(L->pad_lo[l], -(int)floor(-13.0 / 4.0 - 0.5));
         for (int a = 0; a < 3; a++) {
-            const int64_t hi = (int64_t)floor(((double)L->dims[levels - 1][a] + 0.5) * m - 0.5) + 1;
+            int64_t hi = (int64_t)floor(((double)L->dims[levels - 1][a] + 0.5) * m - 0.5) + 1;
+            if (reach) hi = std::max(hi, (int64_t)floor(((double)dims0[a] + 13.0) / 4.0 - 0.5));
             L->pad_hi[l][a] = (int32_t)(hi - (L->dims[l][a] - 1));
             pd[a] = (int64_t)L->dims[l][a] + L->pad_lo[l] + L->pad_hi[l][a];
         }

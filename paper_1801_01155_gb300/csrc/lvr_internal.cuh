@@ -35,7 +35,8 @@ struct lvr_ctx {
     size_t stage_in_bytes = 0;
     void *stage_out = nullptr;
     size_t stage_out_bytes = 0;
-    int render_blocks[16] = {};            // persistent render grid per kernel variant (SMs x resident blocks)
+    int render_blocks[32] = {};            // persistent render grid per kernel variant (SMs x resident blocks):
+                                           // [mode * 2 + layout], batched [16 + mode * 2 + layout]
     // voxeliser: grow-only scatter target of (record, key) pairs
     void *vox_pair = nullptr;
     size_t vox_pair_bytes = 0;

@@ -296,7 +296,10 @@ __device__ __forceinline__ bool key_after(float t, uint32_t k, float lt, uint32_
 // MODE_REP: the image mode with hard shadows against representative lines,
 // a variant of its own so that the walk's registers do not weigh on the
 // other image kernels
-enum { MODE_IMAGE = 0, MODE_LEARNED = 1, MODE_SAMPLES = 2, MODE_JUDGE = 3, MODE_STILL = 4, MODE_REP = 5 };
+// MODE_IMAGE_NC is the image variant for launches that read no counters
+// (the compiler drops the counting, and the AO march its support tests).
+enum { MODE_IMAGE = 0, MODE_LEARNED = 1, MODE_SAMPLES = 2, MODE_JUDGE = 3, MODE_STILL = 4, MODE_REP = 5,
+       MODE_IMAGE_NC = 6 };
 constexpr int JH = 4096;          // judge histogram bins over |e| in [0, 1]
 
 // Shared memory of one block: transfer function, per-lane sorted hit staging
@@ -332,7 +335,7 @@ struct Smem {
     static constexpr int kMode = MODE;
     static constexpr int kLayout = LAYOUT;
     static constexpr bool kBatch = BATCH;   // the transfer function is read from global memory
-    static constexpr bool kVid = MODE != MODE_IMAGE && MODE != MODE_STILL && MODE != MODE_REP;
+    static constexpr bool kVid = MODE != MODE_IMAGE && MODE != MODE_IMAGE_NC && MODE != MODE_STILL && MODE != MODE_REP;
     static constexpr bool kStill = MODE == MODE_STILL;
     float4 tf[BATCH ? 1 : 256];
     float4 hot[BATCH ? 4 : 1][BATCH ? HOT_BYTES / 16 : 1];   // batched: each warp's current view parameters
@@ -622,6 +625,12 @@ __device__ __forceinline__ bool in_support(const RenderParams &P, const Vec &x) 
     return !(x.x < P.lod_lo || x.y < P.lod_lo || x.z < P.lod_lo || x.x > P.lod_hi[0] || x.y > P.lod_hi[1] ||
              x.z > P.lod_hi[2]);
 }
+// Without counting (CNT false) the support tests are left out: the copy of
+// the coarsest level is padded to hold every point within 12 voxels of the
+// grid, which holds every sample of this march, and a sample outside the
+// support has all eight corners outside the grid, so it reads the zeros the
+// test would have given it.
+template <bool CNT>
 __device__ __forceinline__ float march_ao5(const RenderParams &P, Vec p, Vec d, unsigned &nsamp) {
     const int ss[5] = {1, 2, 4, 8, 12}, ll[5] = {0, 1, 2, 2, 2};
     // every sample's corners are requested before the first is used (one
@@ -635,9 +644,13 @@ __device__ __forceinline__ float march_ao5(const RenderParams &P, Vec p, Vec d, 
 #pragma unroll
     for (int k = 0; k < 5; k++) {
         const Vec x = axpy((float)ss[k], d, p);
-        in[k] = in_support(P, x);
         const uint32_t i = corner_cell(P, ll[k], x, fx[k], fy[k], fz[k]);
-        load_cell(P, ll[k], in[k] ? i : P.pzero[ll[k]], A[k], B[k]);
+        if constexpr (CNT) {
+            in[k] = in_support(P, x);
+            load_cell(P, ll[k], in[k] ? i : P.pzero[ll[k]], A[k], B[k]);
+        } else {
+            load_cell(P, ll[k], i, A[k], B[k]);
+        }
     }
     // the march stops at O >= 1 or when a sample leaves the support; terms
     // added after O >= 1 are non-negative and leave min(1, O) = 1, terms past
@@ -645,7 +658,7 @@ __device__ __forceinline__ float march_ao5(const RenderParams &P, Vec p, Vec d, 
     float O = 0.0f;
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-        nsamp += (in[k] && O < 1.0f) ? 1u : 0u;
+        if constexpr (CNT) nsamp += (in[k] && O < 1.0f) ? 1u : 0u;
         const float wl = __int_as_float((127 - 2 * ll[k]) << 23);   // 2^l / 8^l
         O = fmaf(trilerp(A[k], B[k], fx[k], fy[k], fz[k]), wl, O);
     }
@@ -948,13 +961,12 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
     }
     if constexpr (MODE == MODE_LEARNED || MODE == MODE_JUDGE) {
         // learned AO (Sec. 5.3 surrogate), 16 hits per step: per-hit inputs
-        // into a shared tile, then the model on tensor cores. The single-view
-        // variant keeps the activations in the warp's tile (short code that
-        // shares the instruction cache with the traversal: faster where a
-        // warp lights few hits at a time); the batched variant and the judge
-        // keep them in registers (fully unrolled: faster on dense frames).
-        // Both give the same bits. The judge keeps its result in F_V (no
-        // shadows there) beside the traced AO.
+        // into a shared tile, then the model on tensor cores. The learned
+        // variants (one view and batched) keep the activations in the warp's
+        // tile, overlaid on its staging entries (short code that shares the
+        // instruction cache with the traversal); the judge keeps them in
+        // registers (fully unrolled). Both give the same bits. The judge
+        // keeps its result in F_V (no shadows there) beside the traced AO.
         constexpr int FL = MODE == MODE_JUDGE ? F_V : F_AO;
         constexpr bool kAct = SM::kActTile;
         __nv_bfloat16 *h = sm.hin + (kAct ? 0 : warp * 16 * aomlp::HIN_STRIDE);
@@ -1019,7 +1031,8 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
                 const float dx = P.aod[ray][0], dy = P.aod[ray][1], dz = P.aod[ray][2];
                 const Vec d = mk(fmaf(T.x, dx, fmaf(B.x, dy, n.x * dz)), fmaf(T.y, dx, fmaf(B.y, dy, n.y * dz)),
                                  fmaf(T.z, dx, fmaf(B.z, dy, n.z * dz)));
-                o = fminf(1.0f, P.ao_fast ? march_ao5(P, Pg, d, nsamp) : march(P, Pg, d, P.ao_radius, nsamp));
+                o = fminf(1.0f, P.ao_fast ? march_ao5<MODE != MODE_IMAGE_NC>(P, Pg, d, nsamp)
+                                           : march(P, Pg, d, P.ao_radius, nsamp));
             }
             for (int x = G >> 1; x > 0; x >>= 1) o += __shfl_xor_sync(FULL, o, x);
             if (ray == 0 && g < total) {
@@ -1191,7 +1204,7 @@ __device__ __forceinline__ void render_tile(const RenderParams &P, SM &sm, unsig
 
 template <int MODE>
 __device__ __forceinline__ void flush_stats(const RenderParams &P, int lane, Stats &S) {
-    if (P.counters) {
+    if (MODE != MODE_IMAGE_NC && P.counters) {
         const unsigned c0 = __reduce_add_sync(FULL, S.nvox), c1 = __reduce_add_sync(FULL, S.nrec),
                        c2 = __reduce_add_sync(FULL, S.nsamp), c3 = __reduce_add_sync(FULL, S.nhit);
         if (lane == 0) {
@@ -1215,11 +1228,13 @@ __device__ __forceinline__ void flush_stats(const RenderParams &P, int lane, Sta
 }
 
 constexpr int min_blocks(int mode) {
-    return mode == MODE_IMAGE ? 7 : (mode == MODE_JUDGE ? 4 : (mode == MODE_STILL || mode == MODE_LEARNED ? 5 : 6));
+    return mode == MODE_IMAGE || mode == MODE_IMAGE_NC
+               ? 7
+               : (mode == MODE_JUDGE ? 4 : (mode == MODE_STILL || mode == MODE_LEARNED ? 5 : 6));
 }
 // batched: the image variant reads its view from shared memory and needs 80
 // registers
-constexpr int min_blocks_batch(int mode) { return mode == MODE_IMAGE ? 6 : min_blocks(mode); }
+constexpr int min_blocks_batch(int mode) { return mode == MODE_IMAGE || mode == MODE_IMAGE_NC ? 6 : min_blocks(mode); }
 
 // One view: a persistent grid takes 32-ray tiles from a global counter.
 template <int MODE, int LAYOUT>
@@ -1568,6 +1583,8 @@ static RenderKernel pick_kernel(int mode, int layout) {
     case MODE_STILL * 2 + 1: return render_kernel<MODE_STILL, LAYOUT_AOS16>;
     case MODE_REP * 2: return render_kernel<MODE_REP, LAYOUT_AOS8>;
     case MODE_REP * 2 + 1: return render_kernel<MODE_REP, LAYOUT_AOS16>;
+    case MODE_IMAGE_NC * 2: return render_kernel<MODE_IMAGE_NC, LAYOUT_AOS8>;
+    case MODE_IMAGE_NC * 2 + 1: return render_kernel<MODE_IMAGE_NC, LAYOUT_AOS16>;
     default: return nullptr;
     }
 }
@@ -1576,7 +1593,9 @@ static int kernel_mode(const RenderParams &P) {
     return P.judge ? MODE_JUDGE
                    : (P.learned ? MODE_LEARNED
                                 : (P.samp_vox ? MODE_SAMPLES
-                                              : (P.still ? MODE_STILL : (P.shadows == 2 ? MODE_REP : MODE_IMAGE))));
+                                              : (P.still ? MODE_STILL
+                                                        : (P.shadows == 2 ? MODE_REP
+                                                                          : (P.counters ? MODE_IMAGE : MODE_IMAGE_NC)))));
 }
 
 // Persistent grid size of a kernel: SMs x resident blocks (cached per variant).
@@ -1789,8 +1808,8 @@ typedef void (*BatchKernel)(BatchParams);
 
 BatchKernel pick_batch_kernel(int mode, int layout) {
     switch (mode * 2 + layout) {
-    case MODE_IMAGE * 2: return render_batch_kernel<MODE_IMAGE, LAYOUT_AOS8>;
-    case MODE_IMAGE * 2 + 1: return render_batch_kernel<MODE_IMAGE, LAYOUT_AOS16>;
+    case MODE_IMAGE_NC * 2: return render_batch_kernel<MODE_IMAGE_NC, LAYOUT_AOS8>;
+    case MODE_IMAGE_NC * 2 + 1: return render_batch_kernel<MODE_IMAGE_NC, LAYOUT_AOS16>;
     case MODE_REP * 2: return render_batch_kernel<MODE_REP, LAYOUT_AOS8>;
     case MODE_REP * 2 + 1: return render_batch_kernel<MODE_REP, LAYOUT_AOS16>;
     case MODE_LEARNED * 2: return render_batch_kernel<MODE_LEARNED, LAYOUT_AOS8>;
@@ -1817,7 +1836,7 @@ lvr_status batch_build(lvr_ctx *ctx, const lvr_batch_item *items, int n, int til
         if (layout >= 0) d.layout = layout;
         lvr_status st = setup(ctx, it.ls, it.lod, &it.view, &d, it.ao, P[i]);
         if (st != LVR_OK) return st;
-        const int m = P[i].learned ? MODE_LEARNED : (P[i].shadows == 2 ? MODE_REP : MODE_IMAGE);
+        const int m = P[i].learned ? MODE_LEARNED : (P[i].shadows == 2 ? MODE_REP : MODE_IMAGE_NC);   // no counters
         if (mode >= 0 && (m != mode || d.layout != lay))
             return set_err(ctx, LVR_EINVAL,
                            "batch items must share the AO kind, representative-line shadows or not, and the "
@@ -1870,7 +1889,7 @@ lvr_status batch_build(lvr_ctx *ctx, const lvr_batch_item *items, int n, int til
     if (e != cudaSuccess) return fail(cuda_err(ctx, e, "lvr_batch_create"));
     const BatchKernel kern = pick_batch_kernel(mode, lay);
     int blocks;
-    if ((st = grid_blocks(ctx, 8 + mode * 2 + lay, (const void *)kern, &blocks)) != LVR_OK) return fail(st);
+    if ((st = grid_blocks(ctx, 16 + mode * 2 + lay, (const void *)kern, &blocks)) != LVR_OK) return fail(st);
     const int64_t need = (tot + RT / 32 - 1) / (RT / 32);
     const int grid = need < blocks ? (int)need : blocks;
     BatchParams bp;

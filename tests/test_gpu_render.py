@@ -160,6 +160,37 @@ def test_c2_full_frame_sampled(env, c2):
         S.check_image(got, ref, tie, what=f"c2 sampled {kw}", alt=alt)
 
 
+def test_counting_does_not_change_the_image(env, c1t):
+    """A render that fills the traversal counters and one that does not run
+    different kernels (the second drops the counting and the AO march's
+    support tests, relying on the padded coarsest LoD copy): the same bits,
+    on a 32^3 grid where many AO rays of radius 15 leave the grid, in both
+    record layouts and in a batch (which never counts)."""
+    import torch
+    lvr, O, ctx, dev = env
+    assert c1t.glod.info().levels == 3
+    cam = synth.orbit_view((32, 32, 32), 96, 80)
+    lv, _, _ = S.views(cam)
+    for layout in (0, 1):
+        if layout:
+            lvr.lvr_lineset_layout(ctx, c1t.gls, lvr.LAYOUT_AOS16)
+        desc = lvr.make_desc(0.2, c1t.tf, shadows=True, ao_mode=1, ao_radius=15.0, layout=layout)
+        imgs = []
+        for counted in (True, False):
+            out = torch.empty((80, 96, 4), dtype=torch.float32, device=dev)
+            cnt = torch.zeros(4, dtype=torch.int64, device=dev) if counted else None
+            lvr.lvr_render(ctx, c1t.gls, c1t.glod, lv, desc, out, counters=cnt)
+            ctx.sync()
+            imgs.append(out.cpu().numpy())
+        assert imgs[0][..., 3].max() > 0.5
+        np.testing.assert_array_equal(imgs[1], imgs[0])
+        out = torch.empty((80, 96, 4), dtype=torch.float32, device=dev)
+        b = lvr.lvr_batch_create(ctx, [(c1t.gls, c1t.glod, lv, desc, None, out)])
+        lvr.lvr_batch_render(ctx, b)
+        ctx.sync()
+        np.testing.assert_array_equal(out.cpu().numpy(), imgs[0])
+
+
 def test_tile_shapes_bit_identical(env, c1t):
     import torch
     lvr, O, ctx, dev = env
