@@ -157,6 +157,7 @@ extern "C" void lvr_destroy(lvr_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     dev_free(ctx, ctx->scratch);
+    dev_free(ctx, ctx->d_tf);
     dev_free(ctx, ctx->stage_in);
     dev_free(ctx, ctx->stage_out);
     dev_free(ctx, ctx->vox_pair);

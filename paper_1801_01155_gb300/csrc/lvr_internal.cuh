@@ -27,6 +27,7 @@ struct lvr_ctx {
     uint32_t *d_status = nullptr;          // device status word
     unsigned long long *d_u64 = nullptr;   // small device counters [8]
     void *h_pinned = nullptr;              // pinned readback area (256 B)
+    float *d_tf = nullptr;                 // single-view render: the transfer function (1024 floats)
     // grow-only device scratch, reused across calls
     void *scratch = nullptr;
     size_t scratch_bytes = 0;

@@ -79,7 +79,7 @@ struct RenderParams {
     int32_t ao_fast;              // 3 levels, AO radius in [12, 16): the unrolled AO march
     float ao_radius, ka, kd, bg[3];
     float aod[MAX_AO][3];         // hemisphere directions in the (T, B, n) frame
-    const float4 *gtf;            // batched views: this view's transfer function in global memory
+    const float4 *gtf;            // the transfer function in global memory (read through L1)
     float4 *out;                  // may be null (sample mode)
     unsigned long long *counters;
     unsigned *tile_counter;
@@ -337,7 +337,9 @@ struct Smem {
     static constexpr bool kBatch = BATCH;   // the transfer function is read from global memory
     static constexpr bool kVid = MODE != MODE_IMAGE && MODE != MODE_IMAGE_NC && MODE != MODE_STILL && MODE != MODE_REP;
     static constexpr bool kStill = MODE == MODE_STILL;
-    float4 tf[BATCH ? 1 : 256];
+    // one view: the AO directions (lanes read different ones, which the
+    // constant bank would serialise); batched views read them from `hot`
+    float aod[BATCH ? 1 : MAX_AO * 3];
     float4 hot[BATCH ? 4 : 1][BATCH ? HOT_BYTES / 16 : 1];   // batched: each warp's current view parameters
     // the staged (t, k) of each lane's current voxel, ascending: slot-major,
     // lane-minor columns; the single-view learned variant keeps them per
@@ -509,7 +511,7 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                 }
                 Vec n = sub(Pl, axpy(h, ba, a));
                 n = scale(n, rsqrtf(dot(n, n)));
-                const float4 c = SM::kBatch ? __ldg(P.gtf + attr) : sm.tf[attr];
+                const float4 c = __ldg(P.gtf + attr);
                 // front-to-back weight (Sec. 5.1); the opacity update is rounded
                 // step by step so the termination test is reproducible:
                 // A <- A + (1 - A) * alpha
@@ -1019,6 +1021,22 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
         int G = 1;
         while (G < P.ao_rays) G <<= 1;
         const int per = 32 / G, sub = lane / G, ray = lane % G;
+        // each hit's tangent once, one lane per hit, in place of its tube
+        // direction (read after this only by the training-sample mode, which
+        // keeps it and takes the tangent per ray)
+        constexpr bool kTpre = MODE != MODE_SAMPLES;
+        if constexpr (kTpre) {
+            for (int g = lane; g < total; g += 32) {
+                const int ow = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
+                const Vec T = ao_tangent(mk(sm.slot[F_NX][q][ow], sm.slot[F_NY][q][ow], sm.slot[F_NZ][q][ow]),
+                                         mk(sm.slot[F_UX][q][ow], sm.slot[F_UY][q][ow], sm.slot[F_UZ][q][ow]));
+                sm.slot[F_UX][q][ow] = T.x;
+                sm.slot[F_UY][q][ow] = T.y;
+                sm.slot[F_UZ][q][ow] = T.z;
+            }
+            __syncwarp();
+        }
+        const float *aod = SM::kBatch ? &P.aod[0][0] : sm.aod;
         for (int m = 0; m < total; m += per) {
             const int g = m + sub;
             float o = 0.0f;
@@ -1026,9 +1044,10 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
                 const int ow = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
                 const Vec Pg = mk(sm.slot[F_PX][q][ow], sm.slot[F_PY][q][ow], sm.slot[F_PZ][q][ow]);
                 const Vec n = mk(sm.slot[F_NX][q][ow], sm.slot[F_NY][q][ow], sm.slot[F_NZ][q][ow]);
-                const Vec T = ao_tangent(n, mk(sm.slot[F_UX][q][ow], sm.slot[F_UY][q][ow], sm.slot[F_UZ][q][ow]));
+                const Vec u = mk(sm.slot[F_UX][q][ow], sm.slot[F_UY][q][ow], sm.slot[F_UZ][q][ow]);
+                const Vec T = kTpre ? u : ao_tangent(n, u);
                 const Vec B = cross(n, T);
-                const float dx = P.aod[ray][0], dy = P.aod[ray][1], dz = P.aod[ray][2];
+                const float dx = aod[3 * ray], dy = aod[3 * ray + 1], dz = aod[3 * ray + 2];
                 const Vec d = mk(fmaf(T.x, dx, fmaf(B.x, dy, n.x * dz)), fmaf(T.y, dx, fmaf(B.y, dy, n.y * dz)),
                                  fmaf(T.z, dx, fmaf(B.z, dy, n.z * dz)));
                 o = fminf(1.0f, P.ao_fast ? march_ao5<MODE != MODE_IMAGE_NC>(P, Pg, d, nsamp)
@@ -1241,8 +1260,7 @@ template <int MODE, int LAYOUT>
 __global__ void __launch_bounds__(RT, min_blocks(MODE))
 render_kernel(const __grid_constant__ RenderParams P) {
     __shared__ Smem<MODE, LAYOUT, false> sm;
-    for (int i = threadIdx.x; i < 256; i += RT)
-        sm.tf[i] = make_float4(P.tf[4 * i], P.tf[4 * i + 1], P.tf[4 * i + 2], P.tf[4 * i + 3]);
+    for (int i = threadIdx.x; i < MAX_AO * 3; i += RT) sm.aod[i] = P.aod[i / 3][i % 3];
     __syncthreads();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     Stats S;
@@ -1611,16 +1629,35 @@ static lvr_status grid_blocks(lvr_ctx *ctx, int slot, const void *kern, int *blo
     return LVR_OK;
 }
 
+// Before a single-view launch: the transfer function, passed by value, into
+// the context's device copy (the kernels read it through L1, each lane its
+// own entry: from shared memory it would cost 4 KB per block, from the
+// constant bank its divergent reads would serialise), and the tile counter
+// to zero. Stream-ordered, so back-to-back launches on the context's stream
+// each see their own.
+struct TfParam {
+    float v[1024];
+};
+__global__ void __launch_bounds__(256) render_prep_kernel(const __grid_constant__ TfParam t, float *dst,
+                                                          unsigned *tile_counter) {
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) dst[i] = t.v[i];
+    if (threadIdx.x == 0) *tile_counter = 0u;
+}
+
 static lvr_status launch(lvr_ctx *ctx, RenderParams &P, int layout) {
     cudaStream_t s = ctx->stream;
+    lvr_status st;
+    if (!ctx->d_tf && (st = dev_alloc(ctx, (void **)&ctx->d_tf, 4096)) != LVR_OK) return st;
     P.tile_counter = ctx->d_status + 1;
-    LVR_CUDA(ctx, cudaMemsetAsync(P.tile_counter, 0, 4, s));
+    P.gtf = reinterpret_cast<const float4 *>(ctx->d_tf);
+    TfParam t;
+    memcpy(t.v, P.tf, sizeof(t.v));
+    render_prep_kernel<<<1, 256, 0, s>>>(t, ctx->d_tf, P.tile_counter);
     const int mode = kernel_mode(P);
     const RenderKernel kern = pick_kernel(mode, layout);
     if (!kern) return set_err(ctx, LVR_EINVAL, "this render mode has no 16-byte record variant");
     int blocks;
-    lvr_status st = grid_blocks(ctx, mode * 2 + layout, (const void *)kern, &blocks);
-    if (st != LVR_OK) return st;
+    if ((st = grid_blocks(ctx, mode * 2 + layout, (const void *)kern, &blocks)) != LVR_OK) return st;
     const int need = (P.ntiles + RT / 32 - 1) / (RT / 32);
     const int grid = need < blocks ? need : blocks;
     kern<<<grid, RT, 0, s>>>(P);
