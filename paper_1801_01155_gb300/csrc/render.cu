@@ -398,12 +398,14 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                                            unsigned &nrec, unsigned &nhit, int &used) {
     const float Da[3] = {ray.D.x, ray.D.y, ray.D.z};
     do {
-        float se = INFINITY;
+        // exit distance per axis, (face - pl) / D with the face at 1 for
+        // D > 0 and at 0 for D < 0; an axis with D = 0 has 1 / D = inf, face
+        // 1 and pl 0 (set at the ray's start), so its exit is inf
+        float se = ((ray.invD[0] < 0.0f ? 0.0f : 1.0f) - ray.pl[0]) * ray.invD[0];
         int ax = 0;
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const float e = Da[a] > 0.0f ? (1.0f - ray.pl[a]) * ray.invD[a]
-                                        : (Da[a] < 0.0f ? (0.0f - ray.pl[a]) * ray.invD[a] : INFINITY);
+        for (int a = 1; a < 3; a++) {
+            const float e = ((ray.invD[a] < 0.0f ? 0.0f : 1.0f) - ray.pl[a]) * ray.invD[a];
             if (e < se) { se = e; ax = a; }
         }
         se = fmaxf(se, 0.0f);
@@ -1162,7 +1164,7 @@ __device__ __forceinline__ void render_tile(const RenderParams &P, SM &sm, unsig
                 if (vi < 0) { f += (float)vi; vi = 0; }
                 if (vi > P.res[a] - 1) { f += (float)(vi - (P.res[a] - 1)); vi = P.res[a] - 1; }
                 ray.v[a] = vi;
-                ray.pl[a] = f;
+                ray.pl[a] = Da[a] != 0.0f ? f : 0.0f;   // never stepped along a: pl only keeps its exit at inf
                 ray.invD[a] = Da[a] != 0.0f ? 1.0f / Da[a] : INFINITY;
             }
             ray.T = tnear;
