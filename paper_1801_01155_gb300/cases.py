@@ -9,6 +9,13 @@
         the same crop with the learned AO surrogate in place of the traced AO
         rays (a model with seeded random weights: the work does not depend on
         them), after the model is bound to the LoD
+    python -m paper_1801_01155_gb300.cases c1-traced [--reps K]
+    python -m paper_1801_01155_gb300.cases c1-learned [--reps K]
+        the learned-AO benchmark's test frame: a 500 x 64 streamline set
+        (seed 0) in 32^3, 1920 x 1080, transparent tubes r = 0.2 with soft
+        shadows and 16 traced AO rays per hit, or the learned AO surrogate (a
+        model with seeded random weights) in their place: one warm-up render,
+        then K renders
     python -m paper_1801_01155_gb300.cases voxel-term [--reps K]
         the learned-AO model bound to K fresh 3-level LoDs of the config-2 set
         (each bind computes the per-voxel term of every voxel on the tensor
@@ -74,6 +81,41 @@ def render_crop(reps, learned=False):
           f"(median of {reps})")
 
 
+def c1_frame(reps, learned):
+    import torch
+
+    from paper_1801_01155_gb300 import lvr, synth
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(dev)
+    ctx = lvr.Context(0, st)
+    s = synth.make_streamlines(500, 64, 0)
+    tf = synth.tf_ramp(0.05, 0.3)
+    g = lvr.grid_desc(32, 32, scale=32.0, attr_min=float(s.attr.min()), attr_max=float(s.attr.max()))
+    with torch.cuda.stream(st):
+        xyz, attr, offs = (torch.from_numpy(a).to(dev) for a in (s.xyz, s.attr, s.offsets))
+    ls = lvr.lvr_voxelize(ctx, xyz, attr, offs, g)
+    lod = lvr.lvr_build_lod(ctx, ls, 3, synth.sigma_lut(tf))
+    model = None
+    if learned:
+        rng = np.random.default_rng(7)
+        model = lvr.lvr_ao_model_create(ctx, (rng.standard_normal(lvr.lvr_ao_nparams()) * 0.05).astype(np.float32))
+    cam = synth.orbit_view((32, 32, 32), 1920, 1080)
+    view = lvr.make_view(cam["eye"], cam["at"], cam["up"], cam["fovy_deg"], 1920, 1080, cam["light_dir"])
+    desc = lvr.make_desc(0.2, tf, ert_alpha=0.99, shadows=True, ao_mode=2 if learned else 1, ao_rays=16,
+                         ao_radius=15.0)
+    out = torch.empty((1080, 1920, 4), dtype=torch.float32, device=dev)
+    lvr.lvr_render(ctx, ls, lod, view, desc, out, ao_model=model)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lvr.lvr_render(ctx, ls, lod, view, desc, out, ao_model=model)
+        e1.record(st)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(f"c1-{'learned' if learned else 'traced'}: {np.median(ms):.3f} ms per 1920x1080 frame (median of {reps})")
+
+
 def voxel_term(reps):
     import torch
 
@@ -102,13 +144,15 @@ def voxel_term(reps):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["render-crop", "render-crop-learned", "voxel-term"])
+    ap.add_argument("case", choices=["render-crop", "render-crop-learned", "c1-traced", "c1-learned", "voxel-term"])
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args(argv)
     import __graft_entry__ as g
     g.build()
     if a.case == "voxel-term":
         voxel_term(a.reps)
+    elif a.case.startswith("c1-"):
+        c1_frame(a.reps, learned=a.case == "c1-learned")
     else:
         render_crop(a.reps, learned=a.case == "render-crop-learned")
 

@@ -337,9 +337,11 @@ struct Smem {
     static constexpr bool kBatch = BATCH;   // the transfer function is read from global memory
     static constexpr bool kVid = MODE != MODE_IMAGE && MODE != MODE_IMAGE_NC && MODE != MODE_STILL && MODE != MODE_REP;
     static constexpr bool kStill = MODE == MODE_STILL;
-    // one view: the AO directions (lanes read different ones, which the
-    // constant bank would serialise); batched views read them from `hot`
-    float aod[BATCH ? 1 : MAX_AO * 3];
+    // one view with traced AO: the AO directions (lanes read different ones,
+    // which the constant bank would serialise); batched views read them from
+    // `hot`
+    static constexpr bool kAod = !BATCH && MODE != MODE_LEARNED;
+    float aod[kAod ? MAX_AO * 3 : 1];
     float4 hot[BATCH ? 4 : 1][BATCH ? HOT_BYTES / 16 : 1];   // batched: each warp's current view parameters
     // the staged (t, k) of each lane's current voxel, ascending: slot-major,
     // lane-minor columns; the single-view learned variant keeps them per
@@ -1262,7 +1264,8 @@ template <int MODE, int LAYOUT>
 __global__ void __launch_bounds__(RT, min_blocks(MODE))
 render_kernel(const __grid_constant__ RenderParams P) {
     __shared__ Smem<MODE, LAYOUT, false> sm;
-    for (int i = threadIdx.x; i < MAX_AO * 3; i += RT) sm.aod[i] = P.aod[i / 3][i % 3];
+    if constexpr (decltype(sm)::kAod)
+        for (int i = threadIdx.x; i < MAX_AO * 3; i += RT) sm.aod[i] = P.aod[i / 3][i % 3];
     __syncthreads();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     Stats S;
