@@ -159,6 +159,17 @@ __device__ __forceinline__ float sphere_entry(Vec p, Vec D, Vec c, float r2) {
 // solved in closest-approach form in the plane normal to the axis: closest
 // approach parameter sc, perpendicular offset q, half chord
 // sqrt((r^2 - |q|^2) / |D_perp|^2).
+// The early reject of capsule_entry below as a predicate of its own: the
+// record loops branch once around the whole test for the records it rejects
+// (most of them), with the same decision as capsule_entry's own.
+__device__ __forceinline__ bool capsule_rejects(Vec p, Vec D, Vec a, Vec b, float r2) {
+    const Vec ba = sub(b, a);
+    const float L2 = dot(ba, ba);
+    const Vec c = cross(D, ba);
+    const float c2 = dot(c, c);
+    const float wc = dot(sub(a, p), c);
+    return c2 > 1e-4f * L2 && wc * wc > 1.001f * r2 * c2;
+}
 __device__ __forceinline__ float capsule_entry(Vec p, Vec D, Vec a, Vec b, float r2) {
     const Vec ba = sub(b, a);
     const float L2 = dot(ba, ba);
@@ -480,6 +491,7 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                     const Vec o = neighbour_offset(nc);
                     a = mk(a.x + o.x, a.y + o.y, a.z + o.z);
                     b = mk(b.x + o.x, b.y + o.y, b.z + o.z);
+                    if (capsule_rejects(p, ray.D, a, b, P.r2)) continue;
                     stage(capsule_entry(p, ray.D, a, b, P.r2), k, ((attr >> 8) << 5) | nc);
                 }
             } else {
@@ -487,6 +499,7 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                     Vec a, b;
                     uint32_t attr;
                     fetch_record<SM::kLayout>(P, k, a, b, attr);
+                    if (capsule_rejects(p, ray.D, a, b, P.r2)) continue;
                     stage(capsule_entry(p, ray.D, a, b, P.r2), k, 0u);
                 }
             }
