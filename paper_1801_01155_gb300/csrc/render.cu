@@ -337,6 +337,22 @@ __device__ __forceinline__ void fetch_record(const RenderParams &P, uint32_t k, 
     }
 }
 
+// Hit geometry at the local entry point Pl on the tube around [a, b] (Sec. 5,
+// reading S1): the unit normal n = Pl minus its closest point on the segment,
+// and the unit tube direction u (zero for a point segment).
+__device__ __forceinline__ void hit_geometry(Vec Pl, Vec a, Vec b, Vec &n, Vec &u) {
+    const Vec ba = sub(b, a);
+    const float L2 = dot(ba, ba);
+    float h = 0.0f;
+    u = mk(0.0f, 0.0f, 0.0f);
+    if (L2 > 0.0f) {
+        h = fminf(fmaxf(dot(sub(Pl, a), ba) / L2, 0.0f), 1.0f);
+        u = scale(ba, 1.0f / sqrtf(L2));
+    }
+    n = sub(Pl, axpy(h, ba, a));
+    n = scale(n, rsqrtf(dot(n, n)));
+}
+
 // Record layouts: the packed 8-byte record, or 16 bytes with the end points
 // as six half floats (exact for power-of-two bin counts) and the attribute.
 enum { LAYOUT_AOS8 = 0, LAYOUT_AOS16 = 1 };
@@ -348,6 +364,12 @@ struct Smem {
     static constexpr bool kBatch = BATCH;   // the transfer function is read from global memory
     static constexpr bool kVid = MODE != MODE_IMAGE && MODE != MODE_IMAGE_NC && MODE != MODE_STILL && MODE != MODE_REP;
     static constexpr bool kStill = MODE == MODE_STILL;
+    // the per-hit geometry (normal, tube direction) waits for the lighting
+    // phase, where one lane takes one hit: the traversal stores the local
+    // hit point in the normal's fields and the record index in the
+    // direction's (at rest the record's neighbour offset would be needed
+    // too, so that variant computes the geometry where it finds the hit)
+    static constexpr bool kDefer = MODE != MODE_STILL;
     // one view with traced AO: the AO directions (lanes read different ones,
     // which the constant bank would serialise); batched views read them from
     // `hot`
@@ -518,16 +540,6 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                 }
                 attr &= 0xffu;
                 const Vec Pl = axpy(t, ray.D, p);
-                const Vec ba = sub(b, a);
-                const float L2 = dot(ba, ba);
-                float h = 0.0f;
-                Vec u = mk(0.0f, 0.0f, 0.0f);
-                if (L2 > 0.0f) {
-                    h = fminf(fmaxf(dot(sub(Pl, a), ba) / L2, 0.0f), 1.0f);
-                    u = scale(ba, 1.0f / sqrtf(L2));
-                }
-                Vec n = sub(Pl, axpy(h, ba, a));
-                n = scale(n, rsqrtf(dot(n, n)));
                 const float4 c = __ldg(P.gtf + attr);
                 // front-to-back weight (Sec. 5.1); the opacity update is rounded
                 // step by step so the termination test is reproducible:
@@ -549,6 +561,8 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                     if (store) ray.done = true;
                 }
                 if (P.nrays == 0) {
+                    Vec n, u;
+                    hit_geometry(Pl, a, b, n, u);
                     const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
                     const float kk = fmaf(P.kd, fabsf(dot(n, Lt)), P.ka);
                     ray.Cr = fmaf(w * c.x, kk, ray.Cr);
@@ -558,12 +572,21 @@ __device__ __forceinline__ void voxel_step(const RenderParams &P, SM &sm, Ray &r
                     sm.slot[F_PX][used][tid] = (float)ray.v[0] + Pl.x;
                     sm.slot[F_PY][used][tid] = (float)ray.v[1] + Pl.y;
                     sm.slot[F_PZ][used][tid] = (float)ray.v[2] + Pl.z;
-                    sm.slot[F_NX][used][tid] = n.x;
-                    sm.slot[F_NY][used][tid] = n.y;
-                    sm.slot[F_NZ][used][tid] = n.z;
-                    sm.slot[F_UX][used][tid] = u.x;
-                    sm.slot[F_UY][used][tid] = u.y;
-                    sm.slot[F_UZ][used][tid] = u.z;
+                    if constexpr (SM::kDefer) {
+                        sm.slot[F_NX][used][tid] = Pl.x;
+                        sm.slot[F_NY][used][tid] = Pl.y;
+                        sm.slot[F_NZ][used][tid] = Pl.z;
+                        sm.slot[F_UX][used][tid] = __uint_as_float(k);
+                    } else {
+                        Vec n, u;
+                        hit_geometry(Pl, a, b, n, u);
+                        sm.slot[F_NX][used][tid] = n.x;
+                        sm.slot[F_NY][used][tid] = n.y;
+                        sm.slot[F_NZ][used][tid] = n.z;
+                        sm.slot[F_UX][used][tid] = u.x;
+                        sm.slot[F_UY][used][tid] = u.y;
+                        sm.slot[F_UZ][used][tid] = u.z;
+                    }
                     if constexpr (SM::kVid) sm.slot[F_VID][used][tid] = __uint_as_float(vid);
                     sm.slot[F_CR][used][tid] = w * c.x;
                     sm.slot[F_CG][used][tid] = w * c.y;
@@ -968,6 +991,28 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
                            unsigned long long js[4], float &jmax) {
     constexpr int MODE = SM::kMode;
     const Vec Lt = mk(P.Lt[0], P.Lt[1], P.Lt[2]);
+    // the AO tangent frame replaces the tube direction at once where no
+    // learned inputs or training samples read the direction afterwards
+    constexpr bool kTmerge = SM::kDefer && MODE != MODE_LEARNED && MODE != MODE_JUDGE && MODE != MODE_SAMPLES;
+    if constexpr (SM::kDefer) {   // the hits' geometry, one lane per hit (same operations as at the hit)
+        for (int g = lane; g < total; g += 32) {
+            const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
+            const Vec Pl = mk(sm.slot[F_NX][q][o], sm.slot[F_NY][q][o], sm.slot[F_NZ][q][o]);
+            Vec a, b;
+            uint32_t attr;
+            fetch_record<SM::kLayout>(P, __float_as_uint(sm.slot[F_UX][q][o]), a, b, attr);
+            Vec n, u;
+            hit_geometry(Pl, a, b, n, u);
+            if (kTmerge && P.ao) u = ao_tangent(n, u);
+            sm.slot[F_NX][q][o] = n.x;
+            sm.slot[F_NY][q][o] = n.y;
+            sm.slot[F_NZ][q][o] = n.z;
+            sm.slot[F_UX][q][o] = u.x;
+            sm.slot[F_UY][q][o] = u.y;
+            sm.slot[F_UZ][q][o] = u.z;
+        }
+        __syncwarp();
+    }
     if (P.shadows == 1) {
         for (int g = lane; g < total; g += 32) {
             const int o = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
@@ -1042,7 +1087,7 @@ __device__ void light_hits(const RenderParams &P, SM &sm, int warp, int lane, in
         // direction (read after this only by the training-sample mode, which
         // keeps it and takes the tangent per ray)
         constexpr bool kTpre = MODE != MODE_SAMPLES;
-        if constexpr (kTpre) {
+        if constexpr (kTpre && !kTmerge) {
             for (int g = lane; g < total; g += 32) {
                 const int ow = slot_owner(sm, warp, g), q = slot_index(sm, warp, g);
                 const Vec T = ao_tangent(mk(sm.slot[F_NX][q][ow], sm.slot[F_NY][q][ow], sm.slot[F_NZ][q][ow]),
