@@ -30,6 +30,30 @@ __global__ void refresh_kernel(const float *__restrict__ p, bf16 *w1b, bf16 *w2b
     }
 }
 
+// The same bf16 weights as mma B fragments in the order the renderer's lanes
+// read them (see Net): lane (g, t) of n-tile n takes rows n * 8 + g, columns
+// k * 16 + 2t (+1) and k * 16 + 2t + 8 (+1).
+__global__ void frag_kernel(const float *__restrict__ p, uint32_t *f) {
+    for (int i = threadIdx.x; i < 8 * 32 * 18; i += blockDim.x) {
+        const int n = i / (32 * 18), r = i % (32 * 18), lane = r / 18, e = r % 18;
+        const int g = lane >> 2, t = lane & 3, row = n * 8 + g;
+        float lo, hi;
+        if (e < 2) {                                   // layer 1, per-hit k-step
+            const int c = 2 * t + 8 * e;
+            lo = p[OW1 + row * NIN + c];
+            hi = p[OW1 + row * NIN + c + 1];
+        } else {                                       // layers 2, 3: k-step, then b0 / b1
+            const int L = (e - 2) / 8, j = (e - 2) % 8, k = j >> 1, c = k * 16 + 2 * t + 8 * (j & 1);
+            const int off = L == 0 ? OW2 : OW3;
+            lo = p[off + row * NH + c];
+            hi = p[off + row * NH + c + 1];
+        }
+        const uint32_t v = pack_bf16x2(lo, hi);
+        if (e < 2) f[(n * 32 + lane) * 2 + e] = v;
+        else f[8 * 32 * 2 + ((e - 2) / 8) * (8 * 32 * 8) + (n * 32 + lane) * 8 + (e - 2) % 8] = v;
+    }
+}
+
 // ------------------------------------------------------------------ inputs
 // Per-voxel input values of one LoD level: bf16(log1p(8 dens_l / 8^l)),
 // rows (x) of `pitch` elements.
@@ -348,6 +372,10 @@ Net ao_net(const lvr_ao_model *m) {
     n.b3 = m->params + OB3;
     n.w4 = m->w4b;
     n.b4 = m->params + OB4;
+    const uint32_t *f = (const uint32_t *)m->wfrag;
+    n.f1 = reinterpret_cast<const uint2 *>(f);
+    n.f2 = reinterpret_cast<const uint4 *>(f + 8 * 32 * 2);
+    n.f3 = reinterpret_cast<const uint4 *>(f + 8 * 32 * 2 + 8 * 32 * 8);
     return n;
 }
 
@@ -355,6 +383,7 @@ namespace {
 
 lvr_status refresh(lvr_ctx *ctx, lvr_ao_model *m) {
     refresh_kernel<<<64, 256, 0, ctx->stream>>>(m->params, (bf16 *)m->w1b, (bf16 *)m->w2b, (bf16 *)m->w3b, m->w4b);
+    frag_kernel<<<1, 256, 0, ctx->stream>>>(m->params, (uint32_t *)m->wfrag);
     for (auto &b : m->bound) b.gen = 0;   // voxel terms depend on W1
     LVR_CUDA(ctx, cudaGetLastError());
     return LVR_OK;
@@ -366,7 +395,8 @@ lvr_status model_alloc(lvr_ctx *ctx, lvr_ao_model **out) {
     lvr_status st;
     if ((st = dev_alloc(ctx, (void **)&m->params, NPARAM * 4)) != LVR_OK ||
         (st = dev_alloc(ctx, &m->w1b, NH * NIN * 2)) != LVR_OK || (st = dev_alloc(ctx, &m->w2b, NH * NH * 2)) != LVR_OK ||
-        (st = dev_alloc(ctx, &m->w3b, NH * NH * 2)) != LVR_OK || (st = dev_alloc(ctx, (void **)&m->w4b, NH * 4)) != LVR_OK) {
+        (st = dev_alloc(ctx, &m->w3b, NH * NH * 2)) != LVR_OK || (st = dev_alloc(ctx, (void **)&m->w4b, NH * 4)) != LVR_OK ||
+        (st = dev_alloc(ctx, &m->wfrag, 8 * 32 * 18 * 4)) != LVR_OK) {
         lvr_free_ao_model(m);
         return st;
     }
@@ -646,7 +676,7 @@ extern "C" void lvr_free_ao_model(lvr_ao_model *m) {
     if (!m) return;
     lvr_ctx *ctx = m->ctx;
     cudaSetDevice(ctx->device);
-    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w4b, m->logd, m->vcoarse};
+    void *ps[] = {m->params, m->grads, m->adam_m, m->adam_v, m->w1b, m->w2b, m->w3b, m->w4b, m->wfrag, m->logd, m->vcoarse};
     for (void *p : ps) dev_free(ctx, p);
     for (auto &b : m->bound) dev_free(ctx, b.vterm);
     delete m;

@@ -38,6 +38,11 @@ struct Net {
     const float *b1, *b2, *b3; // [64]
     const float *w4;           // [64], values already rounded to bf16
     const float *b4;           // [1]
+    // fragment-ordered copies for the renderer's shared-tile MLP: f1[n][lane]
+    // = (b0, b1) of layer 1's per-hit k-step; f2 / f3 [n][lane][2] = the
+    // (b0, b1) pairs of k-steps 0-1 and 2-3 of layers 2 / 3
+    const uint2 *f1;
+    const uint4 *f2, *f3;
 };
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -254,7 +259,7 @@ __device__ __forceinline__ void act_store(uint8_t *act, int n, const float acc[4
 __device__ __forceinline__ void mlp_tile_smem(const Net &net, const __nv_bfloat16 *vt_lo,
                                               const __nv_bfloat16 *vt_hi, uint8_t *act, float &ao_lo,
                                               float &ao_hi) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int lane = threadIdx.x & 31, t = lane & 3;
     {   // layer 1: b1 + voxel term + the per-hit part (one k-step)
         uint32_t x[4];
         act_a(act, 0, x);
@@ -262,7 +267,8 @@ __device__ __forceinline__ void mlp_tile_smem(const Net &net, const __nv_bfloat1
 #pragma unroll 2
         for (int n = 0; n < 8; n++) {
             const int f = n * 8 + 2 * t;
-            const float b0 = __ldg(net.b1 + f), b1 = __ldg(net.b1 + f + 1);
+            const float2 bb = __ldg(reinterpret_cast<const float2 *>(net.b1 + f));
+            const float b0 = bb.x, b1 = bb.y;
             float lo0 = 0.0f, lo1 = 0.0f, hi0 = 0.0f, hi1 = 0.0f;
             if (vt_lo) {
                 const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(vt_lo + f));
@@ -277,8 +283,8 @@ __device__ __forceinline__ void mlp_tile_smem(const Net &net, const __nv_bfloat1
                 hi1 = __bfloat162float(pr.y);
             }
             float acc[4] = {b0 + lo0, b1 + lo1, b0 + hi0, b1 + hi1};
-            const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w1 + (n * 8 + g) * NIN);
-            mma16816(acc, x, __ldg(wr + t), __ldg(wr + t + 4));
+            const uint2 w = __ldg(net.f1 + n * 32 + lane);
+            mma16816(acc, x, w.x, w.y);
             act_store(act, n, acc);
         }
         __syncwarp();
@@ -291,13 +297,14 @@ __device__ __forceinline__ void mlp_tile_smem(const Net &net, const __nv_bfloat1
 #pragma unroll 2
         for (int n = 0; n < 8; n++) {
             float acc[4];
-            acc[0] = acc[2] = __ldg(net.b2 + n * 8 + 2 * t);
-            acc[1] = acc[3] = __ldg(net.b2 + n * 8 + 2 * t + 1);
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w2 + (n * 8 + g) * NH + k * 16);
-                mma16816(acc, a[k], __ldg(wr + t), __ldg(wr + t + 4));
-            }
+            const float2 bb = __ldg(reinterpret_cast<const float2 *>(net.b2 + n * 8 + 2 * t));
+            acc[0] = acc[2] = bb.x;
+            acc[1] = acc[3] = bb.y;
+            const uint4 w01 = __ldg(net.f2 + (n * 32 + lane) * 2), w23 = __ldg(net.f2 + (n * 32 + lane) * 2 + 1);
+            mma16816(acc, a[0], w01.x, w01.y);
+            mma16816(acc, a[1], w01.z, w01.w);
+            mma16816(acc, a[2], w23.x, w23.y);
+            mma16816(acc, a[3], w23.z, w23.w);
             act_store(act, n, acc);
         }
         __syncwarp();
@@ -310,14 +317,16 @@ __device__ __forceinline__ void mlp_tile_smem(const Net &net, const __nv_bfloat1
 #pragma unroll 2
     for (int n = 0; n < 8; n++) {
         float acc[4];
-        acc[0] = acc[2] = __ldg(net.b3 + n * 8 + 2 * t);
-        acc[1] = acc[3] = __ldg(net.b3 + n * 8 + 2 * t + 1);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t *wr = reinterpret_cast<const uint32_t *>(net.w3 + (n * 8 + g) * NH + k * 16);
-            mma16816(acc, a[k], __ldg(wr + t), __ldg(wr + t + 4));
-        }
-        const float w0 = __ldg(net.w4 + n * 8 + 2 * t), w1 = __ldg(net.w4 + n * 8 + 2 * t + 1);
+        const float2 bb = __ldg(reinterpret_cast<const float2 *>(net.b3 + n * 8 + 2 * t));
+        acc[0] = acc[2] = bb.x;
+        acc[1] = acc[3] = bb.y;
+        const uint4 w01 = __ldg(net.f3 + (n * 32 + lane) * 2), w23 = __ldg(net.f3 + (n * 32 + lane) * 2 + 1);
+        mma16816(acc, a[0], w01.x, w01.y);
+        mma16816(acc, a[1], w01.z, w01.w);
+        mma16816(acc, a[2], w23.x, w23.y);
+        mma16816(acc, a[3], w23.z, w23.w);
+        const float2 w4 = __ldg(reinterpret_cast<const float2 *>(net.w4 + n * 8 + 2 * t));
+        const float w0 = w4.x, w1 = w4.y;
         lo = fmaf(bf16_round(fmaxf(acc[0], 0.0f)), w0, lo);
         lo = fmaf(bf16_round(fmaxf(acc[1], 0.0f)), w1, lo);
         hi = fmaf(bf16_round(fmaxf(acc[2], 0.0f)), w0, hi);

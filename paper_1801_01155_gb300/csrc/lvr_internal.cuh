@@ -115,6 +115,10 @@ struct lvr_ao_model {
     int64_t adam_t = 0;
     void *w1b = nullptr, *w2b = nullptr, *w3b = nullptr;   // bf16 copies
     float *w4b = nullptr;
+    // the renderer's B operands of the mma tiles in fragment order: per
+    // n-tile and lane, layer 1's per-hit k-step (8 bytes), then layers 2 and
+    // 3 (32 bytes each: the four k-steps), refreshed with the bf16 copies
+    void *wfrag = nullptr;
     void *logd = nullptr;         // scratch: bf16 per cell of levels 0..2, log1p(8 dens_l / 8^l)
     size_t logd_bytes = 0;
     float *vcoarse = nullptr;     // scratch: fp32 voxel-term parts of the level-1 and level-2 cells
