@@ -1311,7 +1311,7 @@ __device__ __forceinline__ void flush_stats(const RenderParams &P, int lane, Sta
 constexpr int min_blocks(int mode) {
     return mode == MODE_IMAGE || mode == MODE_IMAGE_NC
                ? 7
-               : (mode == MODE_JUDGE ? 4 : (mode == MODE_STILL || mode == MODE_LEARNED ? 5 : 6));
+               : (mode == MODE_JUDGE ? 4 : (mode == MODE_STILL ? 5 : 6));
 }
 // batched: the image variant reads its view from shared memory and needs 80
 // registers
