@@ -373,10 +373,13 @@ lvr_status lvr_raster(lvr_ctx *ctx, const float *xyz, const float *attr, const i
 
 /* ------------------------------------------------------------------ batched rendering
  * Many views, possibly of different line sets, sizes and tile shapes, in one
- * persistent launch (the paper renders one view at a time): the work queue
- * is the concatenation of every view's 32-ray tiles, largest views first;
- * each warp takes the next tile from one device counter. The launch (counter
- * reset + kernel) is captured once into a CUDA graph and replayed by
+ * CUDA graph (the paper renders one view at a time): views that fill the GPU
+ * on their own (at least 8 tiles per resident warp of the single-view
+ * kernel) get a launch of their own in the graph, as lvr_render would launch
+ * them; the others share one persistent launch whose work queue is the
+ * concatenation of their 32-ray tiles, largest views first, each warp taking
+ * the next tile from one device counter. The graph (those launches, the
+ * counter reset and the queue's kernel) is captured once and replayed by
  * lvr_batch_render. Each view renders exactly as lvr_render would render it
  * alone (bit-identical output). All items share one kind of AO: either all
  * ao_mode 2 (learned) or all ao_mode 0/1, and one record layout; rgba must

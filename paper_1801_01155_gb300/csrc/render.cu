@@ -1709,23 +1709,39 @@ __global__ void __launch_bounds__(256) render_prep_kernel(const __grid_constant_
     if (threadIdx.x == 0) *tile_counter = 0u;
 }
 
-static lvr_status launch(lvr_ctx *ctx, RenderParams &P, int layout) {
-    cudaStream_t s = ctx->stream;
+// A single-view launch in two parts: everything that may fail or allocate
+// (the transfer function's device copy, the kernel, its persistent grid),
+// then the stream work alone (the prep kernel and the render), which a
+// batch also records into its graph.
+struct ViewLaunch {
+    RenderKernel kern = nullptr;
+    int grid = 0;
+};
+static lvr_status prepare_view(lvr_ctx *ctx, RenderParams &P, int layout, ViewLaunch &L) {
     lvr_status st;
     if (!ctx->d_tf && (st = dev_alloc(ctx, (void **)&ctx->d_tf, 4096)) != LVR_OK) return st;
     P.tile_counter = ctx->d_status + 1;
     P.gtf = reinterpret_cast<const float4 *>(ctx->d_tf);
+    const int mode = kernel_mode(P);
+    L.kern = pick_kernel(mode, layout);
+    if (!L.kern) return set_err(ctx, LVR_EINVAL, "this render mode has no 16-byte record variant");
+    int blocks;
+    if ((st = grid_blocks(ctx, mode * 2 + layout, (const void *)L.kern, &blocks)) != LVR_OK) return st;
+    const int need = (P.ntiles + RT / 32 - 1) / (RT / 32);
+    L.grid = need < blocks ? need : blocks;
+    return LVR_OK;
+}
+static void enqueue_view(lvr_ctx *ctx, const RenderParams &P, const ViewLaunch &L) {
     TfParam t;
     memcpy(t.v, P.tf, sizeof(t.v));
-    render_prep_kernel<<<1, 256, 0, s>>>(t, ctx->d_tf, P.tile_counter);
-    const int mode = kernel_mode(P);
-    const RenderKernel kern = pick_kernel(mode, layout);
-    if (!kern) return set_err(ctx, LVR_EINVAL, "this render mode has no 16-byte record variant");
-    int blocks;
-    if ((st = grid_blocks(ctx, mode * 2 + layout, (const void *)kern, &blocks)) != LVR_OK) return st;
-    const int need = (P.ntiles + RT / 32 - 1) / (RT / 32);
-    const int grid = need < blocks ? need : blocks;
-    kern<<<grid, RT, 0, s>>>(P);
+    render_prep_kernel<<<1, 256, 0, ctx->stream>>>(t, ctx->d_tf, P.tile_counter);
+    L.kern<<<L.grid, RT, 0, ctx->stream>>>(P);
+}
+static lvr_status launch(lvr_ctx *ctx, RenderParams &P, int layout) {
+    ViewLaunch L;
+    lvr_status st = prepare_view(ctx, P, layout, L);
+    if (st != LVR_OK) return st;
+    enqueue_view(ctx, P, L);
     LVR_CUDA(ctx, cudaGetLastError());
     return LVR_OK;
 }
@@ -1963,30 +1979,54 @@ lvr_status batch_build(lvr_ctx *ctx, const lvr_batch_item *items, int n, int til
     B->mode = mode;
     B->layout = lay;
     std::vector<RenderParams> sorted(n);
-    std::vector<unsigned> tile0(n + 1);
-    int64_t tot = 0;
     for (int i = 0; i < n; i++) {
         sorted[i] = P[order[i]];
-        tile0[i] = (unsigned)tot;
-        tot += sorted[i].ntiles;
         B->rays += (int64_t)sorted[i].cw * sorted[i].ch;
+        B->tiles += sorted[i].ntiles;
+    }
+    // Views that fill the GPU on their own (at least 8 tiles per resident
+    // warp of the single-view kernel) get their own launch in the graph: the
+    // single-view kernel takes its view's parameters from the constant bank,
+    // where the queue kernel reads them from shared memory at every use. The
+    // queue holds the rest, the largest (sorted first) excluded.
+    std::vector<ViewLaunch> own(n);
+    int nl = 0;
+    for (; nl < n; nl++) {
+        RenderParams q = sorted[nl];
+        lvr_status st = prepare_view(ctx, q, lay, own[nl]);
+        if (st != LVR_OK) {
+            delete B;
+            return st;
+        }
+        if ((int64_t)sorted[nl].ntiles < 8LL * own[nl].grid * (RT / 32)) break;
+        sorted[nl] = q;   // its tile counter and transfer-function copy are the context's
+    }
+    const int nq = n - nl;
+    std::vector<unsigned> tile0(nq + 1);
+    int64_t tot = 0;
+    for (int i = 0; i < nq; i++) {
+        tile0[i] = (unsigned)tot;
+        tot += sorted[nl + i].ntiles;
     }
     if (tot >= (int64_t)0xffffffffu) {
         delete B;
         return set_err(ctx, LVR_EINVAL, "batch too large");
     }
-    tile0[n] = (unsigned)tot;
-    B->tiles = tot;
+    tile0[nq] = (unsigned)tot;
     cudaStream_t s = ctx->stream;
     lvr_status st = LVR_OK;
     auto fail = [&](lvr_status e) { lvr_free_batch(B); return e; };
     if ((st = dev_alloc(ctx, (void **)&B->d_items, sizeof(RenderParams) * n)) != LVR_OK) return fail(st);
-    for (int i = 0; i < n; i++) sorted[i].gtf = reinterpret_cast<const float4 *>(B->d_items[i].tf);
+    std::vector<RenderParams> queued(sorted.begin() + nl, sorted.end());
+    for (int i = 0; i < nq; i++) queued[i].gtf = reinterpret_cast<const float4 *>(B->d_items[i].tf);
     if ((st = dev_alloc(ctx, (void **)&B->d_tile0, sizeof(unsigned) * (n + 1) + 256)) != LVR_OK) return fail(st);
     B->d_counter = B->d_tile0 + ((n + 1 + 63) & ~63);
-    cudaError_t e = cudaMemcpyAsync(B->d_items, sorted.data(), sizeof(RenderParams) * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(B->d_tile0, tile0.data(), sizeof(unsigned) * (n + 1), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    if (nq > 0) {
+        e = cudaMemcpyAsync(B->d_items, queued.data(), sizeof(RenderParams) * nq, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(B->d_tile0, tile0.data(), sizeof(unsigned) * (nq + 1), cudaMemcpyHostToDevice, s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors go out of scope
     if (e != cudaSuccess) return fail(cuda_err(ctx, e, "lvr_batch_create"));
     const BatchKernel kern = pick_batch_kernel(mode, lay);
@@ -1997,13 +2037,17 @@ lvr_status batch_build(lvr_ctx *ctx, const lvr_batch_item *items, int n, int til
     BatchParams bp;
     bp.items = B->d_items;
     bp.tile0 = B->d_tile0;
-    bp.n = n;
+    bp.n = nq;
     bp.counter = B->d_counter;
-    // capture: counter reset + the persistent launch
+    // capture: the views with a launch of their own, then the queue's counter
+    // reset and its persistent launch
     e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(B->d_counter, 0, 4, s);
-        kern<<<grid, RT, 0, s>>>(bp);
+        for (int i = 0; i < nl; i++) enqueue_view(ctx, sorted[i], own[i]);
+        if (nq > 0) {
+            cudaMemsetAsync(B->d_counter, 0, 4, s);
+            kern<<<grid, RT, 0, s>>>(bp);
+        }
         e = cudaStreamEndCapture(s, &B->graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);

@@ -117,6 +117,37 @@ def test_batch_matches_single_renders(env, sets):
             assert np.array_equal(e[5].cpu().numpy(), ref)
 
 
+def test_batch_with_views_of_their_own(env, sets):
+    """Views large enough to fill the GPU on their own (1920 x 1080: 64 800
+    tiles) get their own launch inside the batch's graph, beside the queue of
+    the small ones: every view still equals its single render bit for bit,
+    for traced and for learned AO, and over two replays."""
+    import torch
+    lvr, O, ctx, dev = env
+    rng = np.random.default_rng(5)
+    model = lvr.lvr_ao_model_create(ctx, (rng.standard_normal(lvr.lvr_ao_nparams()) * 0.05).astype(np.float32))
+    for kw, m in ((dict(ert_alpha=0.99, shadows=True, ao_mode=1), None), (dict(ert_alpha=0.99, ao_mode=2), model)):
+        ents, singles = [], []
+        for k, (w, h) in enumerate(((1920, 1080), (96, 64), (1920, 1080), (200, 120))):
+            st = sets[k % 2]
+            view, _ = _view(lvr, st, w, h, k)
+            desc = lvr.make_desc(0.2, st.tf, layout=1, **kw)
+            out = torch.full((h, w, 4), -1.0, dtype=torch.float32, device=dev)
+            ents.append((st.gls, st.glod, view, desc, m, out))
+            singles.append(_single(env, st, view, desc, m, h, w))
+        b = lvr.lvr_batch_create(ctx, ents)
+        tiles, rays = b.size()
+        assert rays == sum(e[5].shape[0] * e[5].shape[1] for e in ents)
+        for _ in range(2):
+            for e in ents:
+                e[5].fill_(-1.0)
+            b.render()
+            ctx.sync()
+            for e, ref in zip(ents, singles):
+                assert np.array_equal(e[5].cpu().numpy(), ref)
+        assert (singles[0][..., 3] > 0).mean() > 0.2
+
+
 def test_batch_view_against_oracle(env, sets):
     import torch
     lvr, O, ctx, dev = env
