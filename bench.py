@@ -558,7 +558,8 @@ C5_VIEWS = 64
 
 def batched(args, lvr, synth, ctx, dev, stream, model):
     """Config 5: 64 views of uneven size over three line sets, transparent
-    with learned AO, in one persistent launch replayed from a CUDA graph;
+    with learned AO, in one CUDA graph (views that fill the GPU on their own
+    as launches of their own, the rest in one persistent queue launch);
     ray tile and record layout from the autotuner (searched on every 4th
     view); compared with one lvr_render call per view."""
     import torch
@@ -648,8 +649,8 @@ def batched(args, lvr, synth, ctx, dev, stream, model):
                         "batch_ms": round(small_batch_ms, 3), "sequential_ms": round(small_seq_ms, 3),
                         "speedup_vs_sequential": round(small_seq_ms / small_batch_ms, 3)},
         "config": "config 5: 64 views (256^2 to 3840x2160) over three line sets (64^3/20k, 256^3/100k, 512^3/2M "
-                  "lines x 150 vertices, r = 0.2/0.15/0.1), transparent (ERT 0.99) with learned AO, one persistent "
-                  "launch from a CUDA graph",
+                  "lines x 150 vertices, r = 0.2/0.15/0.1), transparent (ERT 0.99) with learned AO, one CUDA graph: "
+                  "views that fill the GPU alone as launches of their own, the rest in one persistent queue launch",
         "sets": [{"res": s[2], "lines": C5_SETS[k][0], "segments": s[4]} for k, s in enumerate(sets)],
         "build_s": round(build_s, 3), "views": len(ents), "rays": rays, "tiles": tiles,
         "batch_ms": round(batch_ms, 3), "mrays_s": round(rays / batch_ms / 1e3, 2),
