@@ -155,6 +155,9 @@ def run_gpu(args):
     tune = lvr.lvr_autotune(ctx, [(s0, lod0, view, desc, None, out)], reps=2)
     lod0.free()
     s0.free()
+    if args.launch:   # a fixed ray tile and record layout (profiling runs: a profiler's overhead skews the search)
+        lay, tile = args.launch.split(",")
+        tune = dict(tune, tile=tuple(int(x) for x in tile.split("x")), layout=["aos8", "aos16"].index(lay))
     layout = tune["layout"]
     desc = lvr.make_desc(RADIUS, tf, ert_alpha=ERT, shadows=True, ao_mode=1, ao_rays=16, ao_radius=15.0,
                          tile=tune["tile"], layout=layout)
@@ -272,7 +275,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms / args.steps, 3)},
             "gpu_launches": (LAUNCHES_PER_STEP + (1 if layout else 0)) * args.steps,
             "autotune": {"tile": list(tune["tile"]), "layout": ["aos8", "aos16"][layout],
-                         "ms_per_candidate": [round(m, 3) for m in tune["ms"]]},
+                         "ms_per_candidate": [round(m, 3) for m in tune["ms"]],
+                         **({"fixed_by": "--launch " + args.launch} if args.launch else {})},
             "clocks": clk,
         }
         if world == 1:
@@ -775,6 +779,9 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-views (config 5) block")
     ap.add_argument("--no-raster", action="store_true", help="skip the rasterised comparison block")
+    ap.add_argument("--launch", default=None,
+                    help="fix the headline frame's record layout and ray tile instead of the autotuner's choice, "
+                         "e.g. aos16,4x8 (for runs under a profiler)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
