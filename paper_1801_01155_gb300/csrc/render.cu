@@ -5,19 +5,24 @@
 // occlusion.
 //
 // Execution. A persistent kernel: every warp pulls warp-sized pixel tiles
-// (8x4 by default) from a device counter. Per tile the warp alternates two
+// (8x4 by default) from a device counter. Launches that read no traversal
+// counters (MODE_IMAGE_NC) drop the counting and the AO march's support
+// tests. Per tile the warp alternates two
 // phases until all its rays are finished:
 //   A. traversal (one ray per lane): DDA, capsule tests, per-voxel sort and
 //      front-to-back weighting. The compositing weight of a hit depends only
 //      on the opacities in front of it, never on its lighting, so each hit's
-//      weight, position, normal and tube direction are final here; they go
-//      to the lane's shared-memory hit slots (KS per lane). The warp steps
+//      weight and position are final here; they go to the lane's
+//      shared-memory hit slots (KS per lane) with the record index, from
+//      which phase B derives the normal and tube direction (one lane per
+//      hit there, where the traversal has few lanes on hits). The warp steps
 //      its lanes voxel by voxel until it holds ROUND_TARGET hits, or every
 //      lane is full or finished; a full lane resumes inside the same voxel in
 //      the next round. Lighting in small rounds keeps lanes in dense regions
 //      from idling while a lane in a sparse region looks for hits.
 //   B. lighting (whole warp): the warp's collected hits are lit together:
-//      shadow rays one lane per hit; the AO rays of one hit on a group of
+//      their geometry and shadow rays one lane per hit; the AO rays of one
+//      hit on a group of
 //      adjacent lanes, which sample the same neighbourhood at the same
 //      distances (good cache locality, little divergence), their occlusion
 //      summed by a fixed butterfly. Each hit's lit contribution is written
@@ -108,7 +113,9 @@ struct RenderParams {
     unsigned *judge_max;          // max |e| as float bits
     unsigned *judge_hist;         // [JH] histogram of |e|
     // transfer function: RGBA per attribute byte (last: batched views copy
-    // only the fields before it into shared memory)
+    // only the fields before it into shared memory). The kernels read it
+    // through gtf: a single view's device copy written by the prep kernel,
+    // or a queued view's copy inside the batch's item array.
     alignas(16) float tf[1024];
 };
 constexpr int HOT_BYTES = (int)((offsetof(RenderParams, tf) + 15) & ~(size_t)15);   // fields before tf
