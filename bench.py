@@ -669,7 +669,7 @@ def batched(args, lvr, synth, ctx, dev, stream, model):
 # voxelise: count, 3 scan kernels, scatter, 2 sort kernels; LoD: 1 + 2 pooling + 3 packing; render: the
 # transfer-function upload and the render
 LAUNCHES_PER_STEP = 7 + 3 + 3 + 2
-KERNEL_VERSION = "render-v11"
+KERNEL_VERSION = "render-v12"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_kernel_traffic_c2_1080p.md")
 
 

@@ -242,13 +242,19 @@ __device__ __forceinline__ uint32_t corner_cell(const RenderParams &P, int l, Ve
            P.pbias[l];
 }
 // Cell i of level l (a: slice iz, b: slice iz + 1): two 16-byte loads at
-// one address (two 16-byte loads issue faster here than one 32-byte load).
-// The cell past the last (index pzero) is all zeros, the stand-in for a
-// sample that is not taken.
+// one address (two 16-byte loads issue faster here than one 32-byte load),
+// marked to stay in L1 over the records and offsets the traversal streams
+// through (the AO rays of nearby hits sample the same cells). The cell past
+// the last (index pzero) is all zeros, the stand-in for a sample that is not
+// taken.
 __device__ __forceinline__ void load_cell(const RenderParams &P, int l, uint32_t i, float4 &a, float4 &b) {
     const float4 *c = P.pk[l] + 2 * (size_t)i;
-    a = __ldg(c);
-    b = __ldg(c + 1);
+    asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w)
+        : "l"(c));
+    asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(c + 1));
 }
 __device__ __forceinline__ float trilerp(float4 a, float4 b, float fx, float fy, float fz) {
     const float x00 = fmaf(fx, a.y, a.x), x10 = fmaf(fx, a.w, a.z);
